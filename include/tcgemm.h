@@ -1,0 +1,294 @@
+/*
+ * tcgemm: mixed-precision GEMM on tensor cores for one NVIDIA GB300 (sm_103a).
+ *
+ * C ABI of the library built from paper_1803_04014_gb300/csrc.  The method is
+ * the one of "NVIDIA Tensor Core Programmability, Performance & Precision"
+ * (Markidis et al., arXiv 1803.04014):
+ *   - GEMM C = alpha*A*B + beta*C with low-precision inputs and FP32
+ *     accumulation (Sec. IV, Sec. VI);
+ *   - precision refinement: A = A_hi + R_A, B = B_hi + R_B and the sum of the
+ *     residual products (Sec. V, Eq. 1 and Eq. 2);
+ *   - batched small GEMM (Sec. IV-B);
+ *   - the error measures of Sec. VI.
+ *
+ * Conventions shared by every call
+ *   - Matrix pointers are device pointers owned by the caller unless stated;
+ *     the library never frees caller memory.
+ *   - Sizes and leading dimensions are in elements.  A is m x k, B is k x n,
+ *     C is m x n.  TC_ROW_MAJOR: element (i, j) at p[i*ld + j];
+ *     TC_COL_MAJOR: at p[j*ld + i].  C and C0 are always row-major.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls enqueue work on it and return without synchronising,
+ *     except where a host result is returned (tc_error_norm, tc_sync_status).
+ *   - Errors found on the host are returned at once and nothing is enqueued.
+ *     A kernel that gives up on a bounded wait records TC_ERR_TIMEOUT in a
+ *     per-device status word, frees what it holds and returns; the next
+ *     tc_sync_status() reports and clears it.
+ *   - tc_last_error() gives a message for the last failing call of the
+ *     calling thread.  No C++ exception crosses this interface.
+ */
+#ifndef TCGEMM_H
+#define TCGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tc_status;
+#define TC_OK 0
+#define TC_PENDING 1            /* serve_poll: request not finished yet        */
+#define TC_ERR_INVALID (-1)     /* bad size, pointer, alignment or argument    */
+#define TC_ERR_UNSUPPORTED (-2) /* valid request this build does not implement */
+#define TC_ERR_OOM (-3)         /* device allocation or HBM budget exhausted   */
+#define TC_ERR_CUDA (-4)        /* a CUDA runtime/driver call failed           */
+#define TC_ERR_TIMEOUT (-5)     /* a kernel gave up on a bounded wait          */
+#define TC_ERR_BUSY (-6)        /* serve_submit: queue full, retry later       */
+
+/* input formats of the tensor-core products */
+#define TC_F16 0   /* IEEE binary16 (the paper's half precision)        */
+#define TC_BF16 1  /* bfloat16                                           */
+#define TC_E4M3 2  /* FP8 E4M3 with a per-tensor power-of-two scale     */
+
+#define TC_ROW_MAJOR 0
+#define TC_COL_MAJOR 1
+
+/* ------------------------------------------------------------------------ */
+/* library / device                                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Version string of the library (static storage). */
+const char* tc_version(void);
+
+/* Message of the last failing call of this thread ("" if none). */
+const char* tc_last_error(void);
+
+/* SM count and compute capability of the current device (host pointers). */
+tc_status tc_device_info(int32_t* sm_count, int32_t* cc_major, int32_t* cc_minor);
+
+/* Synchronise `stream`, then read and clear the current device's status
+ * word.  Returns TC_ERR_TIMEOUT if a kernel gave up on a wait since the last
+ * call, TC_ERR_CUDA if the synchronisation failed, TC_OK otherwise. */
+tc_status tc_sync_status(void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Input rounding (Sec. V "rounded" single -> half; Sec. VI: A and B are first
+ * rounded to half precision, untimed in the paper)                           */
+/* ------------------------------------------------------------------------ */
+
+/* dst = round(src) to `dt` with round-to-nearest-even.
+ *   src: rows x cols FP32, row-major with ld_src (device).
+ *   dst: `dt` elements (2 bytes for F16/BF16, 1 byte for E4M3), row-major;
+ *        transpose = 0: rows x cols with ld_dst; transpose = 1: cols x rows
+ *        (dst[c*ld_dst + r] = round(src[r*ld_src + c])) -- used to make a
+ *        K-major copy of a row-major K x N operand.
+ *   scale_out (device float): for E4M3 required; receives s = 2^j, the largest
+ *        power of two with max|src| * s <= 448, and dst = round(src * s) with
+ *        saturation to +-448.  The word is used as the max|src| accumulator
+ *        while the call runs.  For F16/BF16 it may be NULL; if given it
+ *        receives 1.0.
+ * Overflow follows IEEE for F16/BF16 (to +-inf).  rows or cols == 0 is a
+ * no-op (for E4M3 the scale becomes 1). */
+tc_status tc_quantize(int32_t dt, int64_t rows, int64_t cols, const float* src, int64_t ld_src,
+                      void* dst, int64_t ld_dst, int32_t transpose, float* scale_out, void* stream);
+
+/* Residual split (Sec. V: R_A = A_single - A_half, stored in 16 bits):
+ *   hi = round(x), lo = round(x - hi) in `piece` (TC_F16 or TC_BF16), RNE.
+ *   src: rows x cols FP32 row-major (ld_src).  dst_hi / dst_lo: 16-bit,
+ *   row-major rows x cols (transpose = 0) or cols x rows (transpose = 1),
+ *   leading dimension ld_dst.  Values |x| >= 65520 overflow the F16 hi piece. */
+tc_status tc_split(int32_t piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src,
+                   int32_t transpose, void* dst_hi, void* dst_lo, int64_t ld_dst, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* GEMM on tensor cores (Sec. IV: C = alpha*A*B + beta*C; FP32 accumulation) */
+/* ------------------------------------------------------------------------ */
+
+/* C = alpha * descale * (A B) + beta * C, A and B already in format `dt`.
+ *   Layout: A row-major (la = TC_ROW_MAJOR, m x k, lda >= k) and B column-
+ *   major (lb = TC_COL_MAJOR, i.e. stored n x k, ldb >= k): both operands
+ *   K-major.  Other layouts return TC_ERR_UNSUPPORTED; use tc_quantize with
+ *   transpose = 1 to make a K-major B.
+ *   Alignment: A, B 16-byte aligned, lda*size and ldb*size multiples of 16.
+ *   scale_a / scale_b: E4M3 only, device floats from tc_quantize; descale =
+ *   1/(scale_a*scale_b).  NULL for F16/BF16.
+ *   beta == 0: C is not read.  k == 0: C = beta*C.
+ * Runs a persistent tcgen05 kernel: TMA-fed shared-memory ring, one thread
+ * issuing the MMAs into a double-buffered TMEM accumulator, four epilogue
+ * warps. */
+tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha,
+                     const void* A, int64_t lda, int32_t la,
+                     const void* B, int64_t ldb, int32_t lb,
+                     float beta, float* C, int64_t ldc,
+                     const float* scale_a, const float* scale_b, void* stream);
+
+/* Bytes of workspace gemm_split needs for these sizes. */
+size_t gemm_split_workspace_bytes(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k);
+
+/* Precision refinement (Sec. V, Eq. 1 and Eq. 2) in one accumulator:
+ *   C = alpha * sum_{(p,q)} X_p Y_q + beta * C, X_0 = hi(A), X_1 = lo(A),
+ *   Y_0 = hi(B), Y_1 = lo(B), products
+ *     nprod = 2: A_hi B_hi + A_lo B_hi                (Eq. 1)
+ *     nprod = 3: + A_hi B_lo                          (Eq. 2 without R_A R_B)
+ *     nprod = 4: + A_lo B_lo                          (Eq. 2)
+ *   A: m x k FP32, B: k x n FP32, any layout (la, lb); 16-byte aligned.
+ *   piece: TC_F16 or TC_BF16.
+ *   workspace: device memory of gemm_split_workspace_bytes() bytes owned by
+ *   the caller, or NULL to let the call take it from the stream-ordered pool
+ *   (cudaMallocAsync on `stream`, freed on `stream`).
+ * The pieces are formed in registers by one HBM-bound pass and all products
+ * accumulate in one TMEM accumulator in one tcgen05 launch. */
+tc_status gemm_split(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k, float alpha,
+                     const float* A, int64_t lda, int32_t la,
+                     const float* B, int64_t ldb, int32_t lb,
+                     float beta, float* C, int64_t ldc,
+                     void* workspace, size_t workspace_bytes, void* stream);
+
+/* FP32 GEMM on the CUDA cores (no tensor cores): the paper's sgemm
+ * comparison (Sec. VII-A, VII-B).  Any layouts; C row-major. */
+tc_status gemm_sgemm(int64_t m, int64_t n, int64_t k, float alpha,
+                     const float* A, int64_t lda, int32_t la,
+                     const float* B, int64_t ldb, int32_t lb,
+                     float beta, float* C, int64_t ldc, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched and grouped GEMM (Sec. IV-B; Sec. VI: 16x16 problems, one warp per
+ * problem in the paper's WMMA kernel)                                        */
+/* ------------------------------------------------------------------------ */
+
+/* batch independent 16 x 16 x 16 products, C_i = alpha*A_i B_i + beta*C_i.
+ *   dt: TC_F16 or TC_BF16.  m = n = k = 16 (others: TC_ERR_UNSUPPORTED).
+ *   A_i at A + i*stride_a, row-major 16 x 16 (la must be TC_ROW_MAJOR);
+ *   B_i at B + i*stride_b, 16 x 16, row-major (lb = TC_ROW_MAJOR) or
+ *   column-major (TC_COL_MAJOR); C_i at C + i*stride_c, FP32 row-major.
+ *   Strides in elements, multiples of 8 (16 bytes) for A and B, of 2 for C;
+ *   pointers 16-byte aligned. */
+tc_status gemm_batched_strided(int32_t dt, int64_t batch, int32_t m, int32_t n, int32_t k, float alpha,
+                               const void* A, int64_t stride_a, int32_t la,
+                               const void* B, int64_t stride_b, int32_t lb,
+                               float beta, float* C, int64_t stride_c, void* stream);
+
+/* One problem of a grouped GEMM.  Offsets are in elements from the bases
+ * passed at run time; A_g is m x k (row-major, lda), B_g is k x n (layout of
+ * the group, ldb), C_g is m x n FP32 row-major (ldc). */
+typedef struct tc_problem {
+    int32_t m, n, k, reserved;
+    int64_t off_a, off_b, off_c;
+    int32_t lda, ldb, ldc, reserved2;
+} tc_problem;
+
+typedef struct tc_grouped_plan tc_grouped_plan;
+
+/* Validate `count` problems (host array) and build a schedule: every problem
+ * is cut into output tiles, the tiles are ordered longest-first and stored
+ * on the device.  dt: TC_F16 or TC_BF16.  la must be TC_ROW_MAJOR; lb either.
+ * Constraints: m, n, k >= 1; lda, ldb multiples of 8 and offsets of A and B
+ * multiples of 8 (16-byte rows); ldc >= n.  The plan owns its device memory. */
+tc_status gemm_grouped_plan_create(int32_t dt, int32_t count, const tc_problem* problems,
+                                   int32_t la, int32_t lb, tc_grouped_plan** plan_out);
+
+/* One persistent launch over every tile of the plan:
+ * C_g = alpha*A_g B_g + beta*C_g for all g.  use_graph = 1 records the launch
+ * in a CUDA graph on the first call and replays it while the arguments stay
+ * the same. */
+tc_status gemm_grouped_plan_run(tc_grouped_plan* plan, const void* a_base, const void* b_base,
+                                float* c_base, float alpha, float beta, int32_t use_graph, void* stream);
+
+/* Free the plan (synchronises with its last run). */
+tc_status gemm_grouped_plan_destroy(tc_grouped_plan* plan);
+
+/* One-shot convenience: plan, run once, destroy. */
+tc_status gemm_grouped(int32_t dt, int32_t count, const tc_problem* problems,
+                       const void* a_base, int32_t la, const void* b_base, int32_t lb,
+                       float* c_base, float alpha, float beta, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Error measures (Sec. VI: e = C_half - C_single, ||e||_max; normwise
+ * error ||C - C64||_F / (||A||_F ||B||_F) against an FP64 truth)           */
+/* ------------------------------------------------------------------------ */
+
+/* out[0] = sum (C - Cref)^2, out[1] = sum A^2, out[2] = sum B^2,
+ * out[3] = max |C - Cref|, all accumulated in FP64 in a fixed order
+ * (deterministic for the same sizes).  out is a HOST array of 4 doubles;
+ * the call synchronises `stream`.
+ *   C: m x n FP32 row-major (ldc).  Cref: m x n row-major (ldr), FP64 if
+ *   ref_is_f64 = 1, FP32 if 0.  A: a_rows x a_cols FP32 row-major (lda);
+ *   B: b_rows x b_cols FP32 row-major (ldb); either may be NULL (sum 0).
+ * Uses stream-ordered scratch (cudaMallocAsync) for the partial sums. */
+tc_status tc_error_norm(int64_t m, int64_t n, const float* C, int64_t ldc,
+                        const void* Cref, int64_t ldr, int32_t ref_is_f64,
+                        const float* A, int64_t a_rows, int64_t a_cols, int64_t lda,
+                        const float* B, int64_t b_rows, int64_t b_cols, int64_t ldb,
+                        double* out, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of GEMM requests (beyond the paper)          */
+/* ------------------------------------------------------------------------ */
+
+#define TC_MODE_F16 0
+#define TC_MODE_BF16 1
+#define TC_MODE_E4M3 2
+#define TC_MODE_SPLIT3 3
+
+typedef struct tc_serve_cfg {
+    int64_t hbm_budget_bytes; /* device workspace the server may hold at once */
+    int32_t max_inflight;     /* requests on the GPU at once                 */
+    int32_t num_streams;      /* CUDA streams the server launches on         */
+    int32_t queue_capacity;   /* pending requests before serve_submit is BUSY */
+    int32_t reserved;
+} tc_serve_cfg;
+
+/* One request: C = alpha*A*B + beta*C computed in `mode` from FP32 operands
+ * resident on the device.  A: m x k FP32 row-major (lda), B: k x n FP32
+ * row-major (ldb), C: m x n FP32 row-major (ldc).  The caller keeps A, B and
+ * C alive and untouched until serve_poll reports completion. */
+typedef struct tc_request {
+    int32_t mode, reserved;
+    int64_t m, n, k;
+    const float* A; int64_t lda;
+    const float* B; int64_t ldb;
+    float* C; int64_t ldc;
+    float alpha, beta;
+} tc_request;
+
+typedef struct tc_result {
+    int32_t status, reserved;  /* TC_OK or an error of the request            */
+    double t_submit_us;        /* host clock (steady, microseconds)           */
+    double t_start_us;         /* admitted and launched                       */
+    double t_done_us;          /* completion observed (event)                 */
+} tc_result;
+
+typedef struct tc_server tc_server;
+
+/* Start a server on the current device: allocates the budget arena and the
+ * streams, starts the scheduler thread. */
+tc_status serve_open(const tc_serve_cfg* cfg, tc_server** out);
+
+/* Queue a request (non-blocking).  TC_ERR_BUSY if the queue is full,
+ * TC_ERR_INVALID for a malformed request or one whose workspace exceeds the
+ * whole budget.  *ticket identifies it for serve_poll. */
+tc_status serve_submit(tc_server* s, const tc_request* req, uint64_t* ticket);
+
+/* TC_PENDING while the request is queued or running; otherwise fills *out
+ * (if not NULL), forgets the ticket and returns TC_OK (out->status holds the
+ * request's own status).  TC_ERR_INVALID for an unknown ticket. */
+tc_status serve_poll(tc_server* s, uint64_t ticket, tc_result* out);
+
+/* Block until every submitted request finished or `timeout_ms` elapsed
+ * (TC_ERR_TIMEOUT). */
+tc_status serve_drain(tc_server* s, int64_t timeout_ms);
+
+/* Counters: out[0] submitted, out[1] completed, out[2] peak bytes in use,
+ * out[3] peak requests in flight, out[4] times admission waited for budget. */
+tc_status serve_stats(tc_server* s, int64_t* out5);
+
+/* Drain, stop the scheduler, free the arena and streams. */
+tc_status serve_close(tc_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TCGEMM_H */

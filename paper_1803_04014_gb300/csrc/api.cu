@@ -1,0 +1,534 @@
+// Host side of the C ABI (include/tcgemm.h): argument checks, per-device
+// state (SM count, status word), TMA descriptor encoding, workspaces,
+// grouped-GEMM plans and dispatch to the kernels.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "tcgemm.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+tc_status fail(tc_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+tc_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(TC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct Device {
+    bool ready = false;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    int* status = nullptr;  // device status word (first error wins)
+};
+
+std::mutex g_mu;
+Device g_dev[64];
+
+tc_status get_device(Device** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(TC_ERR_INVALID, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    Device& d = g_dev[dev];
+    if (!d.ready) {
+        if ((e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return cuda_fail(e, "cudaDeviceGetAttribute");
+        cudaDeviceGetAttribute(&d.cc_major, cudaDevAttrComputeCapabilityMajor, dev);
+        cudaDeviceGetAttribute(&d.cc_minor, cudaDevAttrComputeCapabilityMinor, dev);
+        if ((e = cudaMalloc(&d.status, 256)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
+        if ((e = cudaMemset(d.status, 0, 256)) != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+        // keep freed stream-ordered workspace cached in the pool instead of returning it each sync
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t threshold = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+        }
+        d.ready = true;
+    }
+    *out = &d;
+    return TC_OK;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 3-D K-major operand: `pieces` stacked matrices of `rows` x `k` elements,
+// row stride ld_bytes, piece stride piece_bytes; box = box_rows x 128 bytes
+// with the 128-byte swizzle; out-of-range elements read as zero.
+tc_status encode_kmajor(CUtensorMap* map, CUtensorMapDataType dtype, int esz, const void* ptr, int64_t k,
+                        int64_t rows, int64_t pieces, int64_t ld_bytes, int64_t piece_bytes, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return fail(TC_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t dims[3] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows),
+                          static_cast<cuuint64_t>(pieces)};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(ld_bytes), static_cast<cuuint64_t>(piece_bytes)};
+    cuuint32_t box[3] = {static_cast<cuuint32_t>(128 / esz), static_cast<cuuint32_t>(box_rows), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, dtype, 3, const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(TC_ERR_INVALID, "cuTensorMapEncodeTiled failed (%d)", static_cast<int>(r));
+    return TC_OK;
+}
+
+inline bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+constexpr int64_t kMaxDim = 0x7FFFFFFF;
+
+int elem_size(int32_t dt) { return dt == TC_E4M3 ? 1 : 2; }
+
+tc_status check_dims(int64_t m, int64_t n, int64_t k) {
+    if (m < 0 || n < 0 || k < 0) return fail(TC_ERR_INVALID, "negative size (m=%lld n=%lld k=%lld)", (long long)m,
+                                             (long long)n, (long long)k);
+    if (m > kMaxDim || n > kMaxDim || k > kMaxDim) return fail(TC_ERR_INVALID, "size above 2^31-1");
+    return TC_OK;
+}
+
+tc_status enqueue(cudaError_t e, const char* what) { return e == cudaSuccess ? TC_OK : cuda_fail(e, what); }
+
+}  // namespace
+
+extern "C" {
+
+const char* tc_version(void) { return "tcgemm 0.1 (sm_103a)"; }
+
+const char* tc_last_error(void) { return g_err.c_str(); }
+
+tc_status tc_device_info(int32_t* sm_count, int32_t* cc_major, int32_t* cc_minor) {
+    Device* d;
+    tc_status s = get_device(&d);
+    if (s != TC_OK) return s;
+    if (sm_count) *sm_count = d->sm_count;
+    if (cc_major) *cc_major = d->cc_major;
+    if (cc_minor) *cc_minor = d->cc_minor;
+    return TC_OK;
+}
+
+tc_status tc_sync_status(void* stream) {
+    Device* d;
+    tc_status s = get_device(&d);
+    if (s != TC_OK) return s;
+    cudaError_t e = cudaStreamSynchronize(as_stream(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int word = 0;
+    if ((e = cudaMemcpy(&word, d->status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(e, "read status");
+    if (word != 0) {
+        cudaMemset(d->status, 0, sizeof(int));
+        return fail(TC_ERR_TIMEOUT, "a kernel gave up on a bounded wait (device status %d)", word);
+    }
+    return TC_OK;
+}
+
+tc_status tc_quantize(int32_t dt, int64_t rows, int64_t cols, const float* src, int64_t ld_src, void* dst,
+                      int64_t ld_dst, int32_t transpose, float* scale_out, void* stream) {
+    if (dt != TC_F16 && dt != TC_BF16 && dt != TC_E4M3) return fail(TC_ERR_INVALID, "tc_quantize: bad dtype %d", dt);
+    if (rows < 0 || cols < 0) return fail(TC_ERR_INVALID, "tc_quantize: negative size");
+    if (dt == TC_E4M3 && scale_out == nullptr) return fail(TC_ERR_INVALID, "tc_quantize: E4M3 needs scale_out");
+    if (scale_out && !aligned(scale_out, 4)) return fail(TC_ERR_INVALID, "tc_quantize: scale_out misaligned");
+    if (rows > 0 && cols > 0) {
+        if (!src || !dst) return fail(TC_ERR_INVALID, "tc_quantize: null pointer");
+        if (ld_src < cols) return fail(TC_ERR_INVALID, "tc_quantize: ld_src < cols");
+        if (ld_dst < (transpose ? rows : cols)) return fail(TC_ERR_INVALID, "tc_quantize: ld_dst too small");
+        if (!aligned(src, 4) || !aligned(dst, elem_size(dt)))
+            return fail(TC_ERR_INVALID, "tc_quantize: misaligned pointer");
+        if (transpose && (cols + 31) / 32 > 0x7FFFFFFF) return fail(TC_ERR_INVALID, "tc_quantize: too many columns");
+        if (transpose && (rows + 31) / 32 > 65535) return fail(TC_ERR_INVALID, "tc_quantize: too many rows to transpose");
+    }
+    Device* d;
+    tc_status s = get_device(&d);
+    if (s != TC_OK) return s;
+    return enqueue(tcg::launch_quantize(dt, rows, cols, src, ld_src, dst, ld_dst, transpose != 0, scale_out,
+                                        as_stream(stream)),
+                   "tc_quantize launch");
+}
+
+tc_status tc_split(int32_t piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src, int32_t transpose,
+                   void* dst_hi, void* dst_lo, int64_t ld_dst, void* stream) {
+    if (piece != TC_F16 && piece != TC_BF16) return fail(TC_ERR_INVALID, "tc_split: piece must be F16 or BF16");
+    if (rows < 0 || cols < 0) return fail(TC_ERR_INVALID, "tc_split: negative size");
+    if (rows > 0 && cols > 0) {
+        if (!src || !dst_hi || !dst_lo) return fail(TC_ERR_INVALID, "tc_split: null pointer");
+        if (ld_src < cols) return fail(TC_ERR_INVALID, "tc_split: ld_src < cols");
+        if (ld_dst < (transpose ? rows : cols)) return fail(TC_ERR_INVALID, "tc_split: ld_dst too small");
+        if (!aligned(src, 4) || !aligned(dst_hi, 2) || !aligned(dst_lo, 2))
+            return fail(TC_ERR_INVALID, "tc_split: misaligned pointer");
+        if (transpose && (rows + 31) / 32 > 65535) return fail(TC_ERR_INVALID, "tc_split: too many rows to transpose");
+    }
+    Device* d;
+    tc_status s = get_device(&d);
+    if (s != TC_OK) return s;
+    return enqueue(tcg::launch_split(piece, rows, cols, src, ld_src, transpose != 0, dst_hi, dst_lo, ld_dst,
+                                     as_stream(stream)),
+                   "tc_split launch");
+}
+
+tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, const void* A, int64_t lda, int32_t la,
+                     const void* B, int64_t ldb, int32_t lb, float beta, float* C, int64_t ldc, const float* scale_a,
+                     const float* scale_b, void* stream) {
+    if (dt != TC_F16 && dt != TC_BF16 && dt != TC_E4M3) return fail(TC_ERR_INVALID, "gemm_mixed: bad dtype %d", dt);
+    tc_status s = check_dims(m, n, k);
+    if (s != TC_OK) return s;
+    if ((la != TC_ROW_MAJOR && la != TC_COL_MAJOR) || (lb != TC_ROW_MAJOR && lb != TC_COL_MAJOR))
+        return fail(TC_ERR_INVALID, "gemm_mixed: bad layout");
+    if (m == 0 || n == 0) return TC_OK;
+    if (!C || ldc < n || !aligned(C, 4)) return fail(TC_ERR_INVALID, "gemm_mixed: bad C / ldc");
+    Device* d;
+    if ((s = get_device(&d)) != TC_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    if (k == 0) return enqueue(tcg::launch_scale_c(m, n, beta, C, ldc, st), "gemm_mixed scale");
+    if (la != TC_ROW_MAJOR || lb != TC_COL_MAJOR)
+        return fail(TC_ERR_UNSUPPORTED, "gemm_mixed: operands must be K-major (A row-major, B column-major)");
+    const int esz = elem_size(dt);
+    if (!A || !B) return fail(TC_ERR_INVALID, "gemm_mixed: null operand");
+    if (lda < k || ldb < k) return fail(TC_ERR_INVALID, "gemm_mixed: lda/ldb < k");
+    if (!aligned(A, 16) || !aligned(B, 16) || (lda * esz) % 16 || (ldb * esz) % 16)
+        return fail(TC_ERR_INVALID, "gemm_mixed: operands and their row strides must be 16-byte aligned");
+    if (dt == TC_E4M3 && (!scale_a || !scale_b)) return fail(TC_ERR_INVALID, "gemm_mixed: E4M3 needs scale_a/scale_b");
+    const CUtensorMapDataType tdt = dt == TC_F16    ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                    : dt == TC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                    : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    tcg::TcGemmLaunch p{};
+    p.kind = dt == TC_E4M3 ? 1 : 0;
+    p.ab_format = dt == TC_BF16 ? 1 : 0;
+    p.na = p.nb = p.nprod = 1;
+    p.bn = 256;
+    p.m = m; p.n = n; p.k = k;
+    p.alpha = alpha; p.beta = beta;
+    p.C = C; p.ldc = ldc;
+    p.scale_a = scale_a; p.scale_b = scale_b;
+    p.status = d->status;
+    p.sm_count = d->sm_count;
+    CUtensorMap ta, tb;
+    if ((s = encode_kmajor(&ta, tdt, esz, A, k, m, 1, lda * esz, m * lda * esz, 128)) != TC_OK) return s;
+    if ((s = encode_kmajor(&tb, tdt, esz, B, k, n, 1, ldb * esz, n * ldb * esz, p.bn)) != TC_OK) return s;
+    return enqueue(tcg::launch_tc_gemm(ta, tb, p, st), "gemm_mixed launch");
+}
+
+static int64_t split_kpad(int64_t k) { return (k + 7) / 8 * 8; }
+
+size_t gemm_split_workspace_bytes(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k) {
+    (void)piece;
+    (void)nprod;
+    if (m < 0 || n < 0 || k < 0) return 0;
+    const int64_t kp = split_kpad(k);
+    // two pieces of A (m x kp) and two of B (n x kp), 2 bytes each, 256-byte aligned halves
+    const int64_t a_bytes = (2 * m * kp * 2 + 255) / 256 * 256;
+    const int64_t b_bytes = (2 * n * kp * 2 + 255) / 256 * 256;
+    return static_cast<size_t>(a_bytes + b_bytes);
+}
+
+tc_status gemm_split(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k, float alpha, const float* A,
+                     int64_t lda, int32_t la, const float* B, int64_t ldb, int32_t lb, float beta, float* C,
+                     int64_t ldc, void* workspace, size_t workspace_bytes, void* stream) {
+    if (piece != TC_F16 && piece != TC_BF16) return fail(TC_ERR_INVALID, "gemm_split: piece must be F16 or BF16");
+    if (nprod < 2 || nprod > 4) return fail(TC_ERR_INVALID, "gemm_split: nprod must be 2, 3 or 4");
+    tc_status s = check_dims(m, n, k);
+    if (s != TC_OK) return s;
+    if ((la != TC_ROW_MAJOR && la != TC_COL_MAJOR) || (lb != TC_ROW_MAJOR && lb != TC_COL_MAJOR))
+        return fail(TC_ERR_INVALID, "gemm_split: bad layout");
+    if (m == 0 || n == 0) return TC_OK;
+    if (!C || ldc < n || !aligned(C, 4)) return fail(TC_ERR_INVALID, "gemm_split: bad C / ldc");
+    Device* d;
+    if ((s = get_device(&d)) != TC_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    if (k == 0) return enqueue(tcg::launch_scale_c(m, n, beta, C, ldc, st), "gemm_split scale");
+    if (!A || !B || !aligned(A, 4) || !aligned(B, 4)) return fail(TC_ERR_INVALID, "gemm_split: bad operand pointer");
+    if (lda < (la == TC_ROW_MAJOR ? k : m) || ldb < (lb == TC_ROW_MAJOR ? n : k))
+        return fail(TC_ERR_INVALID, "gemm_split: leading dimension too small");
+    const size_t need = gemm_split_workspace_bytes(piece, nprod, m, n, k);
+    if (workspace && workspace_bytes < need)
+        return fail(TC_ERR_INVALID, "gemm_split: workspace of %zu bytes, need %zu", workspace_bytes, need);
+    if (workspace && !aligned(workspace, 256)) return fail(TC_ERR_INVALID, "gemm_split: workspace must be 256-byte aligned");
+    void* ws = workspace;
+    cudaError_t e;
+    if (!ws) {
+        if ((e = cudaMallocAsync(&ws, need, st)) != cudaSuccess) return fail(TC_ERR_OOM, "gemm_split: workspace: %s", cudaGetErrorString(e));
+    }
+    const int64_t kp = split_kpad(k);
+    uint8_t* wa = static_cast<uint8_t*>(ws);
+    uint8_t* wb = wa + (2 * m * kp * 2 + 255) / 256 * 256;
+    uint16_t* a_hi = reinterpret_cast<uint16_t*>(wa);
+    uint16_t* a_lo = a_hi + m * kp;
+    uint16_t* b_hi = reinterpret_cast<uint16_t*>(wb);
+    uint16_t* b_lo = b_hi + n * kp;
+    tc_status out = TC_OK;
+    do {
+        // A pieces as m x k (K-major): row-major A directly, column-major A (k x m in memory) transposed
+        e = (la == TC_ROW_MAJOR) ? tcg::launch_split(piece, m, k, A, lda, false, a_hi, a_lo, kp, st)
+                                 : tcg::launch_split(piece, k, m, A, lda, true, a_hi, a_lo, kp, st);
+        if (e != cudaSuccess) { out = cuda_fail(e, "gemm_split: split A"); break; }
+        // B pieces as n x k (K-major): row-major B (k x n) transposed, column-major B directly
+        e = (lb == TC_ROW_MAJOR) ? tcg::launch_split(piece, k, n, B, ldb, true, b_hi, b_lo, kp, st)
+                                 : tcg::launch_split(piece, n, k, B, ldb, false, b_hi, b_lo, kp, st);
+        if (e != cudaSuccess) { out = cuda_fail(e, "gemm_split: split B"); break; }
+        const CUtensorMapDataType tdt = piece == TC_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+        tcg::TcGemmLaunch p{};
+        p.kind = 0;
+        p.ab_format = piece == TC_BF16 ? 1 : 0;
+        p.na = 2;
+        p.nb = nprod == 2 ? 1 : 2;
+        p.nprod = nprod;
+        p.bn = nprod == 2 ? 256 : 128;
+        p.m = m; p.n = n; p.k = k;
+        p.alpha = alpha; p.beta = beta;
+        p.C = C; p.ldc = ldc;
+        p.status = d->status;
+        p.sm_count = d->sm_count;
+        CUtensorMap ta, tb;
+        if ((out = encode_kmajor(&ta, tdt, 2, a_hi, k, m, 2, kp * 2, m * kp * 2, 128)) != TC_OK) break;
+        if ((out = encode_kmajor(&tb, tdt, 2, b_hi, k, n, p.nb, kp * 2, n * kp * 2, p.bn)) != TC_OK) break;
+        e = tcg::launch_tc_gemm(ta, tb, p, st);
+        if (e != cudaSuccess) { out = cuda_fail(e, "gemm_split launch"); break; }
+    } while (false);
+    if (!workspace) cudaFreeAsync(ws, st);
+    return out;
+}
+
+tc_status gemm_sgemm(int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda, int32_t la,
+                     const float* B, int64_t ldb, int32_t lb, float beta, float* C, int64_t ldc, void* stream) {
+    tc_status s = check_dims(m, n, k);
+    if (s != TC_OK) return s;
+    if ((la != TC_ROW_MAJOR && la != TC_COL_MAJOR) || (lb != TC_ROW_MAJOR && lb != TC_COL_MAJOR))
+        return fail(TC_ERR_INVALID, "gemm_sgemm: bad layout");
+    if (m == 0 || n == 0) return TC_OK;
+    if (!C || ldc < n) return fail(TC_ERR_INVALID, "gemm_sgemm: bad C / ldc");
+    if (m > 65535LL * 128) return fail(TC_ERR_INVALID, "gemm_sgemm: m too large");
+    Device* d;
+    if ((s = get_device(&d)) != TC_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    if (k == 0) return enqueue(tcg::launch_scale_c(m, n, beta, C, ldc, st), "gemm_sgemm scale");
+    if (!A || !B) return fail(TC_ERR_INVALID, "gemm_sgemm: null operand");
+    if (lda < (la == TC_ROW_MAJOR ? k : m) || ldb < (lb == TC_ROW_MAJOR ? n : k))
+        return fail(TC_ERR_INVALID, "gemm_sgemm: leading dimension too small");
+    return enqueue(tcg::launch_sgemm(m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ldc, st), "gemm_sgemm launch");
+}
+
+tc_status gemm_batched_strided(int32_t dt, int64_t batch, int32_t m, int32_t n, int32_t k, float alpha, const void* A,
+                               int64_t stride_a, int32_t la, const void* B, int64_t stride_b, int32_t lb, float beta,
+                               float* C, int64_t stride_c, void* stream) {
+    if (dt != TC_F16 && dt != TC_BF16) return fail(TC_ERR_UNSUPPORTED, "gemm_batched_strided: F16 or BF16 only");
+    if (m != 16 || n != 16 || k != 16) return fail(TC_ERR_UNSUPPORTED, "gemm_batched_strided: 16x16x16 problems only");
+    if (la != TC_ROW_MAJOR) return fail(TC_ERR_UNSUPPORTED, "gemm_batched_strided: A must be row-major");
+    if (lb != TC_ROW_MAJOR && lb != TC_COL_MAJOR) return fail(TC_ERR_INVALID, "gemm_batched_strided: bad layout");
+    if (batch < 0) return fail(TC_ERR_INVALID, "gemm_batched_strided: negative batch");
+    if (batch == 0) return TC_OK;
+    if (!A || !B || !C) return fail(TC_ERR_INVALID, "gemm_batched_strided: null pointer");
+    if (stride_a < 256 || stride_b < 256 || stride_c < 256)
+        return fail(TC_ERR_INVALID, "gemm_batched_strided: strides must cover a 16x16 problem");
+    if (stride_a % 8 || stride_b % 8 || stride_c % 2 || !aligned(A, 16) || !aligned(B, 16) || !aligned(C, 8))
+        return fail(TC_ERR_INVALID, "gemm_batched_strided: strides/pointers not aligned");
+    Device* d;
+    tc_status s = get_device(&d);
+    if (s != TC_OK) return s;
+    return enqueue(tcg::launch_batched16(dt, batch, alpha, A, stride_a, B, stride_b, lb, beta, C, stride_c, d->status,
+                                         d->sm_count, as_stream(stream)),
+                   "gemm_batched_strided launch");
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ grouped plans
+
+struct tc_grouped_plan {
+    int dt = 0, la = 0, lb = 0;
+    int32_t count = 0, num_tiles = 0;
+    int dev = 0, sm_count = 0;
+    tcg::GroupedProblemDev* d_probs = nullptr;
+    tcg::GroupedTileDev* d_tiles = nullptr;
+    // graph of the last run
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    const void* g_a = nullptr;
+    const void* g_b = nullptr;
+    float* g_c = nullptr;
+    float g_alpha = 0.f, g_beta = 0.f;
+};
+
+extern "C" {
+
+tc_status gemm_grouped_plan_create(int32_t dt, int32_t count, const tc_problem* problems, int32_t la, int32_t lb,
+                                   tc_grouped_plan** plan_out) {
+    if (!plan_out) return fail(TC_ERR_INVALID, "grouped: null plan_out");
+    *plan_out = nullptr;
+    if (dt != TC_F16 && dt != TC_BF16) return fail(TC_ERR_UNSUPPORTED, "grouped: F16 or BF16 only");
+    if (la != TC_ROW_MAJOR) return fail(TC_ERR_UNSUPPORTED, "grouped: A must be row-major");
+    if (lb != TC_ROW_MAJOR && lb != TC_COL_MAJOR) return fail(TC_ERR_INVALID, "grouped: bad layout");
+    if (count < 0 || (count > 0 && !problems)) return fail(TC_ERR_INVALID, "grouped: bad problem array");
+    std::vector<tcg::GroupedProblemDev> probs(count);
+    struct T { int64_t cost; tcg::GroupedTileDev t; };
+    std::vector<T> tiles;
+    for (int32_t g = 0; g < count; ++g) {
+        const tc_problem& p = problems[g];
+        if (p.m < 1 || p.n < 1 || p.k < 1) return fail(TC_ERR_INVALID, "grouped: problem %d has a zero size", g);
+        if (p.lda < p.k || p.ldb < (lb == TC_ROW_MAJOR ? p.n : p.k) || p.ldc < p.n)
+            return fail(TC_ERR_INVALID, "grouped: problem %d leading dimension too small", g);
+        if (p.lda % 8 || p.ldb % 8 || p.off_a % 8 || p.off_b % 8)
+            return fail(TC_ERR_INVALID, "grouped: problem %d rows not 16-byte aligned", g);
+        if (p.off_a < 0 || p.off_b < 0 || p.off_c < 0) return fail(TC_ERR_INVALID, "grouped: problem %d negative offset", g);
+        probs[g] = {p.m, p.n, p.k, 0, p.off_a, p.off_b, p.off_c, p.lda, p.ldb, p.ldc, 0};
+        const int tm = (p.m + tcg::kGroupedTileM - 1) / tcg::kGroupedTileM;
+        const int tn = (p.n + tcg::kGroupedTileN - 1) / tcg::kGroupedTileN;
+        for (int i = 0; i < tm; ++i)
+            for (int j = 0; j < tn; ++j) {
+                const int64_t rows = std::min(tcg::kGroupedTileM, p.m - i * tcg::kGroupedTileM);
+                const int64_t cols = std::min(tcg::kGroupedTileN, p.n - j * tcg::kGroupedTileN);
+                // bytes the tile moves: its A rows, its B columns, its C block
+                const int64_t cost = 2 * p.k * (rows + cols) + 4 * rows * cols;
+                tiles.push_back({cost, {g, i, j, 0}});
+            }
+    }
+    if (tiles.size() > 0x7FFFFFFF) return fail(TC_ERR_INVALID, "grouped: too many tiles");
+    // longest first: a persistent grid striding over this order balances well
+    std::stable_sort(tiles.begin(), tiles.end(), [](const T& a, const T& b) { return a.cost > b.cost; });
+    std::vector<tcg::GroupedTileDev> tl(tiles.size());
+    for (size_t i = 0; i < tiles.size(); ++i) tl[i] = tiles[i].t;
+
+    Device* d;
+    tc_status s = get_device(&d);
+    if (s != TC_OK) return s;
+    auto* plan = new tc_grouped_plan();
+    plan->dt = dt; plan->la = la; plan->lb = lb;
+    plan->count = count;
+    plan->num_tiles = static_cast<int32_t>(tl.size());
+    plan->sm_count = d->sm_count;
+    cudaGetDevice(&plan->dev);
+    cudaError_t e = cudaSuccess;
+    if (count > 0) {
+        if ((e = cudaMalloc(&plan->d_probs, probs.size() * sizeof(probs[0]))) == cudaSuccess)
+            e = cudaMemcpy(plan->d_probs, probs.data(), probs.size() * sizeof(probs[0]), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && (e = cudaMalloc(&plan->d_tiles, tl.size() * sizeof(tl[0]))) == cudaSuccess)
+            e = cudaMemcpy(plan->d_tiles, tl.data(), tl.size() * sizeof(tl[0]), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        gemm_grouped_plan_destroy(plan);
+        return fail(TC_ERR_OOM, "grouped: plan upload: %s", cudaGetErrorString(e));
+    }
+    *plan_out = plan;
+    return TC_OK;
+}
+
+tc_status gemm_grouped_plan_run(tc_grouped_plan* plan, const void* a_base, const void* b_base, float* c_base,
+                                float alpha, float beta, int32_t use_graph, void* stream) {
+    if (!plan) return fail(TC_ERR_INVALID, "grouped: null plan");
+    if (plan->num_tiles == 0) return TC_OK;
+    if (!a_base || !b_base || !c_base) return fail(TC_ERR_INVALID, "grouped: null base pointer");
+    if (!aligned(a_base, 16) || !aligned(b_base, 16) || !aligned(c_base, 8))
+        return fail(TC_ERR_INVALID, "grouped: base pointers must be 16-byte aligned (C: 8)");
+    cudaStream_t st = as_stream(stream);
+    if (!use_graph)
+        return enqueue(tcg::launch_grouped(plan->dt, plan->lb, plan->d_probs, plan->d_tiles, plan->num_tiles, a_base,
+                                           b_base, c_base, alpha, beta, plan->sm_count, st),
+                       "grouped launch");
+    const bool same = plan->exec && plan->g_a == a_base && plan->g_b == b_base && plan->g_c == c_base &&
+                      plan->g_alpha == alpha && plan->g_beta == beta;
+    cudaError_t e;
+    if (!same) {
+        if (plan->exec) {
+            cudaGraphExecDestroy(plan->exec);
+            plan->exec = nullptr;
+        }
+        if (!plan->cap_stream && (e = cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "grouped: capture stream");
+        if ((e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_fail(e, "grouped: begin capture");
+        cudaError_t le = tcg::launch_grouped(plan->dt, plan->lb, plan->d_probs, plan->d_tiles, plan->num_tiles, a_base,
+                                             b_base, c_base, alpha, beta, plan->sm_count, plan->cap_stream);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(plan->cap_stream, &graph);
+        if (le != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(le != cudaSuccess ? le : e, "grouped: capture");
+        }
+        e = cudaGraphInstantiate(&plan->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "grouped: instantiate");
+        plan->g_a = a_base; plan->g_b = b_base; plan->g_c = c_base;
+        plan->g_alpha = alpha; plan->g_beta = beta;
+    }
+    return enqueue(cudaGraphLaunch(plan->exec, st), "grouped: graph launch");
+}
+
+tc_status gemm_grouped_plan_destroy(tc_grouped_plan* plan) {
+    if (!plan) return TC_OK;
+    cudaDeviceSynchronize();
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+    if (plan->d_probs) cudaFree(plan->d_probs);
+    if (plan->d_tiles) cudaFree(plan->d_tiles);
+    delete plan;
+    return TC_OK;
+}
+
+tc_status gemm_grouped(int32_t dt, int32_t count, const tc_problem* problems, const void* a_base, int32_t la,
+                       const void* b_base, int32_t lb, float* c_base, float alpha, float beta, void* stream) {
+    tc_grouped_plan* plan = nullptr;
+    tc_status s = gemm_grouped_plan_create(dt, count, problems, la, lb, &plan);
+    if (s != TC_OK) return s;
+    s = gemm_grouped_plan_run(plan, a_base, b_base, c_base, alpha, beta, 0, stream);
+    if (s == TC_OK) {
+        cudaError_t e = cudaStreamSynchronize(as_stream(stream));
+        if (e != cudaSuccess) s = cuda_fail(e, "grouped: synchronize");
+    }
+    gemm_grouped_plan_destroy(plan);
+    return s;
+}
+
+tc_status tc_error_norm(int64_t m, int64_t n, const float* C, int64_t ldc, const void* Cref, int64_t ldr,
+                        int32_t ref_is_f64, const float* A, int64_t a_rows, int64_t a_cols, int64_t lda,
+                        const float* B, int64_t b_rows, int64_t b_cols, int64_t ldb, double* out, void* stream) {
+    if (!out) return fail(TC_ERR_INVALID, "tc_error_norm: null out");
+    if (m < 0 || n < 0 || a_rows < 0 || a_cols < 0 || b_rows < 0 || b_cols < 0)
+        return fail(TC_ERR_INVALID, "tc_error_norm: negative size");
+    if (m * n > 0 && (!C || !Cref || ldc < n || ldr < n)) return fail(TC_ERR_INVALID, "tc_error_norm: bad C / Cref");
+    if (A && lda < a_cols) return fail(TC_ERR_INVALID, "tc_error_norm: lda < a_cols");
+    if (B && ldb < b_cols) return fail(TC_ERR_INVALID, "tc_error_norm: ldb < b_cols");
+    Device* d;
+    tc_status s = get_device(&d);
+    if (s != TC_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    double* scratch = nullptr;
+    const size_t bytes = (3 * tcg::kErrBlocks * 2 + 4) * sizeof(double);
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, st);
+    if (e != cudaSuccess) return fail(TC_ERR_OOM, "tc_error_norm: scratch: %s", cudaGetErrorString(e));
+    double* out_dev = scratch + 3 * tcg::kErrBlocks * 2;
+    e = tcg::launch_error_norm(m, n, C, ldc, Cref, ldr, ref_is_f64 != 0, A, A ? a_rows : 0, a_cols, lda, B,
+                               B ? b_rows : 0, b_cols, ldb, scratch, out_dev, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, out_dev, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(scratch, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "tc_error_norm");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "tc_error_norm: synchronize");
+    return TC_OK;
+}
+
+}  // extern "C"

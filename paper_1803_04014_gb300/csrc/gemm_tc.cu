@@ -1,0 +1,350 @@
+// Persistent tcgen05 GEMM for sm_103a: C = alpha * descale * sum_p X_p Y_p + beta * C.
+//
+// Mixed precision (Sec. IV, one product of FP16/BF16/E4M3 operands with FP32
+// accumulation) and the precision refinement of Sec. V (Eq. 1: 2 products,
+// Eq. 2: 4 products, or 3 without R_A R_B) share this kernel: the operands are
+// stacks of "pieces" (A: NA pieces of m x k, B: NB pieces of n x k, all K-major)
+// and every product of the list accumulates into the same TMEM accumulator, so
+// a refined GEMM is one launch instead of the paper's four chained GEMMs.
+//
+// Block of 192 threads, one CTA per SM, persistent over output tiles of
+// 128 x BN:
+//   warp 0     one thread issues TMA loads of every piece's k-block into a
+//              STAGES-deep shared-memory ring (full/empty mbarriers);
+//   warp 1     allocates 2*BN TMEM columns (two accumulators); one thread
+//              issues tcgen05.mma (128 x BN x 16 for 16-bit inputs, x 32 for
+//              E4M3) and commits each stage back to the producer and each
+//              finished accumulator to the epilogue;
+//   warps 2-5  epilogue: tcgen05.ld of the accumulator (each warp owns 32 TMEM
+//              lanes = 32 rows), alpha/beta in FP32, stores to C, then frees
+//              the accumulator so the MMA of tile i+1 overlaps the epilogue of
+//              tile i.
+// Shared-memory tiles use the 128-byte swizzle written by TMA and read by the
+// UMMA descriptors (rows of 128 bytes = one k-block).
+#include "launch.h"
+#include "tc_ptx.cuh"
+
+namespace tcg {
+namespace {
+
+constexpr int BM = 128;
+constexpr int kRowBytes = 128;
+constexpr int kATileBytes = BM * kRowBytes;
+constexpr int kThreads = 192;
+constexpr int kGroupM = 16;  // raster: bands of 16 M-tiles for L2 reuse of B
+
+struct Args {
+    int m, n, k;
+    int num_kb, tiles_m, tiles_n, num_tiles;
+    float alpha, beta;
+    float* C;
+    int64_t ldc;
+    const float* scale_a;
+    const float* scale_b;
+    int* status;
+    uint32_t idesc;
+};
+
+// product p multiplies A piece prod_a(p) with B piece prod_b(p):
+// (hi,hi), (lo,hi), (hi,lo), (lo,lo)
+__host__ __device__ constexpr int prod_a(int p) { return p & 1; }
+__host__ __device__ constexpr int prod_b(int p) { return p >> 1; }
+
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& mb, int& nb) {
+    const int band = kGroupM * tiles_n;
+    const int g = t / band;
+    const int first = g * kGroupM;
+    const int gm = min(tiles_m - first, kGroupM);
+    const int r = t - g * band;
+    mb = first + r % gm;
+    nb = r / gm;
+}
+
+template <int BN, int STAGES, int NA, int NB>
+struct Layout {
+    static constexpr int kBTileBytes = BN * kRowBytes;
+    static constexpr int kStageBytes = NA * kATileBytes + NB * kBTileBytes;
+    static constexpr int kBarOffset = STAGES * kStageBytes;
+    // full[S], empty[S], tfull[2], tempty[2], drain
+    static constexpr int kNumBars = 2 * STAGES + 5;
+    static constexpr int kSlotOffset = kBarOffset + 8 * kNumBars;
+    static constexpr int kBytes = kSlotOffset + 16 + 1024;  // + alignment slack
+    static constexpr int kTmemCols = 2 * BN;
+};
+
+template <int KIND, int BN, int STAGES, int NA, int NB, int NPROD>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Args a) {
+    using L = Layout<BN, STAGES, NA, NB>;
+    static_assert(L::kTmemCols == 256 || L::kTmemCols == 512, "TMEM columns must be a power of two");
+    constexpr int kElemBytes = (KIND == 1) ? 1 : 2;
+    constexpr int BK = kRowBytes / kElemBytes;  // elements per k-block
+    constexpr int kSteps = 4;                   // 4 MMAs of 32 bytes of K per k-block
+
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_addr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* base_ptr = smem_raw + (base - raw);
+    const uint32_t bars = base + L::kBarOffset;
+    auto full_bar = [&](int s) { return bars + 8u * s; };
+    auto empty_bar = [&](int s) { return bars + 8u * (STAGES + s); };
+    auto tfull_bar = [&](int i) { return bars + 8u * (2 * STAGES + i); };
+    auto tempty_bar = [&](int i) { return bars + 8u * (2 * STAGES + 2 + i); };
+    const uint32_t drain_bar = bars + 8u * (2 * STAGES + 4);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + L::kSlotOffset);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(base_ptr + L::kSlotOffset + 4);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(tfull_bar(i), 1);
+            mbar_init(tempty_bar(i), 4);  // one arrival per epilogue warp
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_addr(tmem_slot), L::kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued_phase[STAGES];
+#pragma unroll
+            for (int s = 0; s < STAGES; ++s) issued_phase[s] = -1;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < a.num_tiles; t += gridDim.x) {
+                int mb, nb;
+                tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+                for (int kb = 0; kb < a.num_kb; ++kb) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, a.status)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sbase = base + stage * L::kStageBytes;
+                    mbar_arrive_expect_tx(full_bar(stage), L::kStageBytes);
+#pragma unroll
+                    for (int p = 0; p < NA; ++p)
+                        tma_load_3d(sbase + p * kATileBytes, &tmA, full_bar(stage), kb * BK, mb * BM, p);
+#pragma unroll
+                    for (int p = 0; p < NB; ++p)
+                        tma_load_3d(sbase + NA * kATileBytes + p * L::kBTileBytes, &tmB, full_bar(stage), kb * BK,
+                                    nb * BN, p);
+                    issued_phase[stage] = static_cast<int>(phase);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // leaving early: let the copies already issued land before the CTA exits
+                for (int s = 0; s < STAGES; ++s)
+                    if (issued_phase[s] >= 0)
+                        mbar_wait_bounded(full_bar(s), static_cast<uint32_t>(issued_phase[s]), 100000000ull);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true;
+            bool issued_any = false;
+            for (int t = blockIdx.x; ok && t < a.num_tiles; t += gridDim.x) {
+                if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, a.status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
+                for (int kb = 0; kb < a.num_kb; ++kb) {
+                    if (!mbar_wait(full_bar(stage), phase, abort_flag, a.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sbase = base + stage * L::kStageBytes;
+#pragma unroll
+                    for (int ks = 0; ks < kSteps; ++ks) {
+#pragma unroll
+                        for (int p = 0; p < NPROD; ++p) {
+                            const uint32_t a_addr = sbase + prod_a(p) * kATileBytes + ks * 32;
+                            const uint32_t b_addr = sbase + NA * kATileBytes + prod_b(p) * L::kBTileBytes + ks * 32;
+                            const uint32_t accumulate = (kb | ks | p) != 0 ? 1u : 0u;
+                            if constexpr (KIND == 1)
+                                mma_f8(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), a.idesc,
+                                       accumulate);
+                            else
+                                mma_f16(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), a.idesc,
+                                        accumulate);
+                        }
+                    }
+                    issued_any = true;
+                    mma_commit(empty_bar(stage));  // the stage is free once these MMAs read it
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(tfull_bar(acc));
+                acc ^= 1;
+                if (acc == 0) acc_phase ^= 1u;
+            }
+            if (!ok && issued_any) {
+                // leaving early: wait for the MMAs in flight before TMEM is freed
+                mma_commit(drain_bar);
+                mbar_wait_bounded(drain_bar, 0, 100000000ull);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 2..5)
+        const int quarter = warp & 3;  // TMEM lanes [32*quarter, 32*quarter + 32)
+        float alpha = a.alpha;
+        if constexpr (KIND == 1) alpha = alpha * (1.0f / *a.scale_a) * (1.0f / *a.scale_b);
+        const float beta = a.beta;
+        const bool vec_ok = ((a.ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15u) == 0);
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int t = blockIdx.x; t < a.num_tiles; t += gridDim.x) {
+            int mb, nb;
+            tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+            const bool ok = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, a.status);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const int row = mb * BM + quarter * 32 + lane;
+            const int col0 = nb * BN;
+            const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                                   static_cast<uint32_t>(acc * BN);
+            float* crow = a.C + static_cast<int64_t>(row) * a.ldc + col0;
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                if (col0 + c >= a.n) break;  // uniform across the warp
+                float v[32];
+                tmem_load_32(taddr + c, v);
+                if (row < a.m) {
+                    const int ncols = min(32, a.n - (col0 + c));
+                    float* p = crow + c;
+                    if (ncols == 32 && vec_ok) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            float4 o;
+                            if (beta != 0.0f) {
+                                const float4 old = *reinterpret_cast<const float4*>(p + 4 * j);
+                                o.x = fmaf(alpha, v[4 * j + 0], beta * old.x);
+                                o.y = fmaf(alpha, v[4 * j + 1], beta * old.y);
+                                o.z = fmaf(alpha, v[4 * j + 2], beta * old.z);
+                                o.w = fmaf(alpha, v[4 * j + 3], beta * old.w);
+                            } else {
+                                o.x = alpha * v[4 * j + 0];
+                                o.y = alpha * v[4 * j + 1];
+                                o.z = alpha * v[4 * j + 2];
+                                o.w = alpha * v[4 * j + 3];
+                            }
+                            *reinterpret_cast<float4*>(p + 4 * j) = o;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if (j < ncols) p[j] = (beta != 0.0f) ? fmaf(alpha, v[j], beta * p[j]) : alpha * v[j];
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty_bar(acc));
+            acc ^= 1;
+            if (acc == 0) acc_phase ^= 1u;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, L::kTmemCols);
+    }
+}
+
+template <int KIND, int BN, int STAGES, int NA, int NB, int NPROD>
+cudaError_t run(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args& args, int grid, cudaStream_t st) {
+    using L = Layout<BN, STAGES, NA, NB>;
+    auto kern = k_tc_gemm<KIND, BN, STAGES, NA, NB, NPROD>;
+    static bool configured = false;  // per instantiation; the attribute is per function and device-independent
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    kern<<<grid, kThreads, L::kBytes, st>>>(tmA, tmB, args);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tc_gemm_smem_bytes(int na, int nb, int bn, int* stages_out) {
+    const int stage = na * kATileBytes + nb * bn * kRowBytes;
+    int stages = (192 * 1024) / stage;
+    if (stages > 4) stages = 4;
+    if (stages_out) *stages_out = stages;
+    return static_cast<size_t>(stages) * stage + 8 * (2 * stages + 5) + 16 + 1024;
+}
+
+cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmLaunch& p, cudaStream_t st) {
+    Args a;
+    a.m = static_cast<int>(p.m);
+    a.n = static_cast<int>(p.n);
+    a.k = static_cast<int>(p.k);
+    const int bk = (p.kind == 1) ? 128 : 64;
+    a.num_kb = static_cast<int>((p.k + bk - 1) / bk);
+    a.tiles_m = static_cast<int>((p.m + BM - 1) / BM);
+    a.tiles_n = static_cast<int>((p.n + p.bn - 1) / p.bn);
+    a.num_tiles = a.tiles_m * a.tiles_n;
+    a.alpha = p.alpha;
+    a.beta = p.beta;
+    a.C = p.C;
+    a.ldc = p.ldc;
+    a.scale_a = p.scale_a;
+    a.scale_b = p.scale_b;
+    a.status = p.status;
+    a.idesc = make_idesc(BM, p.bn, static_cast<uint32_t>(p.ab_format));
+    const int grid = a.num_tiles < p.sm_count ? a.num_tiles : p.sm_count;
+    if (grid <= 0) return cudaSuccess;
+
+    if (p.kind == 1) {
+        if (p.na == 1 && p.nb == 1 && p.bn == 256) return run<1, 256, 4, 1, 1, 1>(tmA, tmB, a, grid, st);
+        return cudaErrorInvalidValue;
+    }
+    if (p.na == 1 && p.nb == 1 && p.bn == 256) return run<0, 256, 4, 1, 1, 1>(tmA, tmB, a, grid, st);
+    if (p.na == 2 && p.nb == 1 && p.nprod == 2 && p.bn == 256) return run<0, 256, 3, 2, 1, 2>(tmA, tmB, a, grid, st);
+    if (p.na == 2 && p.nb == 2 && p.nprod == 3 && p.bn == 128) return run<0, 128, 3, 2, 2, 3>(tmA, tmB, a, grid, st);
+    if (p.na == 2 && p.nb == 2 && p.nprod == 4 && p.bn == 128) return run<0, 128, 3, 2, 2, 4>(tmA, tmB, a, grid, st);
+    if (p.na == 2 && p.nb == 2 && p.nprod == 3 && p.bn == 256) return run<0, 256, 2, 2, 2, 3>(tmA, tmB, a, grid, st);
+    if (p.na == 2 && p.nb == 2 && p.nprod == 4 && p.bn == 256) return run<0, 256, 2, 2, 2, 4>(tmA, tmB, a, grid, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace tcg

@@ -1,0 +1,70 @@
+// Internal launchers: each kernel file exposes host functions that enqueue its
+// kernels; api.cu validates arguments and calls them.  Not part of the C ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tcg {
+
+// ---- quantize.cu
+// Round rows x cols FP32 (row-major, ld_src) to dt; transpose writes cols x rows.
+// For E4M3 `scale` is the device word used first as the max|x| accumulator and
+// finally holding the scale.
+cudaError_t launch_quantize(int dt, int64_t rows, int64_t cols, const float* src, int64_t ld_src, void* dst,
+                            int64_t ld_dst, bool transpose, float* scale, cudaStream_t st);
+cudaError_t launch_split(int piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src, bool transpose,
+                         void* hi, void* lo, int64_t ld_dst, cudaStream_t st);
+cudaError_t launch_scale_c(int64_t m, int64_t n, float beta, float* C, int64_t ldc, cudaStream_t st);
+
+// ---- gemm_tc.cu
+struct TcGemmLaunch {
+    int kind;           // 0: 16-bit inputs (F16/BF16), 1: E4M3
+    int ab_format;      // instruction-descriptor operand format
+    int na, nb, nprod;  // pieces of A and B, number of products
+    int64_t m, n, k;
+    float alpha, beta;
+    float* C;
+    int64_t ldc;
+    const float* scale_a;
+    const float* scale_b;
+    int* status;
+    int sm_count;
+    int bn;             // tile width (128 or 256)
+};
+// tmA: 3-D map {k, m, na} with a 128 x (128 bytes) box; tmB: {k, n, nb} with a bn x (128 bytes) box.
+cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmLaunch& p, cudaStream_t st);
+size_t tc_gemm_smem_bytes(int na, int nb, int bn, int* stages_out);
+
+// ---- sgemm.cu
+cudaError_t launch_sgemm(int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda, int la,
+                         const float* B, int64_t ldb, int lb, float beta, float* C, int64_t ldc, cudaStream_t st);
+
+// ---- gemm_small.cu
+cudaError_t launch_batched16(int dt, int64_t batch, float alpha, const void* A, int64_t sa, const void* B, int64_t sb,
+                             int lb, float beta, float* C, int64_t sc, int* status, int sm_count, cudaStream_t st);
+
+struct GroupedProblemDev {   // device copy of one problem
+    int32_t m, n, k, pad;
+    int64_t off_a, off_b, off_c;
+    int32_t lda, ldb, ldc, pad2;
+};
+struct GroupedTileDev {      // one output tile of one problem
+    int32_t prob, tm, tn, pad;
+};
+cudaError_t launch_grouped(int dt, int lb, const GroupedProblemDev* probs, const GroupedTileDev* tiles,
+                           int32_t num_tiles, const void* a_base, const void* b_base, float* c_base, float alpha,
+                           float beta, int sm_count, cudaStream_t st);
+constexpr int kGroupedTileM = 64;
+constexpr int kGroupedTileN = 64;
+
+// ---- errnorm.cu
+constexpr int kErrBlocks = 1024;  // fixed grid: the reduction order does not depend on the GPU
+// partial: 3 * kErrBlocks * 2 doubles of scratch.
+cudaError_t launch_error_norm(int64_t m, int64_t n, const float* C, int64_t ldc, const void* ref, int64_t ldr,
+                              bool ref_f64, const float* A, int64_t ar, int64_t ac, int64_t lda, const float* B,
+                              int64_t br, int64_t bc, int64_t ldb, double* partial, double* out4_dev,
+                              cudaStream_t st);
+
+}  // namespace tcg

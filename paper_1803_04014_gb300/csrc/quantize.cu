@@ -1,0 +1,334 @@
+// Input rounding and residual split (Sec. V; Sec. VI rounds A and B to half
+// precision before the GEMM).
+//
+//   quantize: dst = RNE(src) to F16 / BF16, or RNE_satfinite(src * s) to E4M3
+//             with s = 2^j the largest power of two with max|src| * s <= 448.
+//   split:    hi = RNE16(x), lo = RNE16(x - hi) (the residual R of Sec. V,
+//             stored in 16 bits as Eq. 1 / Eq. 2 multiply it on tensor cores).
+//
+// All of these are HBM-bound streams (4 bytes in, 1-4 bytes out per element):
+// the row kernels move 8 elements per thread with 16-byte loads, the
+// transposing kernels stage 32 x 32 tiles in shared memory so that both the
+// FP32 reads and the narrow writes are coalesced.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "launch.h"
+
+namespace tcg {
+namespace {
+
+constexpr int kDtF16 = 0, kDtBF16 = 1, kDtE4M3 = 2;
+
+// Exponent j of the E4M3 scale: the largest j with amax * 2^j <= 448, capped
+// at 127; amax = 0 or non-finite gives 0.  With amax = m * 2^E, m in [0.5, 1):
+// amax * 2^j <= 0.875 * 2^9  <=>  E + j <= 9 (m <= 0.875) or E + j <= 8.
+__device__ __forceinline__ int e4m3_scale_exp(float amax) {
+    if (!(amax > 0.0f) || !isfinite(amax)) return 0;
+    int E;
+    const float m = frexpf(amax, &E);
+    const int j = (m <= 0.875f) ? (9 - E) : (8 - E);
+    return j > 127 ? 127 : j;
+}
+
+__device__ __forceinline__ float e4m3_scale_from_amax_word(const float* scale_word) {
+    const float amax = __uint_as_float(*reinterpret_cast<const volatile unsigned*>(scale_word));
+    return ldexpf(1.0f, e4m3_scale_exp(amax));
+}
+
+template <int DT>
+struct Narrow;
+template <>
+struct Narrow<kDtF16> {
+    using T = unsigned short;
+    __device__ static T cvt(float x, float) { return __half_as_ushort(__float2half_rn(x)); }
+};
+template <>
+struct Narrow<kDtBF16> {
+    using T = unsigned short;
+    __device__ static T cvt(float x, float) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+};
+template <>
+struct Narrow<kDtE4M3> {
+    using T = unsigned char;
+    __device__ static T cvt(float x, float s) {
+        return static_cast<T>(__nv_cvt_float_to_fp8(x * s, __NV_SATFINITE, __NV_E4M3));
+    }
+};
+
+__global__ void k_absmax(int64_t rows, int64_t cols, const float* __restrict__ src, int64_t ld,
+                         float* scale_word) {
+    float m = 0.0f;
+    const int64_t total = rows * cols;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / cols, c = i - r * cols;
+        m = fmaxf(m, fabsf(src[r * ld + c]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wmax[32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = (threadIdx.x < (blockDim.x >> 5)) ? wmax[threadIdx.x] : 0.0f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        // non-negative floats order like their bit patterns
+        if (threadIdx.x == 0) atomicMax(reinterpret_cast<unsigned*>(scale_word), __float_as_uint(m));
+    }
+}
+
+__global__ void k_e4m3_finalize(float* scale_word) {
+    *scale_word = e4m3_scale_from_amax_word(scale_word);
+}
+
+__global__ void k_store_one(float* p) { *p = 1.0f; }
+
+// 8 consecutive elements per thread; requires cols % 8 == 0 and 16-byte
+// aligned rows of src and dst.
+template <int DT>
+__global__ void __launch_bounds__(256) k_quantize_vec8(int64_t rows, int64_t cols, const float* __restrict__ src,
+                                                       int64_t ld_src, typename Narrow<DT>::T* __restrict__ dst,
+                                                       int64_t ld_dst, const float* scale_word) {
+    using T = typename Narrow<DT>::T;
+    const float s = (DT == kDtE4M3) ? e4m3_scale_from_amax_word(scale_word) : 1.0f;
+    const int64_t vpr = cols / 8;
+    const int64_t total = rows * vpr;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / vpr, c = (i - r * vpr) * 8;
+        const float4* p = reinterpret_cast<const float4*>(src + r * ld_src + c);
+        const float4 a = __ldcs(p), b = __ldcs(p + 1);
+        const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        T o[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o[j] = Narrow<DT>::cvt(v[j], s);
+        if constexpr (sizeof(T) == 2) {
+            uint4 w;
+            w.x = o[0] | (uint32_t(o[1]) << 16);
+            w.y = o[2] | (uint32_t(o[3]) << 16);
+            w.z = o[4] | (uint32_t(o[5]) << 16);
+            w.w = o[6] | (uint32_t(o[7]) << 16);
+            *reinterpret_cast<uint4*>(dst + r * ld_dst + c) = w;
+        } else {
+            uint2 w;
+            w.x = o[0] | (uint32_t(o[1]) << 8) | (uint32_t(o[2]) << 16) | (uint32_t(o[3]) << 24);
+            w.y = o[4] | (uint32_t(o[5]) << 8) | (uint32_t(o[6]) << 16) | (uint32_t(o[7]) << 24);
+            *reinterpret_cast<uint2*>(dst + r * ld_dst + c) = w;
+        }
+    }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(256) k_quantize_scalar(int64_t rows, int64_t cols, const float* __restrict__ src,
+                                                         int64_t ld_src, typename Narrow<DT>::T* __restrict__ dst,
+                                                         int64_t ld_dst, const float* scale_word) {
+    const float s = (DT == kDtE4M3) ? e4m3_scale_from_amax_word(scale_word) : 1.0f;
+    const int64_t total = rows * cols;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / cols, c = i - r * cols;
+        dst[r * ld_dst + c] = Narrow<DT>::cvt(src[r * ld_src + c], s);
+    }
+}
+
+// dst[c * ld_dst + r] = cvt(src[r * ld_src + c]); one 32 x 32 tile per block (32 x 8 threads).
+template <int DT>
+__global__ void __launch_bounds__(256) k_quantize_transpose(int64_t rows, int64_t cols, const float* __restrict__ src,
+                                                            int64_t ld_src, typename Narrow<DT>::T* __restrict__ dst,
+                                                            int64_t ld_dst, const float* scale_word) {
+    __shared__ float tile[32][33];
+    const float s = (DT == kDtE4M3) ? e4m3_scale_from_amax_word(scale_word) : 1.0f;
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t r = r0 + ty + 8 * i, c = c0 + tx;
+        tile[ty + 8 * i][tx] = (r < rows && c < cols) ? __ldcs(src + r * ld_src + c) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t c = c0 + ty + 8 * i, r = r0 + tx;
+        if (r < rows && c < cols) dst[c * ld_dst + r] = Narrow<DT>::cvt(tile[tx][ty + 8 * i], s);
+    }
+}
+
+template <int PIECE>
+__device__ __forceinline__ void split_one(float x, unsigned short& hi, unsigned short& lo) {
+    if constexpr (PIECE == kDtF16) {
+        const __half h = __float2half_rn(x);
+        hi = __half_as_ushort(h);
+        lo = __half_as_ushort(__float2half_rn(x - __half2float(h)));  // x - hi is exact in FP32
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        hi = __bfloat16_as_ushort(h);
+        lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+    }
+}
+
+template <int PIECE>
+__global__ void __launch_bounds__(256) k_split_vec8(int64_t rows, int64_t cols, const float* __restrict__ src,
+                                                    int64_t ld_src, unsigned short* __restrict__ hi,
+                                                    unsigned short* __restrict__ lo, int64_t ld_dst) {
+    const int64_t vpr = cols / 8;
+    const int64_t total = rows * vpr;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / vpr, c = (i - r * vpr) * 8;
+        const float4* p = reinterpret_cast<const float4*>(src + r * ld_src + c);
+        const float4 a = __ldcs(p), b = __ldcs(p + 1);
+        const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        unsigned short h[8], l[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) split_one<PIECE>(v[j], h[j], l[j]);
+        uint4 wh, wl;
+        wh.x = h[0] | (uint32_t(h[1]) << 16); wh.y = h[2] | (uint32_t(h[3]) << 16);
+        wh.z = h[4] | (uint32_t(h[5]) << 16); wh.w = h[6] | (uint32_t(h[7]) << 16);
+        wl.x = l[0] | (uint32_t(l[1]) << 16); wl.y = l[2] | (uint32_t(l[3]) << 16);
+        wl.z = l[4] | (uint32_t(l[5]) << 16); wl.w = l[6] | (uint32_t(l[7]) << 16);
+        *reinterpret_cast<uint4*>(hi + r * ld_dst + c) = wh;
+        *reinterpret_cast<uint4*>(lo + r * ld_dst + c) = wl;
+    }
+}
+
+template <int PIECE>
+__global__ void __launch_bounds__(256) k_split_scalar(int64_t rows, int64_t cols, const float* __restrict__ src,
+                                                      int64_t ld_src, unsigned short* __restrict__ hi,
+                                                      unsigned short* __restrict__ lo, int64_t ld_dst) {
+    const int64_t total = rows * cols;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / cols, c = i - r * cols;
+        unsigned short h, l;
+        split_one<PIECE>(src[r * ld_src + c], h, l);
+        hi[r * ld_dst + c] = h;
+        lo[r * ld_dst + c] = l;
+    }
+}
+
+template <int PIECE>
+__global__ void __launch_bounds__(256) k_split_transpose(int64_t rows, int64_t cols, const float* __restrict__ src,
+                                                         int64_t ld_src, unsigned short* __restrict__ hi,
+                                                         unsigned short* __restrict__ lo, int64_t ld_dst) {
+    __shared__ float tile[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t r = r0 + ty + 8 * i, c = c0 + tx;
+        tile[ty + 8 * i][tx] = (r < rows && c < cols) ? __ldcs(src + r * ld_src + c) : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t c = c0 + ty + 8 * i, r = r0 + tx;
+        if (r < rows && c < cols) {
+            unsigned short h, l;
+            split_one<PIECE>(tile[tx][ty + 8 * i], h, l);
+            hi[c * ld_dst + r] = h;
+            lo[c * ld_dst + r] = l;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scale_c(int64_t m, int64_t n, float beta, float* C, int64_t ldc) {
+    const int64_t total = m * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / n, c = i - r * n;
+        float* p = C + r * ldc + c;
+        *p = (beta == 0.0f) ? 0.0f : beta * *p;
+    }
+}
+
+inline unsigned grid_for(int64_t work, int64_t per_block) {
+    int64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > 152 * 32) g = 152 * 32;  // grid-stride beyond this
+    return static_cast<unsigned>(g);
+}
+
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <int DT>
+cudaError_t quantize_dt(int64_t rows, int64_t cols, const float* src, int64_t ld_src, void* dst, int64_t ld_dst,
+                        bool transpose, const float* scale, cudaStream_t st) {
+    using T = typename Narrow<DT>::T;
+    T* d = static_cast<T*>(dst);
+    if (transpose) {
+        dim3 grid(static_cast<unsigned>((cols + 31) / 32), static_cast<unsigned>((rows + 31) / 32));
+        k_quantize_transpose<DT><<<grid, dim3(32, 8), 0, st>>>(rows, cols, src, ld_src, d, ld_dst, scale);
+    } else {
+        const bool vec = (cols % 8 == 0) && (ld_src % 4 == 0) && ((ld_dst * sizeof(T)) % (8 * sizeof(T)) == 0) &&
+                         aligned16(src) && ((reinterpret_cast<uintptr_t>(dst) % (8 * sizeof(T))) == 0);
+        if (vec) {
+            k_quantize_vec8<DT><<<grid_for(rows * (cols / 8), 256), 256, 0, st>>>(rows, cols, src, ld_src, d, ld_dst,
+                                                                              scale);
+        } else {
+            k_quantize_scalar<DT><<<grid_for(rows * cols, 256), 256, 0, st>>>(rows, cols, src, ld_src, d, ld_dst,
+                                                                           scale);
+        }
+    }
+    return cudaGetLastError();
+}
+
+template <int PIECE>
+cudaError_t split_piece(int64_t rows, int64_t cols, const float* src, int64_t ld_src, bool transpose, void* hi,
+                        void* lo, int64_t ld_dst, cudaStream_t st) {
+    auto* h = static_cast<unsigned short*>(hi);
+    auto* l = static_cast<unsigned short*>(lo);
+    if (transpose) {
+        dim3 grid(static_cast<unsigned>((cols + 31) / 32), static_cast<unsigned>((rows + 31) / 32));
+        k_split_transpose<PIECE><<<grid, dim3(32, 8), 0, st>>>(rows, cols, src, ld_src, h, l, ld_dst);
+    } else {
+        const bool vec = (cols % 8 == 0) && (ld_src % 4 == 0) && (ld_dst % 8 == 0) && aligned16(src) &&
+                         aligned16(hi) && aligned16(lo);
+        if (vec)
+            k_split_vec8<PIECE><<<grid_for(rows * (cols / 8), 256), 256, 0, st>>>(rows, cols, src, ld_src, h, l,
+                                                                               ld_dst);
+        else
+            k_split_scalar<PIECE><<<grid_for(rows * cols, 256), 256, 0, st>>>(rows, cols, src, ld_src, h, l, ld_dst);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_quantize(int dt, int64_t rows, int64_t cols, const float* src, int64_t ld_src, void* dst,
+                            int64_t ld_dst, bool transpose, float* scale, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (dt == kDtE4M3) {
+        e = cudaMemsetAsync(scale, 0, sizeof(float), st);
+        if (e != cudaSuccess) return e;
+        if (rows > 0 && cols > 0) {
+            k_absmax<<<grid_for(rows * cols, 256 * 16), 256, 0, st>>>(rows, cols, src, ld_src, scale);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = quantize_dt<kDtE4M3>(rows, cols, src, ld_src, dst, ld_dst, transpose, scale, st)) != cudaSuccess)
+                return e;
+        }
+        k_e4m3_finalize<<<1, 1, 0, st>>>(scale);
+        return cudaGetLastError();
+    }
+    if (rows > 0 && cols > 0) {
+        e = (dt == kDtF16) ? quantize_dt<kDtF16>(rows, cols, src, ld_src, dst, ld_dst, transpose, nullptr, st)
+                           : quantize_dt<kDtBF16>(rows, cols, src, ld_src, dst, ld_dst, transpose, nullptr, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (scale) {
+        k_store_one<<<1, 1, 0, st>>>(scale);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+cudaError_t launch_split(int piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src, bool transpose,
+                         void* hi, void* lo, int64_t ld_dst, cudaStream_t st) {
+    if (rows == 0 || cols == 0) return cudaSuccess;
+    return piece == kDtF16 ? split_piece<kDtF16>(rows, cols, src, ld_src, transpose, hi, lo, ld_dst, st)
+                           : split_piece<kDtBF16>(rows, cols, src, ld_src, transpose, hi, lo, ld_dst, st);
+}
+
+cudaError_t launch_scale_c(int64_t m, int64_t n, float beta, float* C, int64_t ldc, cudaStream_t st) {
+    if (m == 0 || n == 0) return cudaSuccess;
+    k_scale_c<<<grid_for(m * n, 256), 256, 0, st>>>(m, n, beta, C, ldc);
+    return cudaGetLastError();
+}
+
+}  // namespace tcg

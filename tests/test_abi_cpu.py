@@ -1,0 +1,108 @@
+"""The C-ABI library builds, loads and exports every symbol include/tcgemm.h declares.
+
+No GPU needed: only host-side argument validation is exercised (it answers
+before any device is touched).
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tcgemm.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "defined")))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1803_04014_gb300 import binding
+    return binding.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for must in ("gemm_mixed", "gemm_split", "gemm_grouped", "serve_submit", "serve_poll", "tc_quantize",
+                 "tc_error_norm", "gemm_batched_strided", "gemm_sgemm"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1803_04014_gb300 import binding
+    names = _declared_functions()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(binding.SIGNATURES), set(names) ^ set(binding.SIGNATURES)
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.library_path()], capture_output=True, text=True).stdout
+    exported = set(line.split()[-1] for line in out.splitlines() if line.strip())
+    assert set(names) <= exported
+
+
+def test_struct_layouts_match_header(tmp_path):
+    from paper_1803_04014_gb300 import binding
+    src = tmp_path / "layout.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "tcgemm.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(tc_problem), sizeof(tc_serve_cfg),"
+        " sizeof(tc_request), sizeof(tc_result), offsetof(tc_problem, off_c), offsetof(tc_request, C),"
+        " offsetof(tc_request, alpha)); return 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(binding.tc_problem), ctypes.sizeof(binding.tc_serve_cfg), ctypes.sizeof(binding.tc_request),
+            ctypes.sizeof(binding.tc_result), binding.tc_problem.off_c.offset, binding.tc_request.C.offset,
+            binding.tc_request.alpha.offset]
+    assert got == want
+
+
+def test_version_and_error_string(lib):
+    from paper_1803_04014_gb300 import binding
+    assert "sm_103a" in binding.tc_version()
+    assert isinstance(binding.tc_last_error(), str)
+
+
+def test_host_validation_without_gpu(lib):
+    from paper_1803_04014_gb300 import binding as b
+    cases = [
+        lambda: lib.gemm_mixed(7, 8, 8, 8, 1.0, None, 8, 0, None, 8, 1, 0.0, None, 8, None, None, None),
+        lambda: lib.gemm_mixed(0, -1, 8, 8, 1.0, None, 8, 0, None, 8, 1, 0.0, None, 8, None, None, None),
+        lambda: lib.gemm_mixed(0, 8, 8, 8, 1.0, None, 8, 5, None, 8, 1, 0.0, None, 8, None, None, None),
+        lambda: lib.gemm_split(2, 3, 8, 8, 8, 1.0, None, 8, 0, None, 8, 0, 0.0, None, 8, None, 0, None),
+        lambda: lib.gemm_split(0, 5, 8, 8, 8, 1.0, None, 8, 0, None, 8, 0, 0.0, None, 8, None, 0, None),
+        lambda: lib.tc_quantize(9, 4, 4, None, 4, None, 4, 0, None, None),
+        lambda: lib.tc_quantize(2, 4, 4, None, 4, None, 4, 0, None, None),   # E4M3 without a scale word
+        lambda: lib.tc_split(2, 4, 4, None, 4, 0, None, None, 4, None),
+        lambda: lib.gemm_batched_strided(2, 10, 16, 16, 16, 1.0, None, 256, 0, None, 256, 0, 0.0, None, 256, None),
+        lambda: lib.gemm_batched_strided(0, 10, 32, 16, 16, 1.0, None, 256, 0, None, 256, 0, 0.0, None, 256, None),
+    ]
+    for f in cases:
+        assert f() in (b.TC_ERR_INVALID, b.TC_ERR_UNSUPPORTED)
+    # empty problems are no-ops that touch nothing
+    assert lib.gemm_mixed(0, 0, 8, 8, 1.0, None, 8, 0, None, 8, 1, 0.0, None, 8, None, None, None) == b.TC_OK
+    assert lib.gemm_split_workspace_bytes(0, 3, 100, 50, 30) >= 2 * 2 * (100 + 50) * 30
+
+
+def test_grouped_plan_rejects_bad_problems(lib):
+    from paper_1803_04014_gb300 import binding as b
+    plan = ctypes.c_void_p()
+    bad = b.problems_array([(16, 16, 16, 0, 0, 0, 12, 16, 16)])          # lda not a multiple of 8
+    assert lib.gemm_grouped_plan_create(0, 1, bad, 0, 0, ctypes.byref(plan)) == b.TC_ERR_INVALID
+    zero = b.problems_array([(0, 16, 16, 0, 0, 0, 16, 16, 16)])
+    assert lib.gemm_grouped_plan_create(0, 1, zero, 0, 0, ctypes.byref(plan)) == b.TC_ERR_INVALID
+    assert lib.gemm_grouped_plan_create(2, 1, zero, 0, 0, ctypes.byref(plan)) == b.TC_ERR_UNSUPPORTED
+    assert "grouped" in b.tc_last_error()
+
+
+def test_serve_rejects_bad_config(lib):
+    from paper_1803_04014_gb300 import binding as b
+    cfg = b.tc_serve_cfg(0, 4, 2, 16, 0)
+    srv = ctypes.c_void_p()
+    assert lib.serve_open(ctypes.byref(cfg), ctypes.byref(srv)) == b.TC_ERR_INVALID
+    assert lib.serve_poll(None, 1, None) == b.TC_ERR_INVALID

@@ -1,0 +1,370 @@
+"""GPU parity: every kernel of the path through the C ABI against the CPU oracle.
+
+Rounding, scaling and splitting are compared bit for bit; GEMMs element by
+element within the FP32 accumulation bound and normwise within 1e-5 of the
+oracle's result on the same rounded inputs.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gemm as og
+from oracle import numerics as nm
+from tests.gpu_common import TOL_NORMWISE, dev, elementwise_ok, host, need_gpu, normwise_dev, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def b():
+    need_gpu()
+    from paper_1803_04014_gb300 import binding
+    binding.load()
+    return binding
+
+
+DT_NAME = {0: "f16", 1: "bf16", 2: "e4m3"}
+
+
+def _quant_dev(b, dt, X, transpose=False):
+    """Quantise FP32 numpy X on the GPU; returns (device tensor of codes, device scale word)."""
+    rows, cols = X.shape
+    xt = dev(X)
+    tdt = {0: torch.float16, 1: torch.bfloat16, 2: torch.uint8}[dt]
+    out = torch.empty((cols, rows) if transpose else (rows, cols), dtype=tdt, device="cuda")
+    scale = torch.empty(1, dtype=torch.float32, device="cuda")
+    ld = rows if transpose else cols
+    b.tc_quantize(dt, rows, cols, xt, cols, out, ld, int(transpose), scale)
+    return out, scale
+
+
+def _codes_to_values(dt, t):
+    if dt == 2:
+        return nm.e4m3_value(host(t))
+    return host(t.to(torch.float64))
+
+
+# ------------------------------------------------------------------ rounding
+
+@pytest.mark.parametrize("dt", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(64, 256), (37, 53), (1, 1), (130, 1000)])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_quantize_bit_exact(b, dt, shape, transpose):
+    X = synth.normal(shape, seed=synth.seed_for(1, 7)) * np.float32(30.0)
+    q, scale = _quant_dev(b, dt, X, transpose)
+    got = _codes_to_values(dt, q)
+    if transpose:
+        got = got.T
+    want, s = nm.quantize(X, DT_NAME[dt])
+    assert np.array_equal(got, want) and np.array_equal(np.signbit(got), np.signbit(want))
+    if dt == 2:
+        assert float(host(scale)[0]) == s
+
+
+def test_quantize_special_values(b):
+    X = np.float32([[0.0, -0.0, 65504.0, 65519.0, 65520.0, 1e30, -1e-30, 2.0 ** -25, 1.5 * 2.0 ** -25,
+                     1.0 + 2.0 ** -11, 1.0 + 3 * 2.0 ** -11, np.inf, -np.inf, 5.96e-8, 3.0e-5, 7.0]])
+    for dt in (0, 1):
+        q, _ = _quant_dev(b, dt, X)
+        got = _codes_to_values(dt, q)
+        want = nm.round_to(X, DT_NAME[dt])
+        assert np.array_equal(got, want) and np.array_equal(np.signbit(got), np.signbit(want))
+    # E4M3: scale from the largest finite magnitude (no infinities here)
+    Y = np.float32([[0.0, -0.0, 448.0, 1.0, -3.3, 1e-6, 2.0 ** -12, 0.017]])
+    q, scale = _quant_dev(b, 2, Y)
+    want, s = nm.quantize(Y, "e4m3")
+    assert np.array_equal(_codes_to_values(2, q), want) and float(host(scale)[0]) == s
+
+
+def test_quantize_e4m3_zero_matrix_scale_is_one(b):
+    q, scale = _quant_dev(b, 2, np.zeros((8, 16), np.float32))
+    assert float(host(scale)[0]) == 1.0 and not np.any(host(q))
+
+
+@pytest.mark.parametrize("piece", [0, 1])
+@pytest.mark.parametrize("shape,transpose", [((64, 128), False), ((33, 70), False), ((100, 48), True)])
+def test_split_bit_exact(b, piece, shape, transpose):
+    X = synth.log_uniform_pow2(shape, seed=synth.seed_for(3, 9))
+    rows, cols = shape
+    tdt = torch.float16 if piece == 0 else torch.bfloat16
+    oshape = (cols, rows) if transpose else (rows, cols)
+    hi = torch.empty(oshape, dtype=tdt, device="cuda")
+    lo = torch.empty(oshape, dtype=tdt, device="cuda")
+    b.tc_split(piece, rows, cols, dev(X), cols, int(transpose), hi, lo, oshape[1])
+    h, l = host(hi.to(torch.float64)), host(lo.to(torch.float64))
+    if transpose:
+        h, l = h.T, l.T
+    wh, wl = nm.split(X, DT_NAME[piece])
+    assert np.array_equal(h, wh) and np.array_equal(l, wl)
+
+
+# ------------------------------------------------------------------ mixed GEMM
+
+def _run_mixed(b, dt, A, B, alpha=1.0, beta=0.0, C0=None):
+    m, k = A.shape
+    n = B.shape[1]
+    aq, sa = _quant_dev(b, dt, A)
+    bq, sb = _quant_dev(b, dt, B, transpose=True)   # K-major copy of B (n x k)
+    C = dev(C0) if C0 is not None else torch.full((m, n), float("nan"), dtype=torch.float32, device="cuda")
+    b.gemm_mixed(dt, m, n, k, alpha, aq, k, 0, bq, k, 1, beta, C, n,
+                 sa if dt == 2 else None, sb if dt == 2 else None)
+    b.tc_sync_status()
+    return host(C)
+
+
+def _mag(dt, A, B, alpha, beta, C0):
+    Aq, sa = nm.quantize(A, DT_NAME[dt])
+    Bq, sb = nm.quantize(B, DT_NAME[dt])
+    mag = abs(alpha) * (np.abs(Aq) @ np.abs(Bq)) / (sa * sb)
+    if beta != 0.0:
+        mag = mag + abs(beta) * np.abs(C0.astype(np.float64))
+    return mag
+
+
+@pytest.mark.parametrize("dt", [0, 1, 2])
+@pytest.mark.parametrize("mnk", [(256, 256, 256), (128, 256, 64), (300, 520, 136), (1, 1, 8), (129, 257, 1000),
+                                 (640, 384, 2048)])
+def test_gemm_mixed_parity(b, dt, mnk):
+    m, n, k = mnk
+    if dt == 2 and k % 16:
+        k = (k + 15) // 16 * 16   # E4M3 rows must be 16-byte multiples
+    A = synth.uniform((m, k), seed=synth.seed_for(0, 0))
+    B = synth.uniform((k, n), seed=synth.seed_for(0, 1))
+    C = _run_mixed(b, dt, A, B)
+    ref = og.gemm_mixed(DT_NAME[dt], A, B)
+    ok, info = elementwise_ok(C, ref, _mag(dt, A, B, 1.0, 0.0, None), k)
+    assert ok, info
+    assert normwise_dev(C, ref, A, B) <= TOL_NORMWISE
+
+
+@pytest.mark.parametrize("dt", [0, 2])
+def test_gemm_mixed_alpha_beta(b, dt):
+    m, n, k = 200, 300, 512
+    A = synth.normal((m, k), seed=11)
+    B = synth.normal((k, n), seed=12)
+    C0 = synth.uniform((m, n), seed=13)
+    alpha, beta = 0.75, -1.5
+    C = _run_mixed(b, dt, A, B, alpha, beta, C0)
+    ref = og.gemm_mixed(DT_NAME[dt], A, B, alpha, beta, C0)
+    ok, info = elementwise_ok(C, ref, _mag(dt, A, B, alpha, beta, C0), k)
+    assert ok, info
+    assert normwise_dev(C, ref, A, B, alpha, beta, C0) <= TOL_NORMWISE
+
+
+def test_gemm_mixed_k_zero_scales_c(b):
+    C0 = synth.uniform((10, 12), seed=3)
+    C = dev(C0)
+    a = torch.zeros(16, dtype=torch.float16, device="cuda")
+    b.gemm_mixed(0, 10, 12, 0, 1.0, a, 8, 0, a, 8, 1, 0.5, C, 12)
+    assert np.array_equal(host(C), (0.5 * C0.astype(np.float64)).astype(np.float32))
+
+
+def test_gemm_mixed_rejects_mn_major(b):
+    a = torch.zeros(64, dtype=torch.float16, device="cuda")
+    c = torch.zeros(64, dtype=torch.float32, device="cuda")
+    with pytest.raises(b.TcError) as e:
+        b.gemm_mixed(0, 8, 8, 8, 1.0, a, 8, 0, a, 8, 0, 0.0, c, 8)
+    assert e.value.status == b.TC_ERR_UNSUPPORTED
+
+
+def test_gemm_mixed_is_deterministic(b):
+    A = synth.uniform((384, 1024), seed=21)
+    B = synth.uniform((1024, 512), seed=22)
+    c1 = _run_mixed(b, 0, A, B)
+    c2 = _run_mixed(b, 0, A, B)
+    assert np.array_equal(c1, c2)
+
+
+# ------------------------------------------------------------------ split GEMM (Eq. 1 / Eq. 2)
+
+@pytest.mark.parametrize("piece", [0, 1])
+@pytest.mark.parametrize("nprod", [2, 3, 4])
+@pytest.mark.parametrize("layouts", [(0, 0), (1, 1), (0, 1)])
+def test_gemm_split_parity(b, piece, nprod, layouts):
+    m, n, k = 192, 320, 264
+    la, lb = layouts
+    A = synth.log_uniform_pow2((m, k), seed=synth.seed_for(2, 0))
+    B = synth.log_uniform_pow2((k, n), seed=synth.seed_for(2, 1))
+    Ad = dev(A if la == 0 else np.ascontiguousarray(A.T))
+    Bd = dev(B if lb == 0 else np.ascontiguousarray(B.T))
+    C0 = synth.uniform((m, n), seed=5)
+    C = dev(C0)
+    alpha, beta = 1.0, 0.5
+    b.gemm_split(piece, nprod, m, n, k, alpha, Ad, k if la == 0 else m, la, Bd, n if lb == 0 else k, lb,
+                 beta, C, n)
+    b.tc_sync_status()
+    got = host(C)
+    ref = og.gemm_split(DT_NAME[piece], nprod, A, B, alpha, beta, C0)
+    Ah, Al = nm.split(A, DT_NAME[piece])
+    Bh, Bl = nm.split(B, DT_NAME[piece])
+    mag = (np.abs(Ah) + np.abs(Al)) @ (np.abs(Bh) + np.abs(Bl)) + beta * np.abs(C0.astype(np.float64))
+    ok, info = elementwise_ok(got, ref, mag, nprod * k)
+    assert ok, info
+    assert normwise_dev(got, ref, A, B, alpha, beta, C0) <= TOL_NORMWISE
+
+
+def test_gemm_split_with_caller_workspace(b):
+    m, n, k = 130, 70, 96
+    A = synth.uniform((m, k), seed=31)
+    B = synth.uniform((k, n), seed=32)
+    nbytes = b.gemm_split_workspace_bytes(0, 3, m, n, k)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    C = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    b.gemm_split(0, 3, m, n, k, 1.0, dev(A), k, 0, dev(B), n, 0, 0.0, C, n, ws, nbytes)
+    got = host(C)
+    ref = og.gemm_split("f16", 3, A, B)
+    assert normwise_dev(got, ref, A, B) <= TOL_NORMWISE
+
+
+def test_split_of_half_inputs_matches_mixed(b):
+    m, n, k = 128, 256, 192
+    A = nm.round_to(synth.uniform((m, k), seed=41), "f16").astype(np.float32)
+    B = nm.round_to(synth.uniform((k, n), seed=42), "f16").astype(np.float32)
+    C = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    b.gemm_split(0, 4, m, n, k, 1.0, dev(A), k, 0, dev(B), n, 0, 0.0, C, n)
+    mixed = _run_mixed(b, 0, A, B)
+    ref = og.gemm_mixed("f16", A, B)
+    assert normwise_dev(host(C), ref, A, B) <= TOL_NORMWISE
+    assert normwise_dev(mixed, ref, A, B) <= TOL_NORMWISE
+
+
+# ------------------------------------------------------------------ SIMT FP32 GEMM
+
+@pytest.mark.parametrize("layouts", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_sgemm_parity(b, layouts):
+    m, n, k = 150, 260, 200
+    la, lb = layouts
+    A = synth.normal((m, k), seed=51)
+    B = synth.normal((k, n), seed=52)
+    C0 = synth.uniform((m, n), seed=53)
+    C = dev(C0)
+    b.gemm_sgemm(m, n, k, 1.25, dev(A if la == 0 else A.T), k if la == 0 else m, la,
+                 dev(B if lb == 0 else B.T), n if lb == 0 else k, lb, 0.5, C, n)
+    got = host(C)
+    ref = og.gemm_truth(A, B, 1.25, 0.5, C0)
+    mag = 1.25 * (np.abs(A.astype(np.float64)) @ np.abs(B.astype(np.float64))) + 0.5 * np.abs(C0)
+    ok, info = elementwise_ok(got, ref, mag, k)
+    assert ok, info
+
+
+# ------------------------------------------------------------------ batched 16^3 (Listing 1's unit)
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("lb", [0, 1])
+@pytest.mark.parametrize("batch", [1, 31, 33, 1000])
+def test_batched16_parity(b, dt, lb, batch):
+    A = synth.uniform((batch, 16, 16), seed=61)
+    B = synth.uniform((batch, 16, 16), seed=62)
+    C0 = synth.uniform((batch, 16, 16), seed=63)
+    tdt = torch.float16 if dt == 0 else torch.bfloat16
+    Aq = dev(A, tdt)
+    Bq = dev(B if lb == 0 else np.ascontiguousarray(B.transpose(0, 2, 1)), tdt)
+    C = dev(C0)
+    b.gemm_batched_strided(dt, batch, 16, 16, 16, 1.0, Aq, 256, 0, Bq, 256, lb, 0.25, C, 256)
+    b.tc_sync_status()
+    got = host(C)
+    ref = og.gemm_batched(DT_NAME[dt], A, B, 1.0, 0.25, C0)
+    assert np.max(np.abs(got - ref)) <= 16 * 2.0 ** -22 * 16
+
+
+def test_batched16_padded_strides(b):
+    batch = 50
+    A = synth.uniform((batch, 16, 16), seed=64)
+    B = synth.uniform((batch, 16, 16), seed=65)
+    Ap = np.zeros((batch, 264), np.float32)
+    Bp = np.zeros((batch, 272), np.float32)
+    Ap[:, :256] = A.reshape(batch, 256)
+    Bp[:, :256] = B.reshape(batch, 256)
+    C = torch.zeros((batch, 260), dtype=torch.float32, device="cuda")
+    b.gemm_batched_strided(0, batch, 16, 16, 16, 1.0, dev(Ap, torch.float16), 264, 0, dev(Bp, torch.float16), 272, 0,
+                           0.0, C, 260)
+    got = host(C)[:, :256].reshape(batch, 16, 16)
+    ref = og.gemm_batched("f16", A, B)
+    assert np.max(np.abs(got - ref)) <= 16 * 2.0 ** -22 * 16
+    assert not np.any(host(C)[:, 256:])
+
+
+# ------------------------------------------------------------------ grouped GEMM
+
+def _grouped_case(count, seed, lb, ragged=False):
+    sizes = synth.group_sizes(count, seed)
+    if ragged:
+        sizes = sizes - (synth.words(sizes.size, seed=seed + 1).reshape(sizes.shape) % 9).astype(np.int64)
+        sizes[:, 2] = (sizes[:, 2] + 7) // 8 * 8 if False else sizes[:, 2]
+    rows, Ablocks, Bblocks = [], [], []
+    oa = ob = oc = 0
+    probs = []
+    for g, (m, n, k) in enumerate(sizes):
+        m, n, k = int(m), int(n), int(k)
+        lda = (k + 7) // 8 * 8
+        ldb = ((n if lb == 0 else k) + 7) // 8 * 8
+        A = synth.uniform((m, k), seed=1000 + g)
+        B = synth.uniform((k, n), seed=5000 + g)
+        probs.append((m, n, k, oa, ob, oc, lda, ldb, n, A, B))
+        oa += m * lda
+        ob += (k if lb == 0 else n) * ldb
+        oc += m * n
+    abuf = np.zeros(oa, np.float32)
+    bbuf = np.zeros(ob, np.float32)
+    for (m, n, k, a0, b0, c0, lda, ldb, ldc, A, B) in probs:
+        abuf[a0:a0 + m * lda].reshape(m, lda)[:, :k] = A
+        if lb == 0:
+            bbuf[b0:b0 + k * ldb].reshape(k, ldb)[:, :n] = B
+        else:
+            bbuf[b0:b0 + n * ldb].reshape(n, ldb)[:, :k] = B.T
+    return probs, abuf, bbuf, oc
+
+
+@pytest.mark.parametrize("lb", [0, 1])
+@pytest.mark.parametrize("count,ragged", [(1, False), (7, False), (300, False), (50, True)])
+def test_grouped_parity(b, lb, count, ragged):
+    probs, abuf, bbuf, csize = _grouped_case(count, seed=70 + count, lb=lb, ragged=ragged)
+    C = torch.zeros(csize, dtype=torch.float32, device="cuda")
+    desc = [p[:9] for p in probs]
+    b.gemm_grouped(0, desc, dev(abuf, torch.float16), 0, dev(bbuf, torch.float16), lb, C, 1.0, 0.0)
+    got = host(C)
+    for (m, n, k, a0, b0, c0, lda, ldb, ldc, A, B) in probs:
+        ref = og.gemm_mixed("f16", A, B)
+        g = got[c0:c0 + m * n].reshape(m, n)
+        mag = np.abs(nm.round_to(A, "f16")) @ np.abs(nm.round_to(B, "f16"))
+        ok, info = elementwise_ok(g, ref, mag, k)
+        assert ok, (m, n, k, info)
+
+
+def test_grouped_plan_graph_replay_and_beta(b):
+    probs, abuf, bbuf, csize = _grouped_case(40, seed=90, lb=0)
+    desc = [p[:9] for p in probs]
+    plan = b.gemm_grouped_plan_create(0, desc, 0, 0)
+    try:
+        Ad, Bd = dev(abuf, torch.float16), dev(bbuf, torch.float16)
+        C = torch.ones(csize, dtype=torch.float32, device="cuda")
+        for _ in range(3):   # C <- A B + 0.5 C, three replays of the same graph
+            b.gemm_grouped_plan_run(plan, Ad, Bd, C, 1.0, 0.5, use_graph=1)
+        got = host(C)
+    finally:
+        b.gemm_grouped_plan_destroy(plan)
+    for (m, n, k, a0, b0, c0, lda, ldb, ldc, A, B) in probs:
+        p = og.gemm_mixed("f16", A, B)
+        ref = p * (1 + 0.5 + 0.25) + 0.125
+        g = got[c0:c0 + m * n].reshape(m, n)
+        assert np.max(np.abs(g - ref)) <= 4 * k * 2.0 ** -22 * (np.max(np.abs(ref)) + 1)
+
+
+# ------------------------------------------------------------------ FP64 error reduction
+
+def test_error_norm_matches_oracle(b):
+    m, n, k = 333, 211, 97
+    C = synth.uniform((m, n), seed=81)
+    C64 = C.astype(np.float64) + synth.normal((m, n), seed=82).astype(np.float64) * 1e-3
+    A = synth.uniform((m, k), seed=83)
+    B = synth.uniform((k, n), seed=84)
+    out = b.tc_error_norm(m, n, dev(C), n, dev(C64), n, 1, dev(A), m, k, k, dev(B), k, n, n)
+    want = og.error_sums(C, C64, A, B)
+    for g, w in zip(out, want):
+        assert abs(g - w) <= 1e-12 * abs(w)
+    # the FP32-reference form (the paper's e = C_half - C_single)
+    out32 = b.tc_error_norm(m, n, dev(C), n, dev(C64.astype(np.float32)), n, 0)
+    want32 = og.error_sums(C, C64.astype(np.float32), np.zeros(1), np.zeros(1))
+    assert abs(out32[0] - want32[0]) <= 1e-12 * want32[0] and out32[3] == want32[3]
+    # deterministic
+    assert b.tc_error_norm(m, n, dev(C), n, dev(C64), n, 1, dev(A), m, k, k, dev(B), k, n, n) == out
