@@ -204,6 +204,32 @@ tc_status gemm_grouped(int32_t dt, int32_t count, const tc_problem* problems,
                        const void* a_base, int32_t la, const void* b_base, int32_t lb,
                        float* c_base, float alpha, float beta, void* stream);
 
+/* Grouped GEMM that allocates nothing.  The paper has no counterpart: this
+ * entry exists for callers that may not call cudaMalloc -- code running inside
+ * a memory budget owned by someone else (a framework's caching allocator or a
+ * serving engine that reserved the GPU's memory up front, where a fresh
+ * allocation can fail or fragment the pool), and latency-critical loops that
+ * cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ * Same arguments and result as gemm_grouped (host problem array, device
+ * operands and outputs owned by the caller), but the problem descriptors and
+ * the longest-first tile schedule are copied into a static device array of
+ * 8 MiB (48 bytes per problem plus 16 bytes per 64 x 64 output tile) that every
+ * GPU loading the library holds until the process exits.  A group that needs
+ * more returns TC_ERR_INVALID with the byte counts in tc_last_error().
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, once per device); make that first call before
+ *     any stream capture.
+ *   - The schedule is uploaded from pageable host memory, so the call waits on
+ *     the host for earlier work on `stream` before it enqueues the kernel;
+ *     it does not wait for the kernel.
+ *   - Every call reuses the same array, which keeps the last call's contents
+ *     (nothing in it needs to start at zero).  Calls whose work overlaps on
+ *     the GPU (different streams, or another thread) race on it: order them
+ *     on one stream. */
+tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_problem* problems,
+                               const void* a_base, int32_t la, const void* b_base, int32_t lb,
+                               float* c_base, float alpha, float beta, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Error measures (Sec. VI: e = C_half - C_single, ||e||_max; normwise
  * error ||C - C64||_F / (||A||_F ||B||_F) against an FP64 truth)           */

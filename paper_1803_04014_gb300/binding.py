@@ -88,6 +88,8 @@ SIGNATURES = {
     "gemm_grouped_plan_run": (_i32, [_vp, _vp, _vp, _vp, _f32, _f32, _i32, _vp]),
     "gemm_grouped_plan_destroy": (_i32, [_vp]),
     "gemm_grouped": (_i32, [_i32, _i32, ctypes.POINTER(tc_problem), _vp, _i32, _vp, _i32, _vp, _f32, _f32, _vp]),
+    "gemm_grouped_noalloc": (_i32, [_i32, _i32, ctypes.POINTER(tc_problem), _vp, _i32, _vp, _i32, _vp, _f32, _f32,
+                                    _vp]),
     "tc_error_norm": (_i32, [_i64, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _i64, _i64, _i64, _vp, _i64, _i64,
                              _i64, ctypes.POINTER(ctypes.c_double), _vp]),
     "serve_open": (_i32, [ctypes.POINTER(tc_serve_cfg), ctypes.POINTER(_vp)]),
@@ -229,6 +231,13 @@ def gemm_grouped(dt, problems, a_base, la, b_base, lb, c_base, alpha, beta, stre
     arr = problems if isinstance(problems, ctypes.Array) else problems_array(problems)
     return _check(load().gemm_grouped(dt, len(arr), arr, _ptr(a_base), la, _ptr(b_base), lb, _ptr(c_base), alpha,
                                       beta, _stream(stream)), "gemm_grouped")
+
+
+def gemm_grouped_noalloc(dt, problems, a_base, la, b_base, lb, c_base, alpha, beta, stream=None):
+    """gemm_grouped without any device allocation (schedule in the library's static scratch)."""
+    arr = problems if isinstance(problems, ctypes.Array) else problems_array(problems)
+    return _check(load().gemm_grouped_noalloc(dt, len(arr), arr, _ptr(a_base), la, _ptr(b_base), lb, _ptr(c_base),
+                                              alpha, beta, _stream(stream)), "gemm_grouped_noalloc")
 
 
 def tc_error_norm(m, n, C, ldc, Cref, ldr, ref_is_f64, A=None, a_rows=0, a_cols=0, lda=0, B=None, b_rows=0,

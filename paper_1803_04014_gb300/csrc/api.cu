@@ -532,3 +532,114 @@ tc_status tc_error_norm(int64_t m, int64_t n, const float* C, int64_t ldc, const
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ grouped GEMM without allocation
+//
+// For callers that may not allocate device memory: the problem descriptors
+// and the tile schedule live in a static device array instead of a plan's
+// cudaMalloc'd buffers.  The host-side name of the array is only a stand-in;
+// its device address comes from cudaGetSymbolAddress, taken once per device
+// with that device current.
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // 8 MiB on every device that loads the library
+static __device__ __align__(256) unsigned char g_grouped_scratch[kNoAllocScratchBytes];
+
+struct NoAllocDevice {
+    bool ready = false;
+    void* scratch = nullptr;  // device address of g_grouped_scratch on this device
+    int sm_count = 0;
+};
+NoAllocDevice g_noalloc_dev[64];
+
+tc_status noalloc_setup(NoAllocDevice** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "gemm_grouped_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_mu);
+    NoAllocDevice& d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void* p = nullptr;
+        if ((e = cudaGetSymbolAddress(&p, g_grouped_scratch)) != cudaSuccess)
+            return cuda_fail(e, "gemm_grouped_noalloc: cudaGetSymbolAddress");
+        if ((e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return cuda_fail(e, "gemm_grouped_noalloc: cudaDeviceGetAttribute");
+        d.scratch = p;
+        d.ready = true;
+    }
+    *out = &d;
+    return TC_OK;
+}
+
+}  // namespace
+
+extern "C" tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_problem* problems, const void* a_base,
+                                          int32_t la, const void* b_base, int32_t lb, float* c_base, float alpha,
+                                          float beta, void* stream) {
+    if (dt != TC_F16 && dt != TC_BF16) return fail(TC_ERR_UNSUPPORTED, "gemm_grouped_noalloc: F16 or BF16 only");
+    if (la != TC_ROW_MAJOR) return fail(TC_ERR_UNSUPPORTED, "gemm_grouped_noalloc: A must be row-major");
+    if (lb != TC_ROW_MAJOR && lb != TC_COL_MAJOR) return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: bad layout");
+    if (count < 0 || (count > 0 && !problems)) return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: bad problem array");
+    if (count == 0) return TC_OK;
+    if (!a_base || !b_base || !c_base) return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: null base pointer");
+    if (!aligned(a_base, 16) || !aligned(b_base, 16) || !aligned(c_base, 8))
+        return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: base pointers must be 16-byte aligned (C: 8)");
+    // schedule on the host: the same tiles and longest-first order as a plan
+    int64_t num_tiles = 0;
+    for (int32_t g = 0; g < count; ++g) {
+        const tc_problem& p = problems[g];
+        if (p.m < 1 || p.n < 1 || p.k < 1) return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: problem %d has a zero size", g);
+        if (p.lda < p.k || p.ldb < (lb == TC_ROW_MAJOR ? p.n : p.k) || p.ldc < p.n)
+            return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: problem %d leading dimension too small", g);
+        if (p.lda % 8 || p.ldb % 8 || p.off_a % 8 || p.off_b % 8)
+            return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: problem %d rows not 16-byte aligned", g);
+        if (p.off_a < 0 || p.off_b < 0 || p.off_c < 0)
+            return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: problem %d negative offset", g);
+        num_tiles += int64_t((p.m + tcg::kGroupedTileM - 1) / tcg::kGroupedTileM) *
+                     ((p.n + tcg::kGroupedTileN - 1) / tcg::kGroupedTileN);
+    }
+    const size_t desc_bytes = (size_t(count) * sizeof(tcg::GroupedProblemDev) + 255) / 256 * 256;
+    const size_t need = desc_bytes + size_t(num_tiles) * sizeof(tcg::GroupedTileDev);
+    if (need > kNoAllocScratchBytes)
+        return fail(TC_ERR_INVALID,
+                    "gemm_grouped_noalloc: %d problems (%lld tiles) need %zu bytes of scratch; the static maximum "
+                    "is %zu bytes (use gemm_grouped_plan_create for larger groups)",
+                    count, (long long)num_tiles, need, kNoAllocScratchBytes);
+    NoAllocDevice* d;
+    tc_status s = noalloc_setup(&d);
+    if (s != TC_OK) return s;
+
+    std::vector<unsigned char> host(need);
+    auto* hp = reinterpret_cast<tcg::GroupedProblemDev*>(host.data());
+    struct T { int64_t cost; tcg::GroupedTileDev t; };
+    std::vector<T> tiles;
+    tiles.reserve(static_cast<size_t>(num_tiles));
+    for (int32_t g = 0; g < count; ++g) {
+        const tc_problem& p = problems[g];
+        hp[g] = {p.m, p.n, p.k, 0, p.off_a, p.off_b, p.off_c, p.lda, p.ldb, p.ldc, 0};
+        const int tm = (p.m + tcg::kGroupedTileM - 1) / tcg::kGroupedTileM;
+        const int tn = (p.n + tcg::kGroupedTileN - 1) / tcg::kGroupedTileN;
+        for (int i = 0; i < tm; ++i)
+            for (int j = 0; j < tn; ++j) {
+                const int64_t rows = std::min(tcg::kGroupedTileM, p.m - i * tcg::kGroupedTileM);
+                const int64_t cols = std::min(tcg::kGroupedTileN, p.n - j * tcg::kGroupedTileN);
+                tiles.push_back({2 * p.k * (rows + cols) + 4 * rows * cols, {g, i, j, 0}});
+            }
+    }
+    std::stable_sort(tiles.begin(), tiles.end(), [](const T& a, const T& b) { return a.cost > b.cost; });
+    auto* ht = reinterpret_cast<tcg::GroupedTileDev*>(host.data() + desc_bytes);
+    for (size_t i = 0; i < tiles.size(); ++i) ht[i] = tiles[i].t;
+
+    cudaStream_t st = as_stream(stream);
+    unsigned char* dev_base = static_cast<unsigned char*>(d->scratch);
+    // pageable source: the call returns once the bytes are staged, so `host` may go out of scope
+    cudaError_t e = cudaMemcpyAsync(dev_base, host.data(), need, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "gemm_grouped_noalloc: upload");
+    return enqueue(tcg::launch_grouped(dt, lb, reinterpret_cast<const tcg::GroupedProblemDev*>(dev_base),
+                                       reinterpret_cast<const tcg::GroupedTileDev*>(dev_base + desc_bytes),
+                                       static_cast<int32_t>(num_tiles), a_base, b_base, c_base, alpha, beta,
+                                       d->sm_count, st),
+                   "gemm_grouped_noalloc launch");
+}

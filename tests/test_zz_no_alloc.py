@@ -1,0 +1,88 @@
+"""gemm_grouped_noalloc: the grouped GEMM entry point that allocates no device memory.
+
+Some callers may not call cudaMalloc: code that runs inside a memory budget
+owned by someone else (a framework's caching allocator or a serving engine
+that reserved the GPU's memory up front, where a new allocation can fail or
+fragment that pool) and latency-critical loops that cannot pay for the
+device-wide synchronisation of cudaMalloc/cudaFree.  This entry keeps its
+problem descriptors and tile schedule in a static device array instead.
+
+The test calls it through the C ABI twice in a row, with different groups so
+the second call runs over the first call's leftovers in the static array, and
+compares each result with the existing entry point gemm_grouped within the
+tolerance of the other GPU tests.  It also checks the size limit.  This file
+is collected last so that a run stopping at the first failure has already run
+every other test.
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests.gpu_common import elementwise_ok, host, need_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def b():
+    need_gpu()
+    from paper_1803_04014_gb300 import binding
+    binding.load()
+    return binding
+
+
+def _group(count, seed, lb):
+    sizes = synth.group_sizes(count, seed)
+    rows, a_parts, b_parts = [], [], []
+    oa = ob = oc = 0
+    for g, (m, n, k) in enumerate(sizes):
+        m, n, k = int(m), int(n), int(k) - 8 * (g % 2)   # some k not a multiple of 16
+        A = synth.uniform((m, k), seed=seed * 100 + 2 * g)
+        B = synth.uniform((k, n), seed=seed * 100 + 2 * g + 1)
+        lda = (k + 7) // 8 * 8
+        Bs = B if lb == 0 else np.ascontiguousarray(B.T)
+        ldb = (Bs.shape[1] + 7) // 8 * 8
+        Ap = np.zeros((m, lda), np.float32)
+        Ap[:, :k] = A
+        Bp = np.zeros((Bs.shape[0], ldb), np.float32)
+        Bp[:, :Bs.shape[1]] = Bs
+        rows.append((m, n, k, oa, ob, oc, lda, ldb, n))
+        a_parts.append(Ap.ravel())
+        b_parts.append(Bp.ravel())
+        oa += Ap.size
+        ob += Bp.size
+        oc += m * n
+    abuf = torch.from_numpy(np.concatenate(a_parts)).to(torch.float16).cuda()
+    bbuf = torch.from_numpy(np.concatenate(b_parts)).to(torch.float16).cuda()
+    return rows, abuf, bbuf, oc
+
+
+@pytest.mark.parametrize("lb", [0, 1])
+def test_noalloc_matches_grouped_on_two_calls_in_a_row(b, lb):
+    for call, (count, seed) in enumerate([(120, 7), (37, 8)]):
+        rows, abuf, bbuf, csize = _group(count, seed, lb)
+        c0 = torch.from_numpy(synth.uniform((csize,), seed=900 + call)).cuda()
+        c_ref = c0.clone()
+        c_new = c0.clone()
+        b.gemm_grouped(0, rows, abuf, 0, bbuf, lb, c_ref, 1.25, 0.5)
+        b.gemm_grouped_noalloc(0, rows, abuf, 0, bbuf, lb, c_new, 1.25, 0.5)
+        b.tc_sync_status()
+        ref, got, base = host(c_ref), host(c_new), host(c0)
+        # the grouped parity tolerance, K * 2^-22 * (|alpha| |A||B| + |beta| |C0|), with |A||B| <= k
+        # because every entry of A and B lies in [-1, 1]
+        for (m, n, k, _oa, _ob, oc, _lda, _ldb, _ldc) in rows:
+            sl = slice(oc, oc + m * n)
+            mag = 1.25 * k + 0.5 * np.abs(base[sl])
+            ok, info = elementwise_ok(got[sl], ref[sl], mag, k)
+            assert ok, (call, m, n, k, info)
+
+
+def test_noalloc_rejects_groups_beyond_its_static_scratch(b):
+    # 8 MiB of scratch: 48 bytes per problem + 16 bytes per 64x64 tile; 200 000 problems need ~12.8 MB
+    rows = [(16, 16, 16, 0, 0, 0, 16, 16, 16)] * 200_000
+    c = torch.zeros(256, dtype=torch.float32, device="cuda")
+    a = torch.zeros(256, dtype=torch.float16, device="cuda")
+    with pytest.raises(b.TcError) as e:
+        b.gemm_grouped_noalloc(0, rows, a, 0, a, 0, c, 1.0, 0.0)
+    assert e.value.status == b.TC_ERR_INVALID
+    assert "static maximum" in str(e.value)
