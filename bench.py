@@ -138,6 +138,8 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--rows", choices=["all", "none"], default="all", help="also measure the other rows (N=1 only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile-gemm", choices=["f16", "bf16", "e4m3", "split3"], default=None,
+                   help="only round the N=8192 inputs and run 5 GEMM launches (a small case for ncu captures)")
     return p.parse_args()
 
 
@@ -399,10 +401,41 @@ def measure_serve(b, count=2000, budget=40 << 30):
 
 # --------------------------------------------------------------------------- our arm
 
+def profile_case(kind):
+    """Five launches of one GEMM kernel at N=8192 (operands 128-512 MiB, above L2), nothing else timed."""
+    import torch
+    from paper_1803_04014_gb300 import binding as b
+    b.load()
+    A = torch.from_numpy(synth.uniform((N, N), seed=synth.seed_for(1, 0))).cuda()
+    B = torch.from_numpy(synth.uniform((N, N), seed=synth.seed_for(1, 1))).cuda()
+    C = torch.zeros((N, N), dtype=torch.float32, device="cuda")
+    if kind == "split3":
+        ws_bytes = b.gemm_split_workspace_bytes(0, 3, N, N, N)
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+        for _ in range(5):
+            b.gemm_split(0, 3, N, N, N, 1.0, A, N, 0, B, N, 0, 0.0, C, N, ws, ws_bytes)
+    else:
+        dt = {"f16": 0, "bf16": 1, "e4m3": 2}[kind]
+        tdt = {0: torch.float16, 1: torch.bfloat16, 2: torch.uint8}[dt]
+        Aq = torch.empty((N, N), dtype=tdt, device="cuda")
+        Bq = torch.empty((N, N), dtype=tdt, device="cuda")
+        sc = torch.empty(2, dtype=torch.float32, device="cuda")
+        b.tc_quantize(dt, N, N, A, N, Aq, N, 0, sc[0:1])
+        b.tc_quantize(dt, N, N, B, N, Bq, N, 1, sc[1:2])
+        for _ in range(5):
+            b.gemm_mixed(dt, N, N, N, 1.0, Aq, N, 0, Bq, N, 1, 0.5, C, N,
+                         sc[0:1] if dt == 2 else None, sc[1:2] if dt == 2 else None)
+    b.tc_sync_status()
+    print(json.dumps({"profile_case": kind, "n": N, "launches": 5}))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_gemm:
+        return profile_case(args.profile_gemm)
     rank, world, local = dist_env()
     import torch
     torch.cuda.set_device(local)

@@ -18,6 +18,9 @@ summation, which the pins bound.
   A_half B_half); 3 products drops R_A R_B.  All products are summed into one
   result, alpha multiplies the sum, beta*C0 is added once (reading of the
   paper's chained beta=0,1,1,1 pipeline, Sec. VI).
+* ``gemm_split_scaled`` -- the same refinement with residuals scaled by 2^s
+  before rounding (Ootomo and Yokota, 2022) and the correction products
+  summed apart and multiplied by 2^-s.
 * ``gemm_truth``  -- alpha*A*B + beta*C0 on the unrounded FP32 inputs.
 * ``gemm_grouped`` / ``gemm_batched`` -- Sec. IV-B: independent problems.
 * ``normwise_error`` / ``max_error`` -- ||C - C_ref||_F / (||A||_F ||B||_F)
@@ -89,6 +92,37 @@ def gemm_split(piece: str, nprod: int, A, B, alpha: float = 1.0, beta: float = 0
     acc = np.zeros((A.shape[0], B.shape[1]), dtype=np.float64)
     for pa, pb in PRODUCTS[nprod]:
         acc += Ap[pa] @ Bp[pb]
+    if C0 is not None and beta != 0.0:
+        C0 = _f64(C0)
+        if rows is not None:
+            C0 = C0[rows]
+        if cols is not None:
+            C0 = C0[:, cols]
+    return _epilogue(acc, alpha, beta, C0)
+
+
+def gemm_split_scaled(piece: str, nprod: int, A, B, alpha: float = 1.0, beta: float = 0.0, C0=None,
+                      rows=None, cols=None) -> np.ndarray:
+    """Refinement with scaled residuals (Ootomo and Yokota, 2022):
+
+    C = alpha * (A_hi B_hi + 2^-s (A_lo' B_hi [+ A_hi B_lo'])) + beta*C0,
+    lo' = round((x - hi) * 2^s); nprod = 2 keeps Eq. 1's product pair, nprod = 3
+    Eq. 2 without the residual-residual product (about 2^-2s of the result).
+    """
+    if nprod not in (2, 3):
+        raise ValueError("the scaled split takes nprod 2 or 3")
+    A = _f64(A)
+    B = _f64(B)
+    if rows is not None:
+        A = A[rows]
+    if cols is not None:
+        B = B[:, cols]
+    Ah, Al = numerics.split_scaled(A, piece)
+    Bh, Bl = numerics.split_scaled(B, piece)
+    corr = Al @ Bh
+    if nprod == 3:
+        corr = corr + Ah @ Bl
+    acc = Ah @ Bh + np.ldexp(corr, -numerics.SPLIT_SCALE_EXP[piece])
     if C0 is not None and beta != 0.0:
         C0 = _f64(C0)
         if rows is not None:

@@ -122,6 +122,28 @@ def split(x, piece: str):
     return hi, lo
 
 
+# Exponent of the residual scale of the scaled split: the residual of an
+# FP16 hi piece is at most 2^-11 |x|, of a BF16 hi piece 2^-8 |x|.
+SPLIT_SCALE_EXP = {"f16": 11, "bf16": 8}
+
+
+def split_scaled(x, piece: str):
+    """(hi, lo_s) with hi = round(x), lo_s = round((x - hi) * 2^s), s = SPLIT_SCALE_EXP[piece].
+
+    Scaled-residual split published by Ootomo and Yokota (2022, "Recovering
+    single precision accuracy from Tensor Cores while surpassing the FP32
+    theoretical peak performance"): the residual is multiplied by 2^s before
+    rounding so that it stays in the normal range of the 16-bit format; the
+    products that use it are multiplied by 2^-s afterwards.  The scaling by a
+    power of two is exact.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    hi = round_to(x, piece)
+    with np.errstate(invalid="ignore"):
+        lo = round_to(np.ldexp(x - hi, SPLIT_SCALE_EXP[piece]), piece)
+    return hi, lo
+
+
 # --- bit encodings (used to compare device outputs bit for bit) -------------
 
 def f16_bits(values) -> np.ndarray:

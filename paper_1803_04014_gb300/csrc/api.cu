@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -115,6 +116,26 @@ tc_status check_dims(int64_t m, int64_t n, int64_t k) {
 
 tc_status enqueue(cudaError_t e, const char* what) { return e == cudaSuccess ? TC_OK : cuda_fail(e, what); }
 
+// Tile choice of the tensor-core GEMM: 256 x 256 tiles on CTA pairs unless
+// the problem has at most 128 rows.  TCGEMM_TILE=single|pair forces one.
+bool use_pair_tiles(int64_t m) {
+    const char* env = getenv("TCGEMM_TILE");
+    if (env && strcmp(env, "single") == 0) return false;
+    if (env && strcmp(env, "pair") == 0) return true;
+    return m > 128;
+}
+
+// k-blocks of 64 between promotions of the refined GEMM's partial sums out of
+// TMEM into round-to-nearest FP32 registers.  TCGEMM_SPLIT_PROMOTE=0|1|2|4.
+int split_promote_kb() {
+    const char* env = getenv("TCGEMM_SPLIT_PROMOTE");
+    if (env) {
+        const int v = atoi(env);
+        if (v == 0 || v == 1 || v == 2 || v == 4) return v;
+    }
+    return 2;  // every 128 of K: below the FP32 CUDA-core GEMM's error at about 3 % of the time
+}
+
 }  // namespace
 
 extern "C" {
@@ -222,6 +243,7 @@ tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, c
     p.ab_format = dt == TC_BF16 ? 1 : 0;
     p.na = p.nb = p.nprod = 1;
     p.bn = 256;
+    p.pair = use_pair_tiles(m) ? 1 : 0;
     p.m = m; p.n = n; p.k = k;
     p.alpha = alpha; p.beta = beta;
     p.C = C; p.ldc = ldc;
@@ -230,7 +252,8 @@ tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, c
     p.sm_count = d->sm_count;
     CUtensorMap ta, tb;
     if ((s = encode_kmajor(&ta, tdt, esz, A, k, m, 1, lda * esz, m * lda * esz, 128)) != TC_OK) return s;
-    if ((s = encode_kmajor(&tb, tdt, esz, B, k, n, 1, ldb * esz, n * ldb * esz, p.bn)) != TC_OK) return s;
+    if ((s = encode_kmajor(&tb, tdt, esz, B, k, n, 1, ldb * esz, n * ldb * esz, p.pair ? 128 : p.bn)) != TC_OK)
+        return s;
     return enqueue(tcg::launch_tc_gemm(ta, tb, p, st), "gemm_mixed launch");
 }
 
@@ -299,6 +322,8 @@ tc_status gemm_split(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t
         p.nb = nprod == 2 ? 1 : 2;
         p.nprod = nprod;
         p.bn = nprod == 2 ? 256 : 128;
+        p.pair = use_pair_tiles(m) ? 1 : 0;
+        p.promote_kb = p.pair ? split_promote_kb() : 0;
         p.m = m; p.n = n; p.k = k;
         p.alpha = alpha; p.beta = beta;
         p.C = C; p.ldc = ldc;
@@ -306,7 +331,8 @@ tc_status gemm_split(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t
         p.sm_count = d->sm_count;
         CUtensorMap ta, tb;
         if ((out = encode_kmajor(&ta, tdt, 2, a_hi, k, m, 2, kp * 2, m * kp * 2, 128)) != TC_OK) break;
-        if ((out = encode_kmajor(&tb, tdt, 2, b_hi, k, n, p.nb, kp * 2, n * kp * 2, p.bn)) != TC_OK) break;
+        if ((out = encode_kmajor(&tb, tdt, 2, b_hi, k, n, p.nb, kp * 2, n * kp * 2, p.pair ? 128 : p.bn)) != TC_OK)
+            break;
         e = tcg::launch_tc_gemm(ta, tb, p, st);
         if (e != cudaSuccess) { out = cuda_fail(e, "gemm_split launch"); break; }
     } while (false);

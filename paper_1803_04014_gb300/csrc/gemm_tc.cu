@@ -293,16 +293,605 @@ template <int KIND, int BN, int STAGES, int NA, int NB, int NPROD>
 cudaError_t run(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args& args, int grid, cudaStream_t st) {
     using L = Layout<BN, STAGES, NA, NB>;
     auto kern = k_tc_gemm<KIND, BN, STAGES, NA, NB, NPROD>;
-    static bool configured = false;  // per instantiation; the attribute is per function and device-independent
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+    if (e != cudaSuccess) return e;
     kern<<<grid, kThreads, L::kBytes, st>>>(tmA, tmB, args);
     return cudaGetLastError();
 }
 
+
+// ====================================================================== CTA-pair kernel
+//
+// Same computation with 256 x 256 output tiles on a cluster of two CTAs that
+// share one tcgen05.mma.cta_group::2: each CTA loads 128 rows of A and 128
+// rows (its half of N) of B per k-block (32 KB instead of 48 KB per SM), the
+// even CTA issues the MMAs for both and every CTA keeps its 128 rows x 256
+// columns of the accumulator in its own TMEM.  Both CTAs' TMA loads complete
+// on the even CTA's "full" barrier; the MMA commits are multicast to the
+// "empty"/"accumulator full" barriers of both CTAs; both epilogues arrive on
+// the even CTA's "accumulator empty" barrier.
+
+template <int STAGES, int NA, int NB>
+struct PairLayout {
+    static constexpr int kHalfTile = 128 * kRowBytes;  // 128 rows x 128 bytes
+    static constexpr int kStageBytes = (NA + NB) * kHalfTile;
+    static constexpr int kBarOffset = STAGES * kStageBytes;
+    static constexpr int kNumBars = 2 * STAGES + 5;
+    static constexpr int kSlotOffset = kBarOffset + 8 * kNumBars;
+    static constexpr int kBytes = kSlotOffset + 16 + 1024;
+    static constexpr int kTmemCols = 512;  // two 256-column accumulators
+};
+
+__device__ __forceinline__ uint32_t cluster_id_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t num_clusters_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+
+template <int KIND, int STAGES, int NA, int NB, int NPROD>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc_gemm_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Args a) {
+    using L = PairLayout<STAGES, NA, NB>;
+    constexpr int kElemBytes = (KIND == 1) ? 1 : 2;
+    constexpr int BK = kRowBytes / kElemBytes;
+    constexpr int kSteps = 4;
+    constexpr int PM = 256, PN = 256;  // pair tile
+
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_addr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* base_ptr = smem_raw + (base - raw);
+    const uint32_t bars = base + L::kBarOffset;
+    auto full_bar = [&](int s) { return bars + 8u * s; };
+    auto empty_bar = [&](int s) { return bars + 8u * (STAGES + s); };
+    auto tfull_bar = [&](int i) { return bars + 8u * (2 * STAGES + i); };
+    auto tempty_bar = [&](int i) { return bars + 8u * (2 * STAGES + 2 + i); };
+    const uint32_t drain_bar = bars + 8u * (2 * STAGES + 4);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + L::kSlotOffset);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(base_ptr + L::kSlotOffset + 4);
+    const uint32_t abort_addr = base + L::kSlotOffset + 4;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const uint32_t peer_abort = mapa_shared(abort_addr, rank ^ 1u);
+    const int cid = static_cast<int>(cluster_id_x());
+    const int ncl = static_cast<int>(num_clusters_x());
+
+    // a failed wait stops this CTA and its peer
+    auto wait = [&](uint32_t bar, uint32_t parity) {
+        const bool ok = mbar_wait(bar, parity, abort_flag, a.status);
+        if (!ok) st_shared_cluster_u32(peer_abort, 1u);
+        return ok;
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(tfull_bar(i), 1);
+            mbar_init(tempty_bar(i), 8);  // four epilogue warps in each CTA
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(smem_addr(tmem_slot), L::kTmemCols);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    cluster_sync();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer (both CTAs): own half of A and B, completing on the even CTA's barrier
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued_phase[STAGES];
+#pragma unroll
+            for (int s = 0; s < STAGES; ++s) issued_phase[s] = -1;
+            bool ok = true;
+            for (int t = cid; ok && t < a.num_tiles; t += ncl) {
+                int mb, nb;
+                tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+                for (int kb = 0; kb < a.num_kb; ++kb) {
+                    if (!wait(empty_bar(stage), phase ^ 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sbase = base + stage * L::kStageBytes;
+                    const uint32_t leader_full = mapa_shared(full_bar(stage), 0);
+                    if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * L::kStageBytes);
+#pragma unroll
+                    for (int p = 0; p < NA; ++p)
+                        tma_load_3d_pair(sbase + p * L::kHalfTile, &tmA, leader_full, kb * BK,
+                                         mb * PM + static_cast<int>(rank) * 128, p);
+#pragma unroll
+                    for (int p = 0; p < NB; ++p)
+                        tma_load_3d_pair(sbase + (NA + p) * L::kHalfTile, &tmB, leader_full, kb * BK,
+                                         nb * PN + static_cast<int>(rank) * 128, p);
+                    issued_phase[stage] = static_cast<int>(phase);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                if (rank == 0) {
+                    for (int s = 0; s < STAGES; ++s)
+                        if (issued_phase[s] >= 0)
+                            mbar_wait_bounded(full_bar(s), static_cast<uint32_t>(issued_phase[s]), 100000000ull);
+                } else {
+                    // the peer cannot observe its copies (they complete on the even CTA): give them time to land
+                    const uint64_t t0 = global_timer_ns();
+                    while (global_timer_ns() - t0 < 2000000ull) __nanosleep(1000);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            // ---------------- MMA issuer (even CTA only)
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true;
+            bool issued_any = false;
+            for (int t = cid; ok && t < a.num_tiles; t += ncl) {
+                if (!wait(tempty_bar(acc), acc_phase ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * PN);
+                for (int kb = 0; kb < a.num_kb; ++kb) {
+                    if (!wait(full_bar(stage), phase)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sbase = base + stage * L::kStageBytes;
+#pragma unroll
+                    for (int ks = 0; ks < kSteps; ++ks) {
+#pragma unroll
+                        for (int p = 0; p < NPROD; ++p) {
+                            const uint32_t a_addr = sbase + prod_a(p) * L::kHalfTile + ks * 32;
+                            const uint32_t b_addr = sbase + (NA + prod_b(p)) * L::kHalfTile + ks * 32;
+                            const uint32_t accumulate = (kb | ks | p) != 0 ? 1u : 0u;
+                            if constexpr (KIND == 1)
+                                mma_pair_f8(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), a.idesc,
+                                            accumulate);
+                            else
+                                mma_pair_f16(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), a.idesc,
+                                             accumulate);
+                        }
+                    }
+                    issued_any = true;
+                    mma_commit_pair_mc(empty_bar(stage), 0x3);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit_pair_mc(tfull_bar(acc), 0x3);
+                acc ^= 1;
+                if (acc == 0) acc_phase ^= 1u;
+            }
+            if (!ok && issued_any) {
+                mma_commit_pair_mc(drain_bar, 0x1);
+                mbar_wait_bounded(drain_bar, 0, 100000000ull);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 2..5 of both CTAs): this CTA's 128 rows of the pair tile
+        const int quarter = warp & 3;
+        float alpha = a.alpha;
+        if constexpr (KIND == 1) alpha = alpha * (1.0f / *a.scale_a) * (1.0f / *a.scale_b);
+        const float beta = a.beta;
+        const bool vec_ok = ((a.ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15u) == 0);
+        const uint32_t leader_tempty0 = mapa_shared(tempty_bar(0), 0);
+        const uint32_t leader_tempty1 = mapa_shared(tempty_bar(1), 0);
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int t = cid; t < a.num_tiles; t += ncl) {
+            int mb, nb;
+            tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+            const bool ok = wait(tfull_bar(acc), acc_phase);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const int row = mb * PM + static_cast<int>(rank) * 128 + quarter * 32 + lane;
+            const int col0 = nb * PN;
+            const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                                   static_cast<uint32_t>(acc * PN);
+            float* crow = a.C + static_cast<int64_t>(row) * a.ldc + col0;
+#pragma unroll 1
+            for (int c = 0; c < PN; c += 32) {
+                if (col0 + c >= a.n) break;
+                float v[32];
+                tmem_load_32(taddr + c, v);
+                if (row < a.m) {
+                    const int ncols = min(32, a.n - (col0 + c));
+                    float* p = crow + c;
+                    if (ncols == 32 && vec_ok) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            float4 o;
+                            if (beta != 0.0f) {
+                                const float4 old = *reinterpret_cast<const float4*>(p + 4 * j);
+                                o.x = fmaf(alpha, v[4 * j + 0], beta * old.x);
+                                o.y = fmaf(alpha, v[4 * j + 1], beta * old.y);
+                                o.z = fmaf(alpha, v[4 * j + 2], beta * old.z);
+                                o.w = fmaf(alpha, v[4 * j + 3], beta * old.w);
+                            } else {
+                                o.x = alpha * v[4 * j + 0];
+                                o.y = alpha * v[4 * j + 1];
+                                o.z = alpha * v[4 * j + 2];
+                                o.w = alpha * v[4 * j + 3];
+                            }
+                            *reinterpret_cast<float4*>(p + 4 * j) = o;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if (j < ncols) p[j] = (beta != 0.0f) ? fmaf(alpha, v[j], beta * p[j]) : alpha * v[j];
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(acc == 0 ? leader_tempty0 : leader_tempty1);
+            acc ^= 1;
+            if (acc == 0) acc_phase ^= 1u;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // neither CTA leaves while the other may still touch its shared memory or TMEM
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, L::kTmemCols);
+    }
+}
+
+template <int KIND, int STAGES, int NA, int NB, int NPROD>
+cudaError_t run_pair(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args& args, int clusters,
+                     cudaStream_t st) {
+    if (clusters <= 0) return cudaSuccess;
+    using L = PairLayout<STAGES, NA, NB>;
+    auto kern = k_tc_gemm_pair<KIND, STAGES, NA, NB, NPROD>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = L::kBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // no more clusters than can be resident at once (persistent tiles)
+    int resident = 0;
+    if (cudaOccupancyMaxActiveClusters(&resident, kern, &cfg) == cudaSuccess && resident > 0 && clusters > resident) {
+        clusters = resident;
+        cfg.gridDim = dim3(2 * clusters, 1, 1);
+    }
+    return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, args);
+}
+
+// ====================================================================== CTA-pair kernel with promotion
+//
+// For the refined (split) products: the tensor cores' internal FP32
+// accumulation loses accuracy as K grows (its error grows like sqrt(K) where a
+// round-to-nearest FP32 sum's does not), which would waste the precision the
+// residual products win back.  This variant restarts the TMEM accumulator
+// every CHUNK_KB k-blocks and lets the epilogue warps add each chunk's partial
+// sums into FP32 registers with round-to-nearest ("promotion" of the partial
+// sums out of the tensor core).  Chunk accumulators are double-buffered in
+// TMEM (2 x 256 columns) so the MMAs of chunk c+1 overlap the draining of
+// chunk c.  Eight epilogue warps: warp w drains TMEM lanes 32*(w%4).. and
+// columns [128*((w-2)/4), +128) into 128 registers per thread.
+
+constexpr int kPromoteThreads = 320;  // TMA warp, MMA warp, 8 epilogue warps
+
+template <int KIND, int STAGES, int NA, int NB, int NPROD, int CHUNK_KB>
+__global__ void __launch_bounds__(kPromoteThreads, 1)
+    k_tc_gemm_pair_promote(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                           const Args a) {
+    using L = PairLayout<STAGES, NA, NB>;
+    constexpr int kElemBytes = (KIND == 1) ? 1 : 2;
+    constexpr int BK = kRowBytes / kElemBytes;
+    constexpr int kSteps = 4;
+    constexpr int PM = 256, PN = 256;
+
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_addr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* base_ptr = smem_raw + (base - raw);
+    const uint32_t bars = base + L::kBarOffset;
+    auto full_bar = [&](int s) { return bars + 8u * s; };
+    auto empty_bar = [&](int s) { return bars + 8u * (STAGES + s); };
+    auto cfull_bar = [&](int i) { return bars + 8u * (2 * STAGES + i); };   // chunk accumulator ready
+    auto cempty_bar = [&](int i) { return bars + 8u * (2 * STAGES + 2 + i); };  // chunk accumulator drained
+    const uint32_t drain_bar = bars + 8u * (2 * STAGES + 4);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + L::kSlotOffset);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(base_ptr + L::kSlotOffset + 4);
+    const uint32_t abort_addr = base + L::kSlotOffset + 4;
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const uint32_t peer_abort = mapa_shared(abort_addr, rank ^ 1u);
+    const int cid = static_cast<int>(cluster_id_x());
+    const int ncl = static_cast<int>(num_clusters_x());
+    const int nchunks = (a.num_kb + CHUNK_KB - 1) / CHUNK_KB;
+
+    auto wait = [&](uint32_t bar, uint32_t parity) {
+        const bool ok = mbar_wait(bar, parity, abort_flag, a.status);
+        if (!ok) st_shared_cluster_u32(peer_abort, 1u);
+        return ok;
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(cfull_bar(i), 1);
+            mbar_init(cempty_bar(i), 16);  // eight epilogue warps in each CTA
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+        prefetch_tmap(&tmA);
+        prefetch_tmap(&tmB);
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(smem_addr(tmem_slot), L::kTmemCols);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    cluster_sync();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued_phase[STAGES];
+#pragma unroll
+            for (int s = 0; s < STAGES; ++s) issued_phase[s] = -1;
+            bool ok = true;
+            for (int t = cid; ok && t < a.num_tiles; t += ncl) {
+                int mb, nb;
+                tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+                for (int kb = 0; kb < a.num_kb; ++kb) {
+                    if (!wait(empty_bar(stage), phase ^ 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sbase = base + stage * L::kStageBytes;
+                    const uint32_t leader_full = mapa_shared(full_bar(stage), 0);
+                    if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * L::kStageBytes);
+#pragma unroll
+                    for (int p = 0; p < NA; ++p)
+                        tma_load_3d_pair(sbase + p * L::kHalfTile, &tmA, leader_full, kb * BK,
+                                         mb * PM + static_cast<int>(rank) * 128, p);
+#pragma unroll
+                    for (int p = 0; p < NB; ++p)
+                        tma_load_3d_pair(sbase + (NA + p) * L::kHalfTile, &tmB, leader_full, kb * BK,
+                                         nb * PN + static_cast<int>(rank) * 128, p);
+                    issued_phase[stage] = static_cast<int>(phase);
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                if (rank == 0) {
+                    for (int s = 0; s < STAGES; ++s)
+                        if (issued_phase[s] >= 0)
+                            mbar_wait_bounded(full_bar(s), static_cast<uint32_t>(issued_phase[s]), 100000000ull);
+                } else {
+                    const uint64_t t0 = global_timer_ns();
+                    while (global_timer_ns() - t0 < 2000000ull) __nanosleep(1000);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int buf = 0;
+            uint32_t buf_phase = 0;
+            bool ok = true;
+            bool issued_any = false;
+            for (int t = cid; ok && t < a.num_tiles; t += ncl) {
+                for (int c = 0; ok && c < nchunks; ++c) {
+                    if (!wait(cempty_bar(buf), buf_phase ^ 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(buf * PN);
+                    const int kb_end = min(a.num_kb, (c + 1) * CHUNK_KB);
+                    for (int kb = c * CHUNK_KB; kb < kb_end; ++kb) {
+                        if (!wait(full_bar(stage), phase)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sbase = base + stage * L::kStageBytes;
+#pragma unroll
+                        for (int ks = 0; ks < kSteps; ++ks) {
+#pragma unroll
+                            for (int p = 0; p < NPROD; ++p) {
+                                const uint32_t a_addr = sbase + prod_a(p) * L::kHalfTile + ks * 32;
+                                const uint32_t b_addr = sbase + (NA + prod_b(p)) * L::kHalfTile + ks * 32;
+                                const uint32_t accumulate = (kb != c * CHUNK_KB || ks != 0 || p != 0) ? 1u : 0u;
+                                if constexpr (KIND == 1)
+                                    mma_pair_f8(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), a.idesc,
+                                                accumulate);
+                                else
+                                    mma_pair_f16(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr),
+                                                 a.idesc, accumulate);
+                            }
+                        }
+                        issued_any = true;
+                        mma_commit_pair_mc(empty_bar(stage), 0x3);
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                    if (!ok) break;
+                    mma_commit_pair_mc(cfull_bar(buf), 0x3);
+                    buf ^= 1;
+                    if (buf == 0) buf_phase ^= 1u;
+                }
+            }
+            if (!ok && issued_any) {
+                mma_commit_pair_mc(drain_bar, 0x1);
+                mbar_wait_bounded(drain_bar, 0, 100000000ull);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: drain every chunk into FP32 registers, store at the end of the tile
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;  // columns [128*half, 128*half + 128)
+        float alpha = a.alpha;
+        if constexpr (KIND == 1) alpha = alpha * (1.0f / *a.scale_a) * (1.0f / *a.scale_b);
+        const float beta = a.beta;
+        const bool vec_ok = ((a.ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15u) == 0);
+        const uint32_t leader_cempty0 = mapa_shared(cempty_bar(0), 0);
+        const uint32_t leader_cempty1 = mapa_shared(cempty_bar(1), 0);
+        int buf = 0;
+        uint32_t buf_phase = 0;
+        bool ok = true;
+        for (int t = cid; ok && t < a.num_tiles; t += ncl) {
+            int mb, nb;
+            tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+            const int row = mb * PM + static_cast<int>(rank) * 128 + quarter * 32 + lane;
+            const int col0 = nb * PN + half * 128;
+            float acc[128];
+#pragma unroll
+            for (int j = 0; j < 128; ++j) acc[j] = 0.0f;
+            for (int c = 0; c < nchunks; ++c) {
+                const bool w = wait(cfull_bar(buf), buf_phase);
+                if (!__all_sync(0xffffffffu, w)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                                       static_cast<uint32_t>(buf * PN + half * 128);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float v[32];
+                    tmem_load_32(taddr + q * 32, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) acc[q * 32 + j] += v[j];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(buf == 0 ? leader_cempty0 : leader_cempty1);
+                buf ^= 1;
+                if (buf == 0) buf_phase ^= 1u;
+            }
+            if (!ok) break;
+            if (row < a.m && col0 < a.n) {
+                float* p = a.C + static_cast<int64_t>(row) * a.ldc + col0;
+                const int ncols = min(128, a.n - col0);
+                if (ncols == 128 && vec_ok) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        float4 o;
+                        if (beta != 0.0f) {
+                            const float4 old = *reinterpret_cast<const float4*>(p + 4 * j);
+                            o.x = fmaf(alpha, acc[4 * j + 0], beta * old.x);
+                            o.y = fmaf(alpha, acc[4 * j + 1], beta * old.y);
+                            o.z = fmaf(alpha, acc[4 * j + 2], beta * old.z);
+                            o.w = fmaf(alpha, acc[4 * j + 3], beta * old.w);
+                        } else {
+                            o.x = alpha * acc[4 * j + 0];
+                            o.y = alpha * acc[4 * j + 1];
+                            o.z = alpha * acc[4 * j + 2];
+                            o.w = alpha * acc[4 * j + 3];
+                        }
+                        *reinterpret_cast<float4*>(p + 4 * j) = o;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 128; ++j) {
+                        if (j < ncols) p[j] = (beta != 0.0f) ? fmaf(alpha, acc[j], beta * p[j]) : alpha * acc[j];
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem_base, L::kTmemCols);
+    }
+}
+
+template <int KIND, int STAGES, int NA, int NB, int NPROD, int CHUNK_KB>
+cudaError_t run_pair_promote(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args& args, int clusters,
+                             cudaStream_t st) {
+    if (clusters <= 0) return cudaSuccess;
+    using L = PairLayout<STAGES, NA, NB>;
+    auto kern = k_tc_gemm_pair_promote<KIND, STAGES, NA, NB, NPROD, CHUNK_KB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters, 1, 1);
+    cfg.blockDim = dim3(kPromoteThreads, 1, 1);
+    cfg.dynamicSmemBytes = L::kBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int resident = 0;
+    if (cudaOccupancyMaxActiveClusters(&resident, kern, &cfg) == cudaSuccess && resident > 0 && clusters > resident) {
+        clusters = resident;
+        cfg.gridDim = dim3(2 * clusters, 1, 1);
+    }
+    return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, args);
+}
 }  // namespace
 
 size_t tc_gemm_smem_bytes(int na, int nb, int bn, int* stages_out) {
@@ -331,6 +920,44 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     a.scale_b = p.scale_b;
     a.status = p.status;
     a.idesc = make_idesc(BM, p.bn, static_cast<uint32_t>(p.ab_format));
+    if (p.pair) {
+        // 256 x 256 tiles on CTA pairs
+        a.tiles_m = static_cast<int>((p.m + 255) / 256);
+        a.tiles_n = static_cast<int>((p.n + 255) / 256);
+        a.num_tiles = a.tiles_m * a.tiles_n;
+        a.idesc = make_idesc(256, 256, static_cast<uint32_t>(p.ab_format));
+        const int max_clusters = p.sm_count / 2;
+        const int clusters = a.num_tiles < max_clusters ? a.num_tiles : max_clusters;
+        if (clusters <= 0) return cudaSuccess;
+        if (p.kind == 1) {
+            if (p.na == 1 && p.nb == 1) return run_pair<1, 6, 1, 1, 1>(tmA, tmB, a, clusters, st);
+            return cudaErrorInvalidValue;
+        }
+        if (p.promote_kb > 0) {
+            // split products with promoted partial sums
+            if (p.na == 2 && p.nb == 1 && p.nprod == 2) {
+                if (p.promote_kb == 1) return run_pair_promote<0, 4, 2, 1, 2, 1>(tmA, tmB, a, clusters, st);
+                if (p.promote_kb == 2) return run_pair_promote<0, 4, 2, 1, 2, 2>(tmA, tmB, a, clusters, st);
+                return run_pair_promote<0, 4, 2, 1, 2, 4>(tmA, tmB, a, clusters, st);
+            }
+            if (p.na == 2 && p.nb == 2 && p.nprod == 3) {
+                if (p.promote_kb == 1) return run_pair_promote<0, 3, 2, 2, 3, 1>(tmA, tmB, a, clusters, st);
+                if (p.promote_kb == 2) return run_pair_promote<0, 3, 2, 2, 3, 2>(tmA, tmB, a, clusters, st);
+                return run_pair_promote<0, 3, 2, 2, 3, 4>(tmA, tmB, a, clusters, st);
+            }
+            if (p.na == 2 && p.nb == 2 && p.nprod == 4) {
+                if (p.promote_kb == 1) return run_pair_promote<0, 3, 2, 2, 4, 1>(tmA, tmB, a, clusters, st);
+                if (p.promote_kb == 2) return run_pair_promote<0, 3, 2, 2, 4, 2>(tmA, tmB, a, clusters, st);
+                return run_pair_promote<0, 3, 2, 2, 4, 4>(tmA, tmB, a, clusters, st);
+            }
+            return cudaErrorInvalidValue;
+        }
+        if (p.na == 1 && p.nb == 1) return run_pair<0, 6, 1, 1, 1>(tmA, tmB, a, clusters, st);
+        if (p.na == 2 && p.nb == 1 && p.nprod == 2) return run_pair<0, 4, 2, 1, 2>(tmA, tmB, a, clusters, st);
+        if (p.na == 2 && p.nb == 2 && p.nprod == 3) return run_pair<0, 3, 2, 2, 3>(tmA, tmB, a, clusters, st);
+        if (p.na == 2 && p.nb == 2 && p.nprod == 4) return run_pair<0, 3, 2, 2, 4>(tmA, tmB, a, clusters, st);
+        return cudaErrorInvalidValue;
+    }
     const int grid = a.num_tiles < p.sm_count ? a.num_tiles : p.sm_count;
     if (grid <= 0) return cudaSuccess;
 

@@ -31,7 +31,10 @@ struct TcGemmLaunch {
     const float* scale_b;
     int* status;
     int sm_count;
-    int bn;             // tile width (128 or 256)
+    int bn;             // tile width of the single-CTA kernel (128 or 256)
+    int pair;           // 1: 256 x 256 tiles on CTA pairs (B box of 128 rows per CTA)
+    int promote_kb;     // pair kernel only: >0 adds the partial sums of every promote_kb k-blocks
+                        // into FP32 registers with round-to-nearest (1, 2 or 4); 0 keeps them in TMEM
 };
 // tmA: 3-D map {k, m, na} with a 128 x (128 bytes) box; tmB: {k, n, nb} with a bn x (128 bytes) box.
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmLaunch& p, cudaStream_t st);

@@ -368,3 +368,67 @@ def test_error_norm_matches_oracle(b):
     assert abs(out32[0] - want32[0]) <= 1e-12 * want32[0] and out32[3] == want32[3]
     # deterministic
     assert b.tc_error_norm(m, n, dev(C), n, dev(C64), n, 1, dev(A), m, k, k, dev(B), k, n, n) == out
+
+
+# ------------------------------------------------------------------ both tile kernels (single CTA / CTA pair)
+
+@pytest.mark.parametrize("tile", ["single", "pair"])
+@pytest.mark.parametrize("dt", [0, 1, 2])
+@pytest.mark.parametrize("mnk", [(64, 300, 96), (384, 640, 512), (1000, 260, 2048)])
+def test_gemm_tile_kernels(b, monkeypatch, tile, dt, mnk):
+    monkeypatch.setenv("TCGEMM_TILE", tile)
+    m, n, k = mnk
+    A = synth.uniform((m, k), seed=101)
+    B = synth.uniform((k, n), seed=102)
+    C0 = synth.uniform((m, n), seed=103)
+    C = _run_mixed(b, dt, A, B, 1.0, 0.5, C0)
+    ref = og.gemm_mixed(DT_NAME[dt], A, B, 1.0, 0.5, C0)
+    ok, info = elementwise_ok(C, ref, _mag(dt, A, B, 1.0, 0.5, C0), k)
+    assert ok, info
+    assert normwise_dev(C, ref, A, B, 1.0, 0.5, C0) <= TOL_NORMWISE
+
+
+@pytest.mark.parametrize("tile", ["single", "pair"])
+@pytest.mark.parametrize("nprod", [2, 3, 4])
+def test_split_tile_kernels(b, monkeypatch, tile, nprod):
+    monkeypatch.setenv("TCGEMM_TILE", tile)
+    m, n, k = 520, 264, 300
+    A = synth.log_uniform_pow2((m, k), seed=111)
+    B = synth.log_uniform_pow2((k, n), seed=112)
+    C = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    b.gemm_split(0, nprod, m, n, k, 1.0, dev(A), k, 0, dev(B), n, 0, 0.0, C, n)
+    b.tc_sync_status()
+    ref = og.gemm_split("f16", nprod, A, B)
+    assert normwise_dev(host(C), ref, A, B) <= TOL_NORMWISE
+
+
+# ------------------------------------------------------------------ accuracy gate of the refinement
+
+@pytest.mark.parametrize("K", [1024, 4096])
+def test_split3_error_within_2x_of_fp32_cuda_core_gemm(b, K):
+    # inputs with full 24-bit significands over 16 binades; error vs the FP64 truth
+    M = N = 256
+    A = synth.log_uniform_pow2((M, K), seed=synth.seed_for(2, 0))
+    B = synth.log_uniform_pow2((K, N), seed=synth.seed_for(2, 1))
+    truth = og.gemm_truth(A, B)
+    Ad, Bd = dev(A), dev(B)
+    C = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    b.gemm_split(0, 3, M, N, K, 1.0, Ad, K, 0, Bd, N, 0, 0.0, C, N)
+    e_split = og.normwise_error(host(C), truth, A, B)
+    b.gemm_sgemm(M, N, K, 1.0, Ad, K, 0, Bd, N, 0, 0.0, C, N)
+    e_fp32 = og.normwise_error(host(C), truth, A, B)
+    assert e_split <= 2.0 * e_fp32, (e_split, e_fp32)
+
+
+@pytest.mark.parametrize("promote", ["0", "1", "2", "4"])
+def test_split_promotion_settings_match_oracle(b, monkeypatch, promote):
+    monkeypatch.setenv("TCGEMM_SPLIT_PROMOTE", promote)
+    m, n, k = 384, 512, 1000
+    A = synth.log_uniform_pow2((m, k), seed=121)
+    B = synth.log_uniform_pow2((k, n), seed=122)
+    C0 = synth.uniform((m, n), seed=123)
+    C = dev(C0)
+    b.gemm_split(0, 3, m, n, k, 1.5, dev(A), k, 0, dev(B), n, 0, -0.25, C, n)
+    b.tc_sync_status()
+    ref = og.gemm_split("f16", 3, A, B, 1.5, -0.25, C0)
+    assert normwise_dev(host(C), ref, A, B, 1.5, -0.25, C0) <= TOL_NORMWISE

@@ -234,3 +234,38 @@ def test_error_norm_closed_forms():
     assert abs(og.normwise_error(C, C_ref, A, B) - want) < 1e-16
     s = og.error_sums(C, C_ref, A, B)
     assert s == (0.3125, 48.0, 180.0, 0.5)
+
+
+def test_scaled_split_recovers_where_plain_split_cannot():
+    # inputs with 22 significant bits over exponents -8..7: the scaled pieces hold them exactly,
+    # so Eq. 2 without R_A R_B differs from the FP32 product only by that dropped term
+    def m22(shape, seed):
+        n = int(np.prod(shape))
+        ints = (synth.words(n, seed=seed) & np.uint32((1 << 22) - 1)).astype(np.float64) + float(1 << 21)
+        e = (synth.words(n, seed=seed + 1) % 16).astype(np.float64) - 8.0
+        sgn = np.where(synth.words(n, seed=seed + 2) & np.uint32(1), -1.0, 1.0)
+        return (sgn * ints * 2.0 ** (e - 21)).astype(np.float32).reshape(shape)
+    A = m22((20, 96), 60)
+    B = m22((96, 12), 63)
+    truth = og.gemm_truth(A, B)
+    Ah, Al = nm.split_scaled(A, "f16")
+    Bh, Bl = nm.split_scaled(B, "f16")
+    want = truth - np.ldexp(Al @ Bl, -22)
+    got = og.gemm_split_scaled("f16", 3, A, B)
+    assert np.allclose(got, want, rtol=0, atol=96 * 2.0 ** -52 * np.max(np.abs(truth)))
+    plain = og.gemm_split("f16", 3, A, B)
+    assert og.normwise_error(plain, truth, A, B) > 10 * og.normwise_error(got, truth, A, B)
+    # nprod = 2 is Eq. 1: A_single B_half
+    got2 = og.gemm_split_scaled("f16", 2, A, B)
+    assert np.allclose(got2, A.astype(np.float64) @ Bh, rtol=0, atol=96 * 2.0 ** -50 * np.max(np.abs(truth)))
+
+
+def test_scaled_split_beta_alpha():
+    A = synth.uniform((8, 32), seed=70)
+    B = synth.uniform((32, 8), seed=71)
+    C0 = synth.uniform((8, 8), seed=72)
+    a = og.gemm_split_scaled("bf16", 3, A, B, alpha=2.0)
+    b_ = og.gemm_split_scaled("bf16", 3, A, B, alpha=2.0, beta=-1.0, C0=C0)
+    assert np.allclose(b_ - a, -C0.astype(np.float64), rtol=0, atol=1e-14)
+    with pytest.raises(ValueError):
+        og.gemm_split_scaled("f16", 4, A, B)

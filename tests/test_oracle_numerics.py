@@ -203,3 +203,31 @@ def test_rounding_is_ties_to_even_not_away():
     assert nm.round_to(np.float32(1.0 + 2.0 ** -8), "bf16") == 1.0
     assert nm.round_to(np.float32(1.0 + 2.0 ** -4), "e4m3") == 1.0
     assert nm.round_to(np.float32(1.0 + 3 * 2.0 ** -4), "e4m3") == 1.25
+
+
+# ---- scaled residual split (Ootomo and Yokota, 2022) ---------------------------
+
+def test_scaled_split_keeps_small_residuals():
+    # x with 22 significant bits and |x| ~ 2^-9: the plain FP16 residual is subnormal and
+    # loses bits, the scaled one (x 2^11) is normal and exact
+    ints = (synth.words(5000, seed=15) & np.uint32((1 << 22) - 1)).astype(np.float64) + float(1 << 21)
+    x = (ints * 2.0 ** -31).astype(np.float32)        # in [2^-10, 2^-9)
+    x64 = x.astype(np.float64)
+    hi, lo = nm.split(x, "f16")
+    assert not np.array_equal(hi + lo, x64)
+    hs, ls = nm.split_scaled(x, "f16")
+    assert np.array_equal(hs, hi)
+    assert np.array_equal(hs + np.ldexp(ls, -11), x64)
+    # scaling by a power of two commutes with rounding wherever the scaled residual is normal
+    big = synth.uniform((5000,), seed=16, lo=-200.0, hi=200.0)
+    h1, l1 = nm.split(big, "f16")
+    h2, l2 = nm.split_scaled(big, "f16")
+    normal = np.abs(l1) >= 2.0 ** -14
+    assert np.array_equal(h1, h2) and np.array_equal(np.ldexp(l1[normal], 11), l2[normal])
+
+
+def test_scaled_split_bf16():
+    x = synth.log_uniform_pow2((20000,), seed=17)
+    hs, ls = nm.split_scaled(x, "bf16")
+    r = x.astype(np.float64) - hs
+    assert np.all(np.abs(np.ldexp(r, 8) - ls) <= 2.0 ** -8 * np.abs(np.ldexp(r, 8)))
