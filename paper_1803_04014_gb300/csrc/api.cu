@@ -125,6 +125,13 @@ bool use_pair_tiles(int64_t m) {
     return m > 128;
 }
 
+// Tile raster band of the tensor-core GEMM in M-tiles (TCGEMM_GROUP_M, default 16).
+int gemm_group_m() {
+    const char* env = getenv("TCGEMM_GROUP_M");
+    const int v = env ? atoi(env) : 0;
+    return (v >= 1 && v <= 1024) ? v : 16;
+}
+
 // k-blocks of 64 between promotions of the refined GEMM's partial sums out of
 // TMEM into round-to-nearest FP32 registers.  TCGEMM_SPLIT_PROMOTE=0|1|2|4.
 int split_promote_kb() {
@@ -244,6 +251,7 @@ tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, c
     p.na = p.nb = p.nprod = 1;
     p.bn = 256;
     p.pair = use_pair_tiles(m) ? 1 : 0;
+    p.group_m = gemm_group_m();
     p.m = m; p.n = n; p.k = k;
     p.alpha = alpha; p.beta = beta;
     p.C = C; p.ldc = ldc;
@@ -324,6 +332,7 @@ tc_status gemm_split(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t
         p.bn = nprod == 2 ? 256 : 128;
         p.pair = use_pair_tiles(m) ? 1 : 0;
         p.promote_kb = p.pair ? split_promote_kb() : 0;
+        p.group_m = gemm_group_m();
         p.m = m; p.n = n; p.k = k;
         p.alpha = alpha; p.beta = beta;
         p.C = C; p.ldc = ldc;
@@ -411,8 +420,10 @@ tc_status gemm_grouped_plan_create(int32_t dt, int32_t count, const tc_problem* 
     if (lb != TC_ROW_MAJOR && lb != TC_COL_MAJOR) return fail(TC_ERR_INVALID, "grouped: bad layout");
     if (count < 0 || (count > 0 && !problems)) return fail(TC_ERR_INVALID, "grouped: bad problem array");
     std::vector<tcg::GroupedProblemDev> probs(count);
-    struct T { int64_t cost; tcg::GroupedTileDev t; };
-    std::vector<T> tiles;
+    struct P { int64_t cost; int32_t g; };
+    std::vector<P> order;
+    order.reserve(count);
+    size_t ntiles = 0;
     for (int32_t g = 0; g < count; ++g) {
         const tc_problem& p = problems[g];
         if (p.m < 1 || p.n < 1 || p.k < 1) return fail(TC_ERR_INVALID, "grouped: problem %d has a zero size", g);
@@ -422,22 +433,26 @@ tc_status gemm_grouped_plan_create(int32_t dt, int32_t count, const tc_problem* 
             return fail(TC_ERR_INVALID, "grouped: problem %d rows not 16-byte aligned", g);
         if (p.off_a < 0 || p.off_b < 0 || p.off_c < 0) return fail(TC_ERR_INVALID, "grouped: problem %d negative offset", g);
         probs[g] = {p.m, p.n, p.k, 0, p.off_a, p.off_b, p.off_c, p.lda, p.ldb, p.ldc, 0};
+        const int64_t tm = (p.m + tcg::kGroupedTileM - 1) / tcg::kGroupedTileM;
+        const int64_t tn = (p.n + tcg::kGroupedTileN - 1) / tcg::kGroupedTileN;
+        ntiles += static_cast<size_t>(tm * tn);
+        // bytes every tile of the problem moves together: A panels, B panels, C
+        order.push_back({2 * p.k * (p.m * tn + p.n * tm) + 4 * int64_t(p.m) * p.n, g});
+    }
+    if (ntiles > 0x7FFFFFFF) return fail(TC_ERR_INVALID, "grouped: too many tiles");
+    // problems longest first, each problem's tiles next to each other: CTAs that run at the
+    // same time share the problem's A and B panels through L2, and the longest problems
+    // start first so the static stride of the persistent grid ends evenly
+    std::stable_sort(order.begin(), order.end(), [](const P& a, const P& b) { return a.cost > b.cost; });
+    std::vector<tcg::GroupedTileDev> tl;
+    tl.reserve(ntiles);
+    for (const P& o : order) {
+        const tc_problem& p = problems[o.g];
         const int tm = (p.m + tcg::kGroupedTileM - 1) / tcg::kGroupedTileM;
         const int tn = (p.n + tcg::kGroupedTileN - 1) / tcg::kGroupedTileN;
         for (int i = 0; i < tm; ++i)
-            for (int j = 0; j < tn; ++j) {
-                const int64_t rows = std::min(tcg::kGroupedTileM, p.m - i * tcg::kGroupedTileM);
-                const int64_t cols = std::min(tcg::kGroupedTileN, p.n - j * tcg::kGroupedTileN);
-                // bytes the tile moves: its A rows, its B columns, its C block
-                const int64_t cost = 2 * p.k * (rows + cols) + 4 * rows * cols;
-                tiles.push_back({cost, {g, i, j, 0}});
-            }
+            for (int j = 0; j < tn; ++j) tl.push_back({o.g, i, j, 0});
     }
-    if (tiles.size() > 0x7FFFFFFF) return fail(TC_ERR_INVALID, "grouped: too many tiles");
-    // longest first: a persistent grid striding over this order balances well
-    std::stable_sort(tiles.begin(), tiles.end(), [](const T& a, const T& b) { return a.cost > b.cost; });
-    std::vector<tcg::GroupedTileDev> tl(tiles.size());
-    for (size_t i = 0; i < tiles.size(); ++i) tl[i] = tiles[i].t;
 
     Device* d;
     tc_status s = get_device(&d);

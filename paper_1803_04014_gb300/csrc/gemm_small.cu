@@ -348,17 +348,19 @@ cudaError_t launch_grouped(int dt, int lb, const GroupedProblemDev* probs, const
                            int32_t num_tiles, const void* a_base, const void* b_base, float* c_base, float alpha,
                            float beta, int sm_count, cudaStream_t st) {
     if (num_tiles <= 0) return cudaSuccess;
-    const int want = sm_count * 8;
-    const int grid = num_tiles < want ? num_tiles : want;
     auto* a = static_cast<const uint16_t*>(a_base);
     auto* b = static_cast<const uint16_t*>(b_base);
-    if (dt == 0) {
-        if (lb == 0) k_grouped<0, 0><<<grid, kGThreads, 0, st>>>(probs, tiles, num_tiles, a, b, c_base, alpha, beta);
-        else k_grouped<0, 1><<<grid, kGThreads, 0, st>>>(probs, tiles, num_tiles, a, b, c_base, alpha, beta);
-    } else {
-        if (lb == 0) k_grouped<1, 0><<<grid, kGThreads, 0, st>>>(probs, tiles, num_tiles, a, b, c_base, alpha, beta);
-        else k_grouped<1, 1><<<grid, kGThreads, 0, st>>>(probs, tiles, num_tiles, a, b, c_base, alpha, beta);
-    }
+    void (*kern)(const GroupedProblemDev*, const GroupedTileDev*, int32_t, const uint16_t*, const uint16_t*, float*,
+                 float, float);
+    if (dt == 0) kern = (lb == 0) ? k_grouped<0, 0> : k_grouped<0, 1>;
+    else kern = (lb == 0) ? k_grouped<1, 0> : k_grouped<1, 1>;
+    // persistent grid of exactly the CTAs that can be resident, so the static tile stride has no tail wave
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGThreads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    const int want = sm_count * per_sm;
+    const int grid = num_tiles < want ? num_tiles : want;
+    kern<<<grid, kGThreads, 0, st>>>(probs, tiles, num_tiles, a, b, c_base, alpha, beta);
     return cudaGetLastError();
 }
 

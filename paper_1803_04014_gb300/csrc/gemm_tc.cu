@@ -31,7 +31,6 @@ constexpr int BM = 128;
 constexpr int kRowBytes = 128;
 constexpr int kATileBytes = BM * kRowBytes;
 constexpr int kThreads = 192;
-constexpr int kGroupM = 16;  // raster: bands of 16 M-tiles for L2 reuse of B
 
 struct Args {
     int m, n, k;
@@ -43,6 +42,7 @@ struct Args {
     const float* scale_b;
     int* status;
     uint32_t idesc;
+    int group_m;  // raster: bands of group_m M-tiles, N-tiles swept inside a band (L2 reuse)
 };
 
 // product p multiplies A piece prod_a(p) with B piece prod_b(p):
@@ -50,11 +50,11 @@ struct Args {
 __host__ __device__ constexpr int prod_a(int p) { return p & 1; }
 __host__ __device__ constexpr int prod_b(int p) { return p >> 1; }
 
-__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& mb, int& nb) {
-    const int band = kGroupM * tiles_n;
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int group_m, int& mb, int& nb) {
+    const int band = group_m * tiles_n;
     const int g = t / band;
-    const int first = g * kGroupM;
-    const int gm = min(tiles_m - first, kGroupM);
+    const int first = g * group_m;
+    const int gm = min(tiles_m - first, group_m);
     const int r = t - g * band;
     mb = first + r % gm;
     nb = r / gm;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (int t = blockIdx.x; ok && t < a.num_tiles; t += gridDim.x) {
                 int mb, nb;
-                tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+                tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
                 for (int kb = 0; kb < a.num_kb; ++kb) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, a.status)) {
                         ok = false;
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t acc_phase = 0;
         for (int t = blockIdx.x; t < a.num_tiles; t += gridDim.x) {
             int mb, nb;
-            tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+            tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
             const bool ok = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, a.status);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (int t = cid; ok && t < a.num_tiles; t += ncl) {
                 int mb, nb;
-                tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+                tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
                 for (int kb = 0; kb < a.num_kb; ++kb) {
                     if (!wait(empty_bar(stage), phase ^ 1u)) {
                         ok = false;
@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t acc_phase = 0;
         for (int t = cid; t < a.num_tiles; t += ncl) {
             int mb, nb;
-            tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+            tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
             const bool ok = wait(tfull_bar(acc), acc_phase);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
@@ -687,7 +687,7 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
             bool ok = true;
             for (int t = cid; ok && t < a.num_tiles; t += ncl) {
                 int mb, nb;
-                tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+                tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
                 for (int kb = 0; kb < a.num_kb; ++kb) {
                     if (!wait(empty_bar(stage), phase ^ 1u)) {
                         ok = false;
@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
         bool ok = true;
         for (int t = cid; ok && t < a.num_tiles; t += ncl) {
             int mb, nb;
-            tile_coords(t, a.tiles_m, a.tiles_n, mb, nb);
+            tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
             const int row = mb * PM + static_cast<int>(rank) * 128 + quarter * 32 + lane;
             const int col0 = nb * PN + half * 128;
             float acc[128];
@@ -920,6 +920,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     a.scale_b = p.scale_b;
     a.status = p.status;
     a.idesc = make_idesc(BM, p.bn, static_cast<uint32_t>(p.ab_format));
+    a.group_m = p.group_m > 0 ? p.group_m : 16;
     if (p.pair) {
         // 256 x 256 tiles on CTA pairs
         a.tiles_m = static_cast<int>((p.m + 255) / 256);

@@ -33,6 +33,7 @@ struct TcGemmLaunch {
     int sm_count;
     int bn;             // tile width of the single-CTA kernel (128 or 256)
     int pair;           // 1: 256 x 256 tiles on CTA pairs (B box of 128 rows per CTA)
+    int group_m;        // tile raster band height in M-tiles (0: default)
     int promote_kb;     // pair kernel only: >0 adds the partial sums of every promote_kb k-blocks
                         // into FP32 registers with round-to-nearest (1, 2 or 4); 0 keeps them in TMEM
 };

@@ -8,8 +8,8 @@
 //
 // All of these are HBM-bound streams (4 bytes in, 1-4 bytes out per element):
 // the row kernels move 8 elements per thread with 16-byte loads, the
-// transposing kernels stage 32 x 32 tiles in shared memory so that both the
-// FP32 reads and the narrow writes are coalesced.
+// transposing kernels stage tiles of 64 source rows in shared memory so that
+// the FP32 reads are coalesced and every thread writes one 16-byte chunk.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -57,13 +57,25 @@ struct Narrow<kDtE4M3> {
     }
 };
 
-__global__ void k_absmax(int64_t rows, int64_t cols, const float* __restrict__ src, int64_t ld,
-                         float* scale_word) {
+// max |x| over a rows x cols matrix into the word at scale_word (as FP32 bits;
+// non-negative floats order like their bit patterns).  Grid: x over column
+// chunks of 4 * blockDim.x, y over rows (grid-stride); no divisions per element.
+__global__ void __launch_bounds__(256) k_absmax(int64_t rows, int64_t cols, const float* __restrict__ src, int64_t ld,
+                                                float* scale_word, int vec4) {
     float m = 0.0f;
-    const int64_t total = rows * cols;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = i / cols, c = i - r * cols;
-        m = fmaxf(m, fabsf(src[r * ld + c]));
+    const int64_t chunk = 4 * (int64_t)blockDim.x;
+    for (int64_t r = blockIdx.y; r < rows; r += gridDim.y) {
+        const float* row = src + r * ld;
+        for (int64_t c0 = (int64_t)blockIdx.x * chunk; c0 < cols; c0 += (int64_t)gridDim.x * chunk) {
+            const int64_t c = c0 + 4 * (int64_t)threadIdx.x;
+            if (vec4 && c + 3 < cols) {
+                const float4 v = __ldcs(reinterpret_cast<const float4*>(row + c));
+                m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+            } else {
+                for (int j = 0; j < 4; ++j)
+                    if (c + j < cols) m = fmaxf(m, fabsf(row[c + j]));
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -74,7 +86,6 @@ __global__ void k_absmax(int64_t rows, int64_t cols, const float* __restrict__ s
         m = (threadIdx.x < (blockDim.x >> 5)) ? wmax[threadIdx.x] : 0.0f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        // non-negative floats order like their bit patterns
         if (threadIdx.x == 0) atomicMax(reinterpret_cast<unsigned*>(scale_word), __float_as_uint(m));
     }
 }
@@ -131,25 +142,66 @@ __global__ void __launch_bounds__(256) k_quantize_scalar(int64_t rows, int64_t c
     }
 }
 
-// dst[c * ld_dst + r] = cvt(src[r * ld_src + c]); one 32 x 32 tile per block (32 x 8 threads).
+// dst[c * ld_dst + r] = cvt(src[r * ld_src + c]).  One tile of 64 source rows x
+// TC source columns per block of 256 threads: the FP32 tile is read along its
+// rows (coalesced) into shared memory, then every thread converts
+// 16 / sizeof(T) consecutive source rows of one source column and writes them
+// as one 16-byte chunk of a destination row (TC = 32 for 2-byte outputs, 64 for
+// 1-byte outputs, so the tile's chunks are exactly the block's 256 threads).
+// The aligned path needs ld_dst * sizeof(T) and dst to be 16-byte aligned.
 template <int DT>
 __global__ void __launch_bounds__(256) k_quantize_transpose(int64_t rows, int64_t cols, const float* __restrict__ src,
                                                             int64_t ld_src, typename Narrow<DT>::T* __restrict__ dst,
-                                                            int64_t ld_dst, const float* scale_word) {
-    __shared__ float tile[32][33];
+                                                            int64_t ld_dst, const float* scale_word, int aligned) {
+    using T = typename Narrow<DT>::T;
+    constexpr int TR = 64;
+    constexpr int PER = 16 / sizeof(T);          // source rows per output chunk
+    constexpr int TC = 256 * PER / TR;           // source columns per tile
+    __shared__ float tile[TR][TC + 1];
     const float s = (DT == kDtE4M3) ? e4m3_scale_from_amax_word(scale_word) : 1.0f;
-    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t r0 = (int64_t)blockIdx.y * TR, c0 = (int64_t)blockIdx.x * TC;
+    const int t = threadIdx.x;
+    // load: TR x TC floats, coalesced along the source row; all loads issued before any is used
+    constexpr int NL = TR * TC / 256;
+    float v[NL];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t r = r0 + ty + 8 * i, c = c0 + tx;
-        tile[ty + 8 * i][tx] = (r < rows && c < cols) ? __ldcs(src + r * ld_src + c) : 0.0f;
+    for (int q = 0; q < NL; ++q) {
+        const int i = t + q * 256;
+        const int rr = i / TC, cc = i - rr * TC;
+        const int64_t r = r0 + rr, c = c0 + cc;
+        v[q] = (r < rows && c < cols) ? __ldcs(src + r * ld_src + c) : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        const int i = t + q * 256;
+        tile[i / TC][i % TC] = v[q];
     }
     __syncthreads();
+    const int cc = t / (TR / PER);               // destination row within the tile
+    const int j = t - cc * (TR / PER);           // chunk within the destination row
+    const int64_t c = c0 + cc;
+    if (c >= cols) return;
+    const int64_t rbase = r0 + j * PER;
+    T o[PER];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t c = c0 + ty + 8 * i, r = r0 + tx;
-        if (r < rows && c < cols) dst[c * ld_dst + r] = Narrow<DT>::cvt(tile[tx][ty + 8 * i], s);
+    for (int q = 0; q < PER; ++q) o[q] = Narrow<DT>::cvt(tile[j * PER + q][cc], s);
+    T* d = dst + c * ld_dst + rbase;
+    if (aligned && rbase + PER <= rows) {
+        uint4 w;
+        uint32_t* wp = reinterpret_cast<uint32_t*>(&w);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t v = 0;
+#pragma unroll
+            for (int e = 0; e < 4 / (int)sizeof(T); ++e)
+                v |= uint32_t(o[q * (4 / sizeof(T)) + e]) << (8 * sizeof(T) * e);
+            wp[q] = v;
+        }
+        *reinterpret_cast<uint4*>(d) = w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < PER; ++q)
+            if (rbase + q < rows) d[q] = o[q];
     }
 }
 
@@ -207,25 +259,51 @@ __global__ void __launch_bounds__(256) k_split_scalar(int64_t rows, int64_t cols
 template <int PIECE>
 __global__ void __launch_bounds__(256) k_split_transpose(int64_t rows, int64_t cols, const float* __restrict__ src,
                                                          int64_t ld_src, unsigned short* __restrict__ hi,
-                                                         unsigned short* __restrict__ lo, int64_t ld_dst) {
-    __shared__ float tile[32][33];
-    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;
+                                                         unsigned short* __restrict__ lo, int64_t ld_dst, int aligned) {
+    constexpr int TR = 64, PER = 8, TC = 32;
+    __shared__ float tile[TR][TC + 1];
+    const int64_t r0 = (int64_t)blockIdx.y * TR, c0 = (int64_t)blockIdx.x * TC;
+    const int t = threadIdx.x;
+    constexpr int NL = TR * TC / 256;
+    float v[NL];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t r = r0 + ty + 8 * i, c = c0 + tx;
-        tile[ty + 8 * i][tx] = (r < rows && c < cols) ? __ldcs(src + r * ld_src + c) : 0.0f;
+    for (int q = 0; q < NL; ++q) {
+        const int i = t + q * 256;
+        const int rr = i / TC, cc = i - rr * TC;
+        const int64_t r = r0 + rr, c = c0 + cc;
+        v[q] = (r < rows && c < cols) ? __ldcs(src + r * ld_src + c) : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+        const int i = t + q * 256;
+        tile[i / TC][i % TC] = v[q];
     }
     __syncthreads();
+    const int cc = t / (TR / PER);
+    const int j = t - cc * (TR / PER);
+    const int64_t c = c0 + cc;
+    if (c >= cols) return;
+    const int64_t rbase = r0 + j * PER;
+    unsigned short h[PER], l[PER];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t c = c0 + ty + 8 * i, r = r0 + tx;
-        if (r < rows && c < cols) {
-            unsigned short h, l;
-            split_one<PIECE>(tile[tx][ty + 8 * i], h, l);
-            hi[c * ld_dst + r] = h;
-            lo[c * ld_dst + r] = l;
-        }
+    for (int q = 0; q < PER; ++q) split_one<PIECE>(tile[j * PER + q][cc], h[q], l[q]);
+    unsigned short* dh = hi + c * ld_dst + rbase;
+    unsigned short* dl = lo + c * ld_dst + rbase;
+    if (aligned && rbase + PER <= rows) {
+        uint4 wh, wl;
+        wh.x = h[0] | (uint32_t(h[1]) << 16); wh.y = h[2] | (uint32_t(h[3]) << 16);
+        wh.z = h[4] | (uint32_t(h[5]) << 16); wh.w = h[6] | (uint32_t(h[7]) << 16);
+        wl.x = l[0] | (uint32_t(l[1]) << 16); wl.y = l[2] | (uint32_t(l[3]) << 16);
+        wl.z = l[4] | (uint32_t(l[5]) << 16); wl.w = l[6] | (uint32_t(l[7]) << 16);
+        *reinterpret_cast<uint4*>(dh) = wh;
+        *reinterpret_cast<uint4*>(dl) = wl;
+    } else {
+#pragma unroll
+        for (int q = 0; q < PER; ++q)
+            if (rbase + q < rows) {
+                dh[q] = h[q];
+                dl[q] = l[q];
+            }
     }
 }
 
@@ -253,8 +331,10 @@ cudaError_t quantize_dt(int64_t rows, int64_t cols, const float* src, int64_t ld
     using T = typename Narrow<DT>::T;
     T* d = static_cast<T*>(dst);
     if (transpose) {
-        dim3 grid(static_cast<unsigned>((cols + 31) / 32), static_cast<unsigned>((rows + 31) / 32));
-        k_quantize_transpose<DT><<<grid, dim3(32, 8), 0, st>>>(rows, cols, src, ld_src, d, ld_dst, scale);
+        constexpr int TC = 256 * (16 / sizeof(T)) / 64;
+        dim3 grid(static_cast<unsigned>((cols + TC - 1) / TC), static_cast<unsigned>((rows + 63) / 64));
+        const int al = ((ld_dst * sizeof(T)) % 16 == 0) && aligned16(dst);
+        k_quantize_transpose<DT><<<grid, 256, 0, st>>>(rows, cols, src, ld_src, d, ld_dst, scale, al);
     } else {
         const bool vec = (cols % 8 == 0) && (ld_src % 4 == 0) && ((ld_dst * sizeof(T)) % (8 * sizeof(T)) == 0) &&
                          aligned16(src) && ((reinterpret_cast<uintptr_t>(dst) % (8 * sizeof(T))) == 0);
@@ -275,8 +355,9 @@ cudaError_t split_piece(int64_t rows, int64_t cols, const float* src, int64_t ld
     auto* h = static_cast<unsigned short*>(hi);
     auto* l = static_cast<unsigned short*>(lo);
     if (transpose) {
-        dim3 grid(static_cast<unsigned>((cols + 31) / 32), static_cast<unsigned>((rows + 31) / 32));
-        k_split_transpose<PIECE><<<grid, dim3(32, 8), 0, st>>>(rows, cols, src, ld_src, h, l, ld_dst);
+        dim3 grid(static_cast<unsigned>((cols + 31) / 32), static_cast<unsigned>((rows + 63) / 64));
+        const int al = (ld_dst % 8 == 0) && aligned16(hi) && aligned16(lo);
+        k_split_transpose<PIECE><<<grid, 256, 0, st>>>(rows, cols, src, ld_src, h, l, ld_dst, al);
     } else {
         const bool vec = (cols % 8 == 0) && (ld_src % 4 == 0) && (ld_dst % 8 == 0) && aligned16(src) &&
                          aligned16(hi) && aligned16(lo);
@@ -298,7 +379,12 @@ cudaError_t launch_quantize(int dt, int64_t rows, int64_t cols, const float* src
         e = cudaMemsetAsync(scale, 0, sizeof(float), st);
         if (e != cudaSuccess) return e;
         if (rows > 0 && cols > 0) {
-            k_absmax<<<grid_for(rows * cols, 256 * 16), 256, 0, st>>>(rows, cols, src, ld_src, scale);
+            const int64_t xblocks = (cols + 1023) / 1024;
+            const unsigned gx = static_cast<unsigned>(xblocks < 64 ? xblocks : 64);
+            const int64_t want_y = (152 * 16 + gx - 1) / gx;
+            const unsigned gy = static_cast<unsigned>(rows < want_y ? rows : (want_y < 65535 ? want_y : 65535));
+            const int v4 = (ld_src % 4 == 0) && aligned16(src);
+            k_absmax<<<dim3(gx, gy), 256, 0, st>>>(rows, cols, src, ld_src, scale, v4);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             if ((e = quantize_dt<kDtE4M3>(rows, cols, src, ld_src, dst, ld_dst, transpose, scale, st)) != cudaSuccess)
                 return e;
