@@ -73,6 +73,7 @@ SIGNATURES = {
     "tc_last_error": (ctypes.c_char_p, []),
     "tc_device_info": (_i32, [ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "tc_sync_status": (_i32, [_vp]),
+    "tc_debug_stall_next_gemm": (_i32, [_i32]),
     "tc_quantize": (_i32, [_i32, _i64, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _vp]),
     "tc_split": (_i32, [_i32, _i64, _i64, _vp, _i64, _i32, _vp, _vp, _i64, _vp]),
     "gemm_mixed": (_i32, [_i32, _i64, _i64, _i64, _f32, _vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp, _i64,
@@ -164,6 +165,11 @@ def tc_device_info():
 
 def tc_sync_status(stream=None) -> int:
     return _check(load().tc_sync_status(_stream(stream)), "tc_sync_status")
+
+
+def tc_debug_stall_next_gemm(k_block):
+    """Test hook: the next tensor-core GEMM of this thread withholds one k-block (see tcgemm_debug.h)."""
+    return _check(load().tc_debug_stall_next_gemm(int(k_block)), "tc_debug_stall_next_gemm")
 
 
 def tc_quantize(dt, rows, cols, src, ld_src, dst, ld_dst, transpose=0, scale_out=None, stream=None):

@@ -14,6 +14,7 @@
 
 #include "launch.h"
 #include "tcgemm.h"
+#include "tcgemm_debug.h"
 
 namespace {
 
@@ -125,6 +126,14 @@ bool use_pair_tiles(int64_t m) {
     return m > 128;
 }
 
+// Pending failure-injection request of this thread (tc_debug_stall_next_gemm).
+thread_local int g_stall_next = 0;  // k-block + 1, 0 = none
+int take_stall() {
+    const int v = g_stall_next;
+    g_stall_next = 0;
+    return v;
+}
+
 // Tile raster band of the tensor-core GEMM in M-tiles (TCGEMM_GROUP_M, default 16).
 int gemm_group_m() {
     const char* env = getenv("TCGEMM_GROUP_M");
@@ -148,6 +157,11 @@ int split_promote_kb() {
 extern "C" {
 
 const char* tc_version(void) { return "tcgemm 0.1 (sm_103a)"; }
+
+tc_status tc_debug_stall_next_gemm(int32_t k_block) {
+    g_stall_next = k_block >= 0 ? k_block + 1 : 0;
+    return TC_OK;
+}
 
 const char* tc_last_error(void) { return g_err.c_str(); }
 
@@ -252,6 +266,7 @@ tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, c
     p.bn = 256;
     p.pair = use_pair_tiles(m) ? 1 : 0;
     p.group_m = gemm_group_m();
+    p.stall_at = take_stall();
     p.m = m; p.n = n; p.k = k;
     p.alpha = alpha; p.beta = beta;
     p.C = C; p.ldc = ldc;
@@ -333,6 +348,7 @@ tc_status gemm_split(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t
         p.pair = use_pair_tiles(m) ? 1 : 0;
         p.promote_kb = p.pair ? split_promote_kb() : 0;
         p.group_m = gemm_group_m();
+        p.stall_at = take_stall();
         p.m = m; p.n = n; p.k = k;
         p.alpha = alpha; p.beta = beta;
         p.C = C; p.ldc = ldc;

@@ -43,6 +43,7 @@ struct Args {
     int* status;
     uint32_t idesc;
     int group_m;  // raster: bands of group_m M-tiles, N-tiles swept inside a band (L2 reuse)
+    int stall_kb;  // test hook: >= 0 makes the first CTA (pair) withhold this k-block of its first tile
 };
 
 // product p multiplies A piece prod_a(p) with B piece prod_b(p):
@@ -137,6 +138,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, a.status)) {
                         ok = false;
                         break;
+                    }
+                    if (kb == a.stall_kb && t == static_cast<int>(blockIdx.x) && blockIdx.x == 0) {
+                        // test hook: this stage's barrier is never completed
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                        continue;
                     }
                     const uint32_t sbase = base + stage * L::kStageBytes;
                     mbar_arrive_expect_tx(full_bar(stage), L::kStageBytes);
@@ -410,6 +419,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (!wait(empty_bar(stage), phase ^ 1u)) {
                         ok = false;
                         break;
+                    }
+                    if (kb == a.stall_kb && t == cid && cid == 0 && rank == 0) {
+                        // test hook: the even CTA never arms this stage's barrier
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                        continue;
                     }
                     const uint32_t sbase = base + stage * L::kStageBytes;
                     const uint32_t leader_full = mapa_shared(full_bar(stage), 0);
@@ -693,6 +710,14 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
                         ok = false;
                         break;
                     }
+                    if (kb == a.stall_kb && t == cid && cid == 0 && rank == 0) {
+                        // test hook: the even CTA never arms this stage's barrier
+                        if (++stage == STAGES) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                        continue;
+                    }
                     const uint32_t sbase = base + stage * L::kStageBytes;
                     const uint32_t leader_full = mapa_shared(full_bar(stage), 0);
                     if (rank == 0) mbar_arrive_expect_tx(full_bar(stage), 2 * L::kStageBytes);
@@ -921,6 +946,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     a.status = p.status;
     a.idesc = make_idesc(BM, p.bn, static_cast<uint32_t>(p.ab_format));
     a.group_m = p.group_m > 0 ? p.group_m : 16;
+    a.stall_kb = p.stall_at - 1;
     if (p.pair) {
         // 256 x 256 tiles on CTA pairs
         a.tiles_m = static_cast<int>((p.m + 255) / 256);
