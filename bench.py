@@ -301,7 +301,7 @@ def measure_rows(b, A, B, pk, sm_count):
     out["refinement_n8192"] = _row(refinement)
     torch.cuda.empty_cache()
 
-    def grouped():
+    def grouped(lb):
         sizes = synth.group_sizes(10000, seed=synth.seed_for(3, 0))
         offa = np.zeros(len(sizes), np.int64)
         offb = np.zeros(len(sizes), np.int64)
@@ -319,17 +319,20 @@ def measure_rows(b, A, B, pk, sm_count):
         Ab = torch.empty(a, dtype=torch.float16, device="cuda").uniform_(-1, 1)
         Bb = torch.empty(bb, dtype=torch.float16, device="cuda").uniform_(-1, 1)
         Cb = torch.empty(c, dtype=torch.float32, device="cuda")
-        desc = [(m, n, k, offa[i], offb[i], offc[i], k, n, n) for i, (m, n, k) in enumerate(sizes)]
-        plan = b.gemm_grouped_plan_create(0, desc, 0, 0)
+        # lb = 1: B_g stored n x k (K-major, tensor-core path); lb = 0: k x n (row-major, mma.sync path)
+        desc = [(m, n, k, offa[i], offb[i], offc[i], k, k if lb == 1 else n, n) for i, (m, n, k) in enumerate(sizes)]
+        plan = b.gemm_grouped_plan_create(0, desc, 0, lb)
         try:
             ms = _time_ms(lambda: b.gemm_grouped_plan_run(plan, Ab, Bb, Cb, 1.0, 0.0, use_graph=1), 20)
         finally:
             b.gemm_grouped_plan_destroy(plan)
-        return {"problems": 10000, "ms": ms, "tflops": gflop / (ms * 1e-3) / 1e12,
+        return {"problems": 10000, "b_layout": "K-major (tcgen05 path)" if lb == 1 else "row-major (mma.sync path)",
+                "ms": ms, "tflops": gflop / (ms * 1e-3) / 1e12,
                 "gbs": algo_bytes / (ms * 1e-3) / 1e9, "frac_of_hbm": algo_bytes / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
                 "algorithmic_bytes": algo_bytes}
 
-    out["grouped_10000"] = _row(grouped)
+    out["grouped_10000"] = _row(lambda: grouped(1))
+    out["grouped_10000_rowmajor_b"] = _row(lambda: grouped(0))
     torch.cuda.empty_cache()
 
     def batched():
@@ -412,14 +415,14 @@ def profile_case(kind):
         sizes = synth.group_sizes(10000, seed=synth.seed_for(3, 0))
         desc, a, bb, c = [], 0, 0, 0
         for (m, n, k) in sizes:
-            desc.append((m, n, k, a, bb, c, k, n, n))
+            desc.append((m, n, k, a, bb, c, k, k, n))   # B_g stored n x k (K-major)
             a += m * k
             bb += k * n
             c += m * n
         Ab = torch.empty(a, dtype=torch.float16, device="cuda").uniform_(-1, 1)
         Bb = torch.empty(bb, dtype=torch.float16, device="cuda").uniform_(-1, 1)
         Cb = torch.empty(c, dtype=torch.float32, device="cuda")
-        plan = b.gemm_grouped_plan_create(0, desc, 0, 0)
+        plan = b.gemm_grouped_plan_create(0, desc, 0, 1)
         for _ in range(5):
             b.gemm_grouped_plan_run(plan, Ab, Bb, Cb, 1.0, 0.0, use_graph=0)
         b.tc_sync_status()

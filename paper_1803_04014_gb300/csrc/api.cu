@@ -423,7 +423,60 @@ struct tc_grouped_plan {
     const void* g_b = nullptr;
     float* g_c = nullptr;
     float g_alpha = 0.f, g_beta = 0.f;
+    // tensor-core path (K-major B): 128 x 256 tiles and one pair of TMA maps per problem
+    bool use_tc = false;
+    std::vector<tc_problem> host_probs;
+    tcg::GroupedTcTile* d_tc_tiles = nullptr;
+    int32_t tc_tiles = 0;
+    CUtensorMap* d_maps = nullptr;
+    const void* maps_a = nullptr;  // bases the device maps were encoded for
+    const void* maps_b = nullptr;
+    int* status = nullptr;
 };
+
+namespace {
+
+// Encode every problem's A and B tensor maps for these bases and upload them (stream-ordered).
+tc_status grouped_upload_maps(tc_grouped_plan* plan, const void* a_base, const void* b_base, cudaStream_t st) {
+    const CUtensorMapDataType tdt = plan->dt == TC_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    std::vector<CUtensorMap> maps(2 * static_cast<size_t>(plan->count));
+    const uint8_t* a = static_cast<const uint8_t*>(a_base);
+    const uint8_t* b = static_cast<const uint8_t*>(b_base);
+    for (int32_t g = 0; g < plan->count; ++g) {
+        const tc_problem& p = plan->host_probs[g];
+        tc_status s = encode_kmajor(&maps[2 * g], tdt, 2, a + p.off_a * 2, p.k, p.m, 1, int64_t(p.lda) * 2,
+                                    int64_t(p.m) * p.lda * 2, tcg::kGroupedTcTileM);
+        if (s != TC_OK) return s;
+        s = encode_kmajor(&maps[2 * g + 1], tdt, 2, b + p.off_b * 2, p.k, p.n, 1, int64_t(p.ldb) * 2,
+                          int64_t(p.n) * p.ldb * 2, tcg::grouped_tc_box_rows(p.n));
+        if (s != TC_OK) return s;
+    }
+    // pageable source: returns once the bytes are staged
+    cudaError_t e = cudaMemcpyAsync(plan->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "grouped: upload tensor maps");
+    plan->maps_a = a_base;
+    plan->maps_b = b_base;
+    return TC_OK;
+}
+
+cudaError_t grouped_launch(tc_grouped_plan* plan, const void* a_base, const void* b_base, float* c_base, float alpha,
+                           float beta, cudaStream_t st) {
+    if (plan->use_tc)
+        return tcg::launch_grouped_tc(plan->dt, plan->d_tc_tiles, plan->tc_tiles, plan->d_maps, c_base, alpha, beta,
+                                      plan->status, plan->sm_count, st);
+    return tcg::launch_grouped(plan->dt, plan->lb, plan->d_probs, plan->d_tiles, plan->num_tiles, a_base, b_base,
+                               c_base, alpha, beta, plan->sm_count, st);
+}
+
+// Grouped GEMMs with K-major B run on the tensor cores unless TCGEMM_GROUPED=mma.
+bool grouped_use_tensor_cores(int32_t lb) {
+    if (lb != TC_COL_MAJOR) return false;
+    const char* env = getenv("TCGEMM_GROUPED");
+    return !(env && strcmp(env, "mma") == 0);
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -486,6 +539,25 @@ tc_status gemm_grouped_plan_create(int32_t dt, int32_t count, const tc_problem* 
         if (e == cudaSuccess && (e = cudaMalloc(&plan->d_tiles, tl.size() * sizeof(tl[0]))) == cudaSuccess)
             e = cudaMemcpy(plan->d_tiles, tl.data(), tl.size() * sizeof(tl[0]), cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess && count > 0 && grouped_use_tensor_cores(lb)) {
+        // the same problem order, cut into 128 x 256 tiles
+        std::vector<tcg::GroupedTcTile> tc;
+        for (const P& o : order) {
+            const tc_problem& p = problems[o.g];
+            const int tm = (p.m + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM;
+            const int tn = (p.n + tcg::kGroupedTcTileN - 1) / tcg::kGroupedTcTileN;
+            for (int i = 0; i < tm; ++i)
+                for (int j = 0; j < tn; ++j)
+                    tc.push_back({o.g, i, j, p.m, p.n, p.k, p.ldc, (p.k + 63) / 64, p.off_c, 0});
+        }
+        plan->use_tc = true;
+        plan->tc_tiles = static_cast<int32_t>(tc.size());
+        plan->host_probs.assign(problems, problems + count);
+        plan->status = d->status;
+        if ((e = cudaMalloc(&plan->d_tc_tiles, tc.size() * sizeof(tc[0]))) == cudaSuccess)
+            e = cudaMemcpy(plan->d_tc_tiles, tc.data(), tc.size() * sizeof(tc[0]), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&plan->d_maps, 2 * size_t(count) * sizeof(CUtensorMap));
+    }
     if (e != cudaSuccess) {
         gemm_grouped_plan_destroy(plan);
         return fail(TC_ERR_OOM, "grouped: plan upload: %s", cudaGetErrorString(e));
@@ -502,10 +574,12 @@ tc_status gemm_grouped_plan_run(tc_grouped_plan* plan, const void* a_base, const
     if (!aligned(a_base, 16) || !aligned(b_base, 16) || !aligned(c_base, 8))
         return fail(TC_ERR_INVALID, "grouped: base pointers must be 16-byte aligned (C: 8)");
     cudaStream_t st = as_stream(stream);
+    if (plan->use_tc && (plan->maps_a != a_base || plan->maps_b != b_base)) {
+        tc_status s = grouped_upload_maps(plan, a_base, b_base, st);
+        if (s != TC_OK) return s;
+    }
     if (!use_graph)
-        return enqueue(tcg::launch_grouped(plan->dt, plan->lb, plan->d_probs, plan->d_tiles, plan->num_tiles, a_base,
-                                           b_base, c_base, alpha, beta, plan->sm_count, st),
-                       "grouped launch");
+        return enqueue(grouped_launch(plan, a_base, b_base, c_base, alpha, beta, st), "grouped launch");
     const bool same = plan->exec && plan->g_a == a_base && plan->g_b == b_base && plan->g_c == c_base &&
                       plan->g_alpha == alpha && plan->g_beta == beta;
     cudaError_t e;
@@ -516,10 +590,10 @@ tc_status gemm_grouped_plan_run(tc_grouped_plan* plan, const void* a_base, const
         }
         if (!plan->cap_stream && (e = cudaStreamCreateWithFlags(&plan->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(e, "grouped: capture stream");
+        // only recorded here; the graph is launched on `st`, after the map upload above
         if ((e = cudaStreamBeginCapture(plan->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return cuda_fail(e, "grouped: begin capture");
-        cudaError_t le = tcg::launch_grouped(plan->dt, plan->lb, plan->d_probs, plan->d_tiles, plan->num_tiles, a_base,
-                                             b_base, c_base, alpha, beta, plan->sm_count, plan->cap_stream);
+        cudaError_t le = grouped_launch(plan, a_base, b_base, c_base, alpha, beta, plan->cap_stream);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(plan->cap_stream, &graph);
         if (le != cudaSuccess || e != cudaSuccess) {
@@ -542,6 +616,8 @@ tc_status gemm_grouped_plan_destroy(tc_grouped_plan* plan) {
     if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
     if (plan->d_probs) cudaFree(plan->d_probs);
     if (plan->d_tiles) cudaFree(plan->d_tiles);
+    if (plan->d_tc_tiles) cudaFree(plan->d_tc_tiles);
+    if (plan->d_maps) cudaFree(plan->d_maps);
     delete plan;
     return TC_OK;
 }

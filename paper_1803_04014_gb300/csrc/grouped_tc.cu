@@ -1,0 +1,352 @@
+// Grouped GEMM on the tensor cores (Sec. IV-B generalised to uneven sizes):
+// C_g = alpha * A_g B_g + beta * C_g for every problem g of a plan.
+//
+// The workload moves far more bytes than it computes (about 34 FLOP/byte for
+// m, n, k <= 256), so the kernel is built to keep HBM streaming:
+//   * one persistent CTA per SM walks a longest-first list of output tiles of
+//     128 x 256 (every problem of the benchmark is one or two tiles);
+//   * every problem has its own pair of TMA tensor maps (A: k x m, B: k x n,
+//     K-major) in device memory, so each tile is fetched by TMA with the box
+//     cut to the problem (rows beyond m or n are zero-filled, not read);
+//   * one thread issues the TMA loads into a 4-stage ring and runs ahead across
+//     tile boundaries, so the loads of the next tile overlap the MMAs and the
+//     epilogue of the current one;
+//   * one thread issues tcgen05.mma 128 x N x 16 (N = the problem's n rounded up
+//     to 16, at most 256) into a double-buffered TMEM accumulator;
+//   * four epilogue warps read the accumulator and store C with alpha/beta.
+#include <cstdlib>
+#include <cstring>
+
+#include "launch.h"
+#include "tc_ptx.cuh"
+
+namespace tcg {
+namespace {
+
+constexpr int GM = 128;
+constexpr int GN = 256;
+constexpr int kRow = 128;                    // bytes per k-block row (64 x 16-bit)
+constexpr int kABytes = GM * kRow;           // 16 KB
+constexpr int kBBytes = GN * kRow;           // 32 KB (largest B box)
+constexpr int kStages = 4;
+constexpr int kStage = kABytes + kBBytes;
+constexpr int kBarOff = kStages * kStage;
+constexpr int kNumBars = 2 * kStages + 5;
+constexpr int kSlotOff = kBarOff + 8 * kNumBars;
+constexpr int kEpiOff = kSlotOff + 16;               // 4 warps x 32 x 33 floats of store staging
+constexpr int kEpiWarpFloats = 32 * 33;
+constexpr int kSmem = kEpiOff + 4 * kEpiWarpFloats * 4 + 1024;
+constexpr int kThreads = 192;
+
+struct Args {
+    const GroupedTcTile* tiles;
+    const CUtensorMap* maps;  // [2 * problems]: A map, B map
+    int num_tiles;
+    float* c_base;
+    float alpha, beta;
+    uint32_t ab_format;
+    int* status;
+    int staged_epilogue;  // 1: transpose each 32 x 32 chunk through shared memory for row-contiguous stores
+};
+
+__device__ __forceinline__ GroupedTcTile load_tile(const GroupedTcTile* tiles, int t, int num_tiles) {
+    GroupedTcTile r;
+    if (t < num_tiles) {
+        const int4* p = reinterpret_cast<const int4*>(tiles + t);
+        const int4 x = __ldg(p), y = __ldg(p + 1), z = __ldg(p + 2);
+        r.prob = x.x; r.tm = x.y; r.tn = x.z; r.m = x.w;
+        r.n = y.x; r.k = y.y; r.ldc = y.z; r.nk = y.w;
+        r.off_c = (static_cast<int64_t>(static_cast<uint32_t>(z.y)) << 32) | static_cast<uint32_t>(z.x);
+        r.pad = 0;
+    } else {
+        r = GroupedTcTile{};
+    }
+    return r;
+}
+
+// N of the MMA (and rows of the B box) for a problem: n rounded up to 16, capped at 256.
+__host__ __device__ __forceinline__ int mma_n(int n) {
+    const int r = (n + 15) / 16 * 16;
+    return r < GN ? r : GN;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_addr(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* base_ptr = smem_raw + (base - raw);
+    const uint32_t bars = base + kBarOff;
+    auto full_bar = [&](int s) { return bars + 8u * s; };
+    auto empty_bar = [&](int s) { return bars + 8u * (kStages + s); };
+    auto tfull_bar = [&](int i) { return bars + 8u * (2 * kStages + i); };
+    auto tempty_bar = [&](int i) { return bars + 8u * (2 * kStages + 2 + i); };
+    const uint32_t drain_bar = bars + 8u * (2 * kStages + 4);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base_ptr + kSlotOff);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(base_ptr + kSlotOff + 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(tfull_bar(i), 1);
+            mbar_init(tempty_bar(i), 4);
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_addr(tmem_slot), 2 * GN);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer, running ahead across tiles
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued_phase[kStages];
+#pragma unroll
+            for (int s = 0; s < kStages; ++s) issued_phase[s] = -1;
+            bool ok = true;
+            GroupedTcTile nxt = load_tile(a.tiles, blockIdx.x, a.num_tiles);
+            if (static_cast<int>(blockIdx.x) < a.num_tiles) {
+                tmap_acquire(a.maps + 2 * nxt.prob);
+                tmap_acquire(a.maps + 2 * nxt.prob + 1);
+            }
+            for (int t = blockIdx.x; ok && t < a.num_tiles; t += gridDim.x) {
+                const GroupedTcTile tile = nxt;
+                const CUtensorMap* mA = a.maps + 2 * tile.prob;
+                const CUtensorMap* mB = mA + 1;
+                // fetch the next tile's record and warm its tensor maps while this tile streams
+                nxt = load_tile(a.tiles, t + gridDim.x, a.num_tiles);
+                if (t + static_cast<int>(gridDim.x) < a.num_tiles) {
+                    tmap_acquire(a.maps + 2 * nxt.prob);
+                    tmap_acquire(a.maps + 2 * nxt.prob + 1);
+                    prefetch_tmap(a.maps + 2 * nxt.prob);
+                    prefetch_tmap(a.maps + 2 * nxt.prob + 1);
+                }
+                const int nk = tile.nk;
+                const uint32_t bytes = static_cast<uint32_t>(kABytes + mma_n(tile.n) * kRow);
+                for (int kb = 0; kb < nk; ++kb) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, a.status)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sbase = base + stage * kStage;
+                    mbar_arrive_expect_tx(full_bar(stage), bytes);
+                    tma_load_3d(sbase, mA, full_bar(stage), kb * 64, tile.tm * GM, 0);
+                    tma_load_3d(sbase + kABytes, mB, full_bar(stage), kb * 64, tile.tn * GN, 0);
+                    issued_phase[stage] = static_cast<int>(phase);
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                for (int s = 0; s < kStages; ++s)
+                    if (issued_phase[s] >= 0)
+                        mbar_wait_bounded(full_bar(s), static_cast<uint32_t>(issued_phase[s]), 100000000ull);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true, issued_any = false;
+            GroupedTcTile nxt = load_tile(a.tiles, blockIdx.x, a.num_tiles);
+            for (int t = blockIdx.x; ok && t < a.num_tiles; t += gridDim.x) {
+                const GroupedTcTile tile = nxt;
+                nxt = load_tile(a.tiles, t + gridDim.x, a.num_tiles);
+                const int nk = tile.nk;
+                const uint32_t idesc = make_idesc(GM, mma_n(tile.n), a.ab_format);
+                if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, a.status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * GN);
+                for (int kb = 0; kb < nk; ++kb) {
+                    if (!mbar_wait(full_bar(stage), phase, abort_flag, a.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sbase = base + stage * kStage;
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks)
+                        mma_f16(d_tmem, sw128_kmajor_desc(sbase + ks * 32), sw128_kmajor_desc(sbase + kABytes + ks * 32),
+                                idesc, (kb | ks) != 0 ? 1u : 0u);
+                    issued_any = true;
+                    mma_commit(empty_bar(stage));
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(tfull_bar(acc));
+                acc ^= 1;
+                if (acc == 0) acc_phase ^= 1u;
+            }
+            if (!ok && issued_any) {
+                mma_commit(drain_bar);
+                mbar_wait_bounded(drain_bar, 0, 100000000ull);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 2..5)
+        const int quarter = warp & 3;
+        const float alpha = a.alpha, beta = a.beta;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        GroupedTcTile nxt = load_tile(a.tiles, blockIdx.x, a.num_tiles);
+        for (int t = blockIdx.x; t < a.num_tiles; t += gridDim.x) {
+            const GroupedTcTile P = nxt;
+            const GroupedTcTile& tile = P;
+            nxt = load_tile(a.tiles, t + gridDim.x, a.num_tiles);
+            const bool ok = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, a.status);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const int row = tile.tm * GM + quarter * 32 + lane;
+            const int col0 = tile.tn * GN;
+            const int ncols_tile = min(GN, P.n - col0);
+            const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                                   static_cast<uint32_t>(acc * GN);
+            float* crow = a.c_base + P.off_c + static_cast<int64_t>(row) * P.ldc + col0;
+            const bool vec_ok = ((P.ldc & 3) == 0) && (((P.off_c + col0) & 3) == 0) &&
+                                ((reinterpret_cast<uintptr_t>(a.c_base) & 15u) == 0);
+            if (a.staged_epilogue) {
+                // each warp owns rows r0..r0+31 of the tile; stage 32 x 32 chunks and store whole row segments
+                float* stage = reinterpret_cast<float*>(base_ptr + kEpiOff) + (warp - 2) * kEpiWarpFloats;
+                const int r0 = tile.tm * GM + quarter * 32;
+#pragma unroll 1
+                for (int c = 0; c < ncols_tile; c += 32) {
+                    float v[32];
+                    tmem_load_32(taddr + c, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = v[j];
+                    __syncwarp();
+                    const int nc = min(32, ncols_tile - c);
+                    // lane l writes column (l % 8) * 4 .. +3 of rows q*4 + l/8, q = 0..7
+                    const int cc = (lane & 7) * 4;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int rr = q * 4 + (lane >> 3);
+                        const int grow = r0 + rr;
+                        if (grow < P.m) {
+                            float* p = a.c_base + P.off_c + static_cast<int64_t>(grow) * P.ldc + col0 + c + cc;
+                            const float* sv = stage + rr * 33 + cc;
+                            if (vec_ok && cc + 4 <= nc) {
+                                float4 o = make_float4(alpha * sv[0], alpha * sv[1], alpha * sv[2], alpha * sv[3]);
+                                if (beta != 0.0f) {
+                                    const float4 old = *reinterpret_cast<const float4*>(p);
+                                    o.x = fmaf(beta, old.x, o.x);
+                                    o.y = fmaf(beta, old.y, o.y);
+                                    o.z = fmaf(beta, old.z, o.z);
+                                    o.w = fmaf(beta, old.w, o.w);
+                                }
+                                __stcs(reinterpret_cast<float4*>(p), o);
+                            } else {
+                                for (int e = 0; e < 4; ++e)
+                                    if (cc + e < nc)
+                                        p[e] = (beta != 0.0f) ? fmaf(alpha, sv[e], beta * p[e]) : alpha * sv[e];
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty_bar(acc));
+                acc ^= 1;
+                if (acc == 0) acc_phase ^= 1u;
+                continue;
+            }
+#pragma unroll 1
+            for (int c = 0; c < ncols_tile; c += 32) {
+                float v[32];
+                tmem_load_32(taddr + c, v);
+                if (row < P.m) {
+                    const int nc = min(32, ncols_tile - c);
+                    float* p = crow + c;
+                    if (nc == 32 && vec_ok) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            float4 o;
+                            if (beta != 0.0f) {
+                                const float4 old = *reinterpret_cast<const float4*>(p + 4 * j);
+                                o.x = fmaf(alpha, v[4 * j + 0], beta * old.x);
+                                o.y = fmaf(alpha, v[4 * j + 1], beta * old.y);
+                                o.z = fmaf(alpha, v[4 * j + 2], beta * old.z);
+                                o.w = fmaf(alpha, v[4 * j + 3], beta * old.w);
+                            } else {
+                                o.x = alpha * v[4 * j + 0];
+                                o.y = alpha * v[4 * j + 1];
+                                o.z = alpha * v[4 * j + 2];
+                                o.w = alpha * v[4 * j + 3];
+                            }
+                            __stcs(reinterpret_cast<float4*>(p + 4 * j), o);
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j < nc) p[j] = (beta != 0.0f) ? fmaf(alpha, v[j], beta * p[j]) : alpha * v[j];
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty_bar(acc));
+            acc ^= 1;
+            if (acc == 0) acc_phase ^= 1u;
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, 2 * GN);
+    }
+}
+
+}  // namespace
+
+int grouped_tc_box_rows(int n) { return mma_n(n); }
+
+cudaError_t launch_grouped_tc(int dt, const GroupedTcTile* tiles, int32_t num_tiles, const CUtensorMap* maps,
+                              float* c_base, float alpha, float beta, int* status, int sm_count, cudaStream_t st) {
+    if (num_tiles <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_grouped_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e != cudaSuccess) return e;
+    Args a;
+    a.tiles = tiles;
+    a.maps = maps;
+    a.num_tiles = num_tiles;
+    a.c_base = c_base;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.ab_format = dt == 1 ? 1u : 0u;
+    a.status = status;
+    const char* env = getenv("TCGEMM_GROUPED_EPI");
+    a.staged_epilogue = (env && strcmp(env, "direct") == 0) ? 0 : 1;
+    const int grid = num_tiles < sm_count ? num_tiles : sm_count;
+    k_grouped_tc<<<grid, kThreads, kSmem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace tcg

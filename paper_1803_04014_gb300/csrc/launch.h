@@ -64,6 +64,21 @@ cudaError_t launch_grouped(int dt, int lb, const GroupedProblemDev* probs, const
 constexpr int kGroupedTileM = 64;
 constexpr int kGroupedTileN = 64;
 
+// ---- grouped_tc.cu: tcgen05 grouped GEMM, K-major A and B, 128 x 256 output tiles.
+// maps: per problem g, maps[2g] = A (dims {k, m, 1}, box 64 x 128) and maps[2g+1] =
+// B (dims {k, n, 1}, box 64 x grouped_tc_box_rows(n)), both 128-byte swizzled.
+constexpr int kGroupedTcTileM = 128;
+constexpr int kGroupedTcTileN = 256;
+// Everything a role needs about one output tile, in one 48-byte record (no dependent loads).
+struct alignas(16) GroupedTcTile {
+    int32_t prob, tm, tn, m;  // problem, tile coordinates, problem rows
+    int32_t n, k, ldc, nk;    // problem columns, depth, C row stride, k-blocks of 64
+    int64_t off_c, pad;       // element offset of C_g
+};
+int grouped_tc_box_rows(int n);
+cudaError_t launch_grouped_tc(int dt, const GroupedTcTile* tiles, int32_t num_tiles, const CUtensorMap* maps,
+                              float* c_base, float alpha, float beta, int* status, int sm_count, cudaStream_t st);
+
 // ---- errnorm.cu
 constexpr int kErrBlocks = 1024;  // fixed grid: the reduction order does not depend on the GPU
 // partial: 3 * kErrBlocks * 2 doubles of scratch.

@@ -432,3 +432,59 @@ def test_split_promotion_settings_match_oracle(b, monkeypatch, promote):
     b.tc_sync_status()
     ref = og.gemm_split("f16", 3, A, B, 1.5, -0.25, C0)
     assert normwise_dev(host(C), ref, A, B, 1.5, -0.25, C0) <= TOL_NORMWISE
+
+
+# ------------------------------------------------------------------ grouped GEMM on the tensor cores (K-major B)
+
+@pytest.mark.parametrize("impl", ["tc", "mma"])
+@pytest.mark.parametrize("count,ragged", [(1, False), (9, False), (400, False), (60, True)])
+def test_grouped_kmajor_parity(b, monkeypatch, impl, count, ragged):
+    if impl == "mma":
+        monkeypatch.setenv("TCGEMM_GROUPED", "mma")
+    probs, abuf, bbuf, csize = _grouped_case(count, seed=170 + count, lb=1, ragged=ragged)
+    C0 = synth.uniform((csize,), seed=77)
+    C = dev(C0)
+    desc = [p[:9] for p in probs]
+    b.gemm_grouped(0, desc, dev(abuf, torch.float16), 0, dev(bbuf, torch.float16), 1, C, 0.75, -0.5)
+    b.tc_sync_status()
+    got = host(C)
+    for (m, n, k, a0, b0, c0, lda, ldb, ldc, A, B) in probs:
+        ref = og.gemm_mixed("f16", A, B, 0.75, -0.5, C0[c0:c0 + m * n].reshape(m, n))
+        g = got[c0:c0 + m * n].reshape(m, n)
+        mag = 0.75 * (np.abs(nm.round_to(A, "f16")) @ np.abs(nm.round_to(B, "f16"))) + 0.5 * np.abs(
+            C0[c0:c0 + m * n].reshape(m, n))
+        ok, info = elementwise_ok(g, ref, mag, k)
+        assert ok, (m, n, k, info)
+
+
+def test_grouped_tc_large_problems_and_new_bases(b):
+    # problems above one 128 x 256 tile in both directions, and a second run on moved operands
+    sizes = [(300, 520, 200), (129, 257, 72), (16, 16, 8), (256, 256, 256)]
+    rows, a_parts, b_parts = [], [], []
+    oa = ob = oc = 0
+    data = []
+    for i, (m, n, k) in enumerate(sizes):
+        A = synth.uniform((m, k), seed=300 + i)
+        B = synth.uniform((k, n), seed=400 + i)
+        lda = (k + 7) // 8 * 8
+        Ap = np.zeros((m, lda), np.float32); Ap[:, :k] = A
+        Bp = np.zeros((n, lda), np.float32); Bp[:, :k] = B.T
+        rows.append((m, n, k, oa, ob, oc, lda, lda, n))
+        a_parts.append(Ap.ravel()); b_parts.append(Bp.ravel())
+        data.append((m, n, k, oc, A, B))
+        oa += Ap.size; ob += Bp.size; oc += m * n
+    abuf = np.concatenate(a_parts); bbuf = np.concatenate(b_parts)
+    plan = b.gemm_grouped_plan_create(0, rows, 0, 1)
+    try:
+        for shift in (0, 8):   # second run: same problems at other base addresses
+            Ad = dev(np.concatenate([np.zeros(shift, np.float32), abuf]), torch.float16)[shift:]
+            Bd = dev(np.concatenate([np.zeros(shift, np.float32), bbuf]), torch.float16)[shift:]
+            C = torch.zeros(oc, dtype=torch.float32, device="cuda")
+            b.gemm_grouped_plan_run(plan, Ad, Bd, C, 1.0, 0.0, use_graph=1)
+            b.tc_sync_status()
+            got = host(C)
+            for (m, n, k, c0, A, B) in data:
+                ref = og.gemm_mixed("f16", A, B)
+                assert normwise_dev(got[c0:c0 + m * n].reshape(m, n), ref, A, B) <= TOL_NORMWISE, (m, n, k)
+    finally:
+        b.gemm_grouped_plan_destroy(plan)
