@@ -5,9 +5,10 @@ Headline workload (the square-GEMM configuration at N = 8192): A and B are
 FP32 matrices uniform in [-1, 1] resident in HBM; one step rounds A and B to
 FP16 on the GPU (B into a K-major copy) and runs C = A*B + 0.5*C on the
 tensor cores with FP32 accumulation (two quantize launches and one persistent
-tcgen05 GEMM launch, one stream).  value = 2 N^3 / (device time of a step),
-in TFLOP/s.  A pipelined variant (rounding of the next step on a second
-stream) is reported beside it.
+tcgen05 GEMM launch).  Steps are pipelined: the rounding of step i+1 runs on a
+second stream (CUDA cores, HBM-bound) while the GEMM of step i runs on the
+tensor cores.  value = 2 N^3 / (device time per step), in TFLOP/s; the serial
+step (one stream) is reported beside it.
 The FP32 inputs (2 x 256 MiB) are larger than the 129 MB L2, so no flush is
 needed between steps.
 
@@ -347,6 +348,23 @@ def measure_rows(b, A, B, pk, sm_count):
                 "gbs": byts / (ms * 1e-3) / 1e9, "frac_of_hbm": byts / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
 
     out["batched16_1e6"] = _row(batched)
+
+    def batched_sweep():
+        # the paper's batched-GEMM axis (Sec. VII-A): TFLOP/s against the number of 16x16x16 products
+        res = []
+        top = 1 << 20
+        Ab = torch.empty(top * 256, dtype=torch.float16, device="cuda").uniform_(-1, 1)
+        Bb = torch.empty(top * 256, dtype=torch.float16, device="cuda").uniform_(-1, 1)
+        Cb = torch.empty(top * 256, dtype=torch.float32, device="cuda")
+        for lg in range(10, 21, 2):
+            batch = 1 << lg
+            ms = _time_ms(lambda: b.gemm_batched_strided(0, batch, 16, 16, 16, 1.0, Ab, 256, 0, Bb, 256, 0, 0.0, Cb,
+                                                         256), 20)
+            res.append({"batch": batch, "ms": ms, "tflops": batch * 8192 / (ms * 1e-3) / 1e12,
+                        "gbs": batch * 2048 / (ms * 1e-3) / 1e9})
+        return {"sweep": res, "note": "the paper's V100 WMMA kernel peaked at 4 TFLOP/s at 262 144 products"}
+
+    out["batched16_sweep"] = _row(batched_sweep)
     torch.cuda.empty_cache()
     out["serve"] = _row(lambda: measure_serve(b))
     return out
@@ -552,30 +570,30 @@ def main():
         torch.cuda.synchronize()
 
     K = args.steps
-    # pipelined steps (reported beside the headline): rounding of step i+1 on a second stream
-    for i in range(max(args.warmup, 3)):
-        step_pipelined(i)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    qstream.wait_stream(gstream)
-    ev0.record(gstream)
-    qstream.wait_event(ev0)
-    for i in range(K):
-        step_pipelined(i)
-    ev1.record(gstream)
-    torch.cuda.synchronize()
-    ms_pipelined = ev0.elapsed_time(ev1) / K
-    # timed region: K serial steps (each step's rounding, then its GEMM, one stream)
+    # serial steps (reported beside the headline): each step's rounding, then its GEMM, one stream
     for _ in range(max(args.warmup, 3)):
         step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(K):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_serial = ev0.elapsed_time(ev1) / K
+    # timed region: K pipelined steps (the rounding of step i+1 overlaps the GEMM of step i)
+    for i in range(max(args.warmup, 3)):
+        step_pipelined(i)
     gevs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    ev0.record()
+    qstream.wait_stream(gstream)
+    ev0.record(gstream)
+    qstream.wait_event(ev0)   # the first rounding starts inside the timed region
     for i in range(K):
-        step(gevs[i])
-    ev1.record()
+        step_pipelined(i, gevs[i])
+    ev1.record(gstream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -592,30 +610,58 @@ def main():
     gemm_avg_ms = sum(gemm_ms) / len(gemm_ms)
     gemm_tflops = flops / (gemm_avg_ms * 1e-3) / 1e12
 
-    # end to end through the public calls with host buffers
+    # end to end through the public calls with host buffers: every step copies its FP32 inputs
+    # from pinned host memory, rounds, multiplies and copies C back.  Steps are pipelined over
+    # three streams (copy in / compute / copy out) with double-buffered device buffers, so the
+    # upload of step i+1 overlaps the GEMM and the download of step i.
     Ah = torch.from_numpy(A).pin_memory()
     Bh = torch.from_numpy(B).pin_memory()
     C0h = torch.from_numpy(C0).pin_memory()
-    Ch = torch.empty((N, N), dtype=f32).pin_memory()
+    Ch = [torch.empty((N, N), dtype=f32).pin_memory() for _ in range(2)]
+    del Aq2, Bq2
+    sets = [{"A": Ad, "B": Bd, "C": Cd, "Aq": Aq, "Bq": Bq}]
+    sets.append({k: torch.empty_like(v) for k, v in sets[0].items()})
+    s_in, s_cmp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_cmp = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+    for ev in ev_cmp + ev_out:
+        ev.record()
 
-    def e2e_step():
-        Ad.copy_(Ah, non_blocking=True)
-        Bd.copy_(Bh, non_blocking=True)
-        Cd.copy_(C0h, non_blocking=True)
-        step()
-        Ch.copy_(Cd, non_blocking=True)
+    def e2e_step(i):
+        s = i & 1
+        S = sets[s]
+        s_in.wait_event(ev_cmp[s])          # step i-2 finished reading these inputs
+        s_in.wait_event(ev_out[s])          # and its result left the device
+        with torch.cuda.stream(s_in):
+            S["A"].copy_(Ah, non_blocking=True)
+            S["B"].copy_(Bh, non_blocking=True)
+            S["C"].copy_(C0h, non_blocking=True)
+            ev_in[s].record(s_in)
+        s_cmp.wait_event(ev_in[s])
+        b.tc_quantize(b.TC_F16, N, N, S["A"], N, S["Aq"], N, 0, stream=s_cmp)
+        b.tc_quantize(b.TC_F16, N, N, S["B"], N, S["Bq"], N, 1, stream=s_cmp)
+        b.gemm_mixed(b.TC_F16, N, N, N, 1.0, S["Aq"], N, b.TC_ROW_MAJOR, S["Bq"], N, b.TC_COL_MAJOR, 0.5, S["C"], N,
+                     stream=s_cmp)
+        ev_cmp[s].record(s_cmp)
+        s_out.wait_event(ev_cmp[s])
+        with torch.cuda.stream(s_out):
+            Ch[s].copy_(S["C"], non_blocking=True)
+            ev_out[s].record(s_out)
 
-    for _ in range(2):
-        e2e_step()
+    for i in range(2):
+        e2e_step(i)
     torch.cuda.synchronize()
-    Ke = max(3, min(K, 10))
+    Ke = max(4, min(K, 12))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
         dist.barrier()
-    e0.record()
-    for _ in range(Ke):
-        e2e_step()
-    e1.record()
+    torch.cuda.synchronize()
+    e0.record(s_in)
+    for i in range(Ke):
+        e2e_step(i)
+    s_out.wait_event(ev_out[(Ke - 1) & 1])
+    e1.record(s_out)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / Ke
     if dist:
@@ -623,6 +669,24 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
     e2e_value = world * flops / (e2e_ms * 1e-3) / 1e12
+    # the same, one step at a time on one stream (no overlap), for reference
+    Cd = sets[0]["C"]
+
+    def e2e_serial():
+        sets[0]["A"].copy_(Ah, non_blocking=True)
+        sets[0]["B"].copy_(Bh, non_blocking=True)
+        Cd.copy_(C0h, non_blocking=True)
+        step()
+        Ch[0].copy_(Cd, non_blocking=True)
+
+    e2e_serial()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(3):
+        e2e_serial()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_serial_ms = e0.elapsed_time(e1) / 3
 
     sm_mhz = clocks.get("sm_mhz") or None
     spec_peak_max = sm_count * SPEC_FLOP_PER_CLK_SM * pk["sm_max_mhz"] * 1e6 / 1e12
@@ -633,13 +697,13 @@ def main():
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f16", "data": "synthetic",
         "config": {"workload": WORKLOAD, "m": N, "n": N, "k": N, "alpha": 1.0, "beta": 0.5,
-                   "step": "tc_quantize(A) + tc_quantize(B, K-major) + gemm_mixed, one stream",
+                   "step": "tc_quantize(A) + tc_quantize(B, K-major) + gemm_mixed; the rounding of step i+1 "
+                           "runs on a second stream while the GEMM of step i runs (double-buffered operands)",
                    "l2": "inputs larger than L2 (2 x 256 MiB FP32), no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "gemm_only_tflops": gemm_tflops,
-        "pipelined_step": {"ms_per_step": ms_pipelined, "tflops": world * flops / (ms_pipelined * 1e-3) / 1e12,
-                           "note": "rounding of step i+1 on a second stream while the GEMM of step i runs "
-                                   "(double-buffered operands); power-capped, so the overlap gains little"},
+        "serial_step": {"ms_per_step": ms_serial, "tflops": world * flops / (ms_serial * 1e-3) / 1e12,
+                        "note": "each step's rounding, then its GEMM, on one stream"},
         "pct_of_spec_peak": {"at_max_clock": 100.0 * gemm_tflops / spec_peak_max,
                              "at_sampled_clock": (100.0 * gemm_tflops / spec_peak_clk) if spec_peak_clk else None,
                              "spec_peak_tflops_at_max_clock": spec_peak_max},
@@ -650,15 +714,19 @@ def main():
                      "kernel": "k_tc_gemm_pair (tcgen05.mma.cta_group::2, 256x256 tiles per CTA pair)",
                      "peak_source": f"{pk['source']} bf16 burst"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * N * N * 4,
-                "d2h_bytes_per_step": N * N * 4, "ms_per_step": e2e_ms},
+                "d2h_bytes_per_step": N * N * 4, "ms_per_step": e2e_ms,
+                "note": "pinned host A, B, C0 in and C out every step; copy-in, compute and copy-out on "
+                        "three streams with double-buffered device buffers",
+                "serial_ms_per_step": e2e_serial_ms,
+                "serial_value": world * flops / (e2e_serial_ms * 1e-3) / 1e12},
         "gpu_launches": 3 * K,
         "gpu_launches_note": "per step: 2 rounding kernels + 1 persistent GEMM",
         "clocks": clocks,
         "device": {"sm_count": sm_count, "cc": f"{ccmaj}.{ccmin}"},
     }
-    del Ah, Bh, C0h, Ch
+    del Ah, Bh, C0h, Ch, sets
     if rank == 0 and world == 1 and args.rows == "all":
-        del Aq, Bq, Cd, C0d, Aq2, Bq2
+        del Aq, Bq, Cd, C0d, Ad, Bd
         line["rows"] = measure_rows(b, A, B, pk, sm_count)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows = np.arange(512) * 16

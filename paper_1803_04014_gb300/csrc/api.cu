@@ -141,6 +141,13 @@ int gemm_group_m() {
     return (v >= 1 && v <= 1024) ? v : 16;
 }
 
+// Epilogue of the pair GEMM: stage 32 x 32 chunks in shared memory (default) or store rows
+// directly from the accumulator registers (TCGEMM_EPILOGUE=direct).
+int gemm_staged_epilogue() {
+    const char* env = getenv("TCGEMM_EPILOGUE");
+    return (env && strcmp(env, "direct") == 0) ? 0 : 1;
+}
+
 // k-blocks of 64 between promotions of the refined GEMM's partial sums out of
 // TMEM into round-to-nearest FP32 registers.  TCGEMM_SPLIT_PROMOTE=0|1|2|4.
 int split_promote_kb() {
@@ -267,6 +274,7 @@ tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, c
     p.pair = use_pair_tiles(m) ? 1 : 0;
     p.group_m = gemm_group_m();
     p.stall_at = take_stall();
+    p.staged_epilogue = gemm_staged_epilogue();
     p.m = m; p.n = n; p.k = k;
     p.alpha = alpha; p.beta = beta;
     p.C = C; p.ldc = ldc;

@@ -44,6 +44,7 @@ struct Args {
     uint32_t idesc;
     int group_m;  // raster: bands of group_m M-tiles, N-tiles swept inside a band (L2 reuse)
     int stall_kb;  // test hook: >= 0 makes the first CTA (pair) withhold this k-block of its first tile
+    int staged_epilogue;  // pair kernel: transpose 32 x 32 chunks through shared memory before storing
 };
 
 // product p multiplies A piece prod_a(p) with B piece prod_b(p):
@@ -327,7 +328,8 @@ struct PairLayout {
     static constexpr int kBarOffset = STAGES * kStageBytes;
     static constexpr int kNumBars = 2 * STAGES + 5;
     static constexpr int kSlotOffset = kBarOffset + 8 * kNumBars;
-    static constexpr int kBytes = kSlotOffset + 16 + 1024;
+    static constexpr int kEpiOffset = kSlotOffset + 16;          // 4 warps x 32 x 33 floats of store staging
+    static constexpr int kBytes = kEpiOffset + 4 * 32 * 33 * 4 + 1024;
     static constexpr int kTmemCols = 512;  // two 256-column accumulators
 };
 
@@ -537,6 +539,65 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                    static_cast<uint32_t>(acc * PN);
             float* crow = a.C + static_cast<int64_t>(row) * a.ldc + col0;
+            if (a.staged_epilogue) {
+                // rows r0..r0+31 of this warp: each 32 x 32 chunk goes through shared memory and is
+                // written as four 128-byte row segments per store instruction
+                float* stg = reinterpret_cast<float*>(base_ptr + L::kEpiOffset) + (warp - 2) * (32 * 33);
+                const int r0 = row - lane;
+                const int cc = (lane & 7) * 4;
+#pragma unroll 1
+                for (int c = 0; c < PN; c += 32) {
+                    if (col0 + c >= a.n) break;
+                    const int nc = min(32, a.n - (col0 + c));
+                    // old C of this chunk first: its global-memory latency overlaps the TMEM load
+                    float4 old[8];
+                    if (beta != 0.0f) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int grow = r0 + q * 4 + (lane >> 3);
+                            old[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (grow < a.m && vec_ok && cc + 4 <= nc)
+                                old[q] = *reinterpret_cast<const float4*>(a.C + static_cast<int64_t>(grow) * a.ldc +
+                                                                          col0 + c + cc);
+                        }
+                    }
+                    float v[32];
+                    tmem_load_32(taddr + c, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j];
+                    __syncwarp();
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int rr = q * 4 + (lane >> 3);
+                        const int grow = r0 + rr;
+                        if (grow < a.m) {
+                            float* p = a.C + static_cast<int64_t>(grow) * a.ldc + col0 + c + cc;
+                            const float* sv = stg + rr * 33 + cc;
+                            if (vec_ok && cc + 4 <= nc) {
+                                float4 o = make_float4(alpha * sv[0], alpha * sv[1], alpha * sv[2], alpha * sv[3]);
+                                if (beta != 0.0f) {
+                                    o.x = fmaf(beta, old[q].x, o.x);
+                                    o.y = fmaf(beta, old[q].y, o.y);
+                                    o.z = fmaf(beta, old[q].z, o.z);
+                                    o.w = fmaf(beta, old[q].w, o.w);
+                                }
+                                *reinterpret_cast<float4*>(p) = o;
+                            } else {
+                                for (int e = 0; e < 4; ++e)
+                                    if (cc + e < nc)
+                                        p[e] = (beta != 0.0f) ? fmaf(alpha, sv[e], beta * p[e]) : alpha * sv[e];
+                            }
+                        }
+                    }
+                    __syncwarp();
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(acc == 0 ? leader_tempty0 : leader_tempty1);
+                acc ^= 1;
+                if (acc == 0) acc_phase ^= 1u;
+                continue;
+            }
 #pragma unroll 1
             for (int c = 0; c < PN; c += 32) {
                 if (col0 + c >= a.n) break;
@@ -947,6 +1008,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     a.idesc = make_idesc(BM, p.bn, static_cast<uint32_t>(p.ab_format));
     a.group_m = p.group_m > 0 ? p.group_m : 16;
     a.stall_kb = p.stall_at - 1;
+    a.staged_epilogue = p.staged_epilogue;
     if (p.pair) {
         // 256 x 256 tiles on CTA pairs
         a.tiles_m = static_cast<int>((p.m + 255) / 256);

@@ -33,10 +33,11 @@ constexpr int kStage = kABytes + kBBytes;
 constexpr int kBarOff = kStages * kStage;
 constexpr int kNumBars = 2 * kStages + 5;
 constexpr int kSlotOff = kBarOff + 8 * kNumBars;
-constexpr int kEpiOff = kSlotOff + 16;               // 4 warps x 32 x 33 floats of store staging
+constexpr int kEpiWarps = 8;                         // two warps per TMEM lane quarter, 128 columns each
+constexpr int kEpiOff = kSlotOff + 16;               // kEpiWarps x 32 x 33 floats of store staging
 constexpr int kEpiWarpFloats = 32 * 33;
-constexpr int kSmem = kEpiOff + 4 * kEpiWarpFloats * 4 + 1024;
-constexpr int kThreads = 192;
+constexpr int kSmem = kEpiOff + kEpiWarps * kEpiWarpFloats * 4 + 1024;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 struct Args {
     const GroupedTcTile* tiles;
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(tfull_bar(i), 1);
-            mbar_init(tempty_bar(i), 4);
+            mbar_init(tempty_bar(i), kEpiWarps);
         }
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
@@ -208,8 +209,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue (warps 2..5)
+        // ---------------- epilogue (warps 2..9): lanes 32*(warp%4).., columns [128*half, 128*half + 128)
         const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         const float alpha = a.alpha, beta = a.beta;
         int acc = 0;
         uint32_t acc_phase = 0;
@@ -222,10 +224,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
             const int row = tile.tm * GM + quarter * 32 + lane;
-            const int col0 = tile.tn * GN;
-            const int ncols_tile = min(GN, P.n - col0);
+            const int col0 = tile.tn * GN + half * (GN / 2);
+            const int ncols_tile = max(0, min(GN / 2, P.n - col0));
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                   static_cast<uint32_t>(acc * GN);
+                                   static_cast<uint32_t>(acc * GN + half * (GN / 2));
             float* crow = a.c_base + P.off_c + static_cast<int64_t>(row) * P.ldc + col0;
             const bool vec_ok = ((P.ldc & 3) == 0) && (((P.off_c + col0) & 3) == 0) &&
                                 ((reinterpret_cast<uintptr_t>(a.c_base) & 15u) == 0);
@@ -235,14 +237,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                 const int r0 = tile.tm * GM + quarter * 32;
 #pragma unroll 1
                 for (int c = 0; c < ncols_tile; c += 32) {
+                    const int nc = min(32, ncols_tile - c);
+                    // lane l writes column (l % 8) * 4 .. +3 of rows q*4 + l/8, q = 0..7
+                    const int cc = (lane & 7) * 4;
+                    // old C of this chunk first: its global-memory latency overlaps the TMEM load
+                    float4 old[8];
+                    if (beta != 0.0f) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const int grow = r0 + q * 4 + (lane >> 3);
+                            old[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (grow < P.m && vec_ok && cc + 4 <= nc)
+                                old[q] = *reinterpret_cast<const float4*>(a.c_base + P.off_c +
+                                                                          static_cast<int64_t>(grow) * P.ldc + col0 +
+                                                                          c + cc);
+                        }
+                    }
                     float v[32];
                     tmem_load_32(taddr + c, v);
 #pragma unroll
                     for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = v[j];
                     __syncwarp();
-                    const int nc = min(32, ncols_tile - c);
-                    // lane l writes column (l % 8) * 4 .. +3 of rows q*4 + l/8, q = 0..7
-                    const int cc = (lane & 7) * 4;
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int rr = q * 4 + (lane >> 3);
@@ -253,11 +268,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                             if (vec_ok && cc + 4 <= nc) {
                                 float4 o = make_float4(alpha * sv[0], alpha * sv[1], alpha * sv[2], alpha * sv[3]);
                                 if (beta != 0.0f) {
-                                    const float4 old = *reinterpret_cast<const float4*>(p);
-                                    o.x = fmaf(beta, old.x, o.x);
-                                    o.y = fmaf(beta, old.y, o.y);
-                                    o.z = fmaf(beta, old.z, o.z);
-                                    o.w = fmaf(beta, old.w, o.w);
+                                    o.x = fmaf(beta, old[q].x, o.x);
+                                    o.y = fmaf(beta, old[q].y, o.y);
+                                    o.z = fmaf(beta, old[q].z, o.z);
+                                    o.w = fmaf(beta, old[q].w, o.w);
                                 }
                                 __stcs(reinterpret_cast<float4*>(p), o);
                             } else {

@@ -34,6 +34,7 @@ struct TcGemmLaunch {
     int bn;             // tile width of the single-CTA kernel (128 or 256)
     int pair;           // 1: 256 x 256 tiles on CTA pairs (B box of 128 rows per CTA)
     int group_m;        // tile raster band height in M-tiles (0: default)
+    int staged_epilogue;  // pair kernel: store C through shared memory in row segments
     int stall_at;       // test hook: k-block + 1 to withhold, 0 = off (tc_debug_stall_next_gemm)
     int promote_kb;     // pair kernel only: >0 adds the partial sums of every promote_kb k-blocks
                         // into FP32 registers with round-to-nearest (1, 2 or 4); 0 keeps them in TMEM
