@@ -495,6 +495,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1803_04014_gb300 import binding as b
+    from paper_1803_04014_gb300 import shard
     b.load()
     sm_count, ccmaj, ccmin = b.tc_device_info()
     pk = peaks()
@@ -600,13 +601,9 @@ def main():
     clocks = sampler.stop()
     ms_total = ev0.elapsed_time(ev1)
     gemm_ms = [s.elapsed_time(e) for s, e in gevs]
-    ms_step = ms_total / K
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = shard.max_over_ranks(ms_total / K, dist, device="cuda")
     flops = 2.0 * N ** 3
-    value = world * flops / (ms_step * 1e-3) / 1e12
+    value = shard.weak_scaling_throughput(flops, world, ms_step * 1e-3) / 1e12
     gemm_avg_ms = sum(gemm_ms) / len(gemm_ms)
     gemm_tflops = flops / (gemm_avg_ms * 1e-3) / 1e12
 
@@ -663,12 +660,8 @@ def main():
     s_out.wait_event(ev_out[(Ke - 1) & 1])
     e1.record(s_out)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / Ke
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * flops / (e2e_ms * 1e-3) / 1e12
+    e2e_ms = shard.max_over_ranks(e0.elapsed_time(e1) / Ke, dist, device="cuda")
+    e2e_value = shard.weak_scaling_throughput(flops, world, e2e_ms * 1e-3) / 1e12
     # the same, one step at a time on one stream (no overlap), for reference
     Cd = sets[0]["C"]
 
