@@ -231,6 +231,31 @@ tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_problem* prob
                                float* c_base, float alpha, float beta, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Autotuning (the paper picked the best CUTLASS tiling per size, Sec. VI)    */
+/* ------------------------------------------------------------------------ */
+
+/* Time gemm_mixed's kernel configurations for this shape on scratch operands
+ * and remember the fastest for every later call of the same shape class in
+ * this process.  Candidates: 128x256 tiles on single CTAs or 256x256 tiles on
+ * CTA pairs (cluster of 2), each with raster bands of 8, 16 or 32 M-tiles.
+ * A shape class is (dt, m, n, k) with each size rounded up to a power of two.
+ * Allocates and frees stream-ordered scratch (cudaMallocAsync) and
+ * synchronises `stream`.  *best_ms (host, may be NULL) receives the winner's
+ * time.  TCGEMM_TILE / TCGEMM_GROUP_M, when set, still override the table. */
+tc_status tc_autotune_gemm(int32_t dt, int64_t m, int64_t n, int64_t k, void* stream, double* best_ms);
+
+/* Time the variants of a grouped plan on its own operands (the tensor-core
+ * path with a shared-memory-staged or a direct epilogue, and the mma.sync
+ * path) and keep the fastest in the plan.  C is overwritten (alpha = 1,
+ * beta = 0).  Synchronises `stream`.  A plan with row-major B has one variant. */
+tc_status gemm_grouped_plan_autotune(tc_grouped_plan* plan, const void* a_base, const void* b_base, float* c_base,
+                                     void* stream, double* best_ms);
+
+/* Write / read the gemm_mixed autotune table (text, one shape class per line). */
+tc_status tc_autotune_save(const char* path);
+tc_status tc_autotune_load(const char* path);
+
+/* ------------------------------------------------------------------------ */
 /* Error measures (Sec. VI: e = C_half - C_single, ||e||_max; normwise
  * error ||C - C64||_F / (||A||_F ||B||_F) against an FP64 truth)           */
 /* ------------------------------------------------------------------------ */

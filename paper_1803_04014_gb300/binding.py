@@ -91,6 +91,10 @@ SIGNATURES = {
     "gemm_grouped": (_i32, [_i32, _i32, ctypes.POINTER(tc_problem), _vp, _i32, _vp, _i32, _vp, _f32, _f32, _vp]),
     "gemm_grouped_noalloc": (_i32, [_i32, _i32, ctypes.POINTER(tc_problem), _vp, _i32, _vp, _i32, _vp, _f32, _f32,
                                     _vp]),
+    "tc_autotune_gemm": (_i32, [_i32, _i64, _i64, _i64, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "gemm_grouped_plan_autotune": (_i32, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
+    "tc_autotune_save": (_i32, [ctypes.c_char_p]),
+    "tc_autotune_load": (_i32, [ctypes.c_char_p]),
     "tc_error_norm": (_i32, [_i64, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _i64, _i64, _i64, _vp, _i64, _i64,
                              _i64, ctypes.POINTER(ctypes.c_double), _vp]),
     "serve_open": (_i32, [ctypes.POINTER(tc_serve_cfg), ctypes.POINTER(_vp)]),
@@ -244,6 +248,29 @@ def gemm_grouped_noalloc(dt, problems, a_base, la, b_base, lb, c_base, alpha, be
     arr = problems if isinstance(problems, ctypes.Array) else problems_array(problems)
     return _check(load().gemm_grouped_noalloc(dt, len(arr), arr, _ptr(a_base), la, _ptr(b_base), lb, _ptr(c_base),
                                               alpha, beta, _stream(stream)), "gemm_grouped_noalloc")
+
+
+def tc_autotune_gemm(dt, m, n, k, stream=None):
+    """Time gemm_mixed's configurations for this shape; returns the fastest time in ms."""
+    ms = ctypes.c_double()
+    _check(load().tc_autotune_gemm(dt, m, n, k, _stream(stream), ctypes.byref(ms)), "tc_autotune_gemm")
+    return ms.value
+
+
+def gemm_grouped_plan_autotune(plan, a_base, b_base, c_base, stream=None):
+    """Time the plan's variants on its operands and keep the fastest; returns its time in ms."""
+    ms = ctypes.c_double()
+    _check(load().gemm_grouped_plan_autotune(plan, _ptr(a_base), _ptr(b_base), _ptr(c_base), _stream(stream),
+                                             ctypes.byref(ms)), "gemm_grouped_plan_autotune")
+    return ms.value
+
+
+def tc_autotune_save(path):
+    return _check(load().tc_autotune_save(str(path).encode()), "tc_autotune_save")
+
+
+def tc_autotune_load(path):
+    return _check(load().tc_autotune_load(str(path).encode()), "tc_autotune_load")
 
 
 def tc_error_norm(m, n, C, ldc, Cref, ldr, ref_is_f64, A=None, a_rows=0, a_cols=0, lda=0, B=None, b_rows=0,

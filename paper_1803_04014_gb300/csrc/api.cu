@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -117,12 +118,47 @@ tc_status check_dims(int64_t m, int64_t n, int64_t k) {
 
 tc_status enqueue(cudaError_t e, const char* what) { return e == cudaSuccess ? TC_OK : cuda_fail(e, what); }
 
+// ---- autotune table: shape class -> fastest configuration measured in this process
+struct TuneKey {
+    int dt, lm, ln, lk;  // log2 of m, n, k rounded up to a power of two
+    bool operator<(const TuneKey& o) const {
+        return dt != o.dt ? dt < o.dt : lm != o.lm ? lm < o.lm : ln != o.ln ? ln < o.ln : lk < o.lk;
+    }
+};
+struct TuneCfg {
+    int pair, group_m;
+    double ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneCfg> g_tune;
+thread_local int g_force_pair = -1;   // set while the autotuner times a candidate
+thread_local int g_force_group = 0;
+
+int ceil_log2(int64_t v) {
+    int l = 0;
+    while ((int64_t(1) << l) < v && l < 62) ++l;
+    return l;
+}
+TuneKey tune_key(int dt, int64_t m, int64_t n, int64_t k) { return {dt, ceil_log2(m), ceil_log2(n), ceil_log2(k)}; }
+
+bool tune_lookup(int dt, int64_t m, int64_t n, int64_t k, TuneCfg* out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(dt, m, n, k));
+    if (it == g_tune.end()) return false;
+    *out = it->second;
+    return true;
+}
+
 // Tile choice of the tensor-core GEMM: 256 x 256 tiles on CTA pairs unless
-// the problem has at most 128 rows.  TCGEMM_TILE=single|pair forces one.
-bool use_pair_tiles(int64_t m) {
+// the problem has at most 128 rows.  TCGEMM_TILE=single|pair forces one; the
+// autotune table (tc_autotune_gemm) overrides the default for its shapes.
+bool use_pair_tiles(int64_t m, int dt = -1, int64_t n = 0, int64_t k = 0) {
+    if (g_force_pair >= 0) return g_force_pair != 0;
     const char* env = getenv("TCGEMM_TILE");
     if (env && strcmp(env, "single") == 0) return false;
     if (env && strcmp(env, "pair") == 0) return true;
+    TuneCfg c;
+    if (dt >= 0 && tune_lookup(dt, m, n, k, &c)) return c.pair != 0;
     return m > 128;
 }
 
@@ -134,11 +170,16 @@ int take_stall() {
     return v;
 }
 
-// Tile raster band of the tensor-core GEMM in M-tiles (TCGEMM_GROUP_M, default 16).
-int gemm_group_m() {
+// Tile raster band of the tensor-core GEMM in M-tiles (TCGEMM_GROUP_M, then the
+// autotune table, default 16).
+int gemm_group_m(int dt = -1, int64_t m = 0, int64_t n = 0, int64_t k = 0) {
+    if (g_force_group > 0) return g_force_group;
     const char* env = getenv("TCGEMM_GROUP_M");
     const int v = env ? atoi(env) : 0;
-    return (v >= 1 && v <= 1024) ? v : 16;
+    if (v >= 1 && v <= 1024) return v;
+    TuneCfg c;
+    if (dt >= 0 && tune_lookup(dt, m, n, k, &c)) return c.group_m;
+    return 16;
 }
 
 // Epilogue of the pair GEMM: stage 32 x 32 chunks in shared memory (default) or store rows
@@ -271,8 +312,8 @@ tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, c
     p.ab_format = dt == TC_BF16 ? 1 : 0;
     p.na = p.nb = p.nprod = 1;
     p.bn = 256;
-    p.pair = use_pair_tiles(m) ? 1 : 0;
-    p.group_m = gemm_group_m();
+    p.pair = use_pair_tiles(m, dt, n, k) ? 1 : 0;
+    p.group_m = gemm_group_m(dt, m, n, k);
     p.stall_at = take_stall();
     p.staged_epilogue = gemm_staged_epilogue();
     p.m = m; p.n = n; p.k = k;
@@ -440,6 +481,7 @@ struct tc_grouped_plan {
     const void* maps_a = nullptr;  // bases the device maps were encoded for
     const void* maps_b = nullptr;
     int* status = nullptr;
+    int variant = -1;  // autotuned: 0 tensor cores + staged epilogue, 1 tensor cores + direct, 2 mma.sync
 };
 
 namespace {
@@ -470,9 +512,10 @@ tc_status grouped_upload_maps(tc_grouped_plan* plan, const void* a_base, const v
 
 cudaError_t grouped_launch(tc_grouped_plan* plan, const void* a_base, const void* b_base, float* c_base, float alpha,
                            float beta, cudaStream_t st) {
-    if (plan->use_tc)
+    if (plan->use_tc && plan->variant != 2)
         return tcg::launch_grouped_tc(plan->dt, plan->d_tc_tiles, plan->tc_tiles, plan->d_maps, c_base, alpha, beta,
-                                      plan->status, plan->sm_count, st);
+                                      plan->status, plan->sm_count, st,
+                                      plan->variant < 0 ? -1 : (plan->variant == 0 ? 1 : 0));
     return tcg::launch_grouped(plan->dt, plan->lb, plan->d_probs, plan->d_tiles, plan->num_tiles, a_base, b_base,
                                c_base, alpha, beta, plan->sm_count, st);
 }
@@ -784,3 +827,159 @@ extern "C" tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_pr
                                        d->sm_count, st),
                    "gemm_grouped_noalloc launch");
 }
+
+// ------------------------------------------------------------ autotuning
+
+namespace {
+
+// Mean time of `iters` launches after `warm`, with CUDA events on `st`.
+template <typename F>
+tc_status time_ms(F&& launch, cudaStream_t st, int warm, int iters, double* ms_out) {
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune: event");
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(e, "autotune: event");
+    }
+    tc_status s = TC_OK;
+    for (int i = 0; i < warm && s == TC_OK; ++i) s = launch();
+    cudaEventRecord(e0, st);
+    for (int i = 0; i < iters && s == TC_OK; ++i) s = launch();
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (s == TC_OK && e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != TC_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(e, "autotune: synchronize");
+    *ms_out = ms / iters;
+    return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tc_status tc_autotune_gemm(int32_t dt, int64_t m, int64_t n, int64_t k, void* stream, double* best_ms) {
+    if (dt != TC_F16 && dt != TC_BF16 && dt != TC_E4M3) return fail(TC_ERR_INVALID, "tc_autotune_gemm: bad dtype");
+    tc_status s = check_dims(m, n, k);
+    if (s != TC_OK) return s;
+    if (m < 1 || n < 1 || k < 1) return fail(TC_ERR_INVALID, "tc_autotune_gemm: empty problem");
+    Device* d;
+    if ((s = get_device(&d)) != TC_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    const int esz = elem_size(dt);
+    const int64_t kp = (k + 15) / 16 * 16;
+    const size_t a_bytes = size_t(m) * kp * esz, b_bytes = size_t(n) * kp * esz, c_bytes = size_t(m) * n * 4;
+    void* buf = nullptr;
+    cudaError_t e = cudaMallocAsync(&buf, a_bytes + b_bytes + c_bytes + 256 * 3 + 8, st);
+    if (e != cudaSuccess) return fail(TC_ERR_OOM, "tc_autotune_gemm: scratch: %s", cudaGetErrorString(e));
+    uint8_t* A = static_cast<uint8_t*>(buf);
+    uint8_t* B = A + (a_bytes + 255) / 256 * 256;
+    float* C = reinterpret_cast<float*>(B + (b_bytes + 255) / 256 * 256);
+    float* scales = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(C) + (c_bytes + 255) / 256 * 256);
+    // operands of moderate magnitude (byte 0x3C: 1.05 in FP16, 0.0117 in BF16, 1.5 in E4M3)
+    cudaMemsetAsync(A, 0x3C, a_bytes, st);
+    cudaMemsetAsync(B, 0x3C, b_bytes, st);
+    cudaMemsetAsync(C, 0, c_bytes, st);
+    const float ones[2] = {1.0f, 1.0f};
+    cudaMemcpyAsync(scales, ones, sizeof(ones), cudaMemcpyHostToDevice, st);
+    const int pairs[2] = {0, 1};
+    const int groups[3] = {8, 16, 32};
+    TuneCfg best{-1, 16, 1e30};
+    for (int pi = 0; pi < 2 && s == TC_OK; ++pi) {
+        if (pairs[pi] == 1 && m <= 128) continue;  // a pair tile would leave half of it empty
+        for (int gi = 0; gi < 3 && s == TC_OK; ++gi) {
+            g_force_pair = pairs[pi];
+            g_force_group = groups[gi];
+            double ms = 0;
+            s = time_ms([&] {
+                return gemm_mixed(dt, m, n, k, 1.0f, A, kp, TC_ROW_MAJOR, B, kp, TC_COL_MAJOR, 0.0f, C, n,
+                                  dt == TC_E4M3 ? scales : nullptr, dt == TC_E4M3 ? scales + 1 : nullptr, st);
+            }, st, 2, 5, &ms);
+            g_force_pair = -1;
+            g_force_group = 0;
+            if (s == TC_OK && ms < best.ms) best = {pairs[pi], groups[gi], ms};
+        }
+    }
+    cudaFreeAsync(buf, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (s != TC_OK) return s;
+    if (e2 != cudaSuccess) return cuda_fail(e2, "tc_autotune_gemm: synchronize");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[tune_key(dt, m, n, k)] = best;
+    }
+    if (best_ms) *best_ms = best.ms;
+    return TC_OK;
+}
+
+tc_status gemm_grouped_plan_autotune(tc_grouped_plan* plan, const void* a_base, const void* b_base, float* c_base,
+                                     void* stream, double* best_ms) {
+    if (!plan) return fail(TC_ERR_INVALID, "grouped autotune: null plan");
+    cudaStream_t st = as_stream(stream);
+    const int variants[3] = {0, 1, 2};
+    const int nvar = plan->use_tc ? 3 : 1;
+    double best = 1e30;
+    int best_v = plan->use_tc ? 0 : 2;
+    for (int i = 0; i < nvar; ++i) {
+        plan->variant = plan->use_tc ? variants[i] : 2;
+        double ms = 0;
+        tc_status s = time_ms([&] { return gemm_grouped_plan_run(plan, a_base, b_base, c_base, 1.0f, 0.0f, 0, stream); },
+                              st, 1, 3, &ms);
+        if (s != TC_OK) {
+            plan->variant = -1;
+            return s;
+        }
+        if (ms < best) {
+            best = ms;
+            best_v = plan->variant;
+        }
+    }
+    plan->variant = best_v;
+    if (plan->exec) {  // a recorded graph holds the previous variant
+        cudaGraphExecDestroy(plan->exec);
+        plan->exec = nullptr;
+    }
+    if (best_ms) *best_ms = best;
+    return TC_OK;
+}
+
+tc_status tc_autotune_save(const char* path) {
+    if (!path) return fail(TC_ERR_INVALID, "tc_autotune_save: null path");
+    FILE* f = fopen(path, "w");
+    if (!f) return fail(TC_ERR_INVALID, "tc_autotune_save: cannot open %s", path);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    fprintf(f, "# tcgemm autotune: dt log2m log2n log2k pair group_m ms\n");
+    for (const auto& kv : g_tune)
+        fprintf(f, "%d %d %d %d %d %d %.6f\n", kv.first.dt, kv.first.lm, kv.first.ln, kv.first.lk, kv.second.pair,
+                kv.second.group_m, kv.second.ms);
+    fclose(f);
+    return TC_OK;
+}
+
+tc_status tc_autotune_load(const char* path) {
+    if (!path) return fail(TC_ERR_INVALID, "tc_autotune_load: null path");
+    FILE* f = fopen(path, "r");
+    if (!f) return fail(TC_ERR_INVALID, "tc_autotune_load: cannot open %s", path);
+    char line[256];
+    int n = 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    while (fgets(line, sizeof(line), f)) {
+        if (line[0] == '#') continue;
+        TuneKey key;
+        TuneCfg cfg;
+        if (sscanf(line, "%d %d %d %d %d %d %lf", &key.dt, &key.lm, &key.ln, &key.lk, &cfg.pair, &cfg.group_m,
+                   &cfg.ms) == 7 &&
+            (cfg.pair == 0 || cfg.pair == 1) && cfg.group_m >= 1 && cfg.group_m <= 1024) {
+            g_tune[key] = cfg;
+            ++n;
+        }
+    }
+    fclose(f);
+    return n > 0 ? TC_OK : fail(TC_ERR_INVALID, "tc_autotune_load: no entries in %s", path);
+}
+
+}  // extern "C"

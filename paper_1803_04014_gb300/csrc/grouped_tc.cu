@@ -343,7 +343,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
 int grouped_tc_box_rows(int n) { return mma_n(n); }
 
 cudaError_t launch_grouped_tc(int dt, const GroupedTcTile* tiles, int32_t num_tiles, const CUtensorMap* maps,
-                              float* c_base, float alpha, float beta, int* status, int sm_count, cudaStream_t st) {
+                              float* c_base, float alpha, float beta, int* status, int sm_count, cudaStream_t st,
+                              int staged) {
     if (num_tiles <= 0) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_grouped_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) return e;
@@ -356,8 +357,12 @@ cudaError_t launch_grouped_tc(int dt, const GroupedTcTile* tiles, int32_t num_ti
     a.beta = beta;
     a.ab_format = dt == 1 ? 1u : 0u;
     a.status = status;
-    const char* env = getenv("TCGEMM_GROUPED_EPI");
-    a.staged_epilogue = (env && strcmp(env, "direct") == 0) ? 0 : 1;
+    if (staged >= 0) {
+        a.staged_epilogue = staged;
+    } else {
+        const char* env = getenv("TCGEMM_GROUPED_EPI");
+        a.staged_epilogue = (env && strcmp(env, "direct") == 0) ? 0 : 1;
+    }
     const int grid = num_tiles < sm_count ? num_tiles : sm_count;
     k_grouped_tc<<<grid, kThreads, kSmem, st>>>(a);
     return cudaGetLastError();

@@ -77,8 +77,10 @@ struct alignas(16) GroupedTcTile {
     int64_t off_c, pad;       // element offset of C_g
 };
 int grouped_tc_box_rows(int n);
+// staged: 1 = epilogue through shared memory, 0 = direct row stores, -1 = TCGEMM_GROUPED_EPI or staged
 cudaError_t launch_grouped_tc(int dt, const GroupedTcTile* tiles, int32_t num_tiles, const CUtensorMap* maps,
-                              float* c_base, float alpha, float beta, int* status, int sm_count, cudaStream_t st);
+                              float* c_base, float alpha, float beta, int* status, int sm_count, cudaStream_t st,
+                              int staged = -1);
 
 // ---- errnorm.cu
 constexpr int kErrBlocks = 1024;  // fixed grid: the reduction order does not depend on the GPU

@@ -108,3 +108,21 @@ def test_serve_rejects_bad_config(lib):
     srv = ctypes.c_void_p()
     assert lib.serve_open(ctypes.byref(cfg), ctypes.byref(srv)) == b.TC_ERR_INVALID
     assert lib.serve_poll(None, 1, None) == b.TC_ERR_INVALID
+
+
+def test_autotune_table_save_and_load(lib, tmp_path):
+    from paper_1803_04014_gb300 import binding as b
+    good = tmp_path / "tune.txt"
+    good.write_text("# comment\n0 13 13 13 1 16 0.65\n1 10 10 10 0 8 0.01\n")
+    b.tc_autotune_load(good)
+    out = tmp_path / "out.txt"
+    b.tc_autotune_save(out)
+    lines = [l for l in out.read_text().splitlines() if not l.startswith("#")]
+    assert any(l.startswith("0 13 13 13 1 16") for l in lines)
+    assert any(l.startswith("1 10 10 10 0 8") for l in lines)
+    bad = tmp_path / "bad.txt"
+    bad.write_text("0 13 13 13 7 16 0.5\n")          # pair must be 0 or 1
+    with pytest.raises(b.TcError):
+        b.tc_autotune_load(bad)
+    with pytest.raises(b.TcError):
+        b.tc_autotune_load(tmp_path / "missing.txt")

@@ -488,3 +488,37 @@ def test_grouped_tc_large_problems_and_new_bases(b):
                 assert normwise_dev(got[c0:c0 + m * n].reshape(m, n), ref, A, B) <= TOL_NORMWISE, (m, n, k)
     finally:
         b.gemm_grouped_plan_destroy(plan)
+
+
+# ------------------------------------------------------------------ autotuner
+
+@pytest.mark.parametrize("dt", [0, 2])
+def test_autotuned_gemm_still_matches_oracle(b, dt):
+    m, n, k = 640, 768, 512
+    ms = b.tc_autotune_gemm(dt, m, n, k)
+    assert 0.0 < ms < 100.0
+    A = synth.uniform((m, k), seed=501)
+    B = synth.uniform((k, n), seed=502)
+    C = _run_mixed(b, dt, A, B)
+    ref = og.gemm_mixed(DT_NAME[dt], A, B)
+    assert normwise_dev(C, ref, A, B) <= TOL_NORMWISE
+
+
+def test_autotuned_grouped_plan_still_matches_oracle(b):
+    probs, abuf, bbuf, csize = _grouped_case(120, seed=503, lb=1)
+    desc = [p[:9] for p in probs]
+    Ad, Bd = dev(abuf, torch.float16), dev(bbuf, torch.float16)
+    C = torch.zeros(csize, dtype=torch.float32, device="cuda")
+    plan = b.gemm_grouped_plan_create(0, desc, 0, 1)
+    try:
+        ms = b.gemm_grouped_plan_autotune(plan, Ad, Bd, C)
+        assert 0.0 < ms < 100.0
+        C.zero_()
+        b.gemm_grouped_plan_run(plan, Ad, Bd, C, 1.0, 0.0, use_graph=1)
+        b.tc_sync_status()
+        got = host(C)
+    finally:
+        b.gemm_grouped_plan_destroy(plan)
+    for (m, n, k, a0, b0, c0, lda, ldb, ldc, A, B) in probs:
+        ref = og.gemm_mixed("f16", A, B)
+        assert normwise_dev(got[c0:c0 + m * n].reshape(m, n), ref, A, B) <= TOL_NORMWISE
