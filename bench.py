@@ -367,6 +367,25 @@ def measure_rows(b, A, B, pk, sm_count):
 
     out["batched16_sweep"] = _row(batched_sweep)
     torch.cuda.empty_cache()
+    def error_norm():
+        # the FP64 error reduction of a refined N=8192 result: C (FP32), C64 (FP64), A and B (FP32)
+        Cd = torch.empty((N, N), dtype=torch.float32, device="cuda").uniform_(-1, 1)
+        C64 = Cd.double() + 1e-7
+        Ad = torch.empty((N, N), dtype=torch.float32, device="cuda").uniform_(-1, 1)
+        Bd = torch.empty((N, N), dtype=torch.float32, device="cuda").uniform_(-1, 1)
+        f = lambda: b.tc_error_norm(N, N, Cd, N, C64, N, 1, Ad, N, N, N, Bd, N, N, N)
+        for _ in range(2):
+            f()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            f()
+        ms = (time.perf_counter() - t0) / 5 * 1e3   # the call synchronises and returns host values
+        byts = N * N * (4 + 8 + 4 + 4)
+        return {"ms": ms, "gbs": byts / (ms * 1e-3) / 1e9, "frac_of_hbm": byts / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
+                "bytes": byts, "note": "host wall time of the synchronising call (two kernels + 32-byte read-back)"}
+
+    out["error_norm_n8192"] = _row(error_norm)
+    torch.cuda.empty_cache()
     out["serve"] = _row(lambda: measure_serve(b))
     return out
 

@@ -45,6 +45,16 @@ __device__ __forceinline__ double block_max(double v, double* red) {
     return s;
 }
 
+// Fixed assignment of a rows x cols matrix to the kErrBlocks x kErrThreads
+// threads: thread (b, t) visits rows b, b + kErrBlocks, ... and in each row the
+// columns t, t + kErrThreads, ...  No division per element, coalesced rows, and
+// the same order on every GPU.
+template <typename F>
+__device__ __forceinline__ void for_each_mine(int64_t rows, int64_t cols, F&& f) {
+    for (int64_t r = blockIdx.x; r < rows; r += kErrBlocks)
+        for (int64_t c = threadIdx.x; c < cols; c += kErrThreads) f(r, c);
+}
+
 // partial layout: [3][kErrBlocks][2] = (sum, max) for (C - ref), A, B
 __global__ void __launch_bounds__(kErrThreads) k_err_partials(int64_t m, int64_t n, const float* __restrict__ C,
                                                               int64_t ldc, const void* __restrict__ ref, int64_t ldr,
@@ -53,19 +63,21 @@ __global__ void __launch_bounds__(kErrThreads) k_err_partials(int64_t m, int64_t
                                                               int64_t br, int64_t bc, int64_t ldb,
                                                               double* __restrict__ partial) {
     __shared__ double red[32];
-    const int64_t stride = (int64_t)kErrBlocks * kErrThreads;
-    const int64_t first = (int64_t)blockIdx.x * kErrThreads + threadIdx.x;
-
     double s = 0.0, mx = 0.0;
-    const int64_t tc = m * n;
-    for (int64_t i = first; i < tc; i += stride) {
-        const int64_t r = i / n, c = i - r * n;
-        const double x = static_cast<double>(C[r * ldc + c]);
-        const double y = ref_f64 ? static_cast<const double*>(ref)[r * ldr + c]
-                                 : static_cast<double>(static_cast<const float*>(ref)[r * ldr + c]);
-        const double d = x - y;
-        s += d * d;
-        mx = fmax(mx, fabs(d));
+    if (ref_f64) {
+        const double* R = static_cast<const double*>(ref);
+        for_each_mine(m, n, [&](int64_t r, int64_t c) {
+            const double d = static_cast<double>(C[r * ldc + c]) - R[r * ldr + c];
+            s += d * d;
+            mx = fmax(mx, fabs(d));
+        });
+    } else {
+        const float* R = static_cast<const float*>(ref);
+        for_each_mine(m, n, [&](int64_t r, int64_t c) {
+            const double d = static_cast<double>(C[r * ldc + c]) - static_cast<double>(R[r * ldr + c]);
+            s += d * d;
+            mx = fmax(mx, fabs(d));
+        });
     }
     double bs = block_sum(s, red);
     double bm = block_max(mx, red);
@@ -80,12 +92,12 @@ __global__ void __launch_bounds__(kErrThreads) k_err_partials(int64_t m, int64_t
     for (int w = 0; w < 2; ++w) {
         double t = 0.0;
         if (mats[w] != nullptr) {
-            const int64_t tot = rows[w] * cols[w];
-            for (int64_t i = first; i < tot; i += stride) {
-                const int64_t r = i / cols[w], c = i - r * cols[w];
-                const double x = static_cast<double>(mats[w][r * lds[w] + c]);
+            const float* X = mats[w];
+            const int64_t ld = lds[w];
+            for_each_mine(rows[w], cols[w], [&](int64_t r, int64_t c) {
+                const double x = static_cast<double>(X[r * ld + c]);
                 t += x * x;
-            }
+            });
         }
         const double bt = block_sum(t, red);
         if (threadIdx.x == 0) {
