@@ -21,6 +21,8 @@ summation, which the pins bound.
 * ``gemm_split_scaled`` -- the same refinement with residuals scaled by 2^s
   before rounding (Ootomo and Yokota, 2022) and the correction products
   summed apart and multiplied by 2^-s.
+* ``gemm_split_bf16x3`` -- three BF16 pieces per operand and the six
+  products whose piece orders add up to at most 2 (Henry et al., 2019).
 * ``gemm_truth``  -- alpha*A*B + beta*C0 on the unrounded FP32 inputs.
 * ``gemm_grouped`` / ``gemm_batched`` -- Sec. IV-B: independent problems.
 * ``normwise_error`` / ``max_error`` -- ||C - C_ref||_F / (||A||_F ||B||_F)
@@ -38,6 +40,10 @@ PRODUCTS = {
     3: ((0, 0), (1, 0), (0, 1)),          # Eq. 2 without R_A R_B
     4: ((0, 0), (1, 0), (0, 1), (1, 1)),  # Eq. 2
 }
+
+
+# three-piece BF16 split: (A piece, B piece) with piece order sum <= 2, largest first
+PRODUCTS_BF16X3 = ((0, 0), (1, 0), (0, 1), (2, 0), (1, 1), (0, 2))
 
 
 def _f64(x) -> np.ndarray:
@@ -123,6 +129,33 @@ def gemm_split_scaled(piece: str, nprod: int, A, B, alpha: float = 1.0, beta: fl
     if nprod == 3:
         corr = corr + Ah @ Bl
     acc = Ah @ Bh + np.ldexp(corr, -numerics.SPLIT_SCALE_EXP[piece])
+    if C0 is not None and beta != 0.0:
+        C0 = _f64(C0)
+        if rows is not None:
+            C0 = C0[rows]
+        if cols is not None:
+            C0 = C0[:, cols]
+    return _epilogue(acc, alpha, beta, C0)
+
+
+def gemm_split_bf16x3(A, B, alpha: float = 1.0, beta: float = 0.0, C0=None,
+                      rows=None, cols=None) -> np.ndarray:
+    """C = alpha * sum_{i+j<=2} A_i B_j + beta*C0 over the BF16 triples of A and B.
+
+    The dropped products A_1 B_2, A_2 B_1 and A_2 B_2 are each below 2^-24 of
+    |a||b|, the unit roundoff of FP32.
+    """
+    A = _f64(A)
+    B = _f64(B)
+    if rows is not None:
+        A = A[rows]
+    if cols is not None:
+        B = B[:, cols]
+    Ap = numerics.split_bf16x3(A)
+    Bp = numerics.split_bf16x3(B)
+    acc = np.zeros((A.shape[0], B.shape[1]), dtype=np.float64)
+    for pa, pb in PRODUCTS_BF16X3:
+        acc += Ap[pa] @ Bp[pb]
     if C0 is not None and beta != 0.0:
         C0 = _f64(C0)
         if rows is not None:

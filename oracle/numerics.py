@@ -144,6 +144,27 @@ def split_scaled(x, piece: str):
     return hi, lo
 
 
+def split_bf16x3(x):
+    """(p0, p1, p2): three BF16 pieces, p0 = round(x), p1 = round(x - p0),
+    p2 = round(x - p0 - p1).
+
+    Generalisation of the residual split of Sec. V (Eq. 1 / Eq. 2) to a third
+    piece, in the way Henry, Tang and Heinecke (2019, "Leveraging the bfloat16
+    artificial intelligence datatype for higher-precision computations") split
+    FP32 into BF16 triples: three 8-bit significands hold the 24 bits of an
+    FP32 value, so p0 + p1 + p2 == x whenever no piece falls below the BF16
+    normal range.  BF16 has the exponent range of FP32, so unlike FP16 pieces
+    nothing overflows.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    p0 = round_to(x, "bf16")
+    with np.errstate(invalid="ignore"):
+        r = x - p0
+        p1 = round_to(r, "bf16")
+        p2 = round_to(r - p1, "bf16")
+    return p0, p1, p2
+
+
 # --- bit encodings (used to compare device outputs bit for bit) -------------
 
 def f16_bits(values) -> np.ndarray:

@@ -270,3 +270,51 @@ def test_scaled_split_beta_alpha():
     assert np.allclose(b_ - a, -C0.astype(np.float64), rtol=0, atol=1e-14)
     with pytest.raises(ValueError):
         og.gemm_split_scaled("f16", 4, A, B)
+
+
+def _bits_matrix(shape, bits, seed, e_span=40):
+    """FP32 values with exactly `bits` significant bits and exponents over e_span binades."""
+    n = int(np.prod(shape))
+    ints = (synth.words(n, seed=seed) & np.uint32((1 << (bits - 1)) - 1)).astype(np.float64) + float(1 << (bits - 1))
+    e = (synth.words(n, seed=seed + 1) % e_span).astype(np.float64) - e_span // 2
+    sgn = np.where(synth.words(n, seed=seed + 2) & np.uint32(1), -1.0, 1.0)
+    return (sgn * ints * 2.0 ** (e - (bits - 1))).astype(np.float32).reshape(shape)
+
+
+@pytest.mark.parametrize("bits_a,bits_b", [(16, 16), (24, 8), (8, 24)])
+def test_bf16x3_products_are_exact_when_the_dropped_pieces_vanish(bits_a, bits_b):
+    # the kept products are (0,0) (1,0) (0,1) (2,0) (1,1) (0,2): with 16-bit operands the third
+    # pieces are zero, with 8-bit B its second and third pieces are, so every one of these cases
+    # needs exactly the products that are kept and the result is the FP32 inputs' product
+    K = 96
+    A = _bits_matrix((20, K), bits_a, 80)
+    B = _bits_matrix((K, 12), bits_b, 90)
+    truth = og.gemm_truth(A, B)
+    mag = np.abs(A.astype(np.float64)) @ np.abs(B.astype(np.float64))
+    got = og.gemm_split_bf16x3(A, B)
+    assert np.all(np.abs(got - truth) <= 6 * K * 2.0 ** -52 * mag)
+
+
+def test_bf16x3_error_is_below_fp32_roundoff():
+    # dropped terms A1 B2 + A2 B1 + A2 B2 are at most (2^-24 + 2^-24 + 2^-32) |a||b| each
+    K = 64
+    A = _bits_matrix((24, K), 24, 100)
+    B = _bits_matrix((K, 16), 24, 110)
+    truth = og.gemm_truth(A, B)
+    mag = np.abs(A.astype(np.float64)) @ np.abs(B.astype(np.float64))
+    got = og.gemm_split_bf16x3(A, B)
+    assert np.all(np.abs(got - truth) <= (2.0 ** -23 + 2.0 ** -31 + 6 * K * 2.0 ** -52) * mag)
+    # the two-piece BF16 refinement is far less accurate on the same inputs
+    two = og.gemm_split("bf16", 4, A, B)
+    assert og.normwise_error(two, truth, A, B) > 100 * og.normwise_error(got, truth, A, B)
+
+
+def test_bf16x3_alpha_beta():
+    A = synth.uniform((8, 32), seed=120)
+    B = synth.uniform((32, 8), seed=121)
+    C0 = synth.uniform((8, 8), seed=122)
+    a = og.gemm_split_bf16x3(A, B, alpha=-2.0)
+    b_ = og.gemm_split_bf16x3(A, B, alpha=-2.0, beta=0.5, C0=C0)
+    assert np.allclose(b_ - a, 0.5 * C0.astype(np.float64), rtol=0, atol=1e-14)
+    assert np.array_equal(og.gemm_split_bf16x3(A, B, rows=[3, 1], cols=[0, 7]),
+                          og.gemm_split_bf16x3(A, B)[[3, 1]][:, [0, 7]])

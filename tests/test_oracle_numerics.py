@@ -231,3 +231,38 @@ def test_scaled_split_bf16():
     hs, ls = nm.split_scaled(x, "bf16")
     r = x.astype(np.float64) - hs
     assert np.all(np.abs(np.ldexp(r, 8) - ls) <= 2.0 ** -8 * np.abs(np.ldexp(r, 8)))
+
+
+# ---- three-piece BF16 split (Henry, Tang and Heinecke, 2019) --------------------
+
+def test_bf16x3_pieces_sum_to_x_over_the_fp32_range():
+    # FP32 values with random 24-bit significands over 200 binades: three 8-bit pieces hold them
+    n = 40000
+    ints = (synth.words(n, seed=18) & np.uint32((1 << 23) - 1)).astype(np.float64) + float(1 << 23)
+    e = (synth.words(n, seed=19) % 200).astype(np.float64) - 100.0
+    sgn = np.where(synth.words(n, seed=20) & np.uint32(1), -1.0, 1.0)
+    x = (sgn * ints * 2.0 ** (e - 23)).astype(np.float32)
+    x64 = x.astype(np.float64)
+    p0, p1, p2 = nm.split_bf16x3(x)
+    assert np.array_equal(p0 + p1 + p2, x64)
+    for p in (p0, p1, p2):
+        assert np.array_equal(nm.round_to(p, "bf16"), p)
+    # each piece is at most half an ulp (2^-8 relative) of what is left before it
+    assert np.all(np.abs(p1) <= 2.0 ** -8 * np.abs(x64))
+    assert np.all(np.abs(p2) <= 2.0 ** -8 * np.abs(x64 - p0))
+    # the first piece is the plain BF16 rounding, the second the plain BF16 residual
+    h, l = nm.split(x, "bf16")
+    assert np.array_equal(p0, h) and np.array_equal(p1, l)
+
+
+def test_bf16x3_short_significands_leave_zero_pieces():
+    n = 5000
+    e = (synth.words(n, seed=21) % 60).astype(np.float64) - 30.0
+    b8 = (synth.words(n, seed=22) & np.uint32(0x7F)).astype(np.float64) + 128.0        # 8 bits
+    b16 = (synth.words(n, seed=23) & np.uint32(0x7FFF)).astype(np.float64) + 32768.0   # 16 bits
+    x8 = (b8 * 2.0 ** (e - 7)).astype(np.float32)
+    x16 = (b16 * 2.0 ** (e - 15)).astype(np.float32)
+    p0, p1, p2 = nm.split_bf16x3(x8)
+    assert np.array_equal(p0, x8.astype(np.float64)) and not np.any(p1) and not np.any(p2)
+    p0, p1, p2 = nm.split_bf16x3(x16)
+    assert np.array_equal(p0 + p1, x16.astype(np.float64)) and not np.any(p2)
