@@ -141,7 +141,8 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--rows", choices=["all", "none"], default="all", help="also measure the other rows (N=1 only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--profile-gemm", choices=["f16", "bf16", "e4m3", "split3", "grouped", "batched16"], default=None,
+    p.add_argument("--profile-gemm", choices=["f16", "bf16", "e4m3", "split3", "split3_scaled", "bf16x3", "grouped",
+                                              "batched16"], default=None,
                    help="only round the N=8192 inputs and run 5 GEMM launches (a small case for ncu captures)")
     return p.parse_args()
 
@@ -272,16 +273,26 @@ def measure_rows(b, A, B, pk, sm_count):
         Bs = synth.log_uniform_pow2((N, N), seed=synth.seed_for(2, 1))
         Ad, Bd = torch.from_numpy(As).cuda(), torch.from_numpy(Bs).cuda()
         C = torch.empty((N, N), dtype=torch.float32, device="cuda")
-        ws_bytes = b.gemm_split_workspace_bytes(0, 4, N, N, N)
+        ws_bytes = max(b.gemm_split_workspace_bytes(0, 4, N, N, N), b.gemm_split_workspace_bytes(1, 6, N, N, N))
         ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
         res = {"inputs": "sign * 2^e * m, e uniform in {-8..7}, m in [1,2) (24-bit significands)"}
-        for nprod in (2, 3, 4):
-            g = lambda: b.gemm_split(0, nprod, N, N, N, 1.0, Ad, N, 0, Bd, N, 0, 0.0, C, N, ws, ws_bytes)
+
+        def one(name, nprod, g):
             ms = _time_ms(g, 5)
             tf = flops / (ms * 1e-3) / 1e12
-            res[f"split{nprod}_f16"] = {"ms": ms, "effective_tflops": tf, "executed_tflops": nprod * tf,
-                                        "frac_of_peak_effective": tf / peak,
-                                        "error_vs_fp64": _sampled_errors(C, As, Bs, srows)}
+            res[name] = {"ms": ms, "effective_tflops": tf, "executed_tflops": nprod * tf,
+                         "frac_of_peak_effective": tf / peak,
+                         "error_vs_fp64": _sampled_errors(C, As, Bs, srows)}
+
+        for nprod in (2, 3, 4):
+            one(f"split{nprod}_f16", nprod,
+                lambda: b.gemm_split(0, nprod, N, N, N, 1.0, Ad, N, 0, Bd, N, 0, 0.0, C, N, ws, ws_bytes))
+        # scaled residuals (hi x hi and the corrections in separate accumulators)
+        for nprod in (2, 3):
+            one(f"split{nprod}_scaled_f16", nprod,
+                lambda: b.gemm_split_scaled(0, nprod, N, N, N, 1.0, Ad, N, 0, Bd, N, 0, 0.0, C, N, ws, ws_bytes))
+        # three BF16 pieces, six products
+        one("bf16x3", 6, lambda: b.gemm_split_bf16x3(N, N, N, 1.0, Ad, N, 0, Bd, N, 0, 0.0, C, N, ws, ws_bytes))
         Aq = torch.empty((N, N), dtype=torch.float16, device="cuda")
         Bq = torch.empty((N, N), dtype=torch.float16, device="cuda")
         b.tc_quantize(0, N, N, Ad, N, Aq, N, 0)
@@ -480,11 +491,16 @@ def profile_case(kind):
     A = torch.from_numpy(synth.uniform((N, N), seed=synth.seed_for(1, 0))).cuda()
     B = torch.from_numpy(synth.uniform((N, N), seed=synth.seed_for(1, 1))).cuda()
     C = torch.zeros((N, N), dtype=torch.float32, device="cuda")
-    if kind == "split3":
-        ws_bytes = b.gemm_split_workspace_bytes(0, 3, N, N, N)
+    if kind in ("split3", "split3_scaled", "bf16x3"):
+        ws_bytes = b.gemm_split_workspace_bytes(1, 6 if kind == "bf16x3" else 3, N, N, N)
         ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
         for _ in range(5):
-            b.gemm_split(0, 3, N, N, N, 1.0, A, N, 0, B, N, 0, 0.0, C, N, ws, ws_bytes)
+            if kind == "split3":
+                b.gemm_split(0, 3, N, N, N, 1.0, A, N, 0, B, N, 0, 0.0, C, N, ws, ws_bytes)
+            elif kind == "split3_scaled":
+                b.gemm_split_scaled(0, 3, N, N, N, 1.0, A, N, 0, B, N, 0, 0.0, C, N, ws, ws_bytes)
+            else:
+                b.gemm_split_bf16x3(N, N, N, 1.0, A, N, 0, B, N, 0, 0.0, C, N, ws, ws_bytes)
     else:
         dt = {"f16": 0, "bf16": 1, "e4m3": 2}[kind]
         tdt = {0: torch.float16, 1: torch.bfloat16, 2: torch.uint8}[dt]

@@ -102,6 +102,21 @@ tc_status tc_quantize(int32_t dt, int64_t rows, int64_t cols, const float* src, 
 tc_status tc_split(int32_t piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src,
                    int32_t transpose, void* dst_hi, void* dst_lo, int64_t ld_dst, void* stream);
 
+/* Scaled residual split (Ootomo and Yokota, 2022, refining Sec. V):
+ *   hi = RNE(x), lo = RNE((x - hi) * 2^s), s = 11 for TC_F16, 8 for TC_BF16.
+ *   The scaling keeps residuals of small |x| in the normal range of the
+ *   16-bit format (an FP16 residual below 2^-14 would lose bits).  Arguments,
+ *   layouts and errors as tc_split. */
+tc_status tc_split_scaled(int32_t piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src,
+                          int32_t transpose, void* dst_hi, void* dst_lo, int64_t ld_dst, void* stream);
+
+/* Three BF16 pieces (Sec. V's split carried one piece further, as Henry, Tang
+ * and Heinecke, 2019): p0 = RNE(x), p1 = RNE(x - p0), p2 = RNE(x - p0 - p1);
+ * p0 + p1 + p2 == x for FP32 x whose pieces stay in the normal range.
+ *   dst0, dst1, dst2: BF16 outputs, 2-byte aligned; otherwise as tc_split. */
+tc_status tc_split_bf16x3(int64_t rows, int64_t cols, const float* src, int64_t ld_src, int32_t transpose,
+                          void* dst0, void* dst1, void* dst2, int64_t ld_dst, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* GEMM on tensor cores (Sec. IV: C = alpha*A*B + beta*C; FP32 accumulation) */
 /* ------------------------------------------------------------------------ */
@@ -124,7 +139,8 @@ tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha,
                      float beta, float* C, int64_t ldc,
                      const float* scale_a, const float* scale_b, void* stream);
 
-/* Bytes of workspace gemm_split needs for these sizes. */
+/* Bytes of workspace gemm_split, gemm_split_scaled (nprod 2-4: two pieces per
+ * operand) or gemm_split_bf16x3 (nprod = 6: three pieces) needs. */
 size_t gemm_split_workspace_bytes(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k);
 
 /* Precision refinement (Sec. V, Eq. 1 and Eq. 2) in one accumulator:
@@ -145,6 +161,35 @@ tc_status gemm_split(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t
                      const float* B, int64_t ldb, int32_t lb,
                      float beta, float* C, int64_t ldc,
                      void* workspace, size_t workspace_bytes, void* stream);
+
+/* Refinement with scaled residuals (Ootomo and Yokota, 2022):
+ *   C = alpha * (A_hi B_hi + 2^-s (A_lo' B_hi [+ A_hi B_lo'])) + beta * C,
+ *   lo' = RNE((x - hi) * 2^s) as tc_split_scaled; nprod = 2 keeps Eq. 1's
+ *   pair of products, nprod = 3 Eq. 2 without R_A R_B.
+ * A_hi B_hi accumulates in one TMEM accumulator whose partial sums are added
+ * into round-to-nearest FP32 registers every 128 of K; the correction
+ * products accumulate in a second TMEM accumulator over all of K and are
+ * scaled by 2^-s once per output tile.  piece: TC_F16 or TC_BF16.
+ * Arguments, workspace and errors otherwise as gemm_split. */
+tc_status gemm_split_scaled(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k, float alpha,
+                            const float* A, int64_t lda, int32_t la,
+                            const float* B, int64_t ldb, int32_t lb,
+                            float beta, float* C, int64_t ldc,
+                            void* workspace, size_t workspace_bytes, void* stream);
+
+/* Refinement with three BF16 pieces per operand (tc_split_bf16x3):
+ *   C = alpha * sum_{i + j <= 2} A_i B_j + beta * C  (six products),
+ * FP32-level accuracy over the whole FP32 exponent range, where FP16 pieces
+ * overflow or underflow.  A_0 B_0 is promoted to round-to-nearest FP32
+ * registers every 128 of K; the five correction products accumulate in a
+ * second TMEM accumulator, as in gemm_split_scaled.  Workspace:
+ * gemm_split_workspace_bytes(TC_BF16, 6, m, n, k).  Arguments and errors
+ * otherwise as gemm_split. */
+tc_status gemm_split_bf16x3(int64_t m, int64_t n, int64_t k, float alpha,
+                            const float* A, int64_t lda, int32_t la,
+                            const float* B, int64_t ldb, int32_t lb,
+                            float beta, float* C, int64_t ldc,
+                            void* workspace, size_t workspace_bytes, void* stream);
 
 /* FP32 GEMM on the CUDA cores (no tensor cores): the paper's sgemm
  * comparison (Sec. VII-A, VII-B).  Any layouts; C row-major. */

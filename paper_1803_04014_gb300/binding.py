@@ -78,7 +78,13 @@ SIGNATURES = {
     "tc_split": (_i32, [_i32, _i64, _i64, _vp, _i64, _i32, _vp, _vp, _i64, _vp]),
     "gemm_mixed": (_i32, [_i32, _i64, _i64, _i64, _f32, _vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp, _i64,
                           _vp, _vp, _vp]),
+    "tc_split_scaled": (_i32, [_i32, _i64, _i64, _vp, _i64, _i32, _vp, _vp, _i64, _vp]),
+    "tc_split_bf16x3": (_i32, [_i64, _i64, _vp, _i64, _i32, _vp, _vp, _vp, _i64, _vp]),
     "gemm_split_workspace_bytes": (_sz, [_i32, _i32, _i64, _i64, _i64]),
+    "gemm_split_scaled": (_i32, [_i32, _i32, _i64, _i64, _i64, _f32, _vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp,
+                                 _i64, _vp, _sz, _vp]),
+    "gemm_split_bf16x3": (_i32, [_i64, _i64, _i64, _f32, _vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp, _i64, _vp,
+                                 _sz, _vp]),
     "gemm_split": (_i32, [_i32, _i32, _i64, _i64, _i64, _f32, _vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp, _i64,
                           _vp, _sz, _vp]),
     "gemm_sgemm": (_i32, [_i64, _i64, _i64, _f32, _vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp, _i64, _vp]),
@@ -191,6 +197,16 @@ def gemm_mixed(dt, m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ldc, scale_a
                                     _ptr(scale_a), _ptr(scale_b), _stream(stream)), "gemm_mixed")
 
 
+def tc_split_scaled(piece, rows, cols, src, ld_src, transpose, dst_hi, dst_lo, ld_dst, stream=None):
+    return _check(load().tc_split_scaled(piece, rows, cols, _ptr(src), ld_src, int(transpose), _ptr(dst_hi),
+                                         _ptr(dst_lo), ld_dst, _stream(stream)), "tc_split_scaled")
+
+
+def tc_split_bf16x3(rows, cols, src, ld_src, transpose, dst0, dst1, dst2, ld_dst, stream=None):
+    return _check(load().tc_split_bf16x3(rows, cols, _ptr(src), ld_src, int(transpose), _ptr(dst0), _ptr(dst1),
+                                         _ptr(dst2), ld_dst, _stream(stream)), "tc_split_bf16x3")
+
+
 def gemm_split_workspace_bytes(piece, nprod, m, n, k) -> int:
     return int(load().gemm_split_workspace_bytes(piece, nprod, m, n, k))
 
@@ -199,6 +215,20 @@ def gemm_split(piece, nprod, m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ld
                workspace_bytes=0, stream=None):
     return _check(load().gemm_split(piece, nprod, m, n, k, alpha, _ptr(A), lda, la, _ptr(B), ldb, lb, beta, _ptr(C),
                                     ldc, _ptr(workspace), int(workspace_bytes), _stream(stream)), "gemm_split")
+
+
+def gemm_split_scaled(piece, nprod, m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ldc, workspace=None,
+                      workspace_bytes=0, stream=None):
+    return _check(load().gemm_split_scaled(piece, nprod, m, n, k, alpha, _ptr(A), lda, la, _ptr(B), ldb, lb, beta,
+                                           _ptr(C), ldc, _ptr(workspace), int(workspace_bytes), _stream(stream)),
+                  "gemm_split_scaled")
+
+
+def gemm_split_bf16x3(m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ldc, workspace=None, workspace_bytes=0,
+                      stream=None):
+    return _check(load().gemm_split_bf16x3(m, n, k, alpha, _ptr(A), lda, la, _ptr(B), ldb, lb, beta, _ptr(C), ldc,
+                                           _ptr(workspace), int(workspace_bytes), _stream(stream)),
+                  "gemm_split_bf16x3")
 
 
 def gemm_sgemm(m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ldc, stream=None):

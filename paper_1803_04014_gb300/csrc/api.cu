@@ -262,24 +262,53 @@ tc_status tc_quantize(int32_t dt, int64_t rows, int64_t cols, const float* src, 
                    "tc_quantize launch");
 }
 
-tc_status tc_split(int32_t piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src, int32_t transpose,
-                   void* dst_hi, void* dst_lo, int64_t ld_dst, void* stream) {
-    if (piece != TC_F16 && piece != TC_BF16) return fail(TC_ERR_INVALID, "tc_split: piece must be F16 or BF16");
-    if (rows < 0 || cols < 0) return fail(TC_ERR_INVALID, "tc_split: negative size");
+}  // extern "C"
+
+namespace {
+
+// Shared checks and launch of the three piece-forming entry points.
+tc_status split_entry(const char* name, int scheme, int32_t piece, int64_t rows, int64_t cols, const float* src,
+                      int64_t ld_src, int32_t transpose, void* const* dst, int npieces, int64_t ld_dst,
+                      void* stream) {
+    if (piece != TC_F16 && piece != TC_BF16) return fail(TC_ERR_INVALID, "%s: piece must be F16 or BF16", name);
+    if (rows < 0 || cols < 0) return fail(TC_ERR_INVALID, "%s: negative size", name);
     if (rows > 0 && cols > 0) {
-        if (!src || !dst_hi || !dst_lo) return fail(TC_ERR_INVALID, "tc_split: null pointer");
-        if (ld_src < cols) return fail(TC_ERR_INVALID, "tc_split: ld_src < cols");
-        if (ld_dst < (transpose ? rows : cols)) return fail(TC_ERR_INVALID, "tc_split: ld_dst too small");
-        if (!aligned(src, 4) || !aligned(dst_hi, 2) || !aligned(dst_lo, 2))
-            return fail(TC_ERR_INVALID, "tc_split: misaligned pointer");
-        if (transpose && (rows + 31) / 32 > 65535) return fail(TC_ERR_INVALID, "tc_split: too many rows to transpose");
+        if (!src) return fail(TC_ERR_INVALID, "%s: null pointer", name);
+        for (int q = 0; q < npieces; ++q)
+            if (!dst[q] || !aligned(dst[q], 2)) return fail(TC_ERR_INVALID, "%s: null or misaligned piece", name);
+        if (ld_src < cols) return fail(TC_ERR_INVALID, "%s: ld_src < cols", name);
+        if (ld_dst < (transpose ? rows : cols)) return fail(TC_ERR_INVALID, "%s: ld_dst too small", name);
+        if (!aligned(src, 4)) return fail(TC_ERR_INVALID, "%s: misaligned pointer", name);
+        if (transpose && (rows + 31) / 32 > 65535) return fail(TC_ERR_INVALID, "%s: too many rows to transpose", name);
     }
     Device* d;
     tc_status s = get_device(&d);
     if (s != TC_OK) return s;
-    return enqueue(tcg::launch_split(piece, rows, cols, src, ld_src, transpose != 0, dst_hi, dst_lo, ld_dst,
+    return enqueue(tcg::launch_split(scheme, piece, rows, cols, src, ld_src, transpose != 0, dst, ld_dst,
                                      as_stream(stream)),
-                   "tc_split launch");
+                   name);
+}
+
+}  // namespace
+
+extern "C" {
+
+tc_status tc_split(int32_t piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src, int32_t transpose,
+                   void* dst_hi, void* dst_lo, int64_t ld_dst, void* stream) {
+    void* dst[3] = {dst_hi, dst_lo, nullptr};
+    return split_entry("tc_split", 0, piece, rows, cols, src, ld_src, transpose, dst, 2, ld_dst, stream);
+}
+
+tc_status tc_split_scaled(int32_t piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src,
+                          int32_t transpose, void* dst_hi, void* dst_lo, int64_t ld_dst, void* stream) {
+    void* dst[3] = {dst_hi, dst_lo, nullptr};
+    return split_entry("tc_split_scaled", 1, piece, rows, cols, src, ld_src, transpose, dst, 2, ld_dst, stream);
+}
+
+tc_status tc_split_bf16x3(int64_t rows, int64_t cols, const float* src, int64_t ld_src, int32_t transpose,
+                          void* dst0, void* dst1, void* dst2, int64_t ld_dst, void* stream) {
+    void* dst[3] = {dst0, dst1, dst2};
+    return split_entry("tc_split_bf16x3", 2, TC_BF16, rows, cols, src, ld_src, transpose, dst, 3, ld_dst, stream);
 }
 
 tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, const void* A, int64_t lda, int32_t la,
@@ -333,69 +362,87 @@ static int64_t split_kpad(int64_t k) { return (k + 7) / 8 * 8; }
 
 size_t gemm_split_workspace_bytes(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k) {
     (void)piece;
-    (void)nprod;
     if (m < 0 || n < 0 || k < 0) return 0;
     const int64_t kp = split_kpad(k);
-    // two pieces of A (m x kp) and two of B (n x kp), 2 bytes each, 256-byte aligned halves
-    const int64_t a_bytes = (2 * m * kp * 2 + 255) / 256 * 256;
-    const int64_t b_bytes = (2 * n * kp * 2 + 255) / 256 * 256;
+    const int64_t np = nprod == 6 ? 3 : 2;
+    // np pieces of A (m x kp) and of B (n x kp), 2 bytes each, 256-byte aligned blocks
+    const int64_t a_bytes = (np * m * kp * 2 + 255) / 256 * 256;
+    const int64_t b_bytes = (np * n * kp * 2 + 255) / 256 * 256;
     return static_cast<size_t>(a_bytes + b_bytes);
 }
 
-tc_status gemm_split(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k, float alpha, const float* A,
-                     int64_t lda, int32_t la, const float* B, int64_t ldb, int32_t lb, float beta, float* C,
-                     int64_t ldc, void* workspace, size_t workspace_bytes, void* stream) {
-    if (piece != TC_F16 && piece != TC_BF16) return fail(TC_ERR_INVALID, "gemm_split: piece must be F16 or BF16");
-    if (nprod < 2 || nprod > 4) return fail(TC_ERR_INVALID, "gemm_split: nprod must be 2, 3 or 4");
+}  // extern "C"
+
+namespace {
+
+// Refined GEMM of every scheme: form the pieces of A and B (K-major) in the
+// workspace with one HBM-bound pass each, then one tcgen05 launch.
+//   scheme 0: Eq. 1 / Eq. 2, nprod 2-4;  1: scaled residuals, nprod 2-3;
+//   scheme 2: three BF16 pieces, nprod 6.
+tc_status split_gemm(const char* name, int scheme, int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k,
+                     float alpha, const float* A, int64_t lda, int32_t la, const float* B, int64_t ldb, int32_t lb,
+                     float beta, float* C, int64_t ldc, void* workspace, size_t workspace_bytes, void* stream) {
+    if (piece != TC_F16 && piece != TC_BF16) return fail(TC_ERR_INVALID, "%s: piece must be F16 or BF16", name);
     tc_status s = check_dims(m, n, k);
     if (s != TC_OK) return s;
     if ((la != TC_ROW_MAJOR && la != TC_COL_MAJOR) || (lb != TC_ROW_MAJOR && lb != TC_COL_MAJOR))
-        return fail(TC_ERR_INVALID, "gemm_split: bad layout");
+        return fail(TC_ERR_INVALID, "%s: bad layout", name);
     if (m == 0 || n == 0) return TC_OK;
-    if (!C || ldc < n || !aligned(C, 4)) return fail(TC_ERR_INVALID, "gemm_split: bad C / ldc");
+    if (!C || ldc < n || !aligned(C, 4)) return fail(TC_ERR_INVALID, "%s: bad C / ldc", name);
     Device* d;
     if ((s = get_device(&d)) != TC_OK) return s;
     cudaStream_t st = as_stream(stream);
-    if (k == 0) return enqueue(tcg::launch_scale_c(m, n, beta, C, ldc, st), "gemm_split scale");
-    if (!A || !B || !aligned(A, 4) || !aligned(B, 4)) return fail(TC_ERR_INVALID, "gemm_split: bad operand pointer");
+    if (k == 0) return enqueue(tcg::launch_scale_c(m, n, beta, C, ldc, st), name);
+    if (!A || !B || !aligned(A, 4) || !aligned(B, 4)) return fail(TC_ERR_INVALID, "%s: bad operand pointer", name);
     if (lda < (la == TC_ROW_MAJOR ? k : m) || ldb < (lb == TC_ROW_MAJOR ? n : k))
-        return fail(TC_ERR_INVALID, "gemm_split: leading dimension too small");
+        return fail(TC_ERR_INVALID, "%s: leading dimension too small", name);
     const size_t need = gemm_split_workspace_bytes(piece, nprod, m, n, k);
     if (workspace && workspace_bytes < need)
-        return fail(TC_ERR_INVALID, "gemm_split: workspace of %zu bytes, need %zu", workspace_bytes, need);
-    if (workspace && !aligned(workspace, 256)) return fail(TC_ERR_INVALID, "gemm_split: workspace must be 256-byte aligned");
+        return fail(TC_ERR_INVALID, "%s: workspace of %zu bytes, need %zu", name, workspace_bytes, need);
+    if (workspace && !aligned(workspace, 256)) return fail(TC_ERR_INVALID, "%s: workspace must be 256-byte aligned", name);
     void* ws = workspace;
     cudaError_t e;
     if (!ws) {
-        if ((e = cudaMallocAsync(&ws, need, st)) != cudaSuccess) return fail(TC_ERR_OOM, "gemm_split: workspace: %s", cudaGetErrorString(e));
+        if ((e = cudaMallocAsync(&ws, need, st)) != cudaSuccess)
+            return fail(TC_ERR_OOM, "%s: workspace: %s", name, cudaGetErrorString(e));
     }
+    const int np = scheme == 2 ? 3 : 2;
     const int64_t kp = split_kpad(k);
     uint8_t* wa = static_cast<uint8_t*>(ws);
-    uint8_t* wb = wa + (2 * m * kp * 2 + 255) / 256 * 256;
-    uint16_t* a_hi = reinterpret_cast<uint16_t*>(wa);
-    uint16_t* a_lo = a_hi + m * kp;
-    uint16_t* b_hi = reinterpret_cast<uint16_t*>(wb);
-    uint16_t* b_lo = b_hi + n * kp;
+    uint8_t* wb = wa + (np * m * kp * 2 + 255) / 256 * 256;
+    void* pa[3];
+    void* pb[3];
+    for (int q = 0; q < np; ++q) {
+        pa[q] = reinterpret_cast<uint16_t*>(wa) + q * m * kp;
+        pb[q] = reinterpret_cast<uint16_t*>(wb) + q * n * kp;
+    }
     tc_status out = TC_OK;
     do {
         // A pieces as m x k (K-major): row-major A directly, column-major A (k x m in memory) transposed
-        e = (la == TC_ROW_MAJOR) ? tcg::launch_split(piece, m, k, A, lda, false, a_hi, a_lo, kp, st)
-                                 : tcg::launch_split(piece, k, m, A, lda, true, a_hi, a_lo, kp, st);
-        if (e != cudaSuccess) { out = cuda_fail(e, "gemm_split: split A"); break; }
+        e = (la == TC_ROW_MAJOR) ? tcg::launch_split(scheme, piece, m, k, A, lda, false, pa, kp, st)
+                                 : tcg::launch_split(scheme, piece, k, m, A, lda, true, pa, kp, st);
+        if (e != cudaSuccess) { out = cuda_fail(e, "split of A"); break; }
         // B pieces as n x k (K-major): row-major B (k x n) transposed, column-major B directly
-        e = (lb == TC_ROW_MAJOR) ? tcg::launch_split(piece, k, n, B, ldb, true, b_hi, b_lo, kp, st)
-                                 : tcg::launch_split(piece, n, k, B, ldb, false, b_hi, b_lo, kp, st);
-        if (e != cudaSuccess) { out = cuda_fail(e, "gemm_split: split B"); break; }
+        e = (lb == TC_ROW_MAJOR) ? tcg::launch_split(scheme, piece, k, n, B, ldb, true, pb, kp, st)
+                                 : tcg::launch_split(scheme, piece, n, k, B, ldb, false, pb, kp, st);
+        if (e != cudaSuccess) { out = cuda_fail(e, "split of B"); break; }
         const CUtensorMapDataType tdt = piece == TC_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
         tcg::TcGemmLaunch p{};
         p.kind = 0;
         p.ab_format = piece == TC_BF16 ? 1 : 0;
-        p.na = 2;
-        p.nb = nprod == 2 ? 1 : 2;
+        p.na = np;
+        p.nb = nprod == 2 ? 1 : np;
         p.nprod = nprod;
         p.bn = nprod == 2 ? 256 : 128;
-        p.pair = use_pair_tiles(m) ? 1 : 0;
-        p.promote_kb = p.pair ? split_promote_kb() : 0;
+        if (scheme == 0) {
+            p.pair = use_pair_tiles(m) ? 1 : 0;
+            p.promote_kb = p.pair ? split_promote_kb() : 0;
+        } else {
+            // the scaled and three-piece schemes run on the promoted CTA-pair kernel only
+            p.pair = 1;
+            p.promote_kb = split_promote_kb() == 4 ? 4 : 2;
+            p.corr_exp = scheme == 1 ? (piece == TC_F16 ? 11 : 8) : 0;
+        }
         p.group_m = gemm_group_m();
         p.stall_at = take_stall();
         p.m = m; p.n = n; p.k = k;
@@ -404,14 +451,42 @@ tc_status gemm_split(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t
         p.status = d->status;
         p.sm_count = d->sm_count;
         CUtensorMap ta, tb;
-        if ((out = encode_kmajor(&ta, tdt, 2, a_hi, k, m, 2, kp * 2, m * kp * 2, 128)) != TC_OK) break;
-        if ((out = encode_kmajor(&tb, tdt, 2, b_hi, k, n, p.nb, kp * 2, n * kp * 2, p.pair ? 128 : p.bn)) != TC_OK)
+        if ((out = encode_kmajor(&ta, tdt, 2, pa[0], k, m, np, kp * 2, m * kp * 2, 128)) != TC_OK) break;
+        if ((out = encode_kmajor(&tb, tdt, 2, pb[0], k, n, p.nb, kp * 2, n * kp * 2, p.pair ? 128 : p.bn)) != TC_OK)
             break;
         e = tcg::launch_tc_gemm(ta, tb, p, st);
-        if (e != cudaSuccess) { out = cuda_fail(e, "gemm_split launch"); break; }
+        if (e != cudaSuccess) { out = cuda_fail(e, name); break; }
     } while (false);
     if (!workspace) cudaFreeAsync(ws, st);
     return out;
+}
+
+}  // namespace
+
+extern "C" {
+
+tc_status gemm_split(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k, float alpha, const float* A,
+                     int64_t lda, int32_t la, const float* B, int64_t ldb, int32_t lb, float beta, float* C,
+                     int64_t ldc, void* workspace, size_t workspace_bytes, void* stream) {
+    if (nprod < 2 || nprod > 4) return fail(TC_ERR_INVALID, "gemm_split: nprod must be 2, 3 or 4");
+    return split_gemm("gemm_split", 0, piece, nprod, m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ldc, workspace,
+                      workspace_bytes, stream);
+}
+
+tc_status gemm_split_scaled(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k, float alpha,
+                            const float* A, int64_t lda, int32_t la, const float* B, int64_t ldb, int32_t lb,
+                            float beta, float* C, int64_t ldc, void* workspace, size_t workspace_bytes,
+                            void* stream) {
+    if (nprod != 2 && nprod != 3) return fail(TC_ERR_INVALID, "gemm_split_scaled: nprod must be 2 or 3");
+    return split_gemm("gemm_split_scaled", 1, piece, nprod, m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ldc,
+                      workspace, workspace_bytes, stream);
+}
+
+tc_status gemm_split_bf16x3(int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda, int32_t la,
+                            const float* B, int64_t ldb, int32_t lb, float beta, float* C, int64_t ldc,
+                            void* workspace, size_t workspace_bytes, void* stream) {
+    return split_gemm("gemm_split_bf16x3", 2, TC_BF16, 6, m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ldc,
+                      workspace, workspace_bytes, stream);
 }
 
 tc_status gemm_sgemm(int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda, int32_t la,

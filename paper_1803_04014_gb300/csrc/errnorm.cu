@@ -5,7 +5,8 @@
 // kErrBlocks blocks: each block reduces a fixed strided subset of the
 // elements into partial sums, then one block adds the partials in a fixed
 // tree order, so the result is bit-for-bit repeatable and independent of the
-// GPU's SM count.  Memory-bound: 4 + 8 bytes read per element of C.
+// GPU's SM count.  Memory-bound: 4 + 8 bytes read per element of C (FP64
+// reference), 4 per element of A and B; streamed with 16-byte loads.
 #include "launch.h"
 
 namespace tcg {
@@ -47,36 +48,72 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 
 // Fixed assignment of a rows x cols matrix to the kErrBlocks x kErrThreads
 // threads: thread (b, t) visits rows b, b + kErrBlocks, ... and in each row the
-// columns t, t + kErrThreads, ...  No division per element, coalesced rows, and
-// the same order on every GPU.
-template <typename F>
+// column groups t, t + kErrThreads, ... of VEC consecutive elements, kUnroll
+// groups per step so that several loads are in flight.  No division per
+// element, coalesced rows, and the same order on every GPU.
+constexpr int kUnroll = 4;
+
+template <int VEC, typename F>
 __device__ __forceinline__ void for_each_mine(int64_t rows, int64_t cols, F&& f) {
+    const int64_t groups = cols / VEC;
     for (int64_t r = blockIdx.x; r < rows; r += kErrBlocks)
-        for (int64_t c = threadIdx.x; c < cols; c += kErrThreads) f(r, c);
+        for (int64_t g0 = threadIdx.x; g0 < groups; g0 += kErrThreads * kUnroll) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int64_t g = g0 + u * kErrThreads;
+                if (g < groups) f(r, g * VEC);
+            }
+        }
 }
 
-// partial layout: [3][kErrBlocks][2] = (sum, max) for (C - ref), A, B
+__device__ __forceinline__ void acc_diff(double d, double& s, double& mx) {
+    s += d * d;
+    mx = fmax(mx, fabs(d));
+}
+
+// partial layout: [3][kErrBlocks][2] = (sum, max) for (C - ref), A, B.
+// vec: every row of C, ref, A and B starts on a 16-byte boundary and n, the
+// column counts of A and B are multiples of 4 (4-wide loads); else scalar.
 __global__ void __launch_bounds__(kErrThreads) k_err_partials(int64_t m, int64_t n, const float* __restrict__ C,
                                                               int64_t ldc, const void* __restrict__ ref, int64_t ldr,
                                                               int ref_f64, const float* __restrict__ A, int64_t ar,
                                                               int64_t ac, int64_t lda, const float* __restrict__ B,
-                                                              int64_t br, int64_t bc, int64_t ldb,
+                                                              int64_t br, int64_t bc, int64_t ldb, int vec,
                                                               double* __restrict__ partial) {
     __shared__ double red[32];
     double s = 0.0, mx = 0.0;
-    if (ref_f64) {
+    if (vec) {
+        if (ref_f64) {
+            const double* R = static_cast<const double*>(ref);
+            for_each_mine<4>(m, n, [&](int64_t r, int64_t c) {
+                const float4 x = __ldcs(reinterpret_cast<const float4*>(C + r * ldc + c));
+                const double2 y0 = __ldcs(reinterpret_cast<const double2*>(R + r * ldr + c));
+                const double2 y1 = __ldcs(reinterpret_cast<const double2*>(R + r * ldr + c + 2));
+                acc_diff(static_cast<double>(x.x) - y0.x, s, mx);
+                acc_diff(static_cast<double>(x.y) - y0.y, s, mx);
+                acc_diff(static_cast<double>(x.z) - y1.x, s, mx);
+                acc_diff(static_cast<double>(x.w) - y1.y, s, mx);
+            });
+        } else {
+            const float* R = static_cast<const float*>(ref);
+            for_each_mine<4>(m, n, [&](int64_t r, int64_t c) {
+                const float4 x = __ldcs(reinterpret_cast<const float4*>(C + r * ldc + c));
+                const float4 y = __ldcs(reinterpret_cast<const float4*>(R + r * ldr + c));
+                acc_diff(static_cast<double>(x.x) - static_cast<double>(y.x), s, mx);
+                acc_diff(static_cast<double>(x.y) - static_cast<double>(y.y), s, mx);
+                acc_diff(static_cast<double>(x.z) - static_cast<double>(y.z), s, mx);
+                acc_diff(static_cast<double>(x.w) - static_cast<double>(y.w), s, mx);
+            });
+        }
+    } else if (ref_f64) {
         const double* R = static_cast<const double*>(ref);
-        for_each_mine(m, n, [&](int64_t r, int64_t c) {
-            const double d = static_cast<double>(C[r * ldc + c]) - R[r * ldr + c];
-            s += d * d;
-            mx = fmax(mx, fabs(d));
+        for_each_mine<1>(m, n, [&](int64_t r, int64_t c) {
+            acc_diff(static_cast<double>(C[r * ldc + c]) - R[r * ldr + c], s, mx);
         });
     } else {
         const float* R = static_cast<const float*>(ref);
-        for_each_mine(m, n, [&](int64_t r, int64_t c) {
-            const double d = static_cast<double>(C[r * ldc + c]) - static_cast<double>(R[r * ldr + c]);
-            s += d * d;
-            mx = fmax(mx, fabs(d));
+        for_each_mine<1>(m, n, [&](int64_t r, int64_t c) {
+            acc_diff(static_cast<double>(C[r * ldc + c]) - static_cast<double>(R[r * ldr + c]), s, mx);
         });
     }
     double bs = block_sum(s, red);
@@ -94,10 +131,20 @@ __global__ void __launch_bounds__(kErrThreads) k_err_partials(int64_t m, int64_t
         if (mats[w] != nullptr) {
             const float* X = mats[w];
             const int64_t ld = lds[w];
-            for_each_mine(rows[w], cols[w], [&](int64_t r, int64_t c) {
-                const double x = static_cast<double>(X[r * ld + c]);
-                t += x * x;
-            });
+            if (vec) {
+                for_each_mine<4>(rows[w], cols[w], [&](int64_t r, int64_t c) {
+                    const float4 x = __ldcs(reinterpret_cast<const float4*>(X + r * ld + c));
+                    t += static_cast<double>(x.x) * x.x;
+                    t += static_cast<double>(x.y) * x.y;
+                    t += static_cast<double>(x.z) * x.z;
+                    t += static_cast<double>(x.w) * x.w;
+                });
+            } else {
+                for_each_mine<1>(rows[w], cols[w], [&](int64_t r, int64_t c) {
+                    const double x = static_cast<double>(X[r * ld + c]);
+                    t += x * x;
+                });
+            }
         }
         const double bt = block_sum(t, red);
         if (threadIdx.x == 0) {
@@ -132,8 +179,13 @@ cudaError_t launch_error_norm(int64_t m, int64_t n, const float* C, int64_t ldc,
                               bool ref_f64, const float* A, int64_t ar, int64_t ac, int64_t lda, const float* B,
                               int64_t br, int64_t bc, int64_t ldb, double* partial, double* out4_dev,
                               cudaStream_t st) {
+    auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    const bool vec = (n % 4 == 0) && (ldc % 4 == 0) && al16(C) && al16(ref) &&
+                     (ref_f64 ? (ldr % 2 == 0) : (ldr % 4 == 0)) &&
+                     (A == nullptr || ((ac % 4 == 0) && (lda % 4 == 0) && al16(A))) &&
+                     (B == nullptr || ((bc % 4 == 0) && (ldb % 4 == 0) && al16(B)));
     k_err_partials<<<kErrBlocks, kErrThreads, 0, st>>>(m, n, C, ldc, ref, ldr, ref_f64 ? 1 : 0, A, ar, ac, lda, B, br,
-                                                       bc, ldb, partial);
+                                                       bc, ldb, vec ? 1 : 0, partial);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_err_final<<<1, kErrBlocks, 0, st>>>(partial, out4_dev);

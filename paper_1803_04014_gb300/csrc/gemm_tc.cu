@@ -45,12 +45,24 @@ struct Args {
     int group_m;  // raster: bands of group_m M-tiles, N-tiles swept inside a band (L2 reuse)
     int stall_kb;  // test hook: >= 0 makes the first CTA (pair) withhold this k-block of its first tile
     int staged_epilogue;  // pair kernel: transpose 32 x 32 chunks through shared memory before storing
+    float corr_scale;     // scaled split: 2^-s applied to the correction accumulator
 };
 
-// product p multiplies A piece prod_a(p) with B piece prod_b(p):
-// (hi,hi), (lo,hi), (hi,lo), (lo,lo)
-__host__ __device__ constexpr int prod_a(int p) { return p & 1; }
-__host__ __device__ constexpr int prod_b(int p) { return p >> 1; }
+// product p multiplies A piece prod_a(p) with B piece prod_b(p).  Two pieces:
+// (hi,hi), (lo,hi), (hi,lo), (lo,lo).  Three BF16 pieces (NA = 3): the six
+// products with piece orders adding up to at most 2, largest first:
+// (0,0), (1,0), (0,1), (2,0), (1,1), (0,2).
+template <int NA = 2>
+__host__ __device__ constexpr int prod_a(int p) {
+    return NA == 3 ? (p == 1 || p == 4 ? 1 : (p == 3 ? 2 : 0)) : (p & 1);
+}
+template <int NA = 2>
+__host__ __device__ constexpr int prod_b(int p) {
+    return NA == 3 ? (p == 2 || p == 4 ? 1 : (p == 5 ? 2 : 0)) : (p >> 1);
+}
+static_assert(prod_a<3>(3) == 2 && prod_b<3>(3) == 0 && prod_a<3>(5) == 0 && prod_b<3>(5) == 2 &&
+                  prod_a<3>(4) == 1 && prod_b<3>(4) == 1 && prod_a<3>(2) == 0 && prod_b<3>(2) == 1,
+              "three-piece product table");
 
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int group_m, int& mb, int& nb) {
     const int band = group_m * tiles_n;
@@ -199,8 +211,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int ks = 0; ks < kSteps; ++ks) {
 #pragma unroll
                         for (int p = 0; p < NPROD; ++p) {
-                            const uint32_t a_addr = sbase + prod_a(p) * kATileBytes + ks * 32;
-                            const uint32_t b_addr = sbase + NA * kATileBytes + prod_b(p) * L::kBTileBytes + ks * 32;
+                            const uint32_t a_addr = sbase + prod_a<NA>(p) * kATileBytes + ks * 32;
+                            const uint32_t b_addr = sbase + NA * kATileBytes + prod_b<NA>(p) * L::kBTileBytes + ks * 32;
                             const uint32_t accumulate = (kb | ks | p) != 0 ? 1u : 0u;
                             if constexpr (KIND == 1)
                                 mma_f8(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), a.idesc,
@@ -488,8 +500,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int ks = 0; ks < kSteps; ++ks) {
 #pragma unroll
                         for (int p = 0; p < NPROD; ++p) {
-                            const uint32_t a_addr = sbase + prod_a(p) * L::kHalfTile + ks * 32;
-                            const uint32_t b_addr = sbase + (NA + prod_b(p)) * L::kHalfTile + ks * 32;
+                            const uint32_t a_addr = sbase + prod_a<NA>(p) * L::kHalfTile + ks * 32;
+                            const uint32_t b_addr = sbase + (NA + prod_b<NA>(p)) * L::kHalfTile + ks * 32;
                             const uint32_t accumulate = (kb | ks | p) != 0 ? 1u : 0u;
                             if constexpr (KIND == 1)
                                 mma_pair_f8(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), a.idesc,
@@ -690,10 +702,23 @@ cudaError_t run_pair(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args&
 // TMEM (2 x 256 columns) so the MMAs of chunk c+1 overlap the draining of
 // chunk c.  Eight epilogue warps: warp w drains TMEM lanes 32*(w%4).. and
 // columns [128*((w-2)/4), +128) into 128 registers per thread.
+//
+// SCALED (corrections apart; the scaled-residual split of Ootomo and Yokota,
+// 2022, and the three-piece BF16 split): product 0 (hi x hi) goes to a
+// single-buffered chunk accumulator H (columns 0-255) and is promoted as
+// above; the correction products (for the scaled split lo' x hi and hi x lo',
+// whose residuals were multiplied by 2^s before rounding) accumulate over the
+// whole of K in a second accumulator Y (columns 256-511), which the epilogue
+// adds once per tile times corr_scale (2^-s, or 1 for BF16 pieces).  Kept
+// apart, the small products are not truncated against the large partial sums
+// of hi x hi inside the tensor core.  The correction MMAs of the first
+// k-blocks of a chunk (up to STAGES - 1 of them) are issued before the MMA
+// warp waits for H to be drained, so the drain of chunk c overlaps the
+// corrections of chunk c+1.
 
 constexpr int kPromoteThreads = 320;  // TMA warp, MMA warp, 8 epilogue warps
 
-template <int KIND, int STAGES, int NA, int NB, int NPROD, int CHUNK_KB>
+template <int KIND, int STAGES, int NA, int NB, int NPROD, int CHUNK_KB, bool SCALED>
 __global__ void __launch_bounds__(kPromoteThreads, 1)
     k_tc_gemm_pair_promote(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                            const Args a) {
@@ -810,7 +835,105 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
         }
         __syncwarp();
     } else if (warp == 1) {
-        if (lane == 0 && rank == 0) {
+        if (lane == 0 && rank == 0 && SCALED) {
+            // the corrections of the first kAhead k-blocks of a chunk are issued before the wait for H,
+            // so the drain of the previous chunk overlaps them; one stage stays free for the producer
+            constexpr int kAhead = (CHUNK_KB < STAGES - 1) ? CHUNK_KB : (STAGES - 1);
+            static_assert(kAhead >= 1, "SCALED needs at least two stages");
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t h_phase = 0;
+            bool ok = true;
+            bool issued_any = false;
+            const uint32_t h_tmem = tmem_base;
+            const uint32_t y_tmem = tmem_base + static_cast<uint32_t>(PN);
+            auto advance = [&](int& s_, uint32_t& ph_) {
+                if (++s_ == STAGES) {
+                    s_ = 0;
+                    ph_ ^= 1u;
+                }
+            };
+            auto corrections = [&](int kb, int s_) {
+                const uint32_t sbase = base + s_ * L::kStageBytes;
+#pragma unroll
+                for (int ks = 0; ks < kSteps; ++ks) {
+#pragma unroll
+                    for (int p = 1; p < NPROD; ++p) {
+                        const uint32_t a_addr = sbase + prod_a<NA>(p) * L::kHalfTile + ks * 32;
+                        const uint32_t b_addr = sbase + (NA + prod_b<NA>(p)) * L::kHalfTile + ks * 32;
+                        const uint32_t accumulate = (kb != 0 || ks != 0 || p != 1) ? 1u : 0u;
+                        mma_pair_f16(y_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), a.idesc,
+                                     accumulate);
+                    }
+                }
+            };
+            auto hi_hi = [&](int kb, int kb0, int s_) {
+                const uint32_t sbase = base + s_ * L::kStageBytes;
+#pragma unroll
+                for (int ks = 0; ks < kSteps; ++ks) {
+                    const uint32_t accumulate = (kb != kb0 || ks != 0) ? 1u : 0u;
+                    mma_pair_f16(h_tmem, sw128_kmajor_desc(sbase + ks * 32),
+                                 sw128_kmajor_desc(sbase + NA * L::kHalfTile + ks * 32), a.idesc, accumulate);
+                }
+                mma_commit_pair_mc(empty_bar(s_), 0x3);
+            };
+            for (int t = cid; ok && t < a.num_tiles; t += ncl) {
+                for (int c = 0; ok && c < nchunks; ++c) {
+                    const int kb0 = c * CHUNK_KB;
+                    const int kb_end = min(a.num_kb, kb0 + CHUNK_KB);
+                    const int ahead = min(kb_end - kb0, kAhead);
+                    if (c == 0) {
+                        // Y restarts with this tile: wait until the previous tile's Y and H are drained
+                        if (!wait(cempty_bar(0), h_phase ^ 1u)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    int s2 = stage;
+                    uint32_t ph2 = phase;
+                    for (int kb = kb0; kb < kb0 + ahead; ++kb) {
+                        if (!wait(full_bar(stage), phase)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        corrections(kb, stage);
+                        issued_any = true;
+                        advance(stage, phase);
+                    }
+                    if (!ok) break;
+                    if (c != 0) {
+                        if (!wait(cempty_bar(0), h_phase ^ 1u)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    for (int kb = kb0; kb < kb0 + ahead; ++kb) {
+                        hi_hi(kb, kb0, s2);
+                        advance(s2, ph2);
+                    }
+                    for (int kb = kb0 + ahead; kb < kb_end; ++kb) {
+                        if (!wait(full_bar(stage), phase)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        corrections(kb, stage);
+                        hi_hi(kb, kb0, stage);
+                        advance(stage, phase);
+                    }
+                    if (!ok) break;
+                    mma_commit_pair_mc(cfull_bar(0), 0x3);
+                    h_phase ^= 1u;
+                }
+            }
+            if (!ok && issued_any) {
+                mma_commit_pair_mc(drain_bar, 0x1);
+                mbar_wait_bounded(drain_bar, 0, 100000000ull);
+            }
+        } else if (lane == 0 && rank == 0) {
             int stage = 0;
             uint32_t phase = 0;
             int buf = 0;
@@ -837,8 +960,8 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
                         for (int ks = 0; ks < kSteps; ++ks) {
 #pragma unroll
                             for (int p = 0; p < NPROD; ++p) {
-                                const uint32_t a_addr = sbase + prod_a(p) * L::kHalfTile + ks * 32;
-                                const uint32_t b_addr = sbase + (NA + prod_b(p)) * L::kHalfTile + ks * 32;
+                                const uint32_t a_addr = sbase + prod_a<NA>(p) * L::kHalfTile + ks * 32;
+                                const uint32_t b_addr = sbase + (NA + prod_b<NA>(p)) * L::kHalfTile + ks * 32;
                                 const uint32_t accumulate = (kb != c * CHUNK_KB || ks != 0 || p != 0) ? 1u : 0u;
                                 if constexpr (KIND == 1)
                                     mma_pair_f8(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), a.idesc,
@@ -889,14 +1012,16 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
 #pragma unroll
             for (int j = 0; j < 128; ++j) acc[j] = 0.0f;
             for (int c = 0; c < nchunks; ++c) {
-                const bool w = wait(cfull_bar(buf), buf_phase);
+                // SCALED: one H buffer whose phase flips every chunk; else two buffers in turn
+                const int cb = SCALED ? 0 : buf;
+                const bool w = wait(cfull_bar(cb), buf_phase);
                 if (!__all_sync(0xffffffffu, w)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                       static_cast<uint32_t>(buf * PN + half * 128);
+                                       static_cast<uint32_t>(cb * PN + half * 128);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     float v[32];
@@ -904,11 +1029,25 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
 #pragma unroll
                     for (int j = 0; j < 32; ++j) acc[q * 32 + j] += v[j];
                 }
+                if (SCALED && c == nchunks - 1) {
+                    // the correction accumulator, complete with the tile's last chunk
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float v[32];
+                        tmem_load_32(taddr + PN + q * 32, v);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) acc[q * 32 + j] = fmaf(v[j], a.corr_scale, acc[q * 32 + j]);
+                    }
+                }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(buf == 0 ? leader_cempty0 : leader_cempty1);
-                buf ^= 1;
-                if (buf == 0) buf_phase ^= 1u;
+                if (lane == 0) mbar_arrive_cluster(cb == 0 ? leader_cempty0 : leader_cempty1);
+                if (SCALED) {
+                    buf_phase ^= 1u;
+                } else {
+                    buf ^= 1;
+                    if (buf == 0) buf_phase ^= 1u;
+                }
             }
             if (!ok) break;
             if (row < a.m && col0 < a.n) {
@@ -951,12 +1090,13 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
     }
 }
 
-template <int KIND, int STAGES, int NA, int NB, int NPROD, int CHUNK_KB>
+template <int KIND, int STAGES, int NA, int NB, int NPROD, int CHUNK_KB, bool SCALED = false>
 cudaError_t run_pair_promote(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args& args, int clusters,
                              cudaStream_t st) {
     if (clusters <= 0) return cudaSuccess;
     using L = PairLayout<STAGES, NA, NB>;
-    auto kern = k_tc_gemm_pair_promote<KIND, STAGES, NA, NB, NPROD, CHUNK_KB>;
+    static_assert(L::kBytes <= 227 * 1024, "shared memory of the promoted pair kernel");
+    auto kern = k_tc_gemm_pair_promote<KIND, STAGES, NA, NB, NPROD, CHUNK_KB, SCALED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -1009,6 +1149,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     a.group_m = p.group_m > 0 ? p.group_m : 16;
     a.stall_kb = p.stall_at - 1;
     a.staged_epilogue = p.staged_epilogue;
+    a.corr_scale = 1.0f;
     if (p.pair) {
         // 256 x 256 tiles on CTA pairs
         a.tiles_m = static_cast<int>((p.m + 255) / 256);
@@ -1020,6 +1161,22 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
         if (clusters <= 0) return cudaSuccess;
         if (p.kind == 1) {
             if (p.na == 1 && p.nb == 1) return run_pair<1, 6, 1, 1, 1>(tmA, tmB, a, clusters, st);
+            return cudaErrorInvalidValue;
+        }
+        if (p.corr_exp > 0 || p.na == 3) {
+            // corrections apart from hi x hi: the scaled split (16-bit pieces, 2 or 3 products,
+            // corrections times 2^-s) and the three BF16 pieces (6 products, corrections times 1)
+            a.corr_scale = ldexpf(1.0f, -p.corr_exp);
+            const bool long_chunk = p.promote_kb == 4;
+            if (p.na == 2 && p.nb == 1 && p.nprod == 2)
+                return long_chunk ? run_pair_promote<0, 4, 2, 1, 2, 4, true>(tmA, tmB, a, clusters, st)
+                                  : run_pair_promote<0, 4, 2, 1, 2, 2, true>(tmA, tmB, a, clusters, st);
+            if (p.na == 2 && p.nb == 2 && p.nprod == 3)
+                return long_chunk ? run_pair_promote<0, 3, 2, 2, 3, 4, true>(tmA, tmB, a, clusters, st)
+                                  : run_pair_promote<0, 3, 2, 2, 3, 2, true>(tmA, tmB, a, clusters, st);
+            if (p.na == 3 && p.nb == 3 && p.nprod == 6)
+                return long_chunk ? run_pair_promote<0, 2, 3, 3, 6, 4, true>(tmA, tmB, a, clusters, st)
+                                  : run_pair_promote<0, 2, 3, 3, 6, 2, true>(tmA, tmB, a, clusters, st);
             return cudaErrorInvalidValue;
         }
         if (p.promote_kb > 0) {

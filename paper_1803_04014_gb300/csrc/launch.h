@@ -14,8 +14,9 @@ namespace tcg {
 // finally holding the scale.
 cudaError_t launch_quantize(int dt, int64_t rows, int64_t cols, const float* src, int64_t ld_src, void* dst,
                             int64_t ld_dst, bool transpose, float* scale, cudaStream_t st);
-cudaError_t launch_split(int piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src, bool transpose,
-                         void* hi, void* lo, int64_t ld_dst, cudaStream_t st);
+// scheme 0: (hi, lo); 1: (hi, lo * 2^s); 2: three BF16 pieces.  dst holds 2 or 3 piece pointers.
+cudaError_t launch_split(int scheme, int piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src,
+                         bool transpose, void* const* dst, int64_t ld_dst, cudaStream_t st);
 cudaError_t launch_scale_c(int64_t m, int64_t n, float beta, float* C, int64_t ldc, cudaStream_t st);
 
 // ---- gemm_tc.cu
@@ -38,6 +39,8 @@ struct TcGemmLaunch {
     int stall_at;       // test hook: k-block + 1 to withhold, 0 = off (tc_debug_stall_next_gemm)
     int promote_kb;     // pair kernel only: >0 adds the partial sums of every promote_kb k-blocks
                         // into FP32 registers with round-to-nearest (1, 2 or 4); 0 keeps them in TMEM
+    int corr_exp;       // pair kernel with promotion, s > 0: products 1.. (the corrections of a scaled
+                        // split) accumulate apart and are multiplied by 2^-s in the epilogue
 };
 // tmA: 3-D map {k, m, na} with a 128 x (128 bytes) box; tmB: {k, n, nb} with a bn x (128 bytes) box.
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmLaunch& p, cudaStream_t st);

@@ -4,7 +4,10 @@
 //   quantize: dst = RNE(src) to F16 / BF16, or RNE_satfinite(src * s) to E4M3
 //             with s = 2^j the largest power of two with max|src| * s <= 448.
 //   split:    hi = RNE16(x), lo = RNE16(x - hi) (the residual R of Sec. V,
-//             stored in 16 bits as Eq. 1 / Eq. 2 multiply it on tensor cores).
+//             stored in 16 bits as Eq. 1 / Eq. 2 multiply it on tensor cores);
+//             the scaled variant rounds (x - hi) * 2^s instead (Ootomo and
+//             Yokota, 2022), the BF16x3 variant adds a third BF16 piece
+//             RNE16(x - hi - lo) (Henry, Tang and Heinecke, 2019).
 //
 // All of these are HBM-bound streams (4 bytes in, 1-4 bytes out per element):
 // the row kernels move 8 elements per thread with 16-byte loads, the
@@ -205,23 +208,64 @@ __global__ void __launch_bounds__(256) k_quantize_transpose(int64_t rows, int64_
     }
 }
 
+// Split schemes: 0 = hi, lo (Eq. 1 / Eq. 2); 1 = hi, lo scaled by 2^s before
+// rounding (s = 11 for FP16 pieces, 8 for BF16); 2 = three BF16 pieces.
+constexpr int kSplitPlain = 0, kSplitScaled = 1, kSplitBf16x3 = 2;
+
 template <int PIECE>
-__device__ __forceinline__ void split_one(float x, unsigned short& hi, unsigned short& lo) {
-    if constexpr (PIECE == kDtF16) {
-        const __half h = __float2half_rn(x);
-        hi = __half_as_ushort(h);
-        lo = __half_as_ushort(__float2half_rn(x - __half2float(h)));  // x - hi is exact in FP32
+struct Piece16;
+template <>
+struct Piece16<kDtF16> {
+    __device__ static unsigned short rn(float x) { return __half_as_ushort(__float2half_rn(x)); }
+    __device__ static float back(unsigned short h) { return __half2float(__ushort_as_half(h)); }
+    static constexpr float kScale = 2048.0f;  // 2^11
+};
+template <>
+struct Piece16<kDtBF16> {
+    __device__ static unsigned short rn(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+    __device__ static float back(unsigned short h) { return __bfloat162float(__ushort_as_bfloat16(h)); }
+    static constexpr float kScale = 256.0f;  // 2^8
+};
+
+template <int SCHEME>
+constexpr int pieces_of() {
+    return SCHEME == kSplitBf16x3 ? 3 : 2;
+}
+
+// x - p0 and (x - p0) - p1 are exact in FP32 (the residual of a rounding to a
+// shorter significand is representable), and so is the scaling by 2^s.
+template <int PIECE, int SCHEME>
+__device__ __forceinline__ void split_one(float x, unsigned short (&o)[3]) {
+    using P = Piece16<PIECE>;
+    o[0] = P::rn(x);
+    const float r = x - P::back(o[0]);
+    if constexpr (SCHEME == kSplitPlain) {
+        o[1] = P::rn(r);
+    } else if constexpr (SCHEME == kSplitScaled) {
+        o[1] = P::rn(r * P::kScale);
     } else {
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        hi = __bfloat16_as_ushort(h);
-        lo = __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(h)));
+        o[1] = P::rn(r);
+        o[2] = P::rn(r - P::back(o[1]));
     }
 }
 
-template <int PIECE>
+struct SplitOut {
+    unsigned short* p[3];
+};
+
+__device__ __forceinline__ uint4 pack8(const unsigned short* h) {
+    uint4 w;
+    w.x = h[0] | (uint32_t(h[1]) << 16);
+    w.y = h[2] | (uint32_t(h[3]) << 16);
+    w.z = h[4] | (uint32_t(h[5]) << 16);
+    w.w = h[6] | (uint32_t(h[7]) << 16);
+    return w;
+}
+
+template <int PIECE, int SCHEME>
 __global__ void __launch_bounds__(256) k_split_vec8(int64_t rows, int64_t cols, const float* __restrict__ src,
-                                                    int64_t ld_src, unsigned short* __restrict__ hi,
-                                                    unsigned short* __restrict__ lo, int64_t ld_dst) {
+                                                    int64_t ld_src, SplitOut out, int64_t ld_dst) {
+    constexpr int NP = pieces_of<SCHEME>();
     const int64_t vpr = cols / 8;
     const int64_t total = rows * vpr;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -229,37 +273,37 @@ __global__ void __launch_bounds__(256) k_split_vec8(int64_t rows, int64_t cols, 
         const float4* p = reinterpret_cast<const float4*>(src + r * ld_src + c);
         const float4 a = __ldcs(p), b = __ldcs(p + 1);
         const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        unsigned short h[8], l[8];
+        unsigned short o[3][8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) split_one<PIECE>(v[j], h[j], l[j]);
-        uint4 wh, wl;
-        wh.x = h[0] | (uint32_t(h[1]) << 16); wh.y = h[2] | (uint32_t(h[3]) << 16);
-        wh.z = h[4] | (uint32_t(h[5]) << 16); wh.w = h[6] | (uint32_t(h[7]) << 16);
-        wl.x = l[0] | (uint32_t(l[1]) << 16); wl.y = l[2] | (uint32_t(l[3]) << 16);
-        wl.z = l[4] | (uint32_t(l[5]) << 16); wl.w = l[6] | (uint32_t(l[7]) << 16);
-        *reinterpret_cast<uint4*>(hi + r * ld_dst + c) = wh;
-        *reinterpret_cast<uint4*>(lo + r * ld_dst + c) = wl;
+        for (int j = 0; j < 8; ++j) {
+            unsigned short t[3];
+            split_one<PIECE, SCHEME>(v[j], t);
+#pragma unroll
+            for (int q = 0; q < NP; ++q) o[q][j] = t[q];
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) *reinterpret_cast<uint4*>(out.p[q] + r * ld_dst + c) = pack8(o[q]);
     }
 }
 
-template <int PIECE>
+template <int PIECE, int SCHEME>
 __global__ void __launch_bounds__(256) k_split_scalar(int64_t rows, int64_t cols, const float* __restrict__ src,
-                                                      int64_t ld_src, unsigned short* __restrict__ hi,
-                                                      unsigned short* __restrict__ lo, int64_t ld_dst) {
+                                                      int64_t ld_src, SplitOut out, int64_t ld_dst) {
+    constexpr int NP = pieces_of<SCHEME>();
     const int64_t total = rows * cols;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / cols, c = i - r * cols;
-        unsigned short h, l;
-        split_one<PIECE>(src[r * ld_src + c], h, l);
-        hi[r * ld_dst + c] = h;
-        lo[r * ld_dst + c] = l;
+        unsigned short t[3];
+        split_one<PIECE, SCHEME>(src[r * ld_src + c], t);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) out.p[q][r * ld_dst + c] = t[q];
     }
 }
 
-template <int PIECE>
+template <int PIECE, int SCHEME>
 __global__ void __launch_bounds__(256) k_split_transpose(int64_t rows, int64_t cols, const float* __restrict__ src,
-                                                         int64_t ld_src, unsigned short* __restrict__ hi,
-                                                         unsigned short* __restrict__ lo, int64_t ld_dst, int aligned) {
+                                                         int64_t ld_src, SplitOut out, int64_t ld_dst, int aligned) {
+    constexpr int NP = pieces_of<SCHEME>();
     constexpr int TR = 64, PER = 8, TC = 32;
     __shared__ float tile[TR][TC + 1];
     const int64_t r0 = (int64_t)blockIdx.y * TR, c0 = (int64_t)blockIdx.x * TC;
@@ -284,25 +328,23 @@ __global__ void __launch_bounds__(256) k_split_transpose(int64_t rows, int64_t c
     const int64_t c = c0 + cc;
     if (c >= cols) return;
     const int64_t rbase = r0 + j * PER;
-    unsigned short h[PER], l[PER];
+    unsigned short o[3][PER];
 #pragma unroll
-    for (int q = 0; q < PER; ++q) split_one<PIECE>(tile[j * PER + q][cc], h[q], l[q]);
-    unsigned short* dh = hi + c * ld_dst + rbase;
-    unsigned short* dl = lo + c * ld_dst + rbase;
+    for (int q = 0; q < PER; ++q) {
+        unsigned short w[3];
+        split_one<PIECE, SCHEME>(tile[j * PER + q][cc], w);
+#pragma unroll
+        for (int z = 0; z < NP; ++z) o[z][q] = w[z];
+    }
     if (aligned && rbase + PER <= rows) {
-        uint4 wh, wl;
-        wh.x = h[0] | (uint32_t(h[1]) << 16); wh.y = h[2] | (uint32_t(h[3]) << 16);
-        wh.z = h[4] | (uint32_t(h[5]) << 16); wh.w = h[6] | (uint32_t(h[7]) << 16);
-        wl.x = l[0] | (uint32_t(l[1]) << 16); wl.y = l[2] | (uint32_t(l[3]) << 16);
-        wl.z = l[4] | (uint32_t(l[5]) << 16); wl.w = l[6] | (uint32_t(l[7]) << 16);
-        *reinterpret_cast<uint4*>(dh) = wh;
-        *reinterpret_cast<uint4*>(dl) = wl;
+#pragma unroll
+        for (int z = 0; z < NP; ++z) *reinterpret_cast<uint4*>(out.p[z] + c * ld_dst + rbase) = pack8(o[z]);
     } else {
 #pragma unroll
         for (int q = 0; q < PER; ++q)
             if (rbase + q < rows) {
-                dh[q] = h[q];
-                dl[q] = l[q];
+#pragma unroll
+                for (int z = 0; z < NP; ++z) out.p[z][c * ld_dst + rbase + q] = o[z][q];
             }
     }
 }
@@ -349,23 +391,28 @@ cudaError_t quantize_dt(int64_t rows, int64_t cols, const float* src, int64_t ld
     return cudaGetLastError();
 }
 
-template <int PIECE>
-cudaError_t split_piece(int64_t rows, int64_t cols, const float* src, int64_t ld_src, bool transpose, void* hi,
-                        void* lo, int64_t ld_dst, cudaStream_t st) {
-    auto* h = static_cast<unsigned short*>(hi);
-    auto* l = static_cast<unsigned short*>(lo);
+template <int PIECE, int SCHEME>
+cudaError_t split_piece(int64_t rows, int64_t cols, const float* src, int64_t ld_src, bool transpose,
+                        void* const* dst, int64_t ld_dst, cudaStream_t st) {
+    constexpr int NP = pieces_of<SCHEME>();
+    SplitOut out{};
+    bool all_aligned = true;
+    for (int q = 0; q < NP; ++q) {
+        out.p[q] = static_cast<unsigned short*>(dst[q]);
+        all_aligned = all_aligned && aligned16(dst[q]);
+    }
     if (transpose) {
         dim3 grid(static_cast<unsigned>((cols + 31) / 32), static_cast<unsigned>((rows + 63) / 64));
-        const int al = (ld_dst % 8 == 0) && aligned16(hi) && aligned16(lo);
-        k_split_transpose<PIECE><<<grid, 256, 0, st>>>(rows, cols, src, ld_src, h, l, ld_dst, al);
+        const int al = (ld_dst % 8 == 0) && all_aligned;
+        k_split_transpose<PIECE, SCHEME><<<grid, 256, 0, st>>>(rows, cols, src, ld_src, out, ld_dst, al);
     } else {
-        const bool vec = (cols % 8 == 0) && (ld_src % 4 == 0) && (ld_dst % 8 == 0) && aligned16(src) &&
-                         aligned16(hi) && aligned16(lo);
+        const bool vec = (cols % 8 == 0) && (ld_src % 4 == 0) && (ld_dst % 8 == 0) && aligned16(src) && all_aligned;
         if (vec)
-            k_split_vec8<PIECE><<<grid_for(rows * (cols / 8), 256), 256, 0, st>>>(rows, cols, src, ld_src, h, l,
-                                                                               ld_dst);
+            k_split_vec8<PIECE, SCHEME><<<grid_for(rows * (cols / 8), 256), 256, 0, st>>>(rows, cols, src, ld_src, out,
+                                                                                       ld_dst);
         else
-            k_split_scalar<PIECE><<<grid_for(rows * cols, 256), 256, 0, st>>>(rows, cols, src, ld_src, h, l, ld_dst);
+            k_split_scalar<PIECE, SCHEME><<<grid_for(rows * cols, 256), 256, 0, st>>>(rows, cols, src, ld_src, out,
+                                                                                   ld_dst);
     }
     return cudaGetLastError();
 }
@@ -404,11 +451,16 @@ cudaError_t launch_quantize(int dt, int64_t rows, int64_t cols, const float* src
     return e;
 }
 
-cudaError_t launch_split(int piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src, bool transpose,
-                         void* hi, void* lo, int64_t ld_dst, cudaStream_t st) {
+cudaError_t launch_split(int scheme, int piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src,
+                         bool transpose, void* const* dst, int64_t ld_dst, cudaStream_t st) {
     if (rows == 0 || cols == 0) return cudaSuccess;
-    return piece == kDtF16 ? split_piece<kDtF16>(rows, cols, src, ld_src, transpose, hi, lo, ld_dst, st)
-                           : split_piece<kDtBF16>(rows, cols, src, ld_src, transpose, hi, lo, ld_dst, st);
+    if (scheme == kSplitBf16x3)
+        return split_piece<kDtBF16, kSplitBf16x3>(rows, cols, src, ld_src, transpose, dst, ld_dst, st);
+    if (scheme == kSplitScaled)
+        return piece == kDtF16 ? split_piece<kDtF16, kSplitScaled>(rows, cols, src, ld_src, transpose, dst, ld_dst, st)
+                               : split_piece<kDtBF16, kSplitScaled>(rows, cols, src, ld_src, transpose, dst, ld_dst, st);
+    return piece == kDtF16 ? split_piece<kDtF16, kSplitPlain>(rows, cols, src, ld_src, transpose, dst, ld_dst, st)
+                           : split_piece<kDtBF16, kSplitPlain>(rows, cols, src, ld_src, transpose, dst, ld_dst, st);
 }
 
 cudaError_t launch_scale_c(int64_t m, int64_t n, float beta, float* C, int64_t ldc, cudaStream_t st) {

@@ -352,8 +352,9 @@ def test_grouped_plan_graph_replay_and_beta(b):
 
 # ------------------------------------------------------------------ FP64 error reduction
 
-def test_error_norm_matches_oracle(b):
-    m, n, k = 333, 211, 97
+@pytest.mark.parametrize("m,n,k", [(333, 211, 97), (300, 1032, 96), (256, 512, 99), (2100, 4096, 8)])
+def test_error_norm_matches_oracle(b, m, n, k):
+    # 16-byte loads where every row is 16-byte aligned (n, k multiples of 4), scalar loads otherwise
     C = synth.uniform((m, n), seed=81)
     C64 = C.astype(np.float64) + synth.normal((m, n), seed=82).astype(np.float64) * 1e-3
     A = synth.uniform((m, k), seed=83)

@@ -52,20 +52,32 @@ def test_stalled_gemm_times_out_and_the_context_survives(b, monkeypatch, tile, m
     assert normwise_dev(host(C), ref, A, B) <= TOL_NORMWISE
 
 
-def test_stalled_refined_gemm_times_out_and_the_context_survives(b):
+@pytest.mark.parametrize("scheme", ["eq2", "scaled", "bf16x3"])
+def test_stalled_refined_gemm_times_out_and_the_context_survives(b, scheme):
     m, n, k = 512, 256, 640
     A = synth.log_uniform_pow2((m, k), seed=9)
     B = synth.log_uniform_pow2((k, n), seed=10)
     Ad, Bd = dev(A), dev(B)
     C = torch.zeros((m, n), dtype=torch.float32, device="cuda")
+
+    def run():
+        if scheme == "eq2":
+            b.gemm_split(0, 3, m, n, k, 1.0, Ad, k, 0, Bd, n, 0, 0.0, C, n)
+        elif scheme == "scaled":
+            b.gemm_split_scaled(0, 3, m, n, k, 1.0, Ad, k, 0, Bd, n, 0, 0.0, C, n)
+        else:
+            b.gemm_split_bf16x3(m, n, k, 1.0, Ad, k, 0, Bd, n, 0, 0.0, C, n)
+
     b.tc_debug_stall_next_gemm(3)
-    b.gemm_split(0, 3, m, n, k, 1.0, Ad, k, 0, Bd, n, 0, 0.0, C, n)
+    run()
     with pytest.raises(b.TcError) as e:
         b.tc_sync_status()
     assert e.value.status == b.TC_ERR_TIMEOUT
-    b.gemm_split(0, 3, m, n, k, 1.0, Ad, k, 0, Bd, n, 0, 0.0, C, n)
+    run()
     b.tc_sync_status()
-    ref = og.gemm_split("f16", 3, A, B)
+    ref = {"eq2": lambda: og.gemm_split("f16", 3, A, B),
+           "scaled": lambda: og.gemm_split_scaled("f16", 3, A, B),
+           "bf16x3": lambda: og.gemm_split_bf16x3(A, B)}[scheme]()
     assert normwise_dev(host(C), ref, A, B) <= TOL_NORMWISE
 
 
