@@ -167,7 +167,7 @@ tc_status gemm_split(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t
  *   lo' = RNE((x - hi) * 2^s) as tc_split_scaled; nprod = 2 keeps Eq. 1's
  *   pair of products, nprod = 3 Eq. 2 without R_A R_B.
  * A_hi B_hi accumulates in one TMEM accumulator whose partial sums are added
- * into round-to-nearest FP32 registers every 128 of K; the correction
+ * into round-to-nearest FP32 registers every 256 of K; the correction
  * products accumulate in a second TMEM accumulator over all of K and are
  * scaled by 2^-s once per output tile.  piece: TC_F16 or TC_BF16.
  * Arguments, workspace and errors otherwise as gemm_split. */

@@ -190,14 +190,19 @@ int gemm_staged_epilogue() {
 }
 
 // k-blocks of 64 between promotions of the refined GEMM's partial sums out of
-// TMEM into round-to-nearest FP32 registers.  TCGEMM_SPLIT_PROMOTE=0|1|2|4.
-int split_promote_kb() {
+// TMEM into round-to-nearest FP32 registers.  TCGEMM_SPLIT_PROMOTE=0|1|2|4
+// overrides the default of the scheme: every 128 of K for Eq. 1 / Eq. 2 and
+// the three BF16 pieces (below the FP32 CUDA-core GEMM's error at about 3 % of
+// the time), every 256 of K for the scaled split, whose single-buffered hi x hi
+// accumulator stalls the tensor pipe once per promotion and whose corrections
+// are already kept apart.
+int split_promote_kb(int dflt = 2) {
     const char* env = getenv("TCGEMM_SPLIT_PROMOTE");
     if (env) {
         const int v = atoi(env);
         if (v == 0 || v == 1 || v == 2 || v == 4) return v;
     }
-    return 2;  // every 128 of K: below the FP32 CUDA-core GEMM's error at about 3 % of the time
+    return dflt;
 }
 
 }  // namespace
@@ -440,7 +445,7 @@ tc_status split_gemm(const char* name, int scheme, int32_t piece, int32_t nprod,
         } else {
             // the scaled and three-piece schemes run on the promoted CTA-pair kernel only
             p.pair = 1;
-            p.promote_kb = split_promote_kb() == 4 ? 4 : 2;
+            p.promote_kb = split_promote_kb(scheme == 1 ? 4 : 2) == 4 ? 4 : 2;
             p.corr_exp = scheme == 1 ? (piece == TC_F16 ? 11 : 8) : 0;
         }
         p.group_m = gemm_group_m();

@@ -66,9 +66,30 @@ __device__ __forceinline__ void for_each_mine(int64_t rows, int64_t cols, F&& f)
         }
 }
 
-__device__ __forceinline__ void acc_diff(double d, double& s, double& mx) {
-    s += d * d;
-    mx = fmax(mx, fabs(d));
+// GB300 runs FP64 arithmetic at about 1/64 of the FP32 rate, so this kernel
+// is bound by its FP64 instructions before HBM.  Two changes keep the results
+// bit-identical while halving that count: FP32 -> FP64 conversion of normal
+// values by integer bit assembly (IEEE 754 binary32 -> binary64: same sign,
+// exponent rebiased by 1023 - 127, significand shifted up by 29 bits), and
+// the running max of |d| compared as integer bit patterns (the order of
+// non-negative IEEE values is the order of their patterns).  What remains on
+// the FP64 unit is one subtraction and one fused multiply-add per element of
+// C and one fused multiply-add per element of A and B.
+__device__ __forceinline__ double to_f64(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const uint64_t sign = static_cast<uint64_t>(u & 0x80000000u) << 32;
+    if (e != 0u && e != 0xFFu)
+        return __longlong_as_double(static_cast<long long>(sign | (static_cast<uint64_t>(e + (1023u - 127u)) << 52) |
+                                                           (static_cast<uint64_t>(u & 0x7FFFFFu) << 29)));
+    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double(static_cast<long long>(sign));  // signed zero
+    return static_cast<double>(x);  // subnormal, infinity, NaN
+}
+
+__device__ __forceinline__ void acc_diff(double d, double& s, unsigned long long& mx_bits) {
+    s = fma(d, d, s);
+    const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(d)) & 0x7FFFFFFFFFFFFFFFull;
+    mx_bits = a > mx_bits ? a : mx_bits;
 }
 
 // partial layout: [3][kErrBlocks][2] = (sum, max) for (C - ref), A, B.
@@ -81,7 +102,8 @@ __global__ void __launch_bounds__(kErrThreads) k_err_partials(int64_t m, int64_t
                                                               int64_t br, int64_t bc, int64_t ldb, int vec,
                                                               double* __restrict__ partial) {
     __shared__ double red[32];
-    double s = 0.0, mx = 0.0;
+    double s = 0.0;
+    unsigned long long mx = 0ull;
     if (vec) {
         if (ref_f64) {
             const double* R = static_cast<const double*>(ref);
@@ -89,35 +111,35 @@ __global__ void __launch_bounds__(kErrThreads) k_err_partials(int64_t m, int64_t
                 const float4 x = __ldcs(reinterpret_cast<const float4*>(C + r * ldc + c));
                 const double2 y0 = __ldcs(reinterpret_cast<const double2*>(R + r * ldr + c));
                 const double2 y1 = __ldcs(reinterpret_cast<const double2*>(R + r * ldr + c + 2));
-                acc_diff(static_cast<double>(x.x) - y0.x, s, mx);
-                acc_diff(static_cast<double>(x.y) - y0.y, s, mx);
-                acc_diff(static_cast<double>(x.z) - y1.x, s, mx);
-                acc_diff(static_cast<double>(x.w) - y1.y, s, mx);
+                acc_diff(to_f64(x.x) - y0.x, s, mx);
+                acc_diff(to_f64(x.y) - y0.y, s, mx);
+                acc_diff(to_f64(x.z) - y1.x, s, mx);
+                acc_diff(to_f64(x.w) - y1.y, s, mx);
             });
         } else {
             const float* R = static_cast<const float*>(ref);
             for_each_mine<4>(m, n, [&](int64_t r, int64_t c) {
                 const float4 x = __ldcs(reinterpret_cast<const float4*>(C + r * ldc + c));
                 const float4 y = __ldcs(reinterpret_cast<const float4*>(R + r * ldr + c));
-                acc_diff(static_cast<double>(x.x) - static_cast<double>(y.x), s, mx);
-                acc_diff(static_cast<double>(x.y) - static_cast<double>(y.y), s, mx);
-                acc_diff(static_cast<double>(x.z) - static_cast<double>(y.z), s, mx);
-                acc_diff(static_cast<double>(x.w) - static_cast<double>(y.w), s, mx);
+                acc_diff(to_f64(x.x) - to_f64(y.x), s, mx);
+                acc_diff(to_f64(x.y) - to_f64(y.y), s, mx);
+                acc_diff(to_f64(x.z) - to_f64(y.z), s, mx);
+                acc_diff(to_f64(x.w) - to_f64(y.w), s, mx);
             });
         }
     } else if (ref_f64) {
         const double* R = static_cast<const double*>(ref);
         for_each_mine<1>(m, n, [&](int64_t r, int64_t c) {
-            acc_diff(static_cast<double>(C[r * ldc + c]) - R[r * ldr + c], s, mx);
+            acc_diff(to_f64(C[r * ldc + c]) - R[r * ldr + c], s, mx);
         });
     } else {
         const float* R = static_cast<const float*>(ref);
         for_each_mine<1>(m, n, [&](int64_t r, int64_t c) {
-            acc_diff(static_cast<double>(C[r * ldc + c]) - static_cast<double>(R[r * ldr + c]), s, mx);
+            acc_diff(to_f64(C[r * ldc + c]) - to_f64(R[r * ldr + c]), s, mx);
         });
     }
     double bs = block_sum(s, red);
-    double bm = block_max(mx, red);
+    double bm = block_max(__longlong_as_double(static_cast<long long>(mx)), red);
     if (threadIdx.x == 0) {
         partial[(0 * kErrBlocks + blockIdx.x) * 2 + 0] = bs;
         partial[(0 * kErrBlocks + blockIdx.x) * 2 + 1] = bm;
@@ -134,15 +156,19 @@ __global__ void __launch_bounds__(kErrThreads) k_err_partials(int64_t m, int64_t
             if (vec) {
                 for_each_mine<4>(rows[w], cols[w], [&](int64_t r, int64_t c) {
                     const float4 x = __ldcs(reinterpret_cast<const float4*>(X + r * ld + c));
-                    t += static_cast<double>(x.x) * x.x;
-                    t += static_cast<double>(x.y) * x.y;
-                    t += static_cast<double>(x.z) * x.z;
-                    t += static_cast<double>(x.w) * x.w;
+                    double v = to_f64(x.x);
+                    t = fma(v, v, t);
+                    v = to_f64(x.y);
+                    t = fma(v, v, t);
+                    v = to_f64(x.z);
+                    t = fma(v, v, t);
+                    v = to_f64(x.w);
+                    t = fma(v, v, t);
                 });
             } else {
                 for_each_mine<1>(rows[w], cols[w], [&](int64_t r, int64_t c) {
-                    const double x = static_cast<double>(X[r * ld + c]);
-                    t += x * x;
+                    const double x = to_f64(X[r * ld + c]);
+                    t = fma(x, x, t);
                 });
             }
         }

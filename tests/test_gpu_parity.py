@@ -371,6 +371,34 @@ def test_error_norm_matches_oracle(b, m, n, k):
     assert b.tc_error_norm(m, n, dev(C), n, dev(C64), n, 1, dev(A), m, k, k, dev(B), k, n, n) == out
 
 
+@pytest.mark.parametrize("n", [64, 63])
+def test_error_norm_special_values(b, n):
+    # zeros of both signs, FP32 subnormals and the extremes of the normal range go through the
+    # integer FP32 -> FP64 conversion and its fallback
+    m, k = 40, 12
+    specials = np.array([0.0, -0.0, 1e-40, -3e-39, 2.0 ** -126, -(2.0 ** -126), 3.4e38, -1.5, 2.0 ** -149],
+                        dtype=np.float32)
+    C = synth.uniform((m, n), seed=85)
+    C.flat[: specials.size] = specials
+    C64 = C.astype(np.float64)
+    C64.flat[specials.size:] += synth.normal((m * n - specials.size,), seed=86).astype(np.float64) * 1e-6
+    A = synth.uniform((m, k), seed=87)
+    A.flat[: specials.size - 1] = specials[:-3].tolist() + [1e-45, -1e-44]
+    B = synth.uniform((k, n), seed=88)
+    out = b.tc_error_norm(m, n, dev(C), n, dev(C64), n, 1, dev(A), m, k, k, dev(B), k, n, n)
+    want = og.error_sums(C, C64, A, B)
+    for g, w in zip(out, want):
+        assert abs(g - w) <= 1e-12 * abs(w)
+    # only special values: C against its own exact FP64 copy gives exactly zero error, and the squares
+    # of subnormals (~1e-80, normal in FP64) are summed exactly as the oracle sums them
+    S = np.resize(specials, (2, 8)).astype(np.float32)
+    sub = np.array([[1e-40, -3e-39, 2.0 ** -149, 1e-45, -(2.0 ** -127), 5e-39, 0.0, -0.0]], dtype=np.float32)
+    out = b.tc_error_norm(2, 8, dev(S), 8, dev(S.astype(np.float64)), 8, 1, dev(sub), 1, 8, 8)
+    want = og.error_sums(S, S.astype(np.float64), sub, np.zeros(1))
+    assert out[0] == 0.0 and out[3] == 0.0
+    assert abs(out[1] - want[1]) <= 1e-14 * want[1]
+
+
 # ------------------------------------------------------------------ both tile kernels (single CTA / CTA pair)
 
 @pytest.mark.parametrize("tile", ["single", "pair"])

@@ -99,9 +99,11 @@ def test_gemm_split_scaled_parity(b, piece, nprod, layouts):
     assert normwise_dev(got, ref, A, B, alpha, beta, C0) <= TOL_NORMWISE
 
 
+@pytest.mark.parametrize("promote", ["2", "4"])
 @pytest.mark.parametrize("mnk", [(520, 600, 1000), (256, 256, 64), (100, 40, 8), (300, 520, 2048)])
-def test_gemm_split_scaled_shapes(b, mnk):
-    # several tiles and chunks, ragged edges, k shorter than one promotion chunk
+def test_gemm_split_scaled_shapes(b, monkeypatch, promote, mnk):
+    # several tiles and chunks, ragged edges, k shorter than one promotion chunk; both chunk lengths
+    monkeypatch.setenv("TCGEMM_SPLIT_PROMOTE", promote)
     m, n, k = mnk
     A = synth.uniform((m, k), seed=200)
     B = synth.uniform((k, n), seed=201)
@@ -118,6 +120,16 @@ def test_gemm_split_scaled_shapes(b, mnk):
 @pytest.mark.parametrize("layouts", [(0, 0), (1, 1), (0, 1), (1, 0)])
 @pytest.mark.parametrize("mnk", [(192, 320, 264), (520, 300, 1000)])
 def test_gemm_split_bf16x3_parity(b, layouts, mnk):
+    _bf16x3_case(b, layouts, mnk)
+
+
+@pytest.mark.parametrize("promote", ["2", "4"])
+def test_gemm_split_bf16x3_chunk_lengths(b, monkeypatch, promote):
+    monkeypatch.setenv("TCGEMM_SPLIT_PROMOTE", promote)
+    _bf16x3_case(b, (0, 0), (300, 520, 1100))
+
+
+def _bf16x3_case(b, layouts, mnk):
     m, n, k = mnk
     la, lb = layouts
     A = _bits_matrix((m, k), synth.seed_for(5, 20), -40, 40)
