@@ -401,7 +401,7 @@ def measure_rows(b, A, B, pk, sm_count):
     return out
 
 
-def measure_serve(b, count=2000, budget=40 << 30):
+def measure_serve(b, count=50000, budget=40 << 30):
     """Open-loop Poisson stream through serve_submit/serve_poll; p50/p99 latency and throughput."""
     import torch
     S = 4096
@@ -409,7 +409,7 @@ def measure_serve(b, count=2000, budget=40 << 30):
     Bpool = torch.empty((S, S), dtype=torch.float32, device="cuda").uniform_(-1, 1)
     slots = 64
     Cpool = torch.empty((slots, S * S), dtype=torch.float32, device="cuda")
-    srv = b.serve_open(budget, max_inflight=16, num_streams=4)
+    srv = b.serve_open(budget, max_inflight=32, num_streams=8)
     try:
         def submit(i, m, n, k, mode):
             while True:

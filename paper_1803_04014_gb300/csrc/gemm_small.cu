@@ -338,7 +338,7 @@ cudaError_t launch_batched16(int dt, int64_t batch, float alpha, const void* A, 
     void (*kern)(int64_t, float, const uint16_t*, int64_t, const uint16_t*, int64_t, float, float*, int64_t, int*);
     if (dt == 0) kern = (lb == 0) ? k_batched16<0, 0> : k_batched16<0, 1>;
     else kern = (lb == 0) ? k_batched16<1, 0> : k_batched16<1, 1>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchSmem);
+    cudaError_t e = kernel_setup(reinterpret_cast<const void*>(kern), kBatchSmem, nullptr, 0, nullptr);
     if (e != cudaSuccess) return e;
     kern<<<grid, kBatchThreads, kBatchSmem, st>>>(batch, alpha, a, sa, b, sb, beta, C, sc, status);
     return cudaGetLastError();
@@ -356,8 +356,9 @@ cudaError_t launch_grouped(int dt, int lb, const GroupedProblemDev* probs, const
     else kern = (lb == 0) ? k_grouped<1, 0> : k_grouped<1, 1>;
     // persistent grid of exactly the CTAs that can be resident, so the static tile stride has no tail wave
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGThreads, 0) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
+    const cudaError_t e = kernel_setup(reinterpret_cast<const void*>(kern), 0, nullptr, kGThreads, &per_sm);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
     const int want = sm_count * per_sm;
     const int grid = num_tiles < want ? num_tiles : want;
     kern<<<grid, kGThreads, 0, st>>>(probs, tiles, num_tiles, a, b, c_base, alpha, beta);

@@ -315,7 +315,7 @@ template <int KIND, int BN, int STAGES, int NA, int NB, int NPROD>
 cudaError_t run(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args& args, int grid, cudaStream_t st) {
     using L = Layout<BN, STAGES, NA, NB>;
     auto kern = k_tc_gemm<KIND, BN, STAGES, NA, NB, NPROD>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
+    cudaError_t e = kernel_setup(reinterpret_cast<const void*>(kern), L::kBytes, nullptr, 0, nullptr);
     if (e != cudaSuccess) return e;
     kern<<<grid, kThreads, L::kBytes, st>>>(tmA, tmB, args);
     return cudaGetLastError();
@@ -667,8 +667,6 @@ cudaError_t run_pair(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args&
     if (clusters <= 0) return cudaSuccess;
     using L = PairLayout<STAGES, NA, NB>;
     auto kern = k_tc_gemm_pair<KIND, STAGES, NA, NB, NPROD>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
-    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * clusters, 1, 1);
     cfg.blockDim = dim3(kThreads, 1, 1);
@@ -683,7 +681,9 @@ cudaError_t run_pair(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args&
     cfg.numAttrs = 1;
     // no more clusters than can be resident at once (persistent tiles)
     int resident = 0;
-    if (cudaOccupancyMaxActiveClusters(&resident, kern, &cfg) == cudaSuccess && resident > 0 && clusters > resident) {
+    const cudaError_t e = kernel_setup(reinterpret_cast<const void*>(kern), L::kBytes, &cfg, 0, &resident);
+    if (e != cudaSuccess) return e;
+    if (resident > 0 && clusters > resident) {
         clusters = resident;
         cfg.gridDim = dim3(2 * clusters, 1, 1);
     }
@@ -1097,8 +1097,6 @@ cudaError_t run_pair_promote(const CUtensorMap& tmA, const CUtensorMap& tmB, con
     using L = PairLayout<STAGES, NA, NB>;
     static_assert(L::kBytes <= 227 * 1024, "shared memory of the promoted pair kernel");
     auto kern = k_tc_gemm_pair_promote<KIND, STAGES, NA, NB, NPROD, CHUNK_KB, SCALED>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kBytes);
-    if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * clusters, 1, 1);
     cfg.blockDim = dim3(kPromoteThreads, 1, 1);
@@ -1112,7 +1110,9 @@ cudaError_t run_pair_promote(const CUtensorMap& tmA, const CUtensorMap& tmB, con
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int resident = 0;
-    if (cudaOccupancyMaxActiveClusters(&resident, kern, &cfg) == cudaSuccess && resident > 0 && clusters > resident) {
+    const cudaError_t e = kernel_setup(reinterpret_cast<const void*>(kern), L::kBytes, &cfg, 0, &resident);
+    if (e != cudaSuccess) return e;
+    if (resident > 0 && clusters > resident) {
         clusters = resident;
         cfg.gridDim = dim3(2 * clusters, 1, 1);
     }

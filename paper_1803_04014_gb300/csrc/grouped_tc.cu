@@ -346,7 +346,7 @@ cudaError_t launch_grouped_tc(int dt, const GroupedTcTile* tiles, int32_t num_ti
                               float* c_base, float alpha, float beta, int* status, int sm_count, cudaStream_t st,
                               int staged) {
     if (num_tiles <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_grouped_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_grouped_tc), kSmem, nullptr, 0, nullptr);
     if (e != cudaSuccess) return e;
     Args a;
     a.tiles = tiles;

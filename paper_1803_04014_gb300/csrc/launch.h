@@ -19,6 +19,14 @@ cudaError_t launch_split(int scheme, int piece, int64_t rows, int64_t cols, cons
                          bool transpose, void* const* dst, int64_t ld_dst, cudaStream_t st);
 cudaError_t launch_scale_c(int64_t m, int64_t n, float beta, float* C, int64_t ldc, cudaStream_t st);
 
+// ---- kernel_setup.cu
+// Raises `kern`'s dynamic shared-memory limit to smem_bytes (if > 0) and, with
+// cluster_cfg, returns the resident clusters (cudaOccupancyMaxActiveClusters),
+// else with block_threads > 0 the resident blocks per SM; 0 if unknown.  Done
+// once per (kernel, device), then answered from a cache.
+cudaError_t kernel_setup(const void* kern, int smem_bytes, const cudaLaunchConfig_t* cluster_cfg, int block_threads,
+                         int* resident);
+
 // ---- gemm_tc.cu
 struct TcGemmLaunch {
     int kind;           // 0: 16-bit inputs (F16/BF16), 1: E4M3

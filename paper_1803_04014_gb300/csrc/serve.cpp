@@ -10,7 +10,8 @@
 //      carved out of one allocation made at serve_open),
 //   3. launches each admitted request on the least-recently used of S streams
 //      (round robin), so requests that arrive while others run overlap them
-//      on the GPU.
+//      on the GPU.  Launches happen outside the lock that submit and poll
+//      take.
 // A request's kernels and tile shapes depend only on (mode, m, n, k), so its
 // result is bitwise the same alone and in any mix.
 #include <cuda_runtime.h>
@@ -166,12 +167,19 @@ struct tc_server {
     uint64_t next_ticket = 1;
     bool stop = false;
     int64_t submitted = 0, completed = 0, peak_inflight = 0, budget_waits = 0;
+    size_t launching = 0;  // admitted requests being launched outside the lock
     std::thread sched;
+
+    struct Admitted {
+        Req* q;
+        cudaStream_t st;
+    };
 
     void loop() {
         cudaSetDevice(dev);
         std::unique_lock<std::mutex> lk(mu);
         bool blocked_on_budget = false;
+        std::vector<Admitted> admitted;
         for (;;) {
             // 1. retire
             bool retired = false;
@@ -198,8 +206,9 @@ struct tc_server {
                 blocked_on_budget = false;
                 cv_done.notify_all();
             }
-            // 2. admit in arrival order
-            while (!queue.empty() && static_cast<int>(running.size()) < cfg.max_inflight) {
+            // 2. admit in arrival order: take the workspace, an event and a stream under the lock ...
+            admitted.clear();
+            while (!queue.empty() && static_cast<int>(running.size() + admitted.size()) < cfg.max_inflight) {
                 Req* q = queue.front();
                 void* ws = arena.alloc(q->ws_bytes);
                 if (!ws) {
@@ -216,13 +225,25 @@ struct tc_server {
                 }
                 q->ev = event_pool.back();
                 event_pool.pop_back();
-                cudaStream_t st = streams[next_stream];
+                admitted.push_back({q, streams[next_stream]});
                 next_stream = (next_stream + 1) % streams.size();
-                q->t_start = now_us();
-                q->status = launch_request(q->r, ws, st);
-                cudaEventRecord(q->ev, st);
-                q->state = State::Running;
-                running.push_back(q);
+            }
+            // ... and launch outside it, so submitters and pollers are not held up by the launches;
+            // a request joins `running` (where its event is queried) only once its event is recorded
+            if (!admitted.empty()) {
+                launching = admitted.size();
+                lk.unlock();
+                for (auto& a : admitted) {
+                    a.q->t_start = now_us();
+                    a.q->status = launch_request(a.q->r, a.q->ws, a.st);
+                    cudaEventRecord(a.q->ev, a.st);
+                }
+                lk.lock();
+                launching = 0;
+                for (auto& a : admitted) {
+                    a.q->state = State::Running;
+                    running.push_back(a.q);
+                }
                 if (static_cast<int64_t>(running.size()) > peak_inflight) peak_inflight = running.size();
             }
             if (stop && queue.empty() && running.empty()) break;
@@ -324,7 +345,7 @@ tc_status serve_drain(tc_server* s, int64_t timeout_ms) {
     if (!s) return TC_ERR_INVALID;
     std::unique_lock<std::mutex> lk(s->mu);
     const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
-                                        [&] { return s->queue.empty() && s->running.empty(); });
+                                        [&] { return s->queue.empty() && s->running.empty() && s->launching == 0; });
     return ok ? TC_OK : TC_ERR_TIMEOUT;
 }
 
