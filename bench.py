@@ -26,6 +26,8 @@ path); rank 0 prints.
 from __future__ import annotations
 
 import argparse
+import collections
+import faulthandler
 import hashlib
 import json
 import os
@@ -224,11 +226,18 @@ def _sampled_errors(C_dev, A, B, rows):
             "max_abs": float(np.max(np.abs(d)))}
 
 
-def _row(fn):
+def _progress(msg):
+    print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+
+def _row(name, fn):
+    t0 = time.perf_counter()
     try:
         return fn()
     except Exception as e:  # one failing row must not hide the others
         return {"error": f"{type(e).__name__}: {e}"}
+    finally:
+        print(f"[bench] row {name}: {time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
 
 
 def measure_rows(b, A, B, pk, sm_count):
@@ -261,9 +270,9 @@ def measure_rows(b, A, B, pk, sm_count):
                 "peak_note": "measured bf16 burst" + (" x2 (FP8 rate)" if dt == 2 else ""),
                 "gemm_ms": ms, "quantize_ms": q_ms, "error_vs_fp64": err}
 
-    out["gemm_f16_n8192"] = _row(lambda: mixed(0, "f16"))
-    out["gemm_bf16_n8192"] = _row(lambda: mixed(1, "bf16"))
-    out["gemm_e4m3_n8192"] = _row(lambda: mixed(2, "e4m3"))
+    out["gemm_f16_n8192"] = _row("gemm_f16_n8192", lambda: mixed(0, "f16"))
+    out["gemm_bf16_n8192"] = _row("gemm_bf16_n8192", lambda: mixed(1, "bf16"))
+    out["gemm_e4m3_n8192"] = _row("gemm_e4m3_n8192", lambda: mixed(2, "e4m3"))
     del Ad, Bd
     torch.cuda.empty_cache()
 
@@ -310,7 +319,7 @@ def measure_rows(b, A, B, pk, sm_count):
                                   "error_ratio": e3 / es}
         return res
 
-    out["refinement_n8192"] = _row(refinement)
+    out["refinement_n8192"] = _row("refinement_n8192", refinement)
     torch.cuda.empty_cache()
 
     def grouped(lb):
@@ -344,8 +353,8 @@ def measure_rows(b, A, B, pk, sm_count):
                 "gbs": algo_bytes / (ms * 1e-3) / 1e9, "frac_of_hbm": algo_bytes / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
                 "algorithmic_bytes": algo_bytes}
 
-    out["grouped_10000"] = _row(lambda: grouped(1))
-    out["grouped_10000_rowmajor_b"] = _row(lambda: grouped(0))
+    out["grouped_10000"] = _row("grouped_10000", lambda: grouped(1))
+    out["grouped_10000_rowmajor_b"] = _row("grouped_10000_rowmajor_b", lambda: grouped(0))
     torch.cuda.empty_cache()
 
     def batched():
@@ -359,7 +368,7 @@ def measure_rows(b, A, B, pk, sm_count):
         return {"batch": batch, "ms": ms, "tflops": batch * 8192 / (ms * 1e-3) / 1e12,
                 "gbs": byts / (ms * 1e-3) / 1e9, "frac_of_hbm": byts / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]}
 
-    out["batched16_1e6"] = _row(batched)
+    out["batched16_1e6"] = _row("batched16_1e6", batched)
 
     def batched_sweep():
         # the paper's batched-GEMM axis (Sec. VII-A): TFLOP/s against the number of 16x16x16 products
@@ -376,7 +385,7 @@ def measure_rows(b, A, B, pk, sm_count):
                         "gbs": batch * 2048 / (ms * 1e-3) / 1e9})
         return {"sweep": res, "note": "the paper's V100 WMMA kernel peaked at 4 TFLOP/s at 262 144 products"}
 
-    out["batched16_sweep"] = _row(batched_sweep)
+    out["batched16_sweep"] = _row("batched16_sweep", batched_sweep)
     torch.cuda.empty_cache()
     def error_norm():
         # the FP64 error reduction of a refined N=8192 result: C (FP32), C64 (FP64), A and B (FP32)
@@ -395,9 +404,9 @@ def measure_rows(b, A, B, pk, sm_count):
         return {"ms": ms, "gbs": byts / (ms * 1e-3) / 1e9, "frac_of_hbm": byts / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
                 "bytes": byts, "note": "host wall time of the synchronising call (two kernels + 32-byte read-back)"}
 
-    out["error_norm_n8192"] = _row(error_norm)
+    out["error_norm_n8192"] = _row("error_norm_n8192", error_norm)
     torch.cuda.empty_cache()
-    out["serve"] = _row(lambda: measure_serve(b))
+    out["serve"] = _row("serve", lambda: measure_serve(b))
     return out
 
 
@@ -417,31 +426,44 @@ def measure_serve(b, count=50000, budget=40 << 30):
                 if t is not None:
                     return t
 
-        # capacity: a closed burst of 200 requests
-        _, sizes, modes = synth.serve_stream(200, seed=synth.seed_for(4, 1), rate_per_s=1.0)
+        # capacity: a closed burst of 1000 requests
+        nb = 1000
+        _, sizes, modes = synth.serve_stream(nb, seed=synth.seed_for(4, 1), rate_per_s=1.0)
         t0 = time.perf_counter()
-        tickets = [submit(i, *map(int, sizes[i]), int(modes[i])) for i in range(200)]
-        b.serve_drain(srv, 600_000)
+        tickets = [submit(i, *map(int, sizes[i]), int(modes[i])) for i in range(nb)]
+        b.serve_drain(srv, 120_000)
         burst_s = time.perf_counter() - t0
         for t in tickets:
             b.serve_poll(srv, t)
-        rate = 0.8 * 200 / burst_s
+        rate = 0.8 * nb / burst_s
         arrival, sizes, modes = synth.serve_stream(count, seed=synth.seed_for(4, 0), rate_per_s=rate)
-        lat, pending, flop = [], {}, 0.0
+        lat, flop = [], 0.0
+        pending = collections.deque()
         start = time.perf_counter()
+        next_poll = 0.0
         for i in range(count):
-            while time.perf_counter() - start < arrival[i]:
-                for t in list(pending):
-                    r = b.serve_poll(srv, t)
-                    if r is not None:
-                        lat.append((r["t_done_us"] - r["t_submit_us"]) / 1e3)
-                        del pending[t]
+            while True:
+                now = time.perf_counter() - start
+                if now >= arrival[i]:
+                    break
+                if now < next_poll:
+                    continue
+                # collect from the oldest request on, every 20 us at most (completions come roughly in
+                # order, and the latency is the server's own submit-to-done time, so collecting late does
+                # not change it; polling less often leaves the server's lock to its scheduler)
+                while pending:
+                    r = b.serve_poll(srv, pending[0])
+                    if r is None:
+                        break
+                    lat.append((r["t_done_us"] - r["t_submit_us"]) / 1e3)
+                    pending.popleft()
+                next_poll = now + 20e-6
             m, n, k = map(int, sizes[i])
-            pending[submit(i, m, n, k, int(modes[i]))] = i
+            pending.append(submit(i, m, n, k, int(modes[i])))
             flop += 2.0 * m * n * k
-        b.serve_drain(srv, 600_000)
+        b.serve_drain(srv, 120_000)
         wall = time.perf_counter() - start
-        for t in list(pending):
+        for t in pending:
             r = b.serve_poll(srv, t)
             lat.append((r["t_done_us"] - r["t_submit_us"]) / 1e3)
         st = b.serve_stats(srv)
@@ -519,6 +541,8 @@ def profile_case(kind):
 
 def main():
     args = parse_args()
+    # a run that has not finished in 20 minutes is stuck: print every thread's stack and exit non-zero
+    faulthandler.dump_traceback_later(1200, exit=True)
     if args.impl == "reference":
         return run_reference(args)
     if args.profile_gemm:
@@ -536,6 +560,7 @@ def main():
     sm_count, ccmaj, ccmin = b.tc_device_info()
     pk = peaks()
     # pick the tile kernel (single CTA / CTA pair) and raster band for this shape before timing
+    _progress("autotune")
     tune_ms = b.tc_autotune_gemm(b.TC_F16, N, N, N)
     with tempfile.NamedTemporaryFile(mode="r", suffix=".txt") as tf:
         b.tc_autotune_save(tf.name)
@@ -603,6 +628,7 @@ def main():
     # warm-up, then keep the GPU busy ~1 s so the clock sampler sees it under load
     for _ in range(max(args.warmup, 3)):
         step()
+    _progress("timed steps")
     sampler = ClockSampler(local)
     sampler.start()
     torch.cuda.synchronize()
@@ -713,6 +739,7 @@ def main():
         step()
         Ch[0].copy_(Cd, non_blocking=True)
 
+    _progress("end-to-end leg")
     e2e_serial()
     torch.cuda.synchronize()
     e0.record()

@@ -21,6 +21,9 @@
 //              tile i.
 // Shared-memory tiles use the 128-byte swizzle written by TMA and read by the
 // UMMA descriptors (rows of 128 bytes = one k-block).
+#include <cstdlib>
+#include <cstring>
+
 #include "launch.h"
 #include "tc_ptx.cuh"
 
@@ -46,6 +49,13 @@ struct Args {
     int stall_kb;  // test hook: >= 0 makes the first CTA (pair) withhold this k-block of its first tile
     int staged_epilogue;  // pair kernel: transpose 32 x 32 chunks through shared memory before storing
     float corr_scale;     // scaled split: 2^-s applied to the correction accumulator
+    // pair kernel: work units are the first full_units tiles of the raster (256 x 256) followed by
+    // the remaining tiles cut into two 256 x 128 halves each, num_units in all; idesc_half is the
+    // instruction descriptor of the half-width MMA.  Cutting the last, partial round of tiles in
+    // two lets twice as many CTA pairs share it.
+    int full_units, num_units;
+    uint32_t idesc_half;
+    int split_tail;  // 0 keeps every unit full-width (TCGEMM_PAIR_TAIL=full)
 };
 
 // product p multiplies A piece prod_a(p) with B piece prod_b(p).  Two pieces:
@@ -72,6 +82,21 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
     const int r = t - g * band;
     mb = first + r % gm;
     nb = r / gm;
+}
+
+// Work unit u of the pair kernel: its tile (mb, nb), the column offset inside the 256-wide tile
+// and the unit's width (256, or 128 for the halves of the last tiles).
+__device__ __forceinline__ void unit_coords(const Args& a, int u, int& mb, int& nb, int& coff, int& width) {
+    int t = u;
+    coff = 0;
+    width = 256;
+    if (u >= a.full_units) {
+        const int h = u - a.full_units;
+        t = a.full_units + (h >> 1);
+        coff = (h & 1) * 128;
+        width = 128;
+    }
+    tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
 }
 
 template <int BN, int STAGES, int NA, int NB>
@@ -426,15 +451,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
             for (int s = 0; s < STAGES; ++s) issued_phase[s] = -1;
             bool ok = true;
-            for (int t = cid; ok && t < a.num_tiles; t += ncl) {
-                int mb, nb;
-                tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
+            for (int u = cid; ok && u < a.num_units; u += ncl) {
+                int mb, nb, coff, width;
+                unit_coords(a, u, mb, nb, coff, width);
+                // this CTA's half of the unit's B rows (a half-width unit uses the first 64 of the 128 loaded)
+                const int brow = nb * PN + coff + static_cast<int>(rank) * (width >> 1);
                 for (int kb = 0; kb < a.num_kb; ++kb) {
                     if (!wait(empty_bar(stage), phase ^ 1u)) {
                         ok = false;
                         break;
                     }
-                    if (kb == a.stall_kb && t == cid && cid == 0 && rank == 0) {
+                    if (kb == a.stall_kb && u == cid && cid == 0 && rank == 0) {
                         // test hook: the even CTA never arms this stage's barrier
                         if (++stage == STAGES) {
                             stage = 0;
@@ -451,8 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                          mb * PM + static_cast<int>(rank) * 128, p);
 #pragma unroll
                     for (int p = 0; p < NB; ++p)
-                        tma_load_3d_pair(sbase + (NA + p) * L::kHalfTile, &tmB, leader_full, kb * BK,
-                                         nb * PN + static_cast<int>(rank) * 128, p);
+                        tma_load_3d_pair(sbase + (NA + p) * L::kHalfTile, &tmB, leader_full, kb * BK, brow, p);
                     issued_phase[stage] = static_cast<int>(phase);
                     if (++stage == STAGES) {
                         stage = 0;
@@ -482,13 +508,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t acc_phase = 0;
             bool ok = true;
             bool issued_any = false;
-            for (int t = cid; ok && t < a.num_tiles; t += ncl) {
+            for (int u = cid; ok && u < a.num_units; u += ncl) {
                 if (!wait(tempty_bar(acc), acc_phase ^ 1u)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * PN);
+                const uint32_t idesc = u < a.full_units ? a.idesc : a.idesc_half;
                 for (int kb = 0; kb < a.num_kb; ++kb) {
                     if (!wait(full_bar(stage), phase)) {
                         ok = false;
@@ -504,10 +531,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const uint32_t b_addr = sbase + (NA + prod_b<NA>(p)) * L::kHalfTile + ks * 32;
                             const uint32_t accumulate = (kb | ks | p) != 0 ? 1u : 0u;
                             if constexpr (KIND == 1)
-                                mma_pair_f8(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), a.idesc,
+                                mma_pair_f8(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), idesc,
                                             accumulate);
                             else
-                                mma_pair_f16(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), a.idesc,
+                                mma_pair_f16(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), idesc,
                                              accumulate);
                         }
                     }
@@ -540,14 +567,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t leader_tempty1 = mapa_shared(tempty_bar(1), 0);
         int acc = 0;
         uint32_t acc_phase = 0;
-        for (int t = cid; t < a.num_tiles; t += ncl) {
-            int mb, nb;
-            tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
+        for (int u = cid; u < a.num_units; u += ncl) {
+            int mb, nb, coff, width;
+            unit_coords(a, u, mb, nb, coff, width);
             const bool ok = wait(tfull_bar(acc), acc_phase);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
             const int row = mb * PM + static_cast<int>(rank) * 128 + quarter * 32 + lane;
-            const int col0 = nb * PN;
+            const int col0 = nb * PN + coff;
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                    static_cast<uint32_t>(acc * PN);
             float* crow = a.C + static_cast<int64_t>(row) * a.ldc + col0;
@@ -558,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int r0 = row - lane;
                 const int cc = (lane & 7) * 4;
 #pragma unroll 1
-                for (int c = 0; c < PN; c += 32) {
+                for (int c = 0; c < width; c += 32) {
                     if (col0 + c >= a.n) break;
                     const int nc = min(32, a.n - (col0 + c));
                     // old C of this chunk first: its global-memory latency overlaps the TMEM load
@@ -611,7 +638,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 continue;
             }
 #pragma unroll 1
-            for (int c = 0; c < PN; c += 32) {
+            for (int c = 0; c < width; c += 32) {
                 if (col0 + c >= a.n) break;
                 float v[32];
                 tmem_load_32(taddr + c, v);
@@ -667,6 +694,7 @@ cudaError_t run_pair(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args&
     if (clusters <= 0) return cudaSuccess;
     using L = PairLayout<STAGES, NA, NB>;
     auto kern = k_tc_gemm_pair<KIND, STAGES, NA, NB, NPROD>;
+    Args a = args;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * clusters, 1, 1);
     cfg.blockDim = dim3(kThreads, 1, 1);
@@ -687,7 +715,17 @@ cudaError_t run_pair(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args&
         clusters = resident;
         cfg.gridDim = dim3(2 * clusters, 1, 1);
     }
-    return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, args);
+    // a last round that would leave more than half of the pairs idle (or a grid of fewer tiles than
+    // half the pairs) is cut into half-width units
+    const int rem = a.num_tiles % clusters;
+    a.full_units = a.num_tiles;
+    if (rem > 0 && 2 * rem <= clusters && a.split_tail) a.full_units = a.num_tiles - rem;
+    a.num_units = a.full_units + 2 * (a.num_tiles - a.full_units);
+    if (clusters > a.num_units) {
+        clusters = a.num_units;
+        cfg.gridDim = dim3(2 * clusters, 1, 1);
+    }
+    return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, a);
 }
 
 // ====================================================================== CTA-pair kernel with promotion
@@ -1129,7 +1167,7 @@ size_t tc_gemm_smem_bytes(int na, int nb, int bn, int* stages_out) {
 }
 
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmLaunch& p, cudaStream_t st) {
-    Args a;
+    Args a{};
     a.m = static_cast<int>(p.m);
     a.n = static_cast<int>(p.n);
     a.k = static_cast<int>(p.k);
@@ -1156,11 +1194,17 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
         a.tiles_n = static_cast<int>((p.n + 255) / 256);
         a.num_tiles = a.tiles_m * a.tiles_n;
         a.idesc = make_idesc(256, 256, static_cast<uint32_t>(p.ab_format));
+        a.idesc_half = make_idesc(256, 128, static_cast<uint32_t>(p.ab_format));
+        a.full_units = a.num_units = a.num_tiles;
+        {
+            const char* env = getenv("TCGEMM_PAIR_TAIL");
+            a.split_tail = (env && strcmp(env, "full") == 0) ? 0 : 1;
+        }
         const int max_clusters = p.sm_count / 2;
         const int clusters = a.num_tiles < max_clusters ? a.num_tiles : max_clusters;
         if (clusters <= 0) return cudaSuccess;
         if (p.kind == 1) {
-            if (p.na == 1 && p.nb == 1) return run_pair<1, 6, 1, 1, 1>(tmA, tmB, a, clusters, st);
+            if (p.na == 1 && p.nb == 1) return run_pair<1, 6, 1, 1, 1>(tmA, tmB, a, max_clusters, st);
             return cudaErrorInvalidValue;
         }
         if (p.corr_exp > 0 || p.na == 3) {
@@ -1198,10 +1242,10 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
             }
             return cudaErrorInvalidValue;
         }
-        if (p.na == 1 && p.nb == 1) return run_pair<0, 6, 1, 1, 1>(tmA, tmB, a, clusters, st);
-        if (p.na == 2 && p.nb == 1 && p.nprod == 2) return run_pair<0, 4, 2, 1, 2>(tmA, tmB, a, clusters, st);
-        if (p.na == 2 && p.nb == 2 && p.nprod == 3) return run_pair<0, 3, 2, 2, 3>(tmA, tmB, a, clusters, st);
-        if (p.na == 2 && p.nb == 2 && p.nprod == 4) return run_pair<0, 3, 2, 2, 4>(tmA, tmB, a, clusters, st);
+        if (p.na == 1 && p.nb == 1) return run_pair<0, 6, 1, 1, 1>(tmA, tmB, a, max_clusters, st);
+        if (p.na == 2 && p.nb == 1 && p.nprod == 2) return run_pair<0, 4, 2, 1, 2>(tmA, tmB, a, max_clusters, st);
+        if (p.na == 2 && p.nb == 2 && p.nprod == 3) return run_pair<0, 3, 2, 2, 3>(tmA, tmB, a, max_clusters, st);
+        if (p.na == 2 && p.nb == 2 && p.nprod == 4) return run_pair<0, 3, 2, 2, 4>(tmA, tmB, a, max_clusters, st);
         return cudaErrorInvalidValue;
     }
     const int grid = a.num_tiles < p.sm_count ? a.num_tiles : p.sm_count;

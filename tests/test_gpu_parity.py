@@ -417,6 +417,22 @@ def test_gemm_tile_kernels(b, monkeypatch, tile, dt, mnk):
     assert normwise_dev(C, ref, A, B, 1.0, 0.5, C0) <= TOL_NORMWISE
 
 
+@pytest.mark.parametrize("dt", [0, 1, 2])
+@pytest.mark.parametrize("mnk", [(2560, 2560, 192), (2304, 2600, 320), (256, 2560, 128)])
+def test_gemm_pair_full_and_half_width_units(b, monkeypatch, dt, mnk):
+    # 100 and 99 tiles of 256 x 256 over 76 CTA pairs: the tiles of the partial last round run as
+    # 256 x 128 halves after the full tiles; 10 tiles: every tile runs as two halves
+    monkeypatch.setenv("TCGEMM_TILE", "pair")
+    m, n, k = mnk
+    A = synth.uniform((m, k), seed=131)
+    B = synth.uniform((k, n), seed=132)
+    C0 = synth.uniform((m, n), seed=133)
+    C = _run_mixed(b, dt, A, B, 1.0, -0.5, C0)
+    ref = og.gemm_mixed(DT_NAME[dt], A, B, 1.0, -0.5, C0)
+    ok, info = elementwise_ok(C, ref, _mag(dt, A, B, 1.0, -0.5, C0), k)
+    assert ok, info
+
+
 @pytest.mark.parametrize("tile", ["single", "pair"])
 @pytest.mark.parametrize("nprod", [2, 3, 4])
 def test_split_tile_kernels(b, monkeypatch, tile, nprod):
