@@ -752,7 +752,9 @@ def main():
     sm_mhz = clocks.get("sm_mhz") or None
     spec_peak_max = sm_count * SPEC_FLOP_PER_CLK_SM * pk["sm_max_mhz"] * 1e6 / 1e12
     spec_peak_clk = sm_count * SPEC_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12 if sm_mhz else None
-    peak = pk["bf16_tflops"]
+    # the GEMM runs back to back inside the timed step loop, after a 1 s soak, under the power cap:
+    # the sustained figure is its denominator (the burst one is reported beside it)
+    peak = pk["bf16_tflops_sustained"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -773,7 +775,8 @@ def main():
         "roofline": {"bound": "tensor", "achieved": gemm_tflops, "peak": peak, "unit": "TFLOP/s",
                      "frac": gemm_tflops / peak, "traffic": profiled_traffic(),
                      "kernel": "k_tc_gemm_pair (tcgen05.mma.cta_group::2, 256x256 tiles per CTA pair)",
-                     "peak_source": f"{pk['source']} bf16 burst"},
+                     "peak_source": f"{pk['source']} bf16 sustained (kernel timed inside the step loop)",
+                     "frac_of_burst": gemm_tflops / pk["bf16_tflops"], "burst_peak": pk["bf16_tflops"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * N * N * 4,
                 "d2h_bytes_per_step": N * N * 4, "ms_per_step": e2e_ms,
                 "note": "pinned host A, B, C0 in and C out every step; copy-in, compute and copy-out on "
