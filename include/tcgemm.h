@@ -102,6 +102,27 @@ tc_status tc_quantize(int32_t dt, int64_t rows, int64_t cols, const float* src, 
 tc_status tc_split(int32_t piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src,
                    int32_t transpose, void* dst_hi, void* dst_lo, int64_t ld_dst, void* stream);
 
+/* Many FP32 -> FP16/BF16 roundings (as tc_quantize) in one launch: job j
+ * rounds the rows x cols FP32 matrix at src (row-major, ld_src) into dst
+ * (ld_dst), transposed (dst cols x rows) if transpose != 0.  For a batch of
+ * small operands, where a launch per operand costs more than the rounding.
+ *   dt: TC_F16 or TC_BF16 (E4M3 needs a scale per tensor: use tc_quantize).
+ *   workspace: 256-byte aligned device memory of at least
+ *   tc_quantize_batch_workspace_bytes(count, jobs) bytes for the job table
+ *   and the tile list, not touched by other work until the kernel has
+ *   finished on `stream`.  The job array itself is read on the host. */
+typedef struct tc_quantize_job {
+    int64_t rows, cols;
+    const float* src;
+    int64_t ld_src;
+    void* dst;
+    int64_t ld_dst;
+    int32_t transpose, reserved;
+} tc_quantize_job;
+size_t tc_quantize_batch_workspace_bytes(int32_t count, const tc_quantize_job* jobs);
+tc_status tc_quantize_batch(int32_t dt, int32_t count, const tc_quantize_job* jobs,
+                            void* workspace, size_t workspace_bytes, void* stream);
+
 /* Scaled residual split (Ootomo and Yokota, 2022, refining Sec. V):
  *   hi = RNE(x), lo = RNE((x - hi) * 2^s), s = 11 for TC_F16, 8 for TC_BF16.
  *   The scaling keeps residuals of small |x| in the normal range of the
@@ -274,6 +295,20 @@ tc_status gemm_grouped(int32_t dt, int32_t count, const tc_problem* problems,
 tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_problem* problems,
                                const void* a_base, int32_t la, const void* b_base, int32_t lb,
                                float* c_base, float alpha, float beta, void* stream);
+
+/* The grouped GEMM of gemm_grouped_noalloc, with its problem table and tile
+ * schedule in caller-owned device memory instead of the library's static
+ * array: calls on different streams with different workspaces may overlap.
+ *   workspace: 256-byte aligned device memory of at least
+ *   gemm_grouped_workspace_bytes(count, problems) bytes, not touched by other
+ *   work until this call's kernel has finished on `stream`.
+ * Runs the mma.sync kernel (64 x 64 tiles) for both B layouts; arguments and
+ * errors otherwise as gemm_grouped. */
+size_t gemm_grouped_workspace_bytes(int32_t count, const tc_problem* problems);
+tc_status gemm_grouped_ws(int32_t dt, int32_t count, const tc_problem* problems,
+                          const void* a_base, int32_t la, const void* b_base, int32_t lb,
+                          float* c_base, float alpha, float beta,
+                          void* workspace, size_t workspace_bytes, void* stream);
 
 /* ------------------------------------------------------------------------ */
 /* Autotuning (the paper picked the best CUTLASS tiling per size, Sec. VI)    */

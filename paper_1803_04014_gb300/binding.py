@@ -45,6 +45,12 @@ class tc_problem(ctypes.Structure):
                 ("reserved2", ctypes.c_int32)]
 
 
+class tc_quantize_job(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int64), ("cols", ctypes.c_int64), ("src", ctypes.c_void_p),
+                ("ld_src", ctypes.c_int64), ("dst", ctypes.c_void_p), ("ld_dst", ctypes.c_int64),
+                ("transpose", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class tc_serve_cfg(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
                 ("num_streams", ctypes.c_int32), ("queue_capacity", ctypes.c_int32), ("reserved", ctypes.c_int32)]
@@ -97,6 +103,11 @@ SIGNATURES = {
     "gemm_grouped": (_i32, [_i32, _i32, ctypes.POINTER(tc_problem), _vp, _i32, _vp, _i32, _vp, _f32, _f32, _vp]),
     "gemm_grouped_noalloc": (_i32, [_i32, _i32, ctypes.POINTER(tc_problem), _vp, _i32, _vp, _i32, _vp, _f32, _f32,
                                     _vp]),
+    "gemm_grouped_workspace_bytes": (_sz, [_i32, ctypes.POINTER(tc_problem)]),
+    "gemm_grouped_ws": (_i32, [_i32, _i32, ctypes.POINTER(tc_problem), _vp, _i32, _vp, _i32, _vp, _f32, _f32, _vp,
+                               _sz, _vp]),
+    "tc_quantize_batch_workspace_bytes": (_sz, [_i32, ctypes.POINTER(tc_quantize_job)]),
+    "tc_quantize_batch": (_i32, [_i32, _i32, ctypes.POINTER(tc_quantize_job), _vp, _sz, _vp]),
     "tc_autotune_gemm": (_i32, [_i32, _i64, _i64, _i64, _vp, ctypes.POINTER(ctypes.c_double)]),
     "gemm_grouped_plan_autotune": (_i32, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     "tc_autotune_save": (_i32, [ctypes.c_char_p]),
@@ -278,6 +289,39 @@ def gemm_grouped_noalloc(dt, problems, a_base, la, b_base, lb, c_base, alpha, be
     arr = problems if isinstance(problems, ctypes.Array) else problems_array(problems)
     return _check(load().gemm_grouped_noalloc(dt, len(arr), arr, _ptr(a_base), la, _ptr(b_base), lb, _ptr(c_base),
                                               alpha, beta, _stream(stream)), "gemm_grouped_noalloc")
+
+
+def gemm_grouped_workspace_bytes(problems) -> int:
+    arr = problems if isinstance(problems, ctypes.Array) else problems_array(problems)
+    return int(load().gemm_grouped_workspace_bytes(len(arr), arr))
+
+
+def gemm_grouped_ws(dt, problems, a_base, la, b_base, lb, c_base, alpha, beta, workspace, workspace_bytes,
+                    stream=None):
+    """gemm_grouped_noalloc with the schedule in caller-owned device memory."""
+    arr = problems if isinstance(problems, ctypes.Array) else problems_array(problems)
+    return _check(load().gemm_grouped_ws(dt, len(arr), arr, _ptr(a_base), la, _ptr(b_base), lb, _ptr(c_base), alpha,
+                                         beta, _ptr(workspace), int(workspace_bytes), _stream(stream)),
+                  "gemm_grouped_ws")
+
+
+def quantize_jobs_array(jobs):
+    """[(rows, cols, src, ld_src, dst, ld_dst, transpose)] -> ctypes array of tc_quantize_job."""
+    arr = (tc_quantize_job * len(jobs))()
+    for i, (rows, cols, src, ld_src, dst, ld_dst, tr) in enumerate(jobs):
+        arr[i] = tc_quantize_job(int(rows), int(cols), _ptr(src), int(ld_src), _ptr(dst), int(ld_dst), int(tr), 0)
+    return arr
+
+
+def tc_quantize_batch_workspace_bytes(jobs) -> int:
+    arr = jobs if isinstance(jobs, ctypes.Array) else quantize_jobs_array(jobs)
+    return int(load().tc_quantize_batch_workspace_bytes(len(arr), arr))
+
+
+def tc_quantize_batch(dt, jobs, workspace, workspace_bytes, stream=None):
+    arr = jobs if isinstance(jobs, ctypes.Array) else quantize_jobs_array(jobs)
+    return _check(load().tc_quantize_batch(dt, len(arr), arr, _ptr(workspace), int(workspace_bytes),
+                                           _stream(stream)), "tc_quantize_batch")
 
 
 def tc_autotune_gemm(dt, m, n, k, stream=None):

@@ -839,43 +839,41 @@ tc_status noalloc_setup(NoAllocDevice** out) {
 
 }  // namespace
 
-extern "C" tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_problem* problems, const void* a_base,
-                                          int32_t la, const void* b_base, int32_t lb, float* c_base, float alpha,
-                                          float beta, void* stream) {
-    if (dt != TC_F16 && dt != TC_BF16) return fail(TC_ERR_UNSUPPORTED, "gemm_grouped_noalloc: F16 or BF16 only");
-    if (la != TC_ROW_MAJOR) return fail(TC_ERR_UNSUPPORTED, "gemm_grouped_noalloc: A must be row-major");
-    if (lb != TC_ROW_MAJOR && lb != TC_COL_MAJOR) return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: bad layout");
-    if (count < 0 || (count > 0 && !problems)) return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: bad problem array");
+namespace {
+
+// Host half of a plan-free grouped GEMM on the mma.sync kernel (64 x 64 tiles): checks the
+// call and builds in `host` the problem table (padded to 256 bytes) followed by the tile list,
+// tiles in the longest-first order of a plan.
+tc_status grouped_mma_host(const char* name, int32_t dt, int32_t count, const tc_problem* problems,
+                           const void* a_base, int32_t la, const void* b_base, int32_t lb, const float* c_base,
+                           std::vector<unsigned char>& host, size_t* desc_bytes_out, int64_t* tiles_out) {
+    if (dt != TC_F16 && dt != TC_BF16) return fail(TC_ERR_UNSUPPORTED, "%s: F16 or BF16 only", name);
+    if (la != TC_ROW_MAJOR) return fail(TC_ERR_UNSUPPORTED, "%s: A must be row-major", name);
+    if (lb != TC_ROW_MAJOR && lb != TC_COL_MAJOR) return fail(TC_ERR_INVALID, "%s: bad layout", name);
+    if (count < 0 || (count > 0 && !problems)) return fail(TC_ERR_INVALID, "%s: bad problem array", name);
+    *tiles_out = 0;
+    *desc_bytes_out = 0;
+    host.clear();
     if (count == 0) return TC_OK;
-    if (!a_base || !b_base || !c_base) return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: null base pointer");
+    if (!a_base || !b_base || !c_base) return fail(TC_ERR_INVALID, "%s: null base pointer", name);
     if (!aligned(a_base, 16) || !aligned(b_base, 16) || !aligned(c_base, 8))
-        return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: base pointers must be 16-byte aligned (C: 8)");
-    // schedule on the host: the same tiles and longest-first order as a plan
+        return fail(TC_ERR_INVALID, "%s: base pointers must be 16-byte aligned (C: 8)", name);
     int64_t num_tiles = 0;
     for (int32_t g = 0; g < count; ++g) {
         const tc_problem& p = problems[g];
-        if (p.m < 1 || p.n < 1 || p.k < 1) return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: problem %d has a zero size", g);
+        if (p.m < 1 || p.n < 1 || p.k < 1) return fail(TC_ERR_INVALID, "%s: problem %d has a zero size", name, g);
         if (p.lda < p.k || p.ldb < (lb == TC_ROW_MAJOR ? p.n : p.k) || p.ldc < p.n)
-            return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: problem %d leading dimension too small", g);
+            return fail(TC_ERR_INVALID, "%s: problem %d leading dimension too small", name, g);
         if (p.lda % 8 || p.ldb % 8 || p.off_a % 8 || p.off_b % 8)
-            return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: problem %d rows not 16-byte aligned", g);
+            return fail(TC_ERR_INVALID, "%s: problem %d rows not 16-byte aligned", name, g);
         if (p.off_a < 0 || p.off_b < 0 || p.off_c < 0)
-            return fail(TC_ERR_INVALID, "gemm_grouped_noalloc: problem %d negative offset", g);
+            return fail(TC_ERR_INVALID, "%s: problem %d negative offset", name, g);
         num_tiles += int64_t((p.m + tcg::kGroupedTileM - 1) / tcg::kGroupedTileM) *
                      ((p.n + tcg::kGroupedTileN - 1) / tcg::kGroupedTileN);
     }
+    if (num_tiles > 0x7FFFFFFF) return fail(TC_ERR_INVALID, "%s: too many tiles", name);
     const size_t desc_bytes = (size_t(count) * sizeof(tcg::GroupedProblemDev) + 255) / 256 * 256;
-    const size_t need = desc_bytes + size_t(num_tiles) * sizeof(tcg::GroupedTileDev);
-    if (need > kNoAllocScratchBytes)
-        return fail(TC_ERR_INVALID,
-                    "gemm_grouped_noalloc: %d problems (%lld tiles) need %zu bytes of scratch; the static maximum "
-                    "is %zu bytes (use gemm_grouped_plan_create for larger groups)",
-                    count, (long long)num_tiles, need, kNoAllocScratchBytes);
-    NoAllocDevice* d;
-    tc_status s = noalloc_setup(&d);
-    if (s != TC_OK) return s;
-
-    std::vector<unsigned char> host(need);
+    host.assign(desc_bytes + size_t(num_tiles) * sizeof(tcg::GroupedTileDev), 0);
     auto* hp = reinterpret_cast<tcg::GroupedProblemDev*>(host.data());
     struct T { int64_t cost; tcg::GroupedTileDev t; };
     std::vector<T> tiles;
@@ -895,17 +893,148 @@ extern "C" tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_pr
     std::stable_sort(tiles.begin(), tiles.end(), [](const T& a, const T& b) { return a.cost > b.cost; });
     auto* ht = reinterpret_cast<tcg::GroupedTileDev*>(host.data() + desc_bytes);
     for (size_t i = 0; i < tiles.size(); ++i) ht[i] = tiles[i].t;
+    *desc_bytes_out = desc_bytes;
+    *tiles_out = num_tiles;
+    return TC_OK;
+}
 
-    cudaStream_t st = as_stream(stream);
-    unsigned char* dev_base = static_cast<unsigned char*>(d->scratch);
+// Upload the host half to `dev_base` and launch.
+tc_status grouped_mma_enqueue(const char* name, int32_t dt, int32_t lb, const std::vector<unsigned char>& host,
+                              size_t desc_bytes, int64_t num_tiles, unsigned char* dev_base, const void* a_base,
+                              const void* b_base, float* c_base, float alpha, float beta, int sm_count,
+                              cudaStream_t st) {
     // pageable source: the call returns once the bytes are staged, so `host` may go out of scope
-    cudaError_t e = cudaMemcpyAsync(dev_base, host.data(), need, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "gemm_grouped_noalloc: upload");
+    cudaError_t e = cudaMemcpyAsync(dev_base, host.data(), host.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, name);
     return enqueue(tcg::launch_grouped(dt, lb, reinterpret_cast<const tcg::GroupedProblemDev*>(dev_base),
                                        reinterpret_cast<const tcg::GroupedTileDev*>(dev_base + desc_bytes),
                                        static_cast<int32_t>(num_tiles), a_base, b_base, c_base, alpha, beta,
-                                       d->sm_count, st),
-                   "gemm_grouped_noalloc launch");
+                                       sm_count, st),
+                   name);
+}
+
+}  // namespace
+
+extern "C" tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_problem* problems, const void* a_base,
+                                          int32_t la, const void* b_base, int32_t lb, float* c_base, float alpha,
+                                          float beta, void* stream) {
+    std::vector<unsigned char> host;
+    size_t desc_bytes = 0;
+    int64_t num_tiles = 0;
+    tc_status s = grouped_mma_host("gemm_grouped_noalloc", dt, count, problems, a_base, la, b_base, lb, c_base, host,
+                                   &desc_bytes, &num_tiles);
+    if (s != TC_OK || count == 0) return s;
+    if (host.size() > kNoAllocScratchBytes)
+        return fail(TC_ERR_INVALID,
+                    "gemm_grouped_noalloc: %d problems (%lld tiles) need %zu bytes of scratch; the static maximum "
+                    "is %zu bytes (use gemm_grouped_plan_create for larger groups)",
+                    count, (long long)num_tiles, host.size(), kNoAllocScratchBytes);
+    NoAllocDevice* d;
+    if ((s = noalloc_setup(&d)) != TC_OK) return s;
+    return grouped_mma_enqueue("gemm_grouped_noalloc", dt, lb, host, desc_bytes, num_tiles,
+                               static_cast<unsigned char*>(d->scratch), a_base, b_base, c_base, alpha, beta,
+                               d->sm_count, as_stream(stream));
+}
+
+extern "C" size_t gemm_grouped_workspace_bytes(int32_t count, const tc_problem* problems) {
+    if (count <= 0 || !problems) return 0;
+    int64_t num_tiles = 0;
+    for (int32_t g = 0; g < count; ++g) {
+        const tc_problem& p = problems[g];
+        if (p.m < 1 || p.n < 1) continue;
+        num_tiles += int64_t((p.m + tcg::kGroupedTileM - 1) / tcg::kGroupedTileM) *
+                     ((p.n + tcg::kGroupedTileN - 1) / tcg::kGroupedTileN);
+    }
+    return (size_t(count) * sizeof(tcg::GroupedProblemDev) + 255) / 256 * 256 +
+           size_t(num_tiles) * sizeof(tcg::GroupedTileDev);
+}
+
+extern "C" tc_status gemm_grouped_ws(int32_t dt, int32_t count, const tc_problem* problems, const void* a_base,
+                                     int32_t la, const void* b_base, int32_t lb, float* c_base, float alpha,
+                                     float beta, void* workspace, size_t workspace_bytes, void* stream) {
+    std::vector<unsigned char> host;
+    size_t desc_bytes = 0;
+    int64_t num_tiles = 0;
+    tc_status s = grouped_mma_host("gemm_grouped_ws", dt, count, problems, a_base, la, b_base, lb, c_base, host,
+                                   &desc_bytes, &num_tiles);
+    if (s != TC_OK || count == 0) return s;
+    if (!workspace || !aligned(workspace, 256))
+        return fail(TC_ERR_INVALID, "gemm_grouped_ws: workspace must be a 256-byte aligned device pointer");
+    if (workspace_bytes < host.size())
+        return fail(TC_ERR_INVALID, "gemm_grouped_ws: workspace of %zu bytes, need %zu", workspace_bytes, host.size());
+    Device* d;
+    if ((s = get_device(&d)) != TC_OK) return s;
+    return grouped_mma_enqueue("gemm_grouped_ws", dt, lb, host, desc_bytes, num_tiles,
+                               static_cast<unsigned char*>(workspace), a_base, b_base, c_base, alpha, beta,
+                               d->sm_count, as_stream(stream));
+}
+
+// ------------------------------------------------------------ batched rounding
+
+namespace {
+
+int64_t quant_job_tiles(const tc_quantize_job& j) {
+    return ((j.rows + tcg::kQuantTileRows - 1) / tcg::kQuantTileRows) *
+           ((j.cols + tcg::kQuantTileCols - 1) / tcg::kQuantTileCols);
+}
+
+}  // namespace
+
+extern "C" size_t tc_quantize_batch_workspace_bytes(int32_t count, const tc_quantize_job* jobs) {
+    if (count <= 0 || !jobs) return 0;
+    int64_t tiles = 0;
+    for (int32_t j = 0; j < count; ++j)
+        if (jobs[j].rows > 0 && jobs[j].cols > 0) tiles += quant_job_tiles(jobs[j]);
+    return (size_t(count) * sizeof(tcg::QuantJobDev) + 255) / 256 * 256 + size_t(tiles) * sizeof(tcg::QuantTileDev);
+}
+
+extern "C" tc_status tc_quantize_batch(int32_t dt, int32_t count, const tc_quantize_job* jobs, void* workspace,
+                                       size_t workspace_bytes, void* stream) {
+    if (dt != TC_F16 && dt != TC_BF16) return fail(TC_ERR_UNSUPPORTED, "tc_quantize_batch: F16 or BF16 only");
+    if (count < 0 || (count > 0 && !jobs)) return fail(TC_ERR_INVALID, "tc_quantize_batch: bad job array");
+    if (count == 0) return TC_OK;
+    const size_t desc_bytes = (size_t(count) * sizeof(tcg::QuantJobDev) + 255) / 256 * 256;
+    int64_t ntiles = 0;
+    for (int32_t j = 0; j < count; ++j) {
+        const tc_quantize_job& J = jobs[j];
+        if (J.rows < 0 || J.cols < 0) return fail(TC_ERR_INVALID, "tc_quantize_batch: job %d negative size", j);
+        if (J.rows == 0 || J.cols == 0) continue;
+        if (!J.src || !J.dst) return fail(TC_ERR_INVALID, "tc_quantize_batch: job %d null pointer", j);
+        if (J.ld_src < J.cols || J.ld_dst < (J.transpose ? J.rows : J.cols))
+            return fail(TC_ERR_INVALID, "tc_quantize_batch: job %d leading dimension too small", j);
+        if (!aligned(J.src, 4) || !aligned(J.dst, 2))
+            return fail(TC_ERR_INVALID, "tc_quantize_batch: job %d misaligned pointer", j);
+        ntiles += quant_job_tiles(J);
+    }
+    if (ntiles > 0x7FFFFFFF) return fail(TC_ERR_INVALID, "tc_quantize_batch: too many tiles");
+    const size_t need = desc_bytes + size_t(ntiles) * sizeof(tcg::QuantTileDev);
+    if (!workspace || !aligned(workspace, 256))
+        return fail(TC_ERR_INVALID, "tc_quantize_batch: workspace must be a 256-byte aligned device pointer");
+    if (workspace_bytes < need)
+        return fail(TC_ERR_INVALID, "tc_quantize_batch: workspace of %zu bytes, need %zu", workspace_bytes, need);
+    Device* d;
+    tc_status s = get_device(&d);
+    if (s != TC_OK) return s;
+    std::vector<unsigned char> host(need, 0);
+    auto* hj = reinterpret_cast<tcg::QuantJobDev*>(host.data());
+    auto* ht = reinterpret_cast<tcg::QuantTileDev*>(host.data() + desc_bytes);
+    int64_t t = 0;
+    for (int32_t j = 0; j < count; ++j) {
+        const tc_quantize_job& J = jobs[j];
+        hj[j] = {J.src, J.dst, J.rows, J.cols, J.ld_src, J.ld_dst, J.transpose ? 1 : 0,
+                 (aligned(J.dst, 16) && J.ld_dst % 8 == 0) ? 1 : 0};
+        if (J.rows == 0 || J.cols == 0) continue;
+        for (int64_t r = 0; r < J.rows; r += tcg::kQuantTileRows)
+            for (int64_t c = 0; c < J.cols; c += tcg::kQuantTileCols) ht[t++] = {j, 0, r, c};
+    }
+    cudaStream_t st = as_stream(stream);
+    cudaError_t e = cudaMemcpyAsync(workspace, host.data(), need, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "tc_quantize_batch: upload");
+    auto* dev = static_cast<unsigned char*>(workspace);
+    return enqueue(tcg::launch_quantize_jobs(dt, reinterpret_cast<const tcg::QuantJobDev*>(dev),
+                                             reinterpret_cast<const tcg::QuantTileDev*>(dev + desc_bytes),
+                                             static_cast<int32_t>(ntiles), st),
+                   "tc_quantize_batch launch");
 }
 
 // ------------------------------------------------------------ autotuning

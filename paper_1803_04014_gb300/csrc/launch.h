@@ -18,6 +18,21 @@ cudaError_t launch_quantize(int dt, int64_t rows, int64_t cols, const float* src
 cudaError_t launch_split(int scheme, int piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src,
                          bool transpose, void* const* dst, int64_t ld_dst, cudaStream_t st);
 cudaError_t launch_scale_c(int64_t m, int64_t n, float beta, float* C, int64_t ldc, cudaStream_t st);
+// A batch of FP16/BF16 conversions: job j converts rows x cols FP32 at src (ld_src) into dst
+// (ld_dst), transposed if asked; vec = every 8-element chunk of dst starts on 16 bytes.
+struct QuantJobDev {
+    const float* src;
+    void* dst;
+    int64_t rows, cols, ld_src, ld_dst;
+    int32_t transpose, vec;
+};
+struct QuantTileDev {  // 64 source rows x 32 source columns of one job
+    int32_t job, pad;
+    int64_t r0, c0;
+};
+constexpr int kQuantTileRows = 64, kQuantTileCols = 32;
+cudaError_t launch_quantize_jobs(int dt, const QuantJobDev* jobs, const QuantTileDev* tiles, int32_t ntiles,
+                                 cudaStream_t st);
 
 // ---- kernel_setup.cu
 // Raises `kern`'s dynamic shared-memory limit to smem_bytes (if > 0) and, with

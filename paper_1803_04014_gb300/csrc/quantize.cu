@@ -349,6 +349,73 @@ __global__ void __launch_bounds__(256) k_split_transpose(int64_t rows, int64_t c
     }
 }
 
+// Many independent FP32 -> FP16/BF16 conversions in one launch (a batch of
+// small operands, where one launch per operand would cost more than the
+// conversion).  The host cuts every job into 64 x 32 tiles of its source; a
+// block converts one tile through shared memory and writes it either in the
+// source's layout (rows of 32 elements, four 16-byte chunks each) or
+// transposed (rows of 64 elements, eight chunks each).
+template <int DT>
+__global__ void __launch_bounds__(256) k_quantize_jobs(const QuantJobDev* __restrict__ jobs,
+                                                       const QuantTileDev* __restrict__ tiles, int32_t ntiles) {
+    using T = typename Narrow<DT>::T;
+    constexpr int TR = 64, TC = 32;
+    __shared__ float tile[TR][TC + 1];
+    for (int32_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const QuantTileDev td = tiles[ti];
+        const QuantJobDev J = jobs[td.job];
+        const float* __restrict__ src = J.src;
+        T* __restrict__ dst = static_cast<T*>(J.dst);
+        const int64_t r0 = td.r0, c0 = td.c0;
+        const int t = threadIdx.x;
+        float v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = t + q * 256;
+            const int rr = i / TC, cc = i - rr * TC;
+            const int64_t r = r0 + rr, c = c0 + cc;
+            v[q] = (r < J.rows && c < J.cols) ? __ldcs(src + r * J.ld_src + c) : 0.0f;
+        }
+        __syncthreads();  // the previous tile's readers are done
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = t + q * 256;
+            tile[i / TC][i % TC] = v[q];
+        }
+        __syncthreads();
+        T o[8];
+        T* d;
+        int64_t avail;  // destination elements of this chunk inside the job
+        if (J.transpose) {
+            const int cc = t >> 3, j = t & 7;  // destination row c0 + cc, elements r0 + 8j ..
+            const int64_t c = c0 + cc;
+            avail = (c < J.cols) ? J.rows - (r0 + j * 8) : 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) o[q] = Narrow<DT>::cvt(tile[j * 8 + q][cc], 1.0f);
+            d = dst + c * J.ld_dst + r0 + j * 8;
+        } else {
+            const int rr = t >> 2, q4 = t & 3;  // destination row r0 + rr, elements c0 + 8 q4 ..
+            const int64_t r = r0 + rr;
+            avail = (r < J.rows) ? J.cols - (c0 + q4 * 8) : 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) o[q] = Narrow<DT>::cvt(tile[rr][q4 * 8 + q], 1.0f);
+            d = dst + r * J.ld_dst + c0 + q4 * 8;
+        }
+        if (avail >= 8 && J.vec) {
+            uint4 w;
+            w.x = o[0] | (uint32_t(o[1]) << 16);
+            w.y = o[2] | (uint32_t(o[3]) << 16);
+            w.z = o[4] | (uint32_t(o[5]) << 16);
+            w.w = o[6] | (uint32_t(o[7]) << 16);
+            *reinterpret_cast<uint4*>(d) = w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < avail) d[q] = o[q];
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_scale_c(int64_t m, int64_t n, float beta, float* C, int64_t ldc) {
     const int64_t total = m * n;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
@@ -461,6 +528,17 @@ cudaError_t launch_split(int scheme, int piece, int64_t rows, int64_t cols, cons
                                : split_piece<kDtBF16, kSplitScaled>(rows, cols, src, ld_src, transpose, dst, ld_dst, st);
     return piece == kDtF16 ? split_piece<kDtF16, kSplitPlain>(rows, cols, src, ld_src, transpose, dst, ld_dst, st)
                            : split_piece<kDtBF16, kSplitPlain>(rows, cols, src, ld_src, transpose, dst, ld_dst, st);
+}
+
+cudaError_t launch_quantize_jobs(int dt, const QuantJobDev* jobs, const QuantTileDev* tiles, int32_t ntiles,
+                                 cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    const unsigned grid = static_cast<unsigned>(ntiles < 152 * 16 ? ntiles : 152 * 16);
+    if (dt == kDtF16)
+        k_quantize_jobs<kDtF16><<<grid, 256, 0, st>>>(jobs, tiles, ntiles);
+    else
+        k_quantize_jobs<kDtBF16><<<grid, 256, 0, st>>>(jobs, tiles, ntiles);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_scale_c(int64_t m, int64_t n, float beta, float* C, int64_t ldc, cudaStream_t st) {

@@ -8,15 +8,21 @@
 //   2. admits queued requests in arrival order while an in-flight slot is
 //      free and their workspace fits in the HBM budget (a first-fit arena
 //      carved out of one allocation made at serve_open),
-//   3. launches each admitted request on the least-recently used of S streams
-//      (round robin), so requests that arrive while others run overlap them
-//      on the GPU.  Launches happen outside the lock that submit and poll
-//      take.
-// A request's kernels and tile shapes depend only on (mode, m, n, k), so its
-// result is bitwise the same alone and in any mix.
+//   3. launches the admitted requests on S streams in turn, so requests that
+//      arrive while others run overlap them on the GPU.  Small FP16/BF16
+//      requests (m n k <= 2^28, each of m, n, k <= 4096) admitted together
+//      are batched: their roundings run as one tc_quantize_batch launch and
+//      their GEMMs as one grouped launch (gemm_grouped_ws), grouped by mode,
+//      alpha and beta; every other request gets its own launches.  Launches
+//      happen outside the lock that submit and poll take.
+// Whether a request is batched, and its kernels and tile shapes, depend only
+// on (mode, m, n, k) and its C alignment, so its result is bitwise the same
+// alone and in any mix.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
+#include <cstdint>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -38,8 +44,25 @@ constexpr size_t kAlign = 256;
 inline size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 inline int64_t pad_k(int64_t k, int64_t to) { return (k + to - 1) / to * to; }
 
+constexpr int64_t kBatchWork = int64_t(1) << 28;  // m n k of a request run in a batch
+constexpr int64_t kBatchDim = 4096;
+constexpr size_t kDescBytes = size_t(4) << 20;    // per stream: job tables and tile lists of batches
+constexpr size_t kMaxBatch = 64;
+
+bool batched(const tc_request& r) {
+    return (r.mode == TC_MODE_F16 || r.mode == TC_MODE_BF16) && r.m <= kBatchDim && r.n <= kBatchDim &&
+           r.k <= kBatchDim && r.m * r.n * r.k <= kBatchWork && r.ldc <= 0x7FFFFFFF &&
+           ((reinterpret_cast<uintptr_t>(r.A) | reinterpret_cast<uintptr_t>(r.B) |
+             reinterpret_cast<uintptr_t>(r.C)) & 3u) == 0;
+}
+
 // Workspace a request needs in the arena (quantised copies or split pieces).
 size_t request_bytes(const tc_request& r) {
+    if (batched(r)) {
+        // row-major A (m x kp) and B (k x np), both 16-byte aligned rows
+        return round_up(static_cast<size_t>(r.m * pad_k(r.k, 8) * 2), kAlign) +
+               round_up(static_cast<size_t>(r.k * pad_k(r.n, 8) * 2), kAlign);
+    }
     switch (r.mode) {
         case TC_MODE_F16:
         case TC_MODE_BF16: {
@@ -149,12 +172,63 @@ tc_status launch_request(const tc_request& r, void* ws, cudaStream_t st) {
     }
 }
 
+// One launch pair for `members` (same mode, alpha, beta; all batched): their A and B
+// rounded into their workspaces by one tc_quantize_batch, their GEMMs by one
+// gemm_grouped_ws with the arena as the A and B base.  Job tables and tile lists go to
+// `desc` (kDescBytes of device memory of this stream: stream order keeps an earlier
+// batch's kernels ahead of the next upload).
+tc_status launch_batch(const std::vector<Req*>& members, uint8_t* arena_base, uint8_t* desc, cudaStream_t st) {
+    const tc_request& r0 = members.front()->r;
+    const int32_t dt = r0.mode == TC_MODE_F16 ? TC_F16 : TC_BF16;
+    std::vector<tc_quantize_job> jobs;
+    std::vector<tc_problem> probs;
+    uintptr_t c_lo = UINTPTR_MAX;
+    for (Req* q : members) c_lo = std::min(c_lo, reinterpret_cast<uintptr_t>(q->r.C));
+    c_lo &= ~uintptr_t(7);
+    for (Req* q : members) {
+        const tc_request& r = q->r;
+        const int64_t kp = pad_k(r.k, 8), np = pad_k(r.n, 8);
+        uint8_t* aq = static_cast<uint8_t*>(q->ws);
+        uint8_t* bq = aq + round_up(static_cast<size_t>(r.m * kp * 2), kAlign);
+        jobs.push_back({r.m, r.k, static_cast<const float*>(r.A), r.lda, aq, kp, 0, 0});
+        jobs.push_back({r.k, r.n, static_cast<const float*>(r.B), r.ldb, bq, np, 0, 0});
+        tc_problem p{};
+        p.m = static_cast<int32_t>(r.m);
+        p.n = static_cast<int32_t>(r.n);
+        p.k = static_cast<int32_t>(r.k);
+        p.off_a = (aq - arena_base) / 2;
+        p.off_b = (bq - arena_base) / 2;
+        p.off_c = static_cast<int64_t>((reinterpret_cast<uintptr_t>(r.C) - c_lo) / 4);
+        p.lda = static_cast<int32_t>(kp);
+        p.ldb = static_cast<int32_t>(np);
+        p.ldc = static_cast<int32_t>(r.ldc);
+        probs.push_back(p);
+    }
+    const size_t qbytes = round_up(tc_quantize_batch_workspace_bytes(static_cast<int32_t>(jobs.size()), jobs.data()),
+                                   kAlign);
+    const size_t gbytes = gemm_grouped_workspace_bytes(static_cast<int32_t>(probs.size()), probs.data());
+    if (qbytes + gbytes > kDescBytes) return TC_ERR_INVALID;
+    tc_status s = tc_quantize_batch(dt, static_cast<int32_t>(jobs.size()), jobs.data(), desc, qbytes, st);
+    if (s != TC_OK) return s;
+    return gemm_grouped_ws(dt, static_cast<int32_t>(probs.size()), probs.data(), arena_base, TC_ROW_MAJOR,
+                           arena_base, TC_ROW_MAJOR, reinterpret_cast<float*>(c_lo), r0.alpha, r0.beta, desc + qbytes,
+                           kDescBytes - qbytes, st);
+}
+
+// Descriptor bytes a batch member adds (job table entries, tiles, problem, tiles; an upper bound).
+size_t batch_desc_bytes(const tc_request& r) {
+    auto tiles = [](int64_t rows, int64_t cols, int64_t tr, int64_t tc) { return ((rows + tr - 1) / tr) * ((cols + tc - 1) / tc); };
+    return 2 * 64 + size_t(tiles(r.m, r.k, 64, 32) + tiles(r.k, r.n, 64, 32)) * 32 + 64 +
+           size_t(tiles(r.m, r.n, 64, 64)) * 16;
+}
+
 }  // namespace
 
 struct tc_server {
     tc_serve_cfg cfg{};
     int dev = 0;
     std::vector<cudaStream_t> streams;
+    std::vector<uint8_t*> desc;  // per stream: kDescBytes for batch descriptors
     size_t next_stream = 0;
     Arena arena;
     std::mutex mu;
@@ -171,8 +245,9 @@ struct tc_server {
     std::thread sched;
 
     struct Admitted {
-        Req* q;
+        std::vector<Req*> qs;  // one request, or a batch of batched() requests
         cudaStream_t st;
+        uint8_t* desc;
     };
 
     void loop() {
@@ -180,6 +255,8 @@ struct tc_server {
         std::unique_lock<std::mutex> lk(mu);
         bool blocked_on_budget = false;
         std::vector<Admitted> admitted;
+        std::vector<size_t> open_batches;             // indices into `admitted` of batches
+        std::map<size_t, size_t> batch_bytes;         // their descriptor bytes so far
         for (;;) {
             // 1. retire
             bool retired = false;
@@ -208,7 +285,10 @@ struct tc_server {
             }
             // 2. admit in arrival order: take the workspace, an event and a stream under the lock ...
             admitted.clear();
-            while (!queue.empty() && static_cast<int>(running.size() + admitted.size()) < cfg.max_inflight) {
+            open_batches.clear();
+            batch_bytes.clear();
+            size_t n_admitted = 0;
+            while (!queue.empty() && static_cast<int>(running.size() + n_admitted) < cfg.max_inflight) {
                 Req* q = queue.front();
                 void* ws = arena.alloc(q->ws_bytes);
                 if (!ws) {
@@ -225,25 +305,56 @@ struct tc_server {
                 }
                 q->ev = event_pool.back();
                 event_pool.pop_back();
-                admitted.push_back({q, streams[next_stream]});
+                ++n_admitted;
+                if (batched(q->r)) {
+                    // join an open batch of the same mode, alpha and beta with room left, else open one
+                    Admitted* into = nullptr;
+                    for (size_t bi : open_batches) {
+                        Admitted& a = admitted[bi];
+                        const tc_request& r = a.qs.front()->r;
+                        if (r.mode == q->r.mode && r.alpha == q->r.alpha && r.beta == q->r.beta &&
+                            a.qs.size() < kMaxBatch && batch_bytes[bi] + batch_desc_bytes(q->r) + 1024 <= kDescBytes) {
+                            into = &a;
+                            batch_bytes[bi] += batch_desc_bytes(q->r);
+                            break;
+                        }
+                    }
+                    if (into) {
+                        into->qs.push_back(q);
+                        continue;
+                    }
+                    open_batches.push_back(admitted.size());
+                    batch_bytes[admitted.size()] = batch_desc_bytes(q->r);
+                }
+                admitted.push_back({{q}, streams[next_stream], desc[next_stream]});
                 next_stream = (next_stream + 1) % streams.size();
             }
             // ... and launch outside it, so submitters and pollers are not held up by the launches;
             // a request joins `running` (where its event is queried) only once its event is recorded
             if (!admitted.empty()) {
-                launching = admitted.size();
+                launching = n_admitted;
+                uint8_t* abase = arena.base;
                 lk.unlock();
                 for (auto& a : admitted) {
-                    a.q->t_start = now_us();
-                    a.q->status = launch_request(a.q->r, a.q->ws, a.st);
-                    cudaEventRecord(a.q->ev, a.st);
+                    const double t0 = now_us();
+                    tc_status st = TC_OK;
+                    if (batched(a.qs.front()->r))
+                        st = launch_batch(a.qs, abase, a.desc, a.st);
+                    else
+                        st = launch_request(a.qs.front()->r, a.qs.front()->ws, a.st);
+                    for (Req* q : a.qs) {
+                        q->t_start = t0;
+                        q->status = st;
+                        cudaEventRecord(q->ev, a.st);
+                    }
                 }
                 lk.lock();
                 launching = 0;
-                for (auto& a : admitted) {
-                    a.q->state = State::Running;
-                    running.push_back(a.q);
-                }
+                for (auto& a : admitted)
+                    for (Req* q : a.qs) {
+                        q->state = State::Running;
+                        running.push_back(q);
+                    }
                 if (static_cast<int64_t>(running.size()) > peak_inflight) peak_inflight = running.size();
             }
             if (stop && queue.empty() && running.empty()) break;
@@ -277,13 +388,23 @@ tc_status serve_open(const tc_serve_cfg* cfg, tc_server** out) {
     s->arena.init(static_cast<uint8_t*>(base), static_cast<size_t>(cfg->hbm_budget_bytes));
     for (int i = 0; i < cfg->num_streams; ++i) {
         cudaStream_t st;
+        void* d = nullptr;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
             for (auto x : s->streams) cudaStreamDestroy(x);
+            for (auto x : s->desc) cudaFree(x);
             cudaFree(base);
             delete s;
             return TC_ERR_CUDA;
         }
         s->streams.push_back(st);
+        if (cudaMalloc(&d, kDescBytes) != cudaSuccess) {
+            for (auto x : s->streams) cudaStreamDestroy(x);
+            for (auto x : s->desc) cudaFree(x);
+            cudaFree(base);
+            delete s;
+            return TC_ERR_OOM;
+        }
+        s->desc.push_back(static_cast<uint8_t*>(d));
     }
     s->sched = std::thread([s] { s->loop(); });
     *out = s;
@@ -374,6 +495,7 @@ tc_status serve_close(tc_server* s) {
         cudaStreamDestroy(st);
     }
     for (auto ev : s->event_pool) cudaEventDestroy(ev);
+    for (auto d : s->desc) cudaFree(d);
     for (auto& kv : s->by_ticket) delete kv.second;
     cudaFree(s->arena.base);
     delete s;

@@ -52,15 +52,17 @@ def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "tcgemm.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(tc_problem), sizeof(tc_serve_cfg),"
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", sizeof(tc_problem), sizeof(tc_serve_cfg),"
         " sizeof(tc_request), sizeof(tc_result), offsetof(tc_problem, off_c), offsetof(tc_request, C),"
-        " offsetof(tc_request, alpha)); return 0;}\n")
+        " offsetof(tc_request, alpha), sizeof(tc_quantize_job), offsetof(tc_quantize_job, dst),"
+        " offsetof(tc_quantize_job, transpose)); return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(binding.tc_problem), ctypes.sizeof(binding.tc_serve_cfg), ctypes.sizeof(binding.tc_request),
             ctypes.sizeof(binding.tc_result), binding.tc_problem.off_c.offset, binding.tc_request.C.offset,
-            binding.tc_request.alpha.offset]
+            binding.tc_request.alpha.offset, ctypes.sizeof(binding.tc_quantize_job), binding.tc_quantize_job.dst.offset,
+            binding.tc_quantize_job.transpose.offset]
     assert got == want
 
 

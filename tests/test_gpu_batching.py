@@ -1,0 +1,98 @@
+"""GPU parity of the batched entry points the serving loop uses: many small
+roundings in one launch (tc_quantize_batch) and a grouped GEMM whose schedule
+lives in caller-owned device memory (gemm_grouped_ws)."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import gemm as og
+from oracle import numerics as nm
+from tests.gpu_common import dev, elementwise_ok, host, need_gpu, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def b():
+    need_gpu()
+    from paper_1803_04014_gb300 import binding
+    binding.load()
+    return binding
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+def test_quantize_batch_bit_exact(b, dt):
+    tdt = torch.float16 if dt == 0 else torch.bfloat16
+    # ragged sizes, both layouts, padded and unpadded destinations (vector and scalar stores)
+    shapes = [(1, 1, 0, 0), (37, 70, 0, 2), (64, 32, 1, 0), (130, 33, 1, 5), (300, 257, 0, 8), (65, 129, 1, 8),
+              (16, 16, 0, 0), (200, 1000, 1, 3)]
+    srcs, dsts, jobs, want = [], [], [], []
+    for i, (rows, cols, tr, pad) in enumerate(shapes):
+        X = synth.log_uniform_pow2((rows, cols), seed=synth.seed_for(6, i))
+        Xd = dev(X)
+        drows, dcols = (cols, rows) if tr else (rows, cols)
+        ld = dcols + pad
+        D = torch.full((drows, ld), -7.0, dtype=tdt, device="cuda")
+        jobs.append((rows, cols, Xd, cols, D, ld, tr))
+        srcs.append(Xd)
+        dsts.append(D)
+        w = nm.round_to(X, "f16" if dt == 0 else "bf16")
+        want.append(w.T if tr else w)
+    need = b.tc_quantize_batch_workspace_bytes(jobs)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    b.tc_quantize_batch(dt, jobs, ws, need)
+    for (rows, cols, _, _, D, ld, tr), w in zip(jobs, want):
+        got = host(D.to(torch.float64))
+        dcols = rows if tr else cols
+        assert np.array_equal(got[:, :dcols], w)
+        assert np.all(got[:, dcols:] == -7.0)          # padding untouched
+    with pytest.raises(b.TcError):
+        b.tc_quantize_batch(dt, jobs, ws, need - 16)
+    with pytest.raises(b.TcError):
+        b.tc_quantize_batch(2, jobs, ws, need)          # E4M3 needs a per-tensor scale
+
+
+@pytest.mark.parametrize("lb", [0, 1])
+def test_grouped_ws_matches_oracle_and_runs_concurrently(b, lb):
+    rng_sizes = synth.group_sizes(150, seed=synth.seed_for(6, 40))
+    def build(sizes, seed):
+        offa = offb = offc = 0
+        desc, probs = [], []
+        for g, (m, n, k) in enumerate(sizes):
+            desc.append((m, n, k, offa, offb, offc, k, (n if lb == 0 else k), n))
+            offa += m * k
+            offb += k * n
+            offc += m * n
+        A = synth.uniform((offa,), seed=seed).astype(np.float16)
+        B = synth.uniform((offb,), seed=seed + 1).astype(np.float16)
+        C0 = synth.uniform((offc,), seed=seed + 2)
+        return desc, A, B, C0
+    d1, A1, B1, C1 = build(rng_sizes[:80], synth.seed_for(6, 41))
+    d2, A2, B2, C2 = build(rng_sizes[80:], synth.seed_for(6, 44))
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    for desc, A, B, C0, st in ((d1, A1, B1, C1, s1), (d2, A2, B2, C2, s2)):
+        need = b.gemm_grouped_workspace_bytes(desc)
+        ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+        Ad, Bd, Cd = dev(A), dev(B), dev(C0)
+        torch.cuda.synchronize()
+        b.gemm_grouped_ws(0, desc, Ad, 0, Bd, lb, Cd, 1.0, 0.5, ws, need, stream=st)
+        outs.append((desc, A, B, C0, Cd, ws, Ad, Bd))
+    torch.cuda.synchronize()
+    b.tc_sync_status()
+    for desc, A, B, C0, Cd, _, _, _ in outs:
+        Cg = host(Cd)
+        for (m, n, k, oa, ob, oc, lda, ldb, ldc) in desc:
+            Ag = A[oa:oa + m * k].astype(np.float32).reshape(m, k)
+            if lb == 0:
+                Bg = B[ob:ob + k * n].astype(np.float32).reshape(k, n)
+            else:
+                Bg = B[ob:ob + k * n].astype(np.float32).reshape(n, k).T
+            C0g = C0[oc:oc + m * n].reshape(m, n)
+            ref = og.gemm_mixed("f16", Ag, Bg, 1.0, 0.5, C0g)
+            mag = np.abs(Ag.astype(np.float64)) @ np.abs(Bg.astype(np.float64)) + 0.5 * np.abs(C0g)
+            ok, info = elementwise_ok(Cg[oc:oc + m * n].reshape(m, n), ref, mag, k)
+            assert ok, ((m, n, k), info)
+    desc, _, _, _, Cd, ws, Ad, Bd = outs[0]
+    with pytest.raises(b.TcError):
+        b.gemm_grouped_ws(0, desc, Ad, 0, Bd, lb, Cd, 1.0, 0.0, ws, 64)
