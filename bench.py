@@ -270,6 +270,36 @@ def measure_rows(b, A, B, pk, sm_count):
                 "peak_note": "measured bf16 burst" + (" x2 (FP8 rate)" if dt == 2 else ""),
                 "gemm_ms": ms, "quantize_ms": q_ms, "error_vs_fp64": err}
 
+    def sweep():
+        # the square sweep's sizes: the GEMM alone (operands already rounded, beta = 0.5)
+        torch.manual_seed(1803)
+        res = {}
+        for n_ in (1024, 2048, 4096, 8192, 16384):
+            Xa = torch.empty((n_, n_), dtype=torch.float32, device="cuda").uniform_(-1, 1)
+            Xb = torch.empty((n_, n_), dtype=torch.float32, device="cuda").uniform_(-1, 1)
+            Cs = torch.empty((n_, n_), dtype=torch.float32, device="cuda").uniform_(-1, 1)
+            row = {}
+            for dt, name in ((0, "f16"), (1, "bf16"), (2, "e4m3")):
+                tdt = torch.float16 if dt == 0 else (torch.bfloat16 if dt == 1 else torch.uint8)
+                Aq = torch.empty((n_, n_), dtype=tdt, device="cuda")
+                Bq = torch.empty((n_, n_), dtype=tdt, device="cuda")
+                sc = torch.empty(2, dtype=torch.float32, device="cuda")
+                b.tc_quantize(dt, n_, n_, Xa, n_, Aq, n_, 0, sc[0:1])
+                b.tc_quantize(dt, n_, n_, Xb, n_, Bq, n_, 1, sc[1:2])
+                g = lambda: b.gemm_mixed(dt, n_, n_, n_, 1.0, Aq, n_, 0, Bq, n_, 1, 0.5, Cs, n_,
+                                         sc[0:1] if dt == 2 else None, sc[1:2] if dt == 2 else None)
+                it = max(3, min(50, int(2e-2 / (2.0 * n_ ** 3 / 1.5e15))))
+                ms = _time_ms(g, it)
+                tf = 2.0 * n_ ** 3 / (ms * 1e-3) / 1e12
+                row[name] = {"tflops": tf, "frac_of_peak": tf / (peak * (2.0 if dt == 2 else 1.0)), "ms": ms}
+                del Aq, Bq
+            res[str(n_)] = row
+            del Xa, Xb, Cs
+            torch.cuda.empty_cache()
+        res["note"] = "burst peak (x2 for E4M3); inputs uniform[-1,1] rounded on the GPU"
+        return res
+
+    out["gemm_square_sweep"] = _row("gemm_square_sweep", sweep)
     out["gemm_f16_n8192"] = _row("gemm_f16_n8192", lambda: mixed(0, "f16"))
     out["gemm_bf16_n8192"] = _row("gemm_bf16_n8192", lambda: mixed(1, "bf16"))
     out["gemm_e4m3_n8192"] = _row("gemm_e4m3_n8192", lambda: mixed(2, "e4m3"))
@@ -718,16 +748,21 @@ def main():
     torch.cuda.synchronize()
     Ke = max(4, min(K, 12))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0.record(s_in)
-    for i in range(Ke):
-        e2e_step(i)
-    s_out.wait_event(ev_out[(Ke - 1) & 1])
-    e1.record(s_out)
-    torch.cuda.synchronize()
-    e2e_ms = shard.max_over_ranks(e0.elapsed_time(e1) / Ke, dist, device="cuda")
+    # three windows of Ke steps, the median reported: the host link is shared with the node's
+    # other GPUs and their tenants, and a single window can catch a burst of their traffic
+    windows = []
+    for _ in range(3):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(s_in)
+        for i in range(Ke):
+            e2e_step(i)
+        s_out.wait_event(ev_out[(Ke - 1) & 1])
+        e1.record(s_out)
+        torch.cuda.synchronize()
+        windows.append(e0.elapsed_time(e1) / Ke)
+    e2e_ms = shard.max_over_ranks(statistics.median(windows), dist, device="cuda")
     e2e_value = shard.weak_scaling_throughput(flops, world, e2e_ms * 1e-3) / 1e12
     # the same, one step at a time on one stream (no overlap), for reference
     Cd = sets[0]["C"]
@@ -781,6 +816,7 @@ def main():
                 "d2h_bytes_per_step": N * N * 4, "ms_per_step": e2e_ms,
                 "note": "pinned host A, B, C0 in and C out every step; copy-in, compute and copy-out on "
                         "three streams with double-buffered device buffers",
+                "windows_ms_per_step": windows,
                 "serial_ms_per_step": e2e_serial_ms,
                 "serial_value": world * flops / (e2e_serial_ms * 1e-3) / 1e12},
         "autotune": {"best_ms": tune_ms, "table": [" ".join(r) for r in tune_table],
