@@ -13,7 +13,8 @@
 //     epilogue of the current one;
 //   * one thread issues tcgen05.mma 128 x N x 16 (N = the problem's n rounded up
 //     to 16, at most 256) into a double-buffered TMEM accumulator;
-//   * four epilogue warps read the accumulator and store C with alpha/beta.
+//   * eight epilogue warps read the accumulator and store C with alpha/beta,
+//     the two warps of each TMEM lane quarter taking alternate 32-column chunks.
 #include <cstdlib>
 #include <cstring>
 
@@ -209,7 +210,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue (warps 2..9): lanes 32*(warp%4).., columns [128*half, 128*half + 128)
+        // ---------------- epilogue (warps 2..9): lanes 32*(warp%4).., every other 32-column chunk
+        // (chunks half, half + 2, ...), so both warps of a lane quarter share any width of tile
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
         const float alpha = a.alpha, beta = a.beta;
@@ -224,10 +226,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
             const int row = tile.tm * GM + quarter * 32 + lane;
-            const int col0 = tile.tn * GN + half * (GN / 2);
-            const int ncols_tile = max(0, min(GN / 2, P.n - col0));
+            const int col0 = tile.tn * GN;
+            const int ncols_tile = max(0, min(GN, P.n - col0));
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                   static_cast<uint32_t>(acc * GN + half * (GN / 2));
+                                   static_cast<uint32_t>(acc * GN);
             float* crow = a.c_base + P.off_c + static_cast<int64_t>(row) * P.ldc + col0;
             const bool vec_ok = ((P.ldc & 3) == 0) && (((P.off_c + col0) & 3) == 0) &&
                                 ((reinterpret_cast<uintptr_t>(a.c_base) & 15u) == 0);
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                 float* stage = reinterpret_cast<float*>(base_ptr + kEpiOff) + (warp - 2) * kEpiWarpFloats;
                 const int r0 = tile.tm * GM + quarter * 32;
 #pragma unroll 1
-                for (int c = 0; c < ncols_tile; c += 32) {
+                for (int c = half * 32; c < ncols_tile; c += 64) {
                     const int nc = min(32, ncols_tile - c);
                     // lane l writes column (l % 8) * 4 .. +3 of rows q*4 + l/8, q = 0..7
                     const int cc = (lane & 7) * 4;
@@ -291,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                 continue;
             }
 #pragma unroll 1
-            for (int c = 0; c < ncols_tile; c += 32) {
+            for (int c = half * 32; c < ncols_tile; c += 64) {
                 float v[32];
                 tmem_load_32(taddr + c, v);
                 if (row < P.m) {
