@@ -68,10 +68,15 @@ def peaks():
 
 
 def kernel_sources_sha():
+    """Hash of the GEMM kernel's code (comments and blank space removed, so editing a comment
+    keeps a committed profile valid while any change of code invalidates it)."""
     h = hashlib.sha256()
     for name in ("gemm_tc.cu", "tc_ptx.cuh"):
-        with open(os.path.join(ROOT, "paper_1803_04014_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_1803_04014_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

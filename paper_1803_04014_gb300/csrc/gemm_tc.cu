@@ -21,6 +21,12 @@
 //              tile i.
 // Shared-memory tiles use the 128-byte swizzle written by TMA and read by the
 // UMMA descriptors (rows of 128 bytes = one k-block).
+//
+// Three kernels follow: k_tc_gemm (above, single CTA, used for m <= 128),
+// k_tc_gemm_pair (256 x 256 tiles on CTA pairs, the default) and
+// k_tc_gemm_pair_promote (the refined products with their partial sums
+// promoted to FP32 registers; SCALED keeps the correction products in a second
+// accumulator for the scaled split and the three-piece BF16 split).
 #include <cstdlib>
 #include <cstring>
 
@@ -356,7 +362,9 @@ cudaError_t run(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args& args
 // columns of the accumulator in its own TMEM.  Both CTAs' TMA loads complete
 // on the even CTA's "full" barrier; the MMA commits are multicast to the
 // "empty"/"accumulator full" barriers of both CTAs; both epilogues arrive on
-// the even CTA's "accumulator empty" barrier.
+// the even CTA's "accumulator empty" barrier.  A last round of tiles that would
+// leave more than half of the pairs idle runs as 256 x 128 half-width units
+// (unit_coords).
 
 template <int STAGES, int NA, int NB>
 struct PairLayout {
