@@ -446,7 +446,22 @@ def measure_rows(b, A, B, pk, sm_count):
 
 
 def measure_serve(b, count=50000, budget=40 << 30):
-    """Open-loop Poisson stream through serve_submit/serve_poll; p50/p99 latency and throughput."""
+    """Open-loop Poisson streams through serve_submit/serve_poll at 0.5, 0.8 and 0.95 of the measured
+    capacity and at one fixed rate; p50/p99 latency and throughput.  The returned row is the 0.8 stream,
+    the others are under "loads"."""
+    capacity = {}
+    main = _serve_stream(b, count, budget, rho=0.8, capacity=capacity)
+    loads = []
+    for rho, fixed in ((0.5, None), (0.95, None), (None, 20000.0)):
+        r = _serve_stream(b, count, budget, rho=rho, fixed_rate=fixed, capacity=capacity)
+        loads.append({"rho": rho, "offered_rate_per_s": r["offered_rate_per_s"], "p50_ms": r["p50_ms"],
+                      "p99_ms": r["p99_ms"], "tflops": r["tflops"], "wall_s": r["wall_s"]})
+    main["capacity_per_s"] = capacity.get("rate")
+    main["loads"] = loads
+    return main
+
+
+def _serve_stream(b, count, budget, rho=0.8, fixed_rate=None, capacity=None):
     import torch
     S = 4096
     Apool = torch.empty((S, S), dtype=torch.float32, device="cuda").uniform_(-1, 1)
@@ -461,16 +476,22 @@ def measure_serve(b, count=50000, budget=40 << 30):
                 if t is not None:
                     return t
 
-        # capacity: a closed burst of 1000 requests
-        nb = 1000
-        _, sizes, modes = synth.serve_stream(nb, seed=synth.seed_for(4, 1), rate_per_s=1.0)
-        t0 = time.perf_counter()
-        tickets = [submit(i, *map(int, sizes[i]), int(modes[i])) for i in range(nb)]
-        b.serve_drain(srv, 120_000)
-        burst_s = time.perf_counter() - t0
-        for t in tickets:
-            b.serve_poll(srv, t)
-        rate = 0.8 * nb / burst_s
+        # capacity: a closed burst of 1000 requests (measured once, on the first stream)
+        if capacity is None or "rate" not in capacity:
+            nb = 1000
+            _, sizes, modes = synth.serve_stream(nb, seed=synth.seed_for(4, 1), rate_per_s=1.0)
+            t0 = time.perf_counter()
+            tickets = [submit(i, *map(int, sizes[i]), int(modes[i])) for i in range(nb)]
+            b.serve_drain(srv, 120_000)
+            burst_s = time.perf_counter() - t0
+            for t in tickets:
+                b.serve_poll(srv, t)
+            if capacity is not None:
+                capacity["rate"] = nb / burst_s
+            cap = nb / burst_s
+        else:
+            cap = capacity["rate"]
+        rate = fixed_rate if fixed_rate is not None else rho * cap
         arrival, sizes, modes = synth.serve_stream(count, seed=synth.seed_for(4, 0), rate_per_s=rate)
         lat, flop = [], 0.0
         pending = collections.deque()
@@ -509,6 +530,29 @@ def measure_serve(b, count=50000, budget=40 << 30):
             "p99_ms": float(np.percentile(lat, 99)), "tflops": flop / wall / 1e12, "wall_s": wall,
             "modes": "f16, bf16, e4m3 (scaled), split-3 uniform", "sizes": "m,n,k log-uniform [32,4096], multiple of 16",
             "stats": st}
+
+def oracle_sweep():
+    """The oracle's square GEMM (FP16 rounding, FP64 product, beta = 0.5) at N = 256 ... 4096 on all host
+    cores, and at N = 1024 on one core (a child process with its BLAS held to one thread)."""
+    from oracle import gemm as og
+    out = {"cores": os.cpu_count()}
+    for n_ in (256, 1024, 2048, 4096):
+        A_ = synth.uniform((n_, n_), seed=synth.seed_for(0, 0))
+        B_ = synth.uniform((n_, n_), seed=synth.seed_for(0, 1))
+        C_ = synth.uniform((n_, n_), seed=synth.seed_for(0, 2))
+        t0 = time.perf_counter()
+        og.gemm_mixed("f16", A_, B_, 1.0, 0.5, C_)
+        t = time.perf_counter() - t0
+        out[str(n_)] = {"s": t, "tflops": 2.0 * n_ ** 3 / t / 1e12}
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys, time; sys.path.insert(0, %r); import synth; from oracle import gemm as og; "
+            "A = synth.uniform((1024, 1024), seed=1); B = synth.uniform((1024, 1024), seed=2); "
+            "t0 = time.perf_counter(); og.gemm_mixed('f16', A, B); print(time.perf_counter() - t0)" % ROOT)
+    t1 = float(subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                              timeout=600).stdout.strip().splitlines()[-1])
+    out["1024_one_core"] = {"s": t1, "tflops": 2.0 * 1024 ** 3 / t1 / 1e12}
+    return out
+
 
 # --------------------------------------------------------------------------- our arm
 
@@ -842,6 +886,8 @@ def main():
                                 "kind": "oracle",
                                 "sample": f"{len(rows)} full rows of C (K={N}): FP16 rounding of A rows and all of B "
                                           f"+ FP64 product, {t:.1f} s"}
+        if args.rows == "all":
+            line["cpu_oracle_sweep"] = _row("cpu_oracle_sweep", oracle_sweep)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
