@@ -219,6 +219,30 @@ def _time_ms(fn, iters, warm=2):
     return e0.elapsed_time(e1) / iters
 
 
+def _time_each_ms(fn, iters, warm=3):
+    """Per-launch CUDA-event times (ms) of `iters` back-to-back launches after `warm`."""
+    import torch
+    for _ in range(warm):
+        fn()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(iters + 1)]
+    torch.cuda.synchronize()
+    evs[0].record()
+    for i in range(iters):
+        fn()
+        evs[i + 1].record()
+    torch.cuda.synchronize()
+    return [evs[i].elapsed_time(evs[i + 1]) for i in range(iters)]
+
+
+def _rate_stats(flop, times_ms):
+    """Mean (total work over total time), harmonic mean, median and spread of per-launch TFLOP/s."""
+    rates = [flop / (t * 1e-3) / 1e12 for t in times_ms]
+    return {"tflops": flop * len(times_ms) / (sum(times_ms) * 1e-3) / 1e12,
+            "hmean_tflops": len(rates) / sum(1.0 / r for r in rates),
+            "median_tflops": statistics.median(rates), "min_tflops": min(rates), "max_tflops": max(rates),
+            "launches": len(rates)}
+
+
 def _sampled_errors(C_dev, A, B, rows):
     """Normwise error vs the FP64 truth estimated on sampled rows: ||(C-C64)_S|| / (||A_S|| ||B||)."""
     import torch
@@ -265,7 +289,8 @@ def measure_rows(b, A, B, pk, sm_count):
         b.tc_quantize(dt, N, N, Bd, N, Bq, N, 1, sc[1:2])
         g = lambda: b.gemm_mixed(dt, N, N, N, 1.0, Aq, N, 0, Bq, N, 1, 0.0, C, N,
                                  sc[0:1] if dt == 2 else None, sc[1:2] if dt == 2 else None)
-        ms = _time_ms(g, 10)
+        times = _time_each_ms(g, 20)
+        ms = sum(times) / len(times)
         q_ms = _time_ms(lambda: (b.tc_quantize(dt, N, N, Ad, N, Aq, N, 0, sc[0:1]),
                                  b.tc_quantize(dt, N, N, Bd, N, Bq, N, 1, sc[1:2])), 5)
         err = _sampled_errors(C, A, B, srows)
@@ -273,13 +298,14 @@ def measure_rows(b, A, B, pk, sm_count):
         p = peak * (2.0 if dt == 2 else 1.0)
         return {"gemm_tflops": tf, "frac_of_peak": tf / p, "peak_tflops": p,
                 "peak_note": "measured bf16 burst" + (" x2 (FP8 rate)" if dt == 2 else ""),
-                "gemm_ms": ms, "quantize_ms": q_ms, "error_vs_fp64": err}
+                "gemm_ms": ms, "per_launch": _rate_stats(flops, times), "quantize_ms": q_ms,
+                "error_vs_fp64": err}
 
     def sweep():
         # the square sweep's sizes: the GEMM alone (operands already rounded, beta = 0.5)
         torch.manual_seed(1803)
         res = {}
-        for n_ in (1024, 2048, 4096, 8192, 16384):
+        for n_ in (256, 1024, 2048, 4096, 8192, 16384):
             Xa = torch.empty((n_, n_), dtype=torch.float32, device="cuda").uniform_(-1, 1)
             Xb = torch.empty((n_, n_), dtype=torch.float32, device="cuda").uniform_(-1, 1)
             Cs = torch.empty((n_, n_), dtype=torch.float32, device="cuda").uniform_(-1, 1)
@@ -293,10 +319,12 @@ def measure_rows(b, A, B, pk, sm_count):
                 b.tc_quantize(dt, n_, n_, Xb, n_, Bq, n_, 1, sc[1:2])
                 g = lambda: b.gemm_mixed(dt, n_, n_, n_, 1.0, Aq, n_, 0, Bq, n_, 1, 0.5, Cs, n_,
                                          sc[0:1] if dt == 2 else None, sc[1:2] if dt == 2 else None)
-                it = max(3, min(50, int(2e-2 / (2.0 * n_ ** 3 / 1.5e15))))
-                ms = _time_ms(g, it)
-                tf = 2.0 * n_ ** 3 / (ms * 1e-3) / 1e12
-                row[name] = {"tflops": tf, "frac_of_peak": tf / (peak * (2.0 if dt == 2 else 1.0)), "ms": ms}
+                it = max(5, min(50, int(2e-2 / (2.0 * n_ ** 3 / 1.5e15))))
+                times = _time_each_ms(g, it)
+                st = _rate_stats(2.0 * n_ ** 3, times)
+                row[name] = {"tflops": st["tflops"], "frac_of_peak": st["tflops"] / (peak * (2.0 if dt == 2 else 1.0)),
+                             "ms": sum(times) / len(times), "hmean_tflops": st["hmean_tflops"],
+                             "median_tflops": st["median_tflops"], "launches": it}
                 del Aq, Bq
             res[str(n_)] = row
             del Xa, Xb, Cs
