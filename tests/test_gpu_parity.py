@@ -567,3 +567,71 @@ def test_autotuned_grouped_plan_still_matches_oracle(b):
     for (m, n, k, a0, b0, c0, lda, ldb, ldc, A, B) in probs:
         ref = og.gemm_mixed("f16", A, B)
         assert normwise_dev(got[c0:c0 + m * n].reshape(m, n), ref, A, B) <= TOL_NORMWISE
+
+
+# ------------------------------------------------------------------ padded leading dimensions
+
+@pytest.mark.parametrize("tile", ["single", "pair"])
+@pytest.mark.parametrize("dt", [0, 1, 2])
+def test_gemm_mixed_padded_leading_dims(b, monkeypatch, tile, dt):
+    # operands and C with row padding full of NaN: nothing may read or write the padding
+    monkeypatch.setenv("TCGEMM_TILE", tile)
+    m, n, k = 300, 200, 160
+    pad = 16 if dt == 2 else 8
+    lda, ldb, ldc = k + pad, k + 2 * pad, n + 3
+    A = synth.uniform((m, k), seed=141)
+    B = synth.uniform((k, n), seed=142)
+    C0 = synth.uniform((m, n), seed=143)
+    tdt = {0: torch.float16, 1: torch.bfloat16, 2: torch.uint8}[dt]
+    if dt == 2:
+        Aq = torch.full((m, lda), 0x7F, dtype=tdt, device="cuda")   # E4M3 NaN
+        Bq = torch.full((n, ldb), 0x7F, dtype=tdt, device="cuda")
+    else:
+        Aq = torch.full((m, lda), float("nan"), dtype=tdt, device="cuda")
+        Bq = torch.full((n, ldb), float("nan"), dtype=tdt, device="cuda")
+    sc = torch.empty(2, dtype=torch.float32, device="cuda")
+    b.tc_quantize(dt, m, k, dev(A), k, Aq, lda, 0, sc[0:1])
+    b.tc_quantize(dt, k, n, dev(B), n, Bq, ldb, 1, sc[1:2])
+    Cfull = torch.full((m, ldc), float("nan"), dtype=torch.float32, device="cuda")
+    Cfull[:, :n] = dev(C0)
+    b.gemm_mixed(dt, m, n, k, 1.0, Aq, lda, 0, Bq, ldb, 1, 0.5, Cfull, ldc,
+                 sc[0:1] if dt == 2 else None, sc[1:2] if dt == 2 else None)
+    b.tc_sync_status()
+    got = host(Cfull)
+    assert np.all(np.isnan(got[:, n:]))
+    ref = og.gemm_mixed(DT_NAME[dt], A, B, 1.0, 0.5, C0)
+    ok, info = elementwise_ok(got[:, :n], ref, _mag(dt, A, B, 1.0, 0.5, C0), k)
+    assert ok, info
+
+
+@pytest.mark.parametrize("layouts", [(0, 0), (1, 1)])
+def test_gemm_split_padded_fp32_operands(b, layouts):
+    # FP32 inputs with odd row pitches (the scalar split path) and C with padding
+    la, lb = layouts
+    m, n, k = 260, 136, 200
+    A = synth.log_uniform_pow2((m, k), seed=151)
+    B = synth.log_uniform_pow2((k, n), seed=152)
+    if la == 0:
+        lda = k + 3
+        Ap = np.full((m, lda), np.nan, np.float32)
+        Ap[:, :k] = A
+    else:
+        lda = m + 5
+        Ap = np.full((k, lda), np.nan, np.float32)
+        Ap[:, :m] = A.T
+    if lb == 0:
+        ldb = n + 1
+        Bp = np.full((k, ldb), np.nan, np.float32)
+        Bp[:, :n] = B
+    else:
+        ldb = k + 7
+        Bp = np.full((n, ldb), np.nan, np.float32)
+        Bp[:, :k] = B.T
+    ldc = n + 5
+    C = torch.full((m, ldc), float("nan"), dtype=torch.float32, device="cuda")
+    b.gemm_split(0, 3, m, n, k, 1.0, dev(Ap), lda, la, dev(Bp), ldb, lb, 0.0, C, ldc)
+    b.tc_sync_status()
+    got = host(C)
+    assert np.all(np.isnan(got[:, n:]))
+    ref = og.gemm_split("f16", 3, A, B)
+    assert normwise_dev(got[:, :n], ref, A, B) <= TOL_NORMWISE
