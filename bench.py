@@ -411,7 +411,7 @@ def measure_rows(b, A, B, pk, sm_count):
             ms = _time_ms(lambda: b.gemm_grouped_plan_run(plan, Ab, Bb, Cb, 1.0, 0.0, use_graph=1), 20)
         finally:
             b.gemm_grouped_plan_destroy(plan)
-        return {"problems": 10000, "b_layout": "K-major (tcgen05 path)" if lb == 1 else "row-major (mma.sync path)",
+        return {"problems": 10000, "b_layout": "K-major (tcgen05)" if lb == 1 else "row-major (tcgen05, B read MN-major)",
                 "ms": ms, "autotune_ms": tuned, "tflops": gflop / (ms * 1e-3) / 1e12,
                 "gbs": algo_bytes / (ms * 1e-3) / 1e9, "frac_of_hbm": algo_bytes / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
                 "algorithmic_bytes": algo_bytes}

@@ -143,10 +143,12 @@ tc_status tc_split_bf16x3(int64_t rows, int64_t cols, const float* src, int64_t 
 /* ------------------------------------------------------------------------ */
 
 /* C = alpha * descale * (A B) + beta * C, A and B already in format `dt`.
- *   Layout: A row-major (la = TC_ROW_MAJOR, m x k, lda >= k) and B column-
- *   major (lb = TC_COL_MAJOR, i.e. stored n x k, ldb >= k): both operands
- *   K-major.  Other layouts return TC_ERR_UNSUPPORTED; use tc_quantize with
- *   transpose = 1 to make a K-major B.
+ *   Layout: A row-major (la = TC_ROW_MAJOR, m x k, lda >= k).  B column-
+ *   major (lb = TC_COL_MAJOR, i.e. stored n x k, ldb >= k: K-major) or, for
+ *   TC_F16 and TC_BF16, row-major (lb = TC_ROW_MAJOR, k x n, ldb >= n: read
+ *   by the tensor cores as MN-major, on the CTA-pair kernel).  A column-major
+ *   A and a row-major E4M3 B return TC_ERR_UNSUPPORTED; tc_quantize with
+ *   transpose = 1 makes a K-major copy.
  *   Alignment: A, B 16-byte aligned, lda*size and ldb*size multiples of 16.
  *   scale_a / scale_b: E4M3 only, device floats from tc_quantize; descale =
  *   1/(scale_a*scale_b).  NULL for F16/BF16.
@@ -258,7 +260,9 @@ tc_status gemm_grouped_plan_create(int32_t dt, int32_t count, const tc_problem* 
 /* One persistent launch over every tile of the plan:
  * C_g = alpha*A_g B_g + beta*C_g for all g.  use_graph = 1 records the launch
  * in a CUDA graph on the first call and replays it while the arguments stay
- * the same. */
+ * the same.  Runs on the tensor cores (tcgen05, 128 x 256 tiles, one TMA map
+ * pair per problem) for both B layouts: a row-major B_g is read as MN-major.
+ * TCGEMM_GROUPED=mma selects the mma.sync kernel (64 x 64 tiles) instead. */
 tc_status gemm_grouped_plan_run(tc_grouped_plan* plan, const void* a_base, const void* b_base,
                                 float* c_base, float alpha, float beta, int32_t use_graph, void* stream);
 

@@ -333,11 +333,15 @@ tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, c
     if ((s = get_device(&d)) != TC_OK) return s;
     cudaStream_t st = as_stream(stream);
     if (k == 0) return enqueue(tcg::launch_scale_c(m, n, beta, C, ldc, st), "gemm_mixed scale");
-    if (la != TC_ROW_MAJOR || lb != TC_COL_MAJOR)
-        return fail(TC_ERR_UNSUPPORTED, "gemm_mixed: operands must be K-major (A row-major, B column-major)");
+    if (la != TC_ROW_MAJOR)
+        return fail(TC_ERR_UNSUPPORTED, "gemm_mixed: A must be row-major (K-major)");
+    // B: column-major (K-major), or row-major (MN-major, read by the MMA transposed) for 16-bit types
+    const bool b_mn = lb == TC_ROW_MAJOR;
+    if (b_mn && dt == TC_E4M3)
+        return fail(TC_ERR_UNSUPPORTED, "gemm_mixed: row-major B is supported for F16 and BF16 only");
     const int esz = elem_size(dt);
     if (!A || !B) return fail(TC_ERR_INVALID, "gemm_mixed: null operand");
-    if (lda < k || ldb < k) return fail(TC_ERR_INVALID, "gemm_mixed: lda/ldb < k");
+    if (lda < k || ldb < (b_mn ? n : k)) return fail(TC_ERR_INVALID, "gemm_mixed: lda/ldb too small");
     if (!aligned(A, 16) || !aligned(B, 16) || (lda * esz) % 16 || (ldb * esz) % 16)
         return fail(TC_ERR_INVALID, "gemm_mixed: operands and their row strides must be 16-byte aligned");
     if (dt == TC_E4M3 && (!scale_a || !scale_b)) return fail(TC_ERR_INVALID, "gemm_mixed: E4M3 needs scale_a/scale_b");
@@ -349,7 +353,8 @@ tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, c
     p.ab_format = dt == TC_BF16 ? 1 : 0;
     p.na = p.nb = p.nprod = 1;
     p.bn = 256;
-    p.pair = use_pair_tiles(m, dt, n, k) ? 1 : 0;
+    p.pair = (b_mn || use_pair_tiles(m, dt, n, k)) ? 1 : 0;   // the MN-major path exists on CTA pairs only
+    p.b_mn_major = b_mn ? 1 : 0;
     p.group_m = gemm_group_m(dt, m, n, k);
     p.stall_at = take_stall();
     p.staged_epilogue = gemm_staged_epilogue();
@@ -361,8 +366,12 @@ tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, c
     p.sm_count = d->sm_count;
     CUtensorMap ta, tb;
     if ((s = encode_kmajor(&ta, tdt, esz, A, k, m, 1, lda * esz, m * lda * esz, 128)) != TC_OK) return s;
-    if ((s = encode_kmajor(&tb, tdt, esz, B, k, n, 1, ldb * esz, n * ldb * esz, p.pair ? 128 : p.bn)) != TC_OK)
+    if (b_mn) {
+        // dims {n, k}: boxes of 64 n (128 bytes) x 64 k rows
+        if ((s = encode_kmajor(&tb, tdt, esz, B, n, k, 1, ldb * esz, k * ldb * esz, 64)) != TC_OK) return s;
+    } else if ((s = encode_kmajor(&tb, tdt, esz, B, k, n, 1, ldb * esz, n * ldb * esz, p.pair ? 128 : p.bn)) != TC_OK) {
         return s;
+    }
     return enqueue(tcg::launch_tc_gemm(ta, tb, p, st), "gemm_mixed launch");
 }
 
@@ -580,8 +589,12 @@ tc_status grouped_upload_maps(tc_grouped_plan* plan, const void* a_base, const v
         tc_status s = encode_kmajor(&maps[2 * g], tdt, 2, a + p.off_a * 2, p.k, p.m, 1, int64_t(p.lda) * 2,
                                     int64_t(p.m) * p.lda * 2, tcg::kGroupedTcTileM);
         if (s != TC_OK) return s;
-        s = encode_kmajor(&maps[2 * g + 1], tdt, 2, b + p.off_b * 2, p.k, p.n, 1, int64_t(p.ldb) * 2,
-                          int64_t(p.n) * p.ldb * 2, tcg::grouped_tc_box_rows(p.n));
+        if (plan->lb == TC_ROW_MAJOR)   // B_g k x n: dims {n, k}, boxes of 64 n (128 bytes) x 64 k
+            s = encode_kmajor(&maps[2 * g + 1], tdt, 2, b + p.off_b * 2, p.n, p.k, 1, int64_t(p.ldb) * 2,
+                              int64_t(p.k) * p.ldb * 2, 64);
+        else
+            s = encode_kmajor(&maps[2 * g + 1], tdt, 2, b + p.off_b * 2, p.k, p.n, 1, int64_t(p.ldb) * 2,
+                              int64_t(p.n) * p.ldb * 2, tcg::grouped_tc_box_rows(p.n));
         if (s != TC_OK) return s;
     }
     // pageable source: returns once the bytes are staged
@@ -598,14 +611,16 @@ cudaError_t grouped_launch(tc_grouped_plan* plan, const void* a_base, const void
     if (plan->use_tc && plan->variant != 2)
         return tcg::launch_grouped_tc(plan->dt, plan->d_tc_tiles, plan->tc_tiles, plan->d_maps, c_base, alpha, beta,
                                       plan->status, plan->sm_count, st,
-                                      plan->variant < 0 ? -1 : (plan->variant == 0 ? 1 : 0));
+                                      plan->variant < 0 ? -1 : (plan->variant == 0 ? 1 : 0),
+                                      plan->lb == TC_ROW_MAJOR);
     return tcg::launch_grouped(plan->dt, plan->lb, plan->d_probs, plan->d_tiles, plan->num_tiles, a_base, b_base,
                                c_base, alpha, beta, plan->sm_count, st);
 }
 
-// Grouped GEMMs with K-major B run on the tensor cores unless TCGEMM_GROUPED=mma.
+// Grouped GEMMs run on the tensor cores (B K-major, or row-major read as MN-major) unless
+// TCGEMM_GROUPED=mma selects the mma.sync kernel.
 bool grouped_use_tensor_cores(int32_t lb) {
-    if (lb != TC_COL_MAJOR) return false;
+    (void)lb;
     const char* env = getenv("TCGEMM_GROUPED");
     return !(env && strcmp(env, "mma") == 0);
 }

@@ -90,6 +90,9 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
     nb = r / gm;
 }
 
+// Instruction-descriptor bit that reads B as MN-major (its rows run along N).
+constexpr uint32_t kIdescTransposeB = 1u << 16;
+
 // Work unit u of the pair kernel: its tile (mb, nb), the column offset inside the 256-wide tile
 // and the unit's width (256, or 128 for the halves of the last tiles).
 __device__ __forceinline__ void unit_coords(const Args& a, int u, int& mb, int& nb, int& coff, int& width) {
@@ -389,7 +392,7 @@ __device__ __forceinline__ uint32_t num_clusters_x() {
     return r;
 }
 
-template <int KIND, int STAGES, int NA, int NB, int NPROD>
+template <int KIND, int STAGES, int NA, int NB, int NPROD, bool B_MN = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Args a) {
     using L = PairLayout<STAGES, NA, NB>;
@@ -485,8 +488,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tma_load_3d_pair(sbase + p * L::kHalfTile, &tmA, leader_full, kb * BK,
                                          mb * PM + static_cast<int>(rank) * 128, p);
 #pragma unroll
-                    for (int p = 0; p < NB; ++p)
-                        tma_load_3d_pair(sbase + (NA + p) * L::kHalfTile, &tmB, leader_full, kb * BK, brow, p);
+                    for (int p = 0; p < NB; ++p) {
+                        if constexpr (B_MN) {
+                            // B row-major (k x n): two boxes of 64 k-rows x 64 n (128 bytes) per CTA
+                            tma_load_3d_pair(sbase + (NA + p) * L::kHalfTile, &tmB, leader_full, brow, kb * BK, p);
+                            tma_load_3d_pair(sbase + (NA + p) * L::kHalfTile + L::kHalfTile / 2, &tmB, leader_full,
+                                             brow + 64, kb * BK, p);
+                        } else {
+                            tma_load_3d_pair(sbase + (NA + p) * L::kHalfTile, &tmB, leader_full, kb * BK, brow, p);
+                        }
+                    }
                     issued_phase[stage] = static_cast<int>(phase);
                     if (++stage == STAGES) {
                         stage = 0;
@@ -536,14 +547,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                         for (int p = 0; p < NPROD; ++p) {
                             const uint32_t a_addr = sbase + prod_a<NA>(p) * L::kHalfTile + ks * 32;
-                            const uint32_t b_addr = sbase + (NA + prod_b<NA>(p)) * L::kHalfTile + ks * 32;
                             const uint32_t accumulate = (kb | ks | p) != 0 ? 1u : 0u;
+                            uint64_t bdesc;
+                            if constexpr (B_MN) {
+                                // 16 k-rows of 128 bytes per MMA step; slabs of 64 n are 8 KB apart
+                                const uint32_t b_addr = sbase + (NA + prod_b<NA>(p)) * L::kHalfTile + ks * 2048;
+                                bdesc = sw128_mnmajor_desc(b_addr, L::kHalfTile / 2, 1024);
+                            } else {
+                                const uint32_t b_addr = sbase + (NA + prod_b<NA>(p)) * L::kHalfTile + ks * 32;
+                                bdesc = sw128_kmajor_desc(b_addr);
+                            }
                             if constexpr (KIND == 1)
-                                mma_pair_f8(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), idesc,
-                                            accumulate);
+                                mma_pair_f8(d_tmem, sw128_kmajor_desc(a_addr), bdesc, idesc, accumulate);
                             else
-                                mma_pair_f16(d_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), idesc,
-                                             accumulate);
+                                mma_pair_f16(d_tmem, sw128_kmajor_desc(a_addr), bdesc, idesc, accumulate);
                         }
                     }
                     issued_any = true;
@@ -696,12 +713,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <int KIND, int STAGES, int NA, int NB, int NPROD>
+template <int KIND, int STAGES, int NA, int NB, int NPROD, bool B_MN = false>
 cudaError_t run_pair(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args& args, int clusters,
                      cudaStream_t st) {
     if (clusters <= 0) return cudaSuccess;
     using L = PairLayout<STAGES, NA, NB>;
-    auto kern = k_tc_gemm_pair<KIND, STAGES, NA, NB, NPROD>;
+    auto kern = k_tc_gemm_pair<KIND, STAGES, NA, NB, NPROD, B_MN>;
     Args a = args;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * clusters, 1, 1);
@@ -1250,7 +1267,14 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
             }
             return cudaErrorInvalidValue;
         }
-        if (p.na == 1 && p.nb == 1) return run_pair<0, 6, 1, 1, 1>(tmA, tmB, a, max_clusters, st);
+        if (p.na == 1 && p.nb == 1) {
+            if (p.b_mn_major) {
+                a.idesc |= kIdescTransposeB;
+                a.idesc_half |= kIdescTransposeB;
+                return run_pair<0, 6, 1, 1, 1, true>(tmA, tmB, a, max_clusters, st);
+            }
+            return run_pair<0, 6, 1, 1, 1>(tmA, tmB, a, max_clusters, st);
+        }
         if (p.na == 2 && p.nb == 1 && p.nprod == 2) return run_pair<0, 4, 2, 1, 2>(tmA, tmB, a, max_clusters, st);
         if (p.na == 2 && p.nb == 2 && p.nprod == 3) return run_pair<0, 3, 2, 2, 3>(tmA, tmB, a, max_clusters, st);
         if (p.na == 2 && p.nb == 2 && p.nprod == 4) return run_pair<0, 3, 2, 2, 4>(tmA, tmB, a, max_clusters, st);

@@ -72,6 +72,15 @@ __host__ __device__ __forceinline__ int mma_n(int n) {
     return r < GN ? r : GN;
 }
 
+// With a row-major (MN-major) B the N of the MMA is a whole number of 64-wide swizzle slabs.
+__host__ __device__ __forceinline__ int mma_n_mn(int n) {
+    const int r = (n + 63) / 64 * 64;
+    return r < GN ? r : GN;
+}
+
+// B_MN: B_g is row-major (k x n, maps[2g+1] dims {n, k}, boxes of 64 n x 64 k) and is read by
+// the MMA as MN-major; otherwise B_g is K-major (n x k).
+template <bool B_MN>
 __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_addr(smem_raw);
@@ -136,7 +145,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                     prefetch_tmap(a.maps + 2 * nxt.prob + 1);
                 }
                 const int nk = tile.nk;
-                const uint32_t bytes = static_cast<uint32_t>(kABytes + mma_n(tile.n) * kRow);
+                const int nslabs = B_MN ? mma_n_mn(tile.n) / 64 : 0;
+                const uint32_t bytes = static_cast<uint32_t>(kABytes + (B_MN ? nslabs * 64 : mma_n(tile.n)) * kRow);
                 for (int kb = 0; kb < nk; ++kb) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, a.status)) {
                         ok = false;
@@ -145,7 +155,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                     const uint32_t sbase = base + stage * kStage;
                     mbar_arrive_expect_tx(full_bar(stage), bytes);
                     tma_load_3d(sbase, mA, full_bar(stage), kb * 64, tile.tm * GM, 0);
-                    tma_load_3d(sbase + kABytes, mB, full_bar(stage), kb * 64, tile.tn * GN, 0);
+                    if constexpr (B_MN) {
+                        for (int sl = 0; sl < nslabs; ++sl)
+                            tma_load_3d(sbase + kABytes + sl * 64 * kRow, mB, full_bar(stage), tile.tn * GN + sl * 64,
+                                        kb * 64, 0);
+                    } else {
+                        tma_load_3d(sbase + kABytes, mB, full_bar(stage), kb * 64, tile.tn * GN, 0);
+                    }
                     issued_phase[stage] = static_cast<int>(phase);
                     if (++stage == kStages) {
                         stage = 0;
@@ -173,7 +189,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                 const GroupedTcTile tile = nxt;
                 nxt = load_tile(a.tiles, t + gridDim.x, a.num_tiles);
                 const int nk = tile.nk;
-                const uint32_t idesc = make_idesc(GM, mma_n(tile.n), a.ab_format);
+                const uint32_t idesc = B_MN ? (make_idesc(GM, mma_n_mn(tile.n), a.ab_format) | (1u << 16))
+                                            : make_idesc(GM, mma_n(tile.n), a.ab_format);
                 if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, a.status)) {
                     ok = false;
                     break;
@@ -188,9 +205,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                     tc_fence_after();
                     const uint32_t sbase = base + stage * kStage;
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks)
-                        mma_f16(d_tmem, sw128_kmajor_desc(sbase + ks * 32), sw128_kmajor_desc(sbase + kABytes + ks * 32),
-                                idesc, (kb | ks) != 0 ? 1u : 0u);
+                    for (int ks = 0; ks < 4; ++ks) {
+                        // MN-major B: 16 k-rows of 128 bytes per step, 64-n slabs 8 KB apart
+                        const uint64_t bdesc = B_MN ? sw128_mnmajor_desc(sbase + kABytes + ks * 2048, 64 * kRow, 1024)
+                                                    : sw128_kmajor_desc(sbase + kABytes + ks * 32);
+                        mma_f16(d_tmem, sw128_kmajor_desc(sbase + ks * 32), bdesc, idesc, (kb | ks) != 0 ? 1u : 0u);
+                    }
                     issued_any = true;
                     mma_commit(empty_bar(stage));
                     if (++stage == kStages) {
@@ -346,9 +366,10 @@ int grouped_tc_box_rows(int n) { return mma_n(n); }
 
 cudaError_t launch_grouped_tc(int dt, const GroupedTcTile* tiles, int32_t num_tiles, const CUtensorMap* maps,
                               float* c_base, float alpha, float beta, int* status, int sm_count, cudaStream_t st,
-                              int staged) {
+                              int staged, bool b_mn) {
     if (num_tiles <= 0) return cudaSuccess;
-    cudaError_t e = kernel_setup(reinterpret_cast<const void*>(k_grouped_tc), kSmem, nullptr, 0, nullptr);
+    auto kern = b_mn ? k_grouped_tc<true> : k_grouped_tc<false>;
+    cudaError_t e = kernel_setup(reinterpret_cast<const void*>(kern), kSmem, nullptr, 0, nullptr);
     if (e != cudaSuccess) return e;
     Args a;
     a.tiles = tiles;
@@ -366,7 +387,7 @@ cudaError_t launch_grouped_tc(int dt, const GroupedTcTile* tiles, int32_t num_ti
         a.staged_epilogue = (env && strcmp(env, "direct") == 0) ? 0 : 1;
     }
     const int grid = num_tiles < sm_count ? num_tiles : sm_count;
-    k_grouped_tc<<<grid, kThreads, kSmem, st>>>(a);
+    kern<<<grid, kThreads, kSmem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -62,6 +62,8 @@ struct TcGemmLaunch {
     int stall_at;       // test hook: k-block + 1 to withhold, 0 = off (tc_debug_stall_next_gemm)
     int promote_kb;     // pair kernel only: >0 adds the partial sums of every promote_kb k-blocks
                         // into FP32 registers with round-to-nearest (1, 2 or 4); 0 keeps them in TMEM
+    int b_mn_major;     // pair kernel, one 16-bit product: B is row-major k x n (tmB dims {n, k, 1},
+                        // box 64 x 64), read by the MMA as MN-major
     int corr_exp;       // pair kernel with promotion, s > 0: products 1.. (the corrections of a scaled
                         // split) accumulate apart and are multiplied by 2^-s in the epilogue
 };
@@ -104,9 +106,10 @@ struct alignas(16) GroupedTcTile {
 };
 int grouped_tc_box_rows(int n);
 // staged: 1 = epilogue through shared memory, 0 = direct row stores, -1 = TCGEMM_GROUPED_EPI or staged
+// b_mn: every B_g is row-major (k x n) and maps[2g+1] has dims {n, k, 1} with 64 x 64 boxes.
 cudaError_t launch_grouped_tc(int dt, const GroupedTcTile* tiles, int32_t num_tiles, const CUtensorMap* maps,
                               float* c_base, float alpha, float beta, int* status, int sm_count, cudaStream_t st,
-                              int staged = -1);
+                              int staged = -1, bool b_mn = false);
 
 // ---- errnorm.cu
 constexpr int kErrBlocks = 1024;  // fixed grid: the reduction order does not depend on the GPU

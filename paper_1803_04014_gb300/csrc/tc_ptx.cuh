@@ -207,6 +207,20 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
     return d;
 }
 
+// Shared-memory descriptor of an MN-major operand with the 128-byte swizzle:
+// rows of 128 bytes hold 64 consecutive M (or N) elements of one k; 8 rows
+// (1024 bytes) form a swizzle atom.  sbo = bytes between 8-row groups along K,
+// lbo = bytes between 64-element slabs along M/N.
+__device__ __forceinline__ uint64_t sw128_mnmajor_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+    d |= static_cast<uint64_t>(1u) << 46;
+    d |= static_cast<uint64_t>(2u) << 61;
+    return d;
+}
+
 // Instruction descriptor (kind::f16 and kind::f8f6f4, dense, FP32 accumulator,
 // both operands K-major):
 //   bits 4-5 D format (1 = F32); 7-9 A format; 10-12 B format

@@ -159,12 +159,39 @@ def test_gemm_mixed_k_zero_scales_c(b):
     assert np.array_equal(host(C), (0.5 * C0.astype(np.float64)).astype(np.float32))
 
 
-def test_gemm_mixed_rejects_mn_major(b):
+def test_gemm_mixed_rejects_unsupported_layouts(b):
     a = torch.zeros(64, dtype=torch.float16, device="cuda")
+    a8 = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    s = torch.ones(1, dtype=torch.float32, device="cuda")
     c = torch.zeros(64, dtype=torch.float32, device="cuda")
-    with pytest.raises(b.TcError) as e:
-        b.gemm_mixed(0, 8, 8, 8, 1.0, a, 8, 0, a, 8, 0, 0.0, c, 8)
+    with pytest.raises(b.TcError) as e:                     # column-major A
+        b.gemm_mixed(0, 8, 8, 8, 1.0, a, 8, 1, a, 8, 1, 0.0, c, 8)
     assert e.value.status == b.TC_ERR_UNSUPPORTED
+    with pytest.raises(b.TcError) as e:                     # row-major E4M3 B
+        b.gemm_mixed(2, 8, 8, 16, 1.0, a8, 16, 0, a8, 16, 0, 0.0, c, 8, s, s)
+    assert e.value.status == b.TC_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("dt", [0, 1])
+@pytest.mark.parametrize("mnk", [(300, 200, 160), (64, 256, 96), (520, 600, 1000), (2560, 2560, 128),
+                                 (1000, 1032, 520)])
+def test_gemm_mixed_row_major_b(b, dt, mnk):
+    # B stored k x n (row-major) is read by the tensor cores as MN-major: no transposed copy
+    m, n, k = mnk
+    A = synth.uniform((m, k), seed=161)
+    B = synth.uniform((k, n), seed=162)
+    C0 = synth.uniform((m, n), seed=163)
+    tdt = torch.float16 if dt == 0 else torch.bfloat16
+    Aq = torch.empty((m, k), dtype=tdt, device="cuda")
+    Bq = torch.empty((k, n), dtype=tdt, device="cuda")
+    b.tc_quantize(dt, m, k, dev(A), k, Aq, k, 0)
+    b.tc_quantize(dt, k, n, dev(B), n, Bq, n, 0)            # row-major, not transposed
+    C = dev(C0)
+    b.gemm_mixed(dt, m, n, k, 1.0, Aq, k, 0, Bq, n, 0, 0.5, C, n)
+    b.tc_sync_status()
+    ref = og.gemm_mixed(DT_NAME[dt], A, B, 1.0, 0.5, C0)
+    ok, info = elementwise_ok(host(C), ref, _mag(dt, A, B, 1.0, 0.5, C0), k)
+    assert ok, info
 
 
 def test_gemm_mixed_is_deterministic(b):
@@ -479,18 +506,20 @@ def test_split_promotion_settings_match_oracle(b, monkeypatch, promote):
     assert normwise_dev(host(C), ref, A, B, 1.5, -0.25, C0) <= TOL_NORMWISE
 
 
-# ------------------------------------------------------------------ grouped GEMM on the tensor cores (K-major B)
+# ------------------------------------------------------------------ grouped GEMM: tensor-core and mma.sync kernels
 
+@pytest.mark.parametrize("lb", [1, 0])
 @pytest.mark.parametrize("impl", ["tc", "mma"])
 @pytest.mark.parametrize("count,ragged", [(1, False), (9, False), (400, False), (60, True)])
-def test_grouped_kmajor_parity(b, monkeypatch, impl, count, ragged):
+def test_grouped_kmajor_parity(b, monkeypatch, lb, impl, count, ragged):
+    # lb = 1: B_g K-major; lb = 0: B_g row-major (read by the tensor cores as MN-major)
     if impl == "mma":
         monkeypatch.setenv("TCGEMM_GROUPED", "mma")
-    probs, abuf, bbuf, csize = _grouped_case(count, seed=170 + count, lb=1, ragged=ragged)
+    probs, abuf, bbuf, csize = _grouped_case(count, seed=170 + count, lb=lb, ragged=ragged)
     C0 = synth.uniform((csize,), seed=77)
     C = dev(C0)
     desc = [p[:9] for p in probs]
-    b.gemm_grouped(0, desc, dev(abuf, torch.float16), 0, dev(bbuf, torch.float16), 1, C, 0.75, -0.5)
+    b.gemm_grouped(0, desc, dev(abuf, torch.float16), 0, dev(bbuf, torch.float16), lb, C, 0.75, -0.5)
     b.tc_sync_status()
     got = host(C)
     for (m, n, k, a0, b0, c0, lda, ldb, ldc, A, B) in probs:
