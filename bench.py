@@ -149,7 +149,7 @@ def parse_args():
     p.add_argument("--rows", choices=["all", "none"], default="all", help="also measure the other rows (N=1 only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-gemm", choices=["f16", "bf16", "e4m3", "split3", "split3_scaled", "bf16x3", "grouped",
-                                              "batched16"], default=None,
+                                              "grouped_rowmajor", "batched16"], default=None,
                    help="only round the N=8192 inputs and run 5 GEMM launches (a small case for ncu captures)")
     return p.parse_args()
 
@@ -589,18 +589,19 @@ def profile_case(kind):
     import torch
     from paper_1803_04014_gb300 import binding as b
     b.load()
-    if kind == "grouped":
+    if kind in ("grouped", "grouped_rowmajor"):
+        lb = 1 if kind == "grouped" else 0
         sizes = synth.group_sizes(10000, seed=synth.seed_for(3, 0))
         desc, a, bb, c = [], 0, 0, 0
         for (m, n, k) in sizes:
-            desc.append((m, n, k, a, bb, c, k, k, n))   # B_g stored n x k (K-major)
+            desc.append((m, n, k, a, bb, c, k, k if lb == 1 else n, n))   # B_g n x k (K-major) or k x n
             a += m * k
             bb += k * n
             c += m * n
         Ab = torch.empty(a, dtype=torch.float16, device="cuda").uniform_(-1, 1)
         Bb = torch.empty(bb, dtype=torch.float16, device="cuda").uniform_(-1, 1)
         Cb = torch.empty(c, dtype=torch.float32, device="cuda")
-        plan = b.gemm_grouped_plan_create(0, desc, 0, 1)
+        plan = b.gemm_grouped_plan_create(0, desc, 0, lb)
         for _ in range(5):
             b.gemm_grouped_plan_run(plan, Ab, Bb, Cb, 1.0, 0.0, use_graph=0)
         b.tc_sync_status()
