@@ -281,11 +281,14 @@ tc_status gemm_grouped(int32_t dt, int32_t count, const tc_problem* problems,
  * allocation can fail or fragment the pool), and latency-critical loops that
  * cannot afford the device-wide synchronisation of cudaMalloc/cudaFree.
  * Same arguments and result as gemm_grouped (host problem array, device
- * operands and outputs owned by the caller), but the problem descriptors and
- * the longest-first tile schedule are copied into a static device array of
- * 8 MiB (48 bytes per problem plus 16 bytes per 64 x 64 output tile) that every
- * GPU loading the library holds until the process exits.  A group that needs
- * more returns TC_ERR_INVALID with the byte counts in tc_last_error().
+ * operands and outputs owned by the caller), but what the kernel reads besides
+ * the operands is copied into a static device array of 8 MiB that every GPU
+ * loading the library holds until the process exits: for the tcgen05 kernel
+ * (the default) two TMA tensor maps per problem (256 bytes) and 48 bytes per
+ * 128 x 256 output tile; for a group whose maps do not fit, or with
+ * TCGEMM_GROUPED=mma, the mma.sync kernel's problem table (48 bytes per
+ * problem) and 16 bytes per 64 x 64 tile.  A group that fits neither returns
+ * TC_ERR_INVALID with the byte counts in tc_last_error().
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, once per device); make that first call before
  *     any stream capture.
@@ -306,8 +309,9 @@ tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_problem* prob
  *   workspace: 256-byte aligned device memory of at least
  *   gemm_grouped_workspace_bytes(count, problems) bytes, not touched by other
  *   work until this call's kernel has finished on `stream`.
- * Runs the mma.sync kernel (64 x 64 tiles) for both B layouts; arguments and
- * errors otherwise as gemm_grouped. */
+ * Runs the tcgen05 kernel of gemm_grouped (maps and tiles in the workspace;
+ * the mma.sync kernel with TCGEMM_GROUPED=mma); arguments and errors otherwise
+ * as gemm_grouped. */
 size_t gemm_grouped_workspace_bytes(int32_t count, const tc_problem* problems);
 tc_status gemm_grouped_ws(int32_t dt, int32_t count, const tc_problem* problems,
                           const void* a_base, int32_t la, const void* b_base, int32_t lb,

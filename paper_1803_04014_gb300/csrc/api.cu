@@ -44,6 +44,7 @@ struct Device {
 
 std::mutex g_mu;
 Device g_dev[64];
+static __device__ __align__(256) int g_status_word[64];  // one copy per device; word 0 is used
 
 tc_status get_device(Device** out) {
     int dev = 0;
@@ -57,8 +58,11 @@ tc_status get_device(Device** out) {
             return cuda_fail(e, "cudaDeviceGetAttribute");
         cudaDeviceGetAttribute(&d.cc_major, cudaDevAttrComputeCapabilityMajor, dev);
         cudaDeviceGetAttribute(&d.cc_minor, cudaDevAttrComputeCapabilityMinor, dev);
-        if ((e = cudaMalloc(&d.status, 256)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(status)");
-        if ((e = cudaMemset(d.status, 0, 256)) != cudaSuccess) return cuda_fail(e, "cudaMemset(status)");
+        // the status word is a static device variable (zero at module load): no allocation
+        void* sw = nullptr;
+        if ((e = cudaGetSymbolAddress(&sw, g_status_word)) != cudaSuccess)
+            return cuda_fail(e, "cudaGetSymbolAddress(status)");
+        d.status = static_cast<int*>(sw);
         // keep freed stream-ordered workspace cached in the pool instead of returning it each sync
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
@@ -864,7 +868,8 @@ namespace {
 // tiles in the longest-first order of a plan.
 tc_status grouped_mma_host(const char* name, int32_t dt, int32_t count, const tc_problem* problems,
                            const void* a_base, int32_t la, const void* b_base, int32_t lb, const float* c_base,
-                           std::vector<unsigned char>& host, size_t* desc_bytes_out, int64_t* tiles_out) {
+                           std::vector<unsigned char>& host, size_t* desc_bytes_out, int64_t* tiles_out,
+                           bool pack = true) {
     if (dt != TC_F16 && dt != TC_BF16) return fail(TC_ERR_UNSUPPORTED, "%s: F16 or BF16 only", name);
     if (la != TC_ROW_MAJOR) return fail(TC_ERR_UNSUPPORTED, "%s: A must be row-major", name);
     if (lb != TC_ROW_MAJOR && lb != TC_COL_MAJOR) return fail(TC_ERR_INVALID, "%s: bad layout", name);
@@ -890,6 +895,8 @@ tc_status grouped_mma_host(const char* name, int32_t dt, int32_t count, const tc
                      ((p.n + tcg::kGroupedTileN - 1) / tcg::kGroupedTileN);
     }
     if (num_tiles > 0x7FFFFFFF) return fail(TC_ERR_INVALID, "%s: too many tiles", name);
+    *tiles_out = num_tiles;
+    if (!pack) return TC_OK;  // checked only
     const size_t desc_bytes = (size_t(count) * sizeof(tcg::GroupedProblemDev) + 255) / 256 * 256;
     host.assign(desc_bytes + size_t(num_tiles) * sizeof(tcg::GroupedTileDev), 0);
     auto* hp = reinterpret_cast<tcg::GroupedProblemDev*>(host.data());
@@ -931,6 +938,70 @@ tc_status grouped_mma_enqueue(const char* name, int32_t dt, int32_t lb, const st
                    name);
 }
 
+// Host half of a plan-free grouped GEMM on the tensor-core kernel: one pair of TMA maps per
+// problem (encoded for these bases; 256-byte aligned table first), then the 128 x 256 tiles in
+// the longest-first problem order of a plan.  The problems were checked by grouped_mma_host.
+tc_status grouped_tc_host(int32_t dt, int32_t count, const tc_problem* problems, const void* a_base,
+                          const void* b_base, int32_t lb, std::vector<unsigned char>& host, size_t* maps_bytes_out,
+                          int32_t* tiles_out) {
+    const CUtensorMapDataType tdt = dt == TC_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const size_t maps_bytes = (2 * size_t(count) * sizeof(CUtensorMap) + 255) / 256 * 256;
+    struct P { int64_t cost; int32_t g; };
+    std::vector<P> order;
+    order.reserve(count);
+    int64_t ntiles = 0;
+    for (int32_t g = 0; g < count; ++g) {
+        const tc_problem& p = problems[g];
+        const int64_t tm = (p.m + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM;
+        const int64_t tn = (p.n + tcg::kGroupedTcTileN - 1) / tcg::kGroupedTcTileN;
+        ntiles += tm * tn;
+        order.push_back({2 * p.k * (p.m * tn + p.n * tm) + 4 * int64_t(p.m) * p.n, g});
+    }
+    if (ntiles > 0x7FFFFFFF) return fail(TC_ERR_INVALID, "grouped: too many tiles");
+    std::stable_sort(order.begin(), order.end(), [](const P& x, const P& y) { return x.cost > y.cost; });
+    host.assign(maps_bytes + size_t(ntiles) * sizeof(tcg::GroupedTcTile), 0);
+    auto* maps = reinterpret_cast<CUtensorMap*>(host.data());
+    const uint8_t* a = static_cast<const uint8_t*>(a_base);
+    const uint8_t* b = static_cast<const uint8_t*>(b_base);
+    for (int32_t g = 0; g < count; ++g) {
+        const tc_problem& p = problems[g];
+        tc_status st = encode_kmajor(&maps[2 * g], tdt, 2, a + p.off_a * 2, p.k, p.m, 1, int64_t(p.lda) * 2,
+                                     int64_t(p.m) * p.lda * 2, tcg::kGroupedTcTileM);
+        if (st != TC_OK) return st;
+        if (lb == TC_ROW_MAJOR)
+            st = encode_kmajor(&maps[2 * g + 1], tdt, 2, b + p.off_b * 2, p.n, p.k, 1, int64_t(p.ldb) * 2,
+                               int64_t(p.k) * p.ldb * 2, 64);
+        else
+            st = encode_kmajor(&maps[2 * g + 1], tdt, 2, b + p.off_b * 2, p.k, p.n, 1, int64_t(p.ldb) * 2,
+                               int64_t(p.n) * p.ldb * 2, tcg::grouped_tc_box_rows(p.n));
+        if (st != TC_OK) return st;
+    }
+    auto* tl = reinterpret_cast<tcg::GroupedTcTile*>(host.data() + maps_bytes);
+    size_t t = 0;
+    for (const P& o : order) {
+        const tc_problem& p = problems[o.g];
+        const int tm = (p.m + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM;
+        const int tn = (p.n + tcg::kGroupedTcTileN - 1) / tcg::kGroupedTcTileN;
+        for (int i = 0; i < tm; ++i)
+            for (int j = 0; j < tn; ++j) tl[t++] = {o.g, i, j, p.m, p.n, p.k, p.ldc, (p.k + 63) / 64, p.off_c, 0};
+    }
+    *maps_bytes_out = maps_bytes;
+    *tiles_out = static_cast<int32_t>(ntiles);
+    return TC_OK;
+}
+
+// Upload the tensor-core host half to `dev_base` and launch.
+tc_status grouped_tc_enqueue(const char* name, int32_t dt, int32_t lb, const std::vector<unsigned char>& host,
+                             size_t maps_bytes, int32_t ntiles, unsigned char* dev_base, float* c_base, float alpha,
+                             float beta, int* status, int sm_count, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(dev_base, host.data(), host.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, name);
+    return enqueue(tcg::launch_grouped_tc(dt, reinterpret_cast<const tcg::GroupedTcTile*>(dev_base + maps_bytes),
+                                          ntiles, reinterpret_cast<const CUtensorMap*>(dev_base), c_base, alpha, beta,
+                                          status, sm_count, st, -1, lb == TC_ROW_MAJOR),
+                   name);
+}
+
 }  // namespace
 
 extern "C" tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_problem* problems, const void* a_base,
@@ -939,16 +1010,35 @@ extern "C" tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_pr
     std::vector<unsigned char> host;
     size_t desc_bytes = 0;
     int64_t num_tiles = 0;
+    const bool tc = grouped_use_tensor_cores(lb);
     tc_status s = grouped_mma_host("gemm_grouped_noalloc", dt, count, problems, a_base, la, b_base, lb, c_base, host,
-                                   &desc_bytes, &num_tiles);
+                                   &desc_bytes, &num_tiles, !tc);
     if (s != TC_OK || count == 0) return s;
+    NoAllocDevice* d;
+    if ((s = noalloc_setup(&d)) != TC_OK) return s;
+    if (tc) {
+        std::vector<unsigned char> tch;
+        size_t maps_bytes = 0;
+        int32_t tc_tiles = 0;
+        if ((s = grouped_tc_host(dt, count, problems, a_base, b_base, lb, tch, &maps_bytes, &tc_tiles)) != TC_OK)
+            return s;
+        if (tch.size() <= kNoAllocScratchBytes) {
+            Device* dev;  // sm_count and the status word (a static variable): nothing is allocated
+            if ((s = get_device(&dev)) != TC_OK) return s;
+            return grouped_tc_enqueue("gemm_grouped_noalloc", dt, lb, tch, maps_bytes, tc_tiles,
+                                      static_cast<unsigned char*>(d->scratch), c_base, alpha, beta, dev->status,
+                                      d->sm_count, as_stream(stream));
+        }
+        // more problems than the static table holds maps for: the mma.sync schedule is smaller
+        if ((s = grouped_mma_host("gemm_grouped_noalloc", dt, count, problems, a_base, la, b_base, lb, c_base, host,
+                                  &desc_bytes, &num_tiles)) != TC_OK)
+            return s;
+    }
     if (host.size() > kNoAllocScratchBytes)
         return fail(TC_ERR_INVALID,
                     "gemm_grouped_noalloc: %d problems (%lld tiles) need %zu bytes of scratch; the static maximum "
                     "is %zu bytes (use gemm_grouped_plan_create for larger groups)",
                     count, (long long)num_tiles, host.size(), kNoAllocScratchBytes);
-    NoAllocDevice* d;
-    if ((s = noalloc_setup(&d)) != TC_OK) return s;
     return grouped_mma_enqueue("gemm_grouped_noalloc", dt, lb, host, desc_bytes, num_tiles,
                                static_cast<unsigned char*>(d->scratch), a_base, b_base, c_base, alpha, beta,
                                d->sm_count, as_stream(stream));
@@ -956,15 +1046,21 @@ extern "C" tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_pr
 
 extern "C" size_t gemm_grouped_workspace_bytes(int32_t count, const tc_problem* problems) {
     if (count <= 0 || !problems) return 0;
-    int64_t num_tiles = 0;
+    int64_t mma_tiles = 0, tc_tiles = 0;
     for (int32_t g = 0; g < count; ++g) {
         const tc_problem& p = problems[g];
         if (p.m < 1 || p.n < 1) continue;
-        num_tiles += int64_t((p.m + tcg::kGroupedTileM - 1) / tcg::kGroupedTileM) *
+        mma_tiles += int64_t((p.m + tcg::kGroupedTileM - 1) / tcg::kGroupedTileM) *
                      ((p.n + tcg::kGroupedTileN - 1) / tcg::kGroupedTileN);
+        tc_tiles += int64_t((p.m + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM) *
+                    ((p.n + tcg::kGroupedTcTileN - 1) / tcg::kGroupedTcTileN);
     }
-    return (size_t(count) * sizeof(tcg::GroupedProblemDev) + 255) / 256 * 256 +
-           size_t(num_tiles) * sizeof(tcg::GroupedTileDev);
+    // enough for either kernel: the mma.sync schedule or the tensor-core maps and tiles
+    const size_t mma = (size_t(count) * sizeof(tcg::GroupedProblemDev) + 255) / 256 * 256 +
+                       size_t(mma_tiles) * sizeof(tcg::GroupedTileDev);
+    const size_t tc = (2 * size_t(count) * sizeof(CUtensorMap) + 255) / 256 * 256 +
+                      size_t(tc_tiles) * sizeof(tcg::GroupedTcTile);
+    return mma > tc ? mma : tc;
 }
 
 extern "C" tc_status gemm_grouped_ws(int32_t dt, int32_t count, const tc_problem* problems, const void* a_base,
@@ -973,15 +1069,29 @@ extern "C" tc_status gemm_grouped_ws(int32_t dt, int32_t count, const tc_problem
     std::vector<unsigned char> host;
     size_t desc_bytes = 0;
     int64_t num_tiles = 0;
+    const bool tc = grouped_use_tensor_cores(lb);
     tc_status s = grouped_mma_host("gemm_grouped_ws", dt, count, problems, a_base, la, b_base, lb, c_base, host,
-                                   &desc_bytes, &num_tiles);
+                                   &desc_bytes, &num_tiles, !tc);
     if (s != TC_OK || count == 0) return s;
     if (!workspace || !aligned(workspace, 256))
         return fail(TC_ERR_INVALID, "gemm_grouped_ws: workspace must be a 256-byte aligned device pointer");
-    if (workspace_bytes < host.size())
-        return fail(TC_ERR_INVALID, "gemm_grouped_ws: workspace of %zu bytes, need %zu", workspace_bytes, host.size());
     Device* d;
     if ((s = get_device(&d)) != TC_OK) return s;
+    if (tc) {
+        std::vector<unsigned char> tch;
+        size_t maps_bytes = 0;
+        int32_t tc_tiles = 0;
+        if ((s = grouped_tc_host(dt, count, problems, a_base, b_base, lb, tch, &maps_bytes, &tc_tiles)) != TC_OK)
+            return s;
+        if (workspace_bytes < tch.size())
+            return fail(TC_ERR_INVALID, "gemm_grouped_ws: workspace of %zu bytes, need %zu", workspace_bytes,
+                        tch.size());
+        return grouped_tc_enqueue("gemm_grouped_ws", dt, lb, tch, maps_bytes, tc_tiles,
+                                  static_cast<unsigned char*>(workspace), c_base, alpha, beta, d->status,
+                                  d->sm_count, as_stream(stream));
+    }
+    if (workspace_bytes < host.size())
+        return fail(TC_ERR_INVALID, "gemm_grouped_ws: workspace of %zu bytes, need %zu", workspace_bytes, host.size());
     return grouped_mma_enqueue("gemm_grouped_ws", dt, lb, host, desc_bytes, num_tiles,
                                static_cast<unsigned char*>(workspace), a_base, b_base, c_base, alpha, beta,
                                d->sm_count, as_stream(stream));

@@ -215,11 +215,13 @@ tc_status launch_batch(const std::vector<Req*>& members, uint8_t* arena_base, ui
                            kDescBytes - qbytes, st);
 }
 
-// Descriptor bytes a batch member adds (job table entries, tiles, problem, tiles; an upper bound).
+// Descriptor bytes a batch member adds (job table entries, tiles, then the larger of the two
+// grouped layouts: tensor maps and 128 x 256 tiles, or problem entry and 64 x 64 tiles; an upper bound).
 size_t batch_desc_bytes(const tc_request& r) {
     auto tiles = [](int64_t rows, int64_t cols, int64_t tr, int64_t tc) { return ((rows + tr - 1) / tr) * ((cols + tc - 1) / tc); };
-    return 2 * 64 + size_t(tiles(r.m, r.k, 64, 32) + tiles(r.k, r.n, 64, 32)) * 32 + 64 +
-           size_t(tiles(r.m, r.n, 64, 64)) * 16;
+    const size_t mma = 64 + size_t(tiles(r.m, r.n, 64, 64)) * 16;
+    const size_t tc = 256 + size_t(tiles(r.m, r.n, 128, 256)) * 48;
+    return 2 * 64 + size_t(tiles(r.m, r.k, 64, 32) + tiles(r.k, r.n, 64, 32)) * 32 + std::max(mma, tc);
 }
 
 }  // namespace

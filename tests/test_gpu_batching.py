@@ -1,6 +1,6 @@
 """GPU parity of the batched entry points the serving loop uses: many small
 roundings in one launch (tc_quantize_batch) and a grouped GEMM whose schedule
-lives in caller-owned device memory (gemm_grouped_ws)."""
+lives in caller-owned device memory (gemm_grouped_ws), on the tcgen05 kernel and on the mma.sync kernel."""
 import numpy as np
 import pytest
 
@@ -52,8 +52,11 @@ def test_quantize_batch_bit_exact(b, dt):
         b.tc_quantize_batch(2, jobs, ws, need)          # E4M3 needs a per-tensor scale
 
 
+@pytest.mark.parametrize("impl", ["tc", "mma"])
 @pytest.mark.parametrize("lb", [0, 1])
-def test_grouped_ws_matches_oracle_and_runs_concurrently(b, lb):
+def test_grouped_ws_matches_oracle_and_runs_concurrently(b, lb, impl, monkeypatch):
+    if impl == "mma":
+        monkeypatch.setenv("TCGEMM_GROUPED", "mma")
     rng_sizes = synth.group_sizes(150, seed=synth.seed_for(6, 40))
     def build(sizes, seed):
         offa = offb = offc = 0

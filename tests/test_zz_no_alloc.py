@@ -4,8 +4,10 @@ Some callers may not call cudaMalloc: code that runs inside a memory budget
 owned by someone else (a framework's caching allocator or a serving engine
 that reserved the GPU's memory up front, where a new allocation can fail or
 fragment that pool) and latency-critical loops that cannot pay for the
-device-wide synchronisation of cudaMalloc/cudaFree.  This entry keeps its
-problem descriptors and tile schedule in a static device array instead.
+device-wide synchronisation of cudaMalloc/cudaFree.  This entry keeps what
+its kernel reads besides the operands (the tcgen05 kernel's tensor maps and
+tiles, or the mma.sync kernel's problem table and tiles) in a static device
+array instead.
 
 The test calls it through the C ABI twice in a row, with different groups so
 the second call runs over the first call's leftovers in the static array, and
@@ -57,8 +59,11 @@ def _group(count, seed, lb):
     return rows, abuf, bbuf, oc
 
 
+@pytest.mark.parametrize("impl", ["tc", "mma"])
 @pytest.mark.parametrize("lb", [0, 1])
-def test_noalloc_matches_grouped_on_two_calls_in_a_row(b, lb):
+def test_noalloc_matches_grouped_on_two_calls_in_a_row(b, lb, impl, monkeypatch):
+    if impl == "mma":
+        monkeypatch.setenv("TCGEMM_GROUPED", "mma")
     for call, (count, seed) in enumerate([(120, 7), (37, 8)]):
         rows, abuf, bbuf, csize = _group(count, seed, lb)
         c0 = torch.from_numpy(synth.uniform((csize,), seed=900 + call)).cuda()
@@ -77,8 +82,31 @@ def test_noalloc_matches_grouped_on_two_calls_in_a_row(b, lb):
             assert ok, (call, m, n, k, info)
 
 
+def test_noalloc_falls_back_to_the_smaller_schedule(b):
+    # 40 000 problems: tensor maps and tiles need 40 000 * (256 + 48) bytes ~ 12.2 MB, more than the
+    # 8 MiB array; the mma.sync table and tiles need 40 000 * (48 + 16) bytes ~ 2.6 MB and fit
+    count = 40_000
+    rng = np.random.default_rng(synth.seed_for(6, 60))
+    A = torch.from_numpy(synth.uniform((count * 16 * 16,), seed=synth.seed_for(6, 61))).to(torch.float16).cuda()
+    B = torch.from_numpy(synth.uniform((count * 16 * 16,), seed=synth.seed_for(6, 62))).to(torch.float16).cuda()
+    rows = []
+    for g in range(count):
+        m, n = int(rng.integers(1, 17)), 16
+        rows.append((m, n, 16, g * 256, g * 256, g * 256, 16, 16, 16))
+    c0 = torch.from_numpy(synth.uniform((count * 256,), seed=synth.seed_for(6, 63))).cuda()
+    c_ref, c_new = c0.clone(), c0.clone()
+    b.gemm_grouped(0, rows, A, 0, B, 0, c_ref, 1.0, 0.5)
+    b.gemm_grouped_noalloc(0, rows, A, 0, B, 0, c_new, 1.0, 0.5)
+    b.tc_sync_status()
+    ref, got, base = host(c_ref), host(c_new), host(c0)
+    mag = 16 + 0.5 * np.abs(base)
+    ok, info = elementwise_ok(got, ref, mag, 16)
+    assert ok, info
+
+
 def test_noalloc_rejects_groups_beyond_its_static_scratch(b):
-    # 8 MiB of scratch: 48 bytes per problem + 16 bytes per 64x64 tile; 200 000 problems need ~12.8 MB
+    # 8 MiB of scratch; the smaller schedule (mma.sync: 48 bytes per problem + 16 bytes per 64x64
+    # tile) of 200 000 problems needs ~12.8 MB
     rows = [(16, 16, 16, 0, 0, 0, 16, 16, 16)] * 200_000
     c = torch.zeros(256, dtype=torch.float32, device="cuda")
     a = torch.zeros(256, dtype=torch.float16, device="cuda")
