@@ -151,6 +151,9 @@ def parse_args():
     p.add_argument("--profile-gemm", choices=["f16", "bf16", "e4m3", "split3", "split3_scaled", "bf16x3", "grouped",
                                               "grouped_rowmajor", "batched16"], default=None,
                    help="only round the N=8192 inputs and run 5 GEMM launches (a small case for ncu captures)")
+    p.add_argument("--serve-row", action="store_true",
+                   help="only measure the served stream and print it as one JSON line (the serve row runs so, "
+                        "in a child process with a time limit)")
     return p.parse_args()
 
 
@@ -469,8 +472,30 @@ def measure_rows(b, A, B, pk, sm_count):
 
     out["error_norm_n8192"] = _row("error_norm_n8192", error_norm)
     torch.cuda.empty_cache()
-    out["serve"] = _row("serve", lambda: measure_serve(b))
+    out["serve"] = _row("serve", serve_row_in_child)
     return out
+
+
+SERVE_ROW_TIMEOUT_S = 420
+
+
+def serve_row_in_child():
+    """The served-stream row in its own process (own CUDA context, own server thread): a stream that
+    stalls is ended after SERVE_ROW_TIMEOUT_S by killing that process, and the other rows and the
+    headline are still reported."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--serve-row"]
+    try:
+        r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                           timeout=SERVE_ROW_TIMEOUT_S, cwd=ROOT)
+    except subprocess.TimeoutExpired as e:
+        tail = (e.stderr or b"")
+        tail = tail.decode(errors="replace") if isinstance(tail, bytes) else tail
+        return {"error": f"served stream did not finish in {SERVE_ROW_TIMEOUT_S} s",
+                "stderr_tail": tail[-2000:]}
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return {"error": f"serve child exited {r.returncode}", "stderr_tail": r.stderr[-2000:]}
+    return json.loads(lines[-1])
 
 
 def measure_serve(b, count=50000, budget=40 << 30):
@@ -655,6 +680,13 @@ def main():
         return run_reference(args)
     if args.profile_gemm:
         return profile_case(args.profile_gemm)
+    if args.serve_row:
+        import torch
+        from paper_1803_04014_gb300 import binding as b
+        b.load()
+        faulthandler.dump_traceback_later(SERVE_ROW_TIMEOUT_S - 30, exit=True)   # stacks on stderr first
+        print(json.dumps(measure_serve(b)), flush=True)
+        return 0
     rank, world, local = dist_env()
     import torch
     torch.cuda.set_device(local)
