@@ -568,7 +568,7 @@ struct tc_grouped_plan {
     const void* g_b = nullptr;
     float* g_c = nullptr;
     float g_alpha = 0.f, g_beta = 0.f;
-    // tensor-core path (K-major B): 128 x 256 tiles and one pair of TMA maps per problem
+    // tensor-core path: 128 x 256 tiles and two TMA maps per problem (A, B)
     bool use_tc = false;
     std::vector<tc_problem> host_probs;
     tcg::GroupedTcTile* d_tc_tiles = nullptr;
@@ -582,25 +582,36 @@ struct tc_grouped_plan {
 
 namespace {
 
-// Encode every problem's A and B tensor maps for these bases and upload them (stream-ordered).
-tc_status grouped_upload_maps(tc_grouped_plan* plan, const void* a_base, const void* b_base, cudaStream_t st) {
-    const CUtensorMapDataType tdt = plan->dt == TC_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    std::vector<CUtensorMap> maps(2 * static_cast<size_t>(plan->count));
+// Every problem's tensor maps for these bases, two per problem: A_g (dims {k, m}) and B_g
+// (dims {k, n} K-major, or {n, k} row-major).
+tc_status encode_grouped_maps(int32_t dt, int32_t lb, int32_t count, const tc_problem* problems, const void* a_base,
+                              const void* b_base, CUtensorMap* maps) {
+    const CUtensorMapDataType tdt = dt == TC_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const uint8_t* a = static_cast<const uint8_t*>(a_base);
     const uint8_t* b = static_cast<const uint8_t*>(b_base);
-    for (int32_t g = 0; g < plan->count; ++g) {
-        const tc_problem& p = plan->host_probs[g];
-        tc_status s = encode_kmajor(&maps[2 * g], tdt, 2, a + p.off_a * 2, p.k, p.m, 1, int64_t(p.lda) * 2,
+    constexpr int kM = tcg::kGroupedTcMapsPerProblem;
+    for (int32_t g = 0; g < count; ++g) {
+        const tc_problem& p = problems[g];
+        tc_status s = encode_kmajor(&maps[kM * g], tdt, 2, a + p.off_a * 2, p.k, p.m, 1, int64_t(p.lda) * 2,
                                     int64_t(p.m) * p.lda * 2, tcg::kGroupedTcTileM);
         if (s != TC_OK) return s;
-        if (plan->lb == TC_ROW_MAJOR)   // B_g k x n: dims {n, k}, boxes of 64 n (128 bytes) x 64 k
-            s = encode_kmajor(&maps[2 * g + 1], tdt, 2, b + p.off_b * 2, p.n, p.k, 1, int64_t(p.ldb) * 2,
+        if (lb == TC_ROW_MAJOR)   // B_g k x n: dims {n, k}, boxes of 64 n (128 bytes) x 64 k
+            s = encode_kmajor(&maps[kM * g + 1], tdt, 2, b + p.off_b * 2, p.n, p.k, 1, int64_t(p.ldb) * 2,
                               int64_t(p.k) * p.ldb * 2, 64);
         else
-            s = encode_kmajor(&maps[2 * g + 1], tdt, 2, b + p.off_b * 2, p.k, p.n, 1, int64_t(p.ldb) * 2,
+            s = encode_kmajor(&maps[kM * g + 1], tdt, 2, b + p.off_b * 2, p.k, p.n, 1, int64_t(p.ldb) * 2,
                               int64_t(p.n) * p.ldb * 2, tcg::grouped_tc_box_rows(p.n));
         if (s != TC_OK) return s;
     }
+    return TC_OK;
+}
+
+// Encode every problem's tensor maps for these bases and upload them (stream-ordered).
+tc_status grouped_upload_maps(tc_grouped_plan* plan, const void* a_base, const void* b_base, cudaStream_t st) {
+    std::vector<CUtensorMap> maps(tcg::kGroupedTcMapsPerProblem * static_cast<size_t>(plan->count));
+    tc_status s = encode_grouped_maps(plan->dt, plan->lb, plan->count, plan->host_probs.data(), a_base, b_base,
+                                      maps.data());
+    if (s != TC_OK) return s;
     // pageable source: returns once the bytes are staged
     cudaError_t e = cudaMemcpyAsync(plan->d_maps, maps.data(), maps.size() * sizeof(CUtensorMap),
                                     cudaMemcpyHostToDevice, st);
@@ -709,7 +720,8 @@ tc_status gemm_grouped_plan_create(int32_t dt, int32_t count, const tc_problem* 
         plan->status = d->status;
         if ((e = cudaMalloc(&plan->d_tc_tiles, tc.size() * sizeof(tc[0]))) == cudaSuccess)
             e = cudaMemcpy(plan->d_tc_tiles, tc.data(), tc.size() * sizeof(tc[0]), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMalloc(&plan->d_maps, 2 * size_t(count) * sizeof(CUtensorMap));
+        if (e == cudaSuccess)
+            e = cudaMalloc(&plan->d_maps, tcg::kGroupedTcMapsPerProblem * size_t(count) * sizeof(CUtensorMap));
     }
     if (e != cudaSuccess) {
         gemm_grouped_plan_destroy(plan);
@@ -938,14 +950,15 @@ tc_status grouped_mma_enqueue(const char* name, int32_t dt, int32_t lb, const st
                    name);
 }
 
-// Host half of a plan-free grouped GEMM on the tensor-core kernel: one pair of TMA maps per
-// problem (encoded for these bases; 256-byte aligned table first), then the 128 x 256 tiles in
-// the longest-first problem order of a plan.  The problems were checked by grouped_mma_host.
+// Host half of a plan-free grouped GEMM on the tensor-core kernel: two TMA maps per problem
+// (encoded for these bases; 256-byte aligned table first), then the 128 x 256 tiles in the
+// longest-first problem order of a plan.  Nothing is built when the result would exceed
+// max_bytes (*fits = false).  The problems were checked by grouped_mma_host.
 tc_status grouped_tc_host(int32_t dt, int32_t count, const tc_problem* problems, const void* a_base,
-                          const void* b_base, int32_t lb, std::vector<unsigned char>& host, size_t* maps_bytes_out,
-                          int32_t* tiles_out) {
-    const CUtensorMapDataType tdt = dt == TC_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    const size_t maps_bytes = (2 * size_t(count) * sizeof(CUtensorMap) + 255) / 256 * 256;
+                          const void* b_base, int32_t lb, size_t max_bytes, std::vector<unsigned char>& host,
+                          size_t* maps_bytes_out, int32_t* tiles_out, bool* fits) {
+    const size_t maps_bytes =
+        (tcg::kGroupedTcMapsPerProblem * size_t(count) * sizeof(CUtensorMap) + 255) / 256 * 256;
     struct P { int64_t cost; int32_t g; };
     std::vector<P> order;
     order.reserve(count);
@@ -958,24 +971,14 @@ tc_status grouped_tc_host(int32_t dt, int32_t count, const tc_problem* problems,
         order.push_back({2 * p.k * (p.m * tn + p.n * tm) + 4 * int64_t(p.m) * p.n, g});
     }
     if (ntiles > 0x7FFFFFFF) return fail(TC_ERR_INVALID, "grouped: too many tiles");
+    const size_t total = maps_bytes + size_t(ntiles) * sizeof(tcg::GroupedTcTile);
+    *fits = total <= max_bytes;
+    if (!*fits) return TC_OK;
     std::stable_sort(order.begin(), order.end(), [](const P& x, const P& y) { return x.cost > y.cost; });
-    host.assign(maps_bytes + size_t(ntiles) * sizeof(tcg::GroupedTcTile), 0);
-    auto* maps = reinterpret_cast<CUtensorMap*>(host.data());
-    const uint8_t* a = static_cast<const uint8_t*>(a_base);
-    const uint8_t* b = static_cast<const uint8_t*>(b_base);
-    for (int32_t g = 0; g < count; ++g) {
-        const tc_problem& p = problems[g];
-        tc_status st = encode_kmajor(&maps[2 * g], tdt, 2, a + p.off_a * 2, p.k, p.m, 1, int64_t(p.lda) * 2,
-                                     int64_t(p.m) * p.lda * 2, tcg::kGroupedTcTileM);
-        if (st != TC_OK) return st;
-        if (lb == TC_ROW_MAJOR)
-            st = encode_kmajor(&maps[2 * g + 1], tdt, 2, b + p.off_b * 2, p.n, p.k, 1, int64_t(p.ldb) * 2,
-                               int64_t(p.k) * p.ldb * 2, 64);
-        else
-            st = encode_kmajor(&maps[2 * g + 1], tdt, 2, b + p.off_b * 2, p.k, p.n, 1, int64_t(p.ldb) * 2,
-                               int64_t(p.n) * p.ldb * 2, tcg::grouped_tc_box_rows(p.n));
-        if (st != TC_OK) return st;
-    }
+    host.assign(total, 0);
+    tc_status st =
+        encode_grouped_maps(dt, lb, count, problems, a_base, b_base, reinterpret_cast<CUtensorMap*>(host.data()));
+    if (st != TC_OK) return st;
     auto* tl = reinterpret_cast<tcg::GroupedTcTile*>(host.data() + maps_bytes);
     size_t t = 0;
     for (const P& o : order) {
@@ -1020,9 +1023,11 @@ extern "C" tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_pr
         std::vector<unsigned char> tch;
         size_t maps_bytes = 0;
         int32_t tc_tiles = 0;
-        if ((s = grouped_tc_host(dt, count, problems, a_base, b_base, lb, tch, &maps_bytes, &tc_tiles)) != TC_OK)
+        bool fits = false;
+        if ((s = grouped_tc_host(dt, count, problems, a_base, b_base, lb, kNoAllocScratchBytes, tch, &maps_bytes,
+                                 &tc_tiles, &fits)) != TC_OK)
             return s;
-        if (tch.size() <= kNoAllocScratchBytes) {
+        if (fits) {
             Device* dev;  // sm_count and the status word (a static variable): nothing is allocated
             if ((s = get_device(&dev)) != TC_OK) return s;
             return grouped_tc_enqueue("gemm_grouped_noalloc", dt, lb, tch, maps_bytes, tc_tiles,
@@ -1058,7 +1063,7 @@ extern "C" size_t gemm_grouped_workspace_bytes(int32_t count, const tc_problem* 
     // enough for either kernel: the mma.sync schedule or the tensor-core maps and tiles
     const size_t mma = (size_t(count) * sizeof(tcg::GroupedProblemDev) + 255) / 256 * 256 +
                        size_t(mma_tiles) * sizeof(tcg::GroupedTileDev);
-    const size_t tc = (2 * size_t(count) * sizeof(CUtensorMap) + 255) / 256 * 256 +
+    const size_t tc = (tcg::kGroupedTcMapsPerProblem * size_t(count) * sizeof(CUtensorMap) + 255) / 256 * 256 +
                       size_t(tc_tiles) * sizeof(tcg::GroupedTcTile);
     return mma > tc ? mma : tc;
 }
@@ -1081,11 +1086,13 @@ extern "C" tc_status gemm_grouped_ws(int32_t dt, int32_t count, const tc_problem
         std::vector<unsigned char> tch;
         size_t maps_bytes = 0;
         int32_t tc_tiles = 0;
-        if ((s = grouped_tc_host(dt, count, problems, a_base, b_base, lb, tch, &maps_bytes, &tc_tiles)) != TC_OK)
+        bool fits = false;
+        if ((s = grouped_tc_host(dt, count, problems, a_base, b_base, lb, workspace_bytes, tch, &maps_bytes, &tc_tiles,
+                                 &fits)) != TC_OK)
             return s;
-        if (workspace_bytes < tch.size())
-            return fail(TC_ERR_INVALID, "gemm_grouped_ws: workspace of %zu bytes, need %zu", workspace_bytes,
-                        tch.size());
+        if (!fits)
+            return fail(TC_ERR_INVALID, "gemm_grouped_ws: workspace of %zu bytes is smaller than "
+                        "gemm_grouped_workspace_bytes", workspace_bytes);
         return grouped_tc_enqueue("gemm_grouped_ws", dt, lb, tch, maps_bytes, tc_tiles,
                                   static_cast<unsigned char*>(workspace), c_base, alpha, beta, d->status,
                                   d->sm_count, as_stream(stream));

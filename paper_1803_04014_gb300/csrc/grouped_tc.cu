@@ -14,7 +14,11 @@
 //   * one thread issues tcgen05.mma 128 x N x 16 (N = the problem's n rounded up
 //     to 16, at most 256) into a double-buffered TMEM accumulator;
 //   * eight epilogue warps read the accumulator and store C with alpha/beta,
-//     the two warps of each TMEM lane quarter taking alternate 32-column chunks.
+//     the two warps of each TMEM lane quarter taking alternate 32-column chunks;
+//     each chunk (32 rows x 32 columns) is transposed through a 4 KB swizzled
+//     shared-memory slot of the warp so that C leaves as whole row segments.
+//     (Storing the chunks by TMA instead was measured slower: the stores queue
+//     behind the operand loads in the SM's one TMA unit.)
 #include <cstdlib>
 #include <cstring>
 
@@ -35,9 +39,17 @@ constexpr int kBarOff = kStages * kStage;
 constexpr int kNumBars = 2 * kStages + 5;
 constexpr int kSlotOff = kBarOff + 8 * kNumBars;
 constexpr int kEpiWarps = 8;                         // two warps per TMEM lane quarter, 128 columns each
-constexpr int kEpiOff = kSlotOff + 16;               // kEpiWarps x 32 x 33 floats of store staging
-constexpr int kEpiWarpFloats = 32 * 33;
-constexpr int kSmem = kEpiOff + kEpiWarps * kEpiWarpFloats * 4 + 1024;
+constexpr int kEpiWarpBytes = 32 * 32 * 4;           // one 32 x 32 FP32 chunk, 128-byte rows
+constexpr int kEpiOff = (kSlotOff + 16 + 127) / 128 * 128;
+constexpr int kSmem = kEpiOff + kEpiWarps * kEpiWarpBytes + 1024;
+static_assert(kSmem <= 232448, "shared memory per CTA");
+
+// Byte offset of the 16-byte group `g` (columns 4g..4g+3) of row `r` in a chunk slot: the
+// group index is XORed with the row mod 8, so a warp's 16-byte accesses are free of bank
+// conflicts both when each lane writes its own row and when 8 lanes read one row.
+__device__ __forceinline__ uint32_t slot_off(int r, int g) {
+    return static_cast<uint32_t>(r * 128 + ((g ^ (r & 7)) << 4));
+}
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 struct Args {
@@ -253,15 +265,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
             float* crow = a.c_base + P.off_c + static_cast<int64_t>(row) * P.ldc + col0;
             const bool vec_ok = ((P.ldc & 3) == 0) && (((P.off_c + col0) & 3) == 0) &&
                                 ((reinterpret_cast<uintptr_t>(a.c_base) & 15u) == 0);
+            uint8_t* slot_ptr = base_ptr + kEpiOff + (warp - 2) * kEpiWarpBytes;
+            const int r0 = tile.tm * GM + quarter * 32;
+            // a warp whose 32 rows all lie past the last row of C_g has nothing to read or store
+            const int ncols_warp = r0 < P.m ? ncols_tile : 0;
             if (a.staged_epilogue) {
                 // each warp owns rows r0..r0+31 of the tile; stage 32 x 32 chunks and store whole row segments
-                float* stage = reinterpret_cast<float*>(base_ptr + kEpiOff) + (warp - 2) * kEpiWarpFloats;
-                const int r0 = tile.tm * GM + quarter * 32;
 #pragma unroll 1
-                for (int c = half * 32; c < ncols_tile; c += 64) {
+                for (int c = half * 32; c < ncols_warp; c += 64) {
                     const int nc = min(32, ncols_tile - c);
-                    // lane l writes column (l % 8) * 4 .. +3 of rows q*4 + l/8, q = 0..7
-                    const int cc = (lane & 7) * 4;
+                    // lane l writes 16-byte group g = l % 8 (columns 4g..4g+3) of rows q*4 + l/8, q = 0..7
+                    const int g = lane & 7;
+                    const int cc = g * 4;
                     // old C of this chunk first: its global-memory latency overlaps the TMEM load
                     float4 old[8];
                     if (beta != 0.0f) {
@@ -278,7 +293,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                     float v[32];
                     tmem_load_32(taddr + c, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = v[j];
+                    for (int q = 0; q < 8; ++q)
+                        *reinterpret_cast<float4*>(slot_ptr + slot_off(lane, q)) =
+                            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                     __syncwarp();
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
@@ -286,9 +303,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                         const int grow = r0 + rr;
                         if (grow < P.m) {
                             float* p = a.c_base + P.off_c + static_cast<int64_t>(grow) * P.ldc + col0 + c + cc;
-                            const float* sv = stage + rr * 33 + cc;
+                            const float4 sv = *reinterpret_cast<const float4*>(slot_ptr + slot_off(rr, g));
                             if (vec_ok && cc + 4 <= nc) {
-                                float4 o = make_float4(alpha * sv[0], alpha * sv[1], alpha * sv[2], alpha * sv[3]);
+                                float4 o = make_float4(alpha * sv.x, alpha * sv.y, alpha * sv.z, alpha * sv.w);
                                 if (beta != 0.0f) {
                                     o.x = fmaf(beta, old[q].x, o.x);
                                     o.y = fmaf(beta, old[q].y, o.y);
@@ -297,9 +314,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                                 }
                                 __stcs(reinterpret_cast<float4*>(p), o);
                             } else {
+                                const float e4[4] = {sv.x, sv.y, sv.z, sv.w};
+#pragma unroll
                                 for (int e = 0; e < 4; ++e)
                                     if (cc + e < nc)
-                                        p[e] = (beta != 0.0f) ? fmaf(alpha, sv[e], beta * p[e]) : alpha * sv[e];
+                                        p[e] = (beta != 0.0f) ? fmaf(alpha, e4[e], beta * p[e]) : alpha * e4[e];
                             }
                         }
                     }
@@ -313,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                 continue;
             }
 #pragma unroll 1
-            for (int c = half * 32; c < ncols_tile; c += 64) {
+            for (int c = half * 32; c < ncols_warp; c += 64) {
                 float v[32];
                 tmem_load_32(taddr + c, v);
                 if (row < P.m) {

@@ -105,6 +105,7 @@ struct alignas(16) GroupedTcTile {
     int64_t off_c, pad;       // element offset of C_g
 };
 int grouped_tc_box_rows(int n);
+constexpr int kGroupedTcMapsPerProblem = 2;
 // staged: 1 = epilogue through shared memory, 0 = direct row stores, -1 = TCGEMM_GROUPED_EPI or staged
 // b_mn: every B_g is row-major (k x n) and maps[2g+1] has dims {n, k, 1} with 64 x 64 boxes.
 cudaError_t launch_grouped_tc(int dt, const GroupedTcTile* tiles, int32_t num_tiles, const CUtensorMap* maps,

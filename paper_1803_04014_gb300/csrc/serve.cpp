@@ -220,7 +220,7 @@ tc_status launch_batch(const std::vector<Req*>& members, uint8_t* arena_base, ui
 size_t batch_desc_bytes(const tc_request& r) {
     auto tiles = [](int64_t rows, int64_t cols, int64_t tr, int64_t tc) { return ((rows + tr - 1) / tr) * ((cols + tc - 1) / tc); };
     const size_t mma = 64 + size_t(tiles(r.m, r.n, 64, 64)) * 16;
-    const size_t tc = 256 + size_t(tiles(r.m, r.n, 128, 256)) * 48;
+    const size_t tc = 2 * 128 + size_t(tiles(r.m, r.n, 128, 256)) * 48;
     return 2 * 64 + size_t(tiles(r.m, r.k, 64, 32) + tiles(r.k, r.n, 64, 32)) * 32 + std::max(mma, tc);
 }
 

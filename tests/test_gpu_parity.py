@@ -314,10 +314,12 @@ def test_batched16_padded_strides(b):
 # ------------------------------------------------------------------ grouped GEMM
 
 def _grouped_case(count, seed, lb, ragged=False):
+    # ragged: m, n, k each reduced by 0..8; "mk": only m and k, so every C_g row stays 16-byte aligned
     sizes = synth.group_sizes(count, seed)
     if ragged:
         sizes = sizes - (synth.words(sizes.size, seed=seed + 1).reshape(sizes.shape) % 9).astype(np.int64)
-        sizes[:, 2] = (sizes[:, 2] + 7) // 8 * 8 if False else sizes[:, 2]
+        if ragged == "mk":
+            sizes[:, 1] = (sizes[:, 1] + 3) // 4 * 4
     rows, Ablocks, Bblocks = [], [], []
     oa = ob = oc = 0
     probs = []
@@ -509,12 +511,16 @@ def test_split_promotion_settings_match_oracle(b, monkeypatch, promote):
 # ------------------------------------------------------------------ grouped GEMM: tensor-core and mma.sync kernels
 
 @pytest.mark.parametrize("lb", [1, 0])
-@pytest.mark.parametrize("impl", ["tc", "mma"])
-@pytest.mark.parametrize("count,ragged", [(1, False), (9, False), (400, False), (60, True)])
+@pytest.mark.parametrize("impl", ["tc", "tc_direct", "mma"])
+@pytest.mark.parametrize("count,ragged", [(1, False), (9, False), (400, False), (60, True), (60, "mk")])
 def test_grouped_kmajor_parity(b, monkeypatch, lb, impl, count, ragged):
-    # lb = 1: B_g K-major; lb = 0: B_g row-major (read by the tensor cores as MN-major)
+    # lb = 1: B_g K-major; lb = 0: B_g row-major (read by the tensor cores as MN-major).
+    # tc: C chunks transposed through shared memory and stored as row segments (vector stores
+    # where C_g rows are 16-byte aligned, ragged n is not); tc_direct: each lane stores its row.
     if impl == "mma":
         monkeypatch.setenv("TCGEMM_GROUPED", "mma")
+    if impl == "tc_direct":
+        monkeypatch.setenv("TCGEMM_GROUPED_EPI", "direct")
     probs, abuf, bbuf, csize = _grouped_case(count, seed=170 + count, lb=lb, ragged=ragged)
     C0 = synth.uniform((csize,), seed=77)
     C = dev(C0)
