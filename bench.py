@@ -237,6 +237,34 @@ def _time_each_ms(fn, iters, warm=3):
     return [evs[i].elapsed_time(evs[i + 1]) for i in range(iters)]
 
 
+def _graph_ms_per_launch(fn, reps, replays=10):
+    """Device time per launch of `reps` launches of `fn` captured in one CUDA graph (operands stay
+    in L2 between launches when they fit)."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for _ in range(reps):
+            fn()
+    graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(replays):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (replays * reps)
+    del graph
+    return ms
+
+
 def _rate_stats(flop, times_ms):
     """Mean (total work over total time), harmonic mean, median and spread of per-launch TFLOP/s."""
     rates = [flop / (t * 1e-3) / 1e12 for t in times_ms]
@@ -328,11 +356,19 @@ def measure_rows(b, A, B, pk, sm_count):
                 row[name] = {"tflops": st["tflops"], "frac_of_peak": st["tflops"] / (peak * (2.0 if dt == 2 else 1.0)),
                              "ms": sum(times) / len(times), "hmean_tflops": st["hmean_tflops"],
                              "median_tflops": st["median_tflops"], "launches": it}
+                if n_ <= 2048:
+                    # launches submitted one by one from Python are host-bound here (about 10 us per call
+                    # on the Grace host); replaying them from a CUDA graph gives the kernel's own time
+                    gms = _graph_ms_per_launch(g, 50)
+                    row[name]["graph_us_per_launch"] = gms * 1e3
+                    row[name]["graph_tflops"] = 2.0 * n_ ** 3 / (gms * 1e-3) / 1e12
                 del Aq, Bq
             res[str(n_)] = row
             del Xa, Xb, Cs
             torch.cuda.empty_cache()
-        res["note"] = "burst peak (x2 for E4M3); inputs uniform[-1,1] rounded on the GPU"
+        res["note"] = ("burst peak (x2 for E4M3); inputs uniform[-1,1] rounded on the GPU; tflops from launches "
+                       "submitted one by one (host-bound below N = 2048), graph_* from 50 launches replayed from "
+                       "one CUDA graph")
         return res
 
     out["gemm_square_sweep"] = _row("gemm_square_sweep", sweep)

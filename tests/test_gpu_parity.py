@@ -447,6 +447,21 @@ def test_gemm_tile_kernels(b, monkeypatch, tile, dt, mnk):
 
 
 @pytest.mark.parametrize("dt", [0, 1, 2])
+@pytest.mark.parametrize("mnk", [(256, 256, 256), (1024, 1024, 1024), (1536, 1400, 208)])
+def test_gemm_default_tiles_at_small_sizes(b, dt, mnk):
+    # the small square sizes of the sweep with the default tile choice (CTA pairs, grids of
+    # 1, 16 and 36 pairs)
+    m, n, k = mnk
+    A = synth.uniform((m, k), seed=151)
+    B = synth.uniform((k, n), seed=152)
+    C0 = synth.uniform((m, n), seed=153)
+    C = _run_mixed(b, dt, A, B, 1.0, 0.5, C0)
+    ref = og.gemm_mixed(DT_NAME[dt], A, B, 1.0, 0.5, C0)
+    ok, info = elementwise_ok(C, ref, _mag(dt, A, B, 1.0, 0.5, C0), k)
+    assert ok, info
+
+
+@pytest.mark.parametrize("dt", [0, 1, 2])
 @pytest.mark.parametrize("mnk", [(2560, 2560, 192), (2304, 2600, 320), (256, 2560, 128)])
 def test_gemm_pair_full_and_half_width_units(b, monkeypatch, dt, mnk):
     # 100 and 99 tiles of 256 x 256 over 76 CTA pairs: the tiles of the partial last round run as
