@@ -104,6 +104,25 @@ def test_grouped_plan_rejects_bad_problems(lib):
     assert "grouped" in b.tc_last_error()
 
 
+def test_grouped_workspace_covers_both_kernels(lib):
+    # gemm_grouped_ws puts either kernel's data in the caller's workspace: for the tcgen05 kernel
+    # two 128-byte tensor maps per problem and a 48-byte record per 128 x 256 tile, for the
+    # mma.sync kernel a 48-byte problem entry and a 16-byte record per 64 x 64 tile
+    from paper_1803_04014_gb300 import binding as b
+    assert lib.gemm_grouped_workspace_bytes(0, None) == 0
+    one = b.problems_array([(16, 16, 16, 0, 0, 0, 16, 16, 16)])
+    assert lib.gemm_grouped_workspace_bytes(1, one) >= 2 * 128 + 48
+    big = b.problems_array([(300, 600, 64, 0, 0, 0, 64, 64, 600)])      # 3 x 3 tcgen05 tiles, 5 x 10 mma.sync tiles
+    assert lib.gemm_grouped_workspace_bytes(1, big) >= max(2 * 128 + 9 * 48, 48 + 50 * 16)
+    rows = [(16 * (1 + g % 16), 16 * (1 + g % 7), 32, 0, 0, 0, 32, 32, 256) for g in range(1000)]
+    sizes = [lib.gemm_grouped_workspace_bytes(c, b.problems_array(rows[:c])) for c in (10, 100, 1000)]
+    assert sizes[0] < sizes[1] < sizes[2] and sizes[2] >= 1000 * (2 * 128 + 48)
+    # a workspace that is not a 256-byte aligned device pointer is refused before any device work
+    st = lib.gemm_grouped_ws(0, 1, one, ctypes.c_void_p(256), 0, ctypes.c_void_p(256), 0, ctypes.c_void_p(256),
+                             1.0, 0.0, None, 1 << 20, None)
+    assert st == b.TC_ERR_INVALID and "workspace" in b.tc_last_error()
+
+
 def test_serve_rejects_bad_config(lib):
     from paper_1803_04014_gb300 import binding as b
     cfg = b.tc_serve_cfg(0, 4, 2, 16, 0)
