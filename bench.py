@@ -149,8 +149,9 @@ def parse_args():
     p.add_argument("--rows", choices=["all", "none"], default="all", help="also measure the other rows (N=1 only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-gemm", choices=["f16", "bf16", "e4m3", "split3", "split3_scaled", "bf16x3", "grouped",
-                                              "grouped_rowmajor", "batched16"], default=None,
-                   help="only round the N=8192 inputs and run 5 GEMM launches (a small case for ncu captures)")
+                                              "grouped_rowmajor", "batched16", "batched16_250k", "quantize",
+                                              "errnorm"], default=None,
+                   help="only run 5 launches of one kernel on one case, nothing timed (cases for ncu captures)")
     p.add_argument("--serve-row", action="store_true",
                    help="only measure the served stream and print it as one JSON line (the serve row runs so, "
                         "in a child process with a time limit)")
@@ -669,8 +670,29 @@ def profile_case(kind):
         b.gemm_grouped_plan_destroy(plan)
         print(json.dumps({"profile_case": kind, "problems": 10000, "launches": 5}))
         return 0
-    if kind == "batched16":
-        batch = 1_000_000
+    if kind == "quantize":
+        # FP32 -> FP16 rounding of the headline's A (row-major) and B (into K-major), N = 8192
+        A = torch.from_numpy(synth.uniform((N, N), seed=synth.seed_for(1, 0))).cuda()
+        Aq = torch.empty((N, N), dtype=torch.float16, device="cuda")
+        for _ in range(5):
+            b.tc_quantize(0, N, N, A, N, Aq, N, 0)
+            b.tc_quantize(0, N, N, A, N, Aq, N, 1)
+        b.tc_sync_status()
+        print(json.dumps({"profile_case": kind, "n": N, "launches": 10}))
+        return 0
+    if kind == "errnorm":
+        # the FP64 error reduction at N = 4096: C (FP32), C64 (FP64), A and B (FP32), 320 MiB in all
+        n_ = 4096
+        Cd = torch.empty((n_, n_), dtype=torch.float32, device="cuda").uniform_(-1, 1)
+        C64 = Cd.double() + 1e-7
+        Ad = torch.empty((n_, n_), dtype=torch.float32, device="cuda").uniform_(-1, 1)
+        Bd = torch.empty((n_, n_), dtype=torch.float32, device="cuda").uniform_(-1, 1)
+        for _ in range(5):
+            b.tc_error_norm(n_, n_, Cd, n_, C64, n_, 1, Ad, n_, n_, n_, Bd, n_, n_, n_)
+        print(json.dumps({"profile_case": kind, "n": n_, "launches": 5}))
+        return 0
+    if kind in ("batched16", "batched16_250k"):
+        batch = 1_000_000 if kind == "batched16" else 250_000
         Ab = torch.empty(batch * 256, dtype=torch.float16, device="cuda").uniform_(-1, 1)
         Bb = torch.empty(batch * 256, dtype=torch.float16, device="cuda").uniform_(-1, 1)
         Cb = torch.empty(batch * 256, dtype=torch.float32, device="cuda")
