@@ -428,6 +428,16 @@ def test_error_norm_special_values(b, n):
     assert abs(out[1] - want[1]) <= 1e-14 * want[1]
 
 
+def test_binding_enqueues_on_torchs_current_stream(b):
+    # entry points called without a stream go to torch's current stream, including inside a
+    # stream context (the binding reads it through torch's raw-stream query when available)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        assert b._stream(None) == side.cuda_stream
+    assert b._stream(None) == torch.cuda.current_stream().cuda_stream
+    assert b._stream(side) == side.cuda_stream
+
+
 # ------------------------------------------------------------------ both tile kernels (single CTA / CTA pair)
 
 @pytest.mark.parametrize("tile", ["single", "pair"])
