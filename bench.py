@@ -513,7 +513,7 @@ def measure_rows(b, A, B, pk, sm_count):
     return out
 
 
-SERVE_ROW_TIMEOUT_S = 420
+SERVE_ROW_TIMEOUT_S = 240
 
 
 def serve_row_in_child():
