@@ -559,12 +559,19 @@ def _serve_stream(b, count, budget, rho=0.8, fixed_rate=None, capacity=None):
     slots = 64
     Cpool = torch.empty((slots, S * S), dtype=torch.float32, device="cuda")
     srv = b.serve_open(budget, max_inflight=32, num_streams=8)
+    deadline = time.perf_counter() + 90.0   # one stream takes a few seconds; fail fast if it stalls
+
+    def check_deadline():
+        if time.perf_counter() > deadline:
+            raise TimeoutError(f"served stream still running after 90 s: {b.serve_stats(srv)}")
+
     try:
         def submit(i, m, n, k, mode):
             while True:
                 t = b.serve_submit(srv, mode, m, n, k, Apool, S, Bpool, S, Cpool[i % slots], n)
                 if t is not None:
                     return t
+                check_deadline()
 
         # capacity: a closed burst of 1000 requests (measured once, on the first stream)
         if capacity is None or "rate" not in capacity:
@@ -594,6 +601,7 @@ def _serve_stream(b, count, budget, rho=0.8, fixed_rate=None, capacity=None):
                     break
                 if now < next_poll:
                     continue
+                check_deadline()
                 # collect from the oldest request on, every 20 us at most (completions come roughly in
                 # order, and the latency is the server's own submit-to-done time, so collecting late does
                 # not change it; polling less often leaves the server's lock to its scheduler)
