@@ -117,6 +117,9 @@ tc_status check_dims(int64_t m, int64_t n, int64_t k) {
     if (m < 0 || n < 0 || k < 0) return fail(TC_ERR_INVALID, "negative size (m=%lld n=%lld k=%lld)", (long long)m,
                                              (long long)n, (long long)k);
     if (m > kMaxDim || n > kMaxDim || k > kMaxDim) return fail(TC_ERR_INVALID, "size above 2^31-1");
+    // the kernels count output tiles (at least 128 x 128) and their halves in 32-bit integers
+    if (((m + 127) / 128) * ((n + 127) / 128) > (int64_t(1) << 29))
+        return fail(TC_ERR_INVALID, "m x n above 2^43 elements");
     return TC_OK;
 }
 

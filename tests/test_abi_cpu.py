@@ -78,6 +78,9 @@ def test_host_validation_without_gpu(lib):
         lambda: lib.gemm_mixed(7, 8, 8, 8, 1.0, None, 8, 0, None, 8, 1, 0.0, None, 8, None, None, None),
         lambda: lib.gemm_mixed(0, -1, 8, 8, 1.0, None, 8, 0, None, 8, 1, 0.0, None, 8, None, None, None),
         lambda: lib.gemm_mixed(0, 8, 8, 8, 1.0, None, 8, 5, None, 8, 1, 0.0, None, 8, None, None, None),
+        # more output tiles than the kernels count in 32 bits
+        lambda: lib.gemm_mixed(0, 1 << 30, 1 << 30, 8, 1.0, None, 8, 0, None, 8, 1, 0.0, None, 1 << 30, None, None,
+                               None),
         lambda: lib.gemm_split(2, 3, 8, 8, 8, 1.0, None, 8, 0, None, 8, 0, 0.0, None, 8, None, 0, None),
         lambda: lib.gemm_split(0, 5, 8, 8, 8, 1.0, None, 8, 0, None, 8, 0, 0.0, None, 8, None, 0, None),
         lambda: lib.tc_quantize(9, 4, 4, None, 4, None, 4, 0, None, None),
