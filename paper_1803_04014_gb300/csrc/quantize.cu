@@ -152,10 +152,64 @@ __global__ void __launch_bounds__(256) k_quantize_scalar(int64_t rows, int64_t c
 // as one 16-byte chunk of a destination row (TC = 32 for 2-byte outputs, 64 for
 // 1-byte outputs, so the tile's chunks are exactly the block's 256 threads).
 // The aligned path needs ld_dst * sizeof(T) and dst to be 16-byte aligned.
+// Load a TR x TC tile of the FP32 source (rows r0.., columns c0..) into shared memory, zero
+// outside the matrix; all loads are issued before any is stored.  vec4: every source row
+// starts on 16 bytes, so a thread loads 4 consecutive columns at once (fewer, wider loads).
+template <int TR, int TC>
+__device__ __forceinline__ void load_tile_t(float (&tile)[TR][TC + 1], const float* __restrict__ src, int64_t rows,
+                                            int64_t cols, int64_t ld_src, int64_t r0, int64_t c0, int vec4) {
+    const int t = threadIdx.x;
+    if (vec4) {
+        constexpr int C4 = TC / 4;
+        constexpr int NL4 = TR * C4 / 256;
+        float4 v[NL4];
+#pragma unroll
+        for (int q = 0; q < NL4; ++q) {
+            const int i = t + q * 256;
+            const int rr = i / C4, c4 = i - rr * C4;
+            const int64_t r = r0 + rr, c = c0 + 4 * c4;
+            if (r < rows && c + 3 < cols) {
+                v[q] = __ldcs(reinterpret_cast<const float4*>(src + r * ld_src + c));
+            } else {
+                const float* p = src + r * ld_src + c;
+                v[q].x = (r < rows && c + 0 < cols) ? __ldcs(p + 0) : 0.0f;
+                v[q].y = (r < rows && c + 1 < cols) ? __ldcs(p + 1) : 0.0f;
+                v[q].z = (r < rows && c + 2 < cols) ? __ldcs(p + 2) : 0.0f;
+                v[q].w = (r < rows && c + 3 < cols) ? __ldcs(p + 3) : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NL4; ++q) {
+            const int i = t + q * 256;
+            const int rr = i / C4, c4 = i - rr * C4;
+            tile[rr][4 * c4 + 0] = v[q].x;
+            tile[rr][4 * c4 + 1] = v[q].y;
+            tile[rr][4 * c4 + 2] = v[q].z;
+            tile[rr][4 * c4 + 3] = v[q].w;
+        }
+    } else {
+        constexpr int NL = TR * TC / 256;
+        float v[NL];
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+            const int i = t + q * 256;
+            const int rr = i / TC, cc = i - rr * TC;
+            const int64_t r = r0 + rr, c = c0 + cc;
+            v[q] = (r < rows && c < cols) ? __ldcs(src + r * ld_src + c) : 0.0f;
+        }
+#pragma unroll
+        for (int q = 0; q < NL; ++q) {
+            const int i = t + q * 256;
+            tile[i / TC][i % TC] = v[q];
+        }
+    }
+}
+
 template <int DT>
 __global__ void __launch_bounds__(256) k_quantize_transpose(int64_t rows, int64_t cols, const float* __restrict__ src,
                                                             int64_t ld_src, typename Narrow<DT>::T* __restrict__ dst,
-                                                            int64_t ld_dst, const float* scale_word, int aligned) {
+                                                            int64_t ld_dst, const float* scale_word, int aligned,
+                                                            int vec4) {
     using T = typename Narrow<DT>::T;
     constexpr int TR = 64;
     constexpr int PER = 16 / sizeof(T);          // source rows per output chunk
@@ -164,21 +218,8 @@ __global__ void __launch_bounds__(256) k_quantize_transpose(int64_t rows, int64_
     const float s = (DT == kDtE4M3) ? e4m3_scale_from_amax_word(scale_word) : 1.0f;
     const int64_t r0 = (int64_t)blockIdx.y * TR, c0 = (int64_t)blockIdx.x * TC;
     const int t = threadIdx.x;
-    // load: TR x TC floats, coalesced along the source row; all loads issued before any is used
-    constexpr int NL = TR * TC / 256;
-    float v[NL];
-#pragma unroll
-    for (int q = 0; q < NL; ++q) {
-        const int i = t + q * 256;
-        const int rr = i / TC, cc = i - rr * TC;
-        const int64_t r = r0 + rr, c = c0 + cc;
-        v[q] = (r < rows && c < cols) ? __ldcs(src + r * ld_src + c) : 0.0f;
-    }
-#pragma unroll
-    for (int q = 0; q < NL; ++q) {
-        const int i = t + q * 256;
-        tile[i / TC][i % TC] = v[q];
-    }
+    // load: TR x TC floats, coalesced along the source row
+    load_tile_t<TR, TC>(tile, src, rows, cols, ld_src, r0, c0, vec4);
     __syncthreads();
     const int cc = t / (TR / PER);               // destination row within the tile
     const int j = t - cc * (TR / PER);           // chunk within the destination row
@@ -302,26 +343,14 @@ __global__ void __launch_bounds__(256) k_split_scalar(int64_t rows, int64_t cols
 
 template <int PIECE, int SCHEME>
 __global__ void __launch_bounds__(256) k_split_transpose(int64_t rows, int64_t cols, const float* __restrict__ src,
-                                                         int64_t ld_src, SplitOut out, int64_t ld_dst, int aligned) {
+                                                         int64_t ld_src, SplitOut out, int64_t ld_dst, int aligned,
+                                                         int vec4) {
     constexpr int NP = pieces_of<SCHEME>();
     constexpr int TR = 64, PER = 8, TC = 32;
     __shared__ float tile[TR][TC + 1];
     const int64_t r0 = (int64_t)blockIdx.y * TR, c0 = (int64_t)blockIdx.x * TC;
     const int t = threadIdx.x;
-    constexpr int NL = TR * TC / 256;
-    float v[NL];
-#pragma unroll
-    for (int q = 0; q < NL; ++q) {
-        const int i = t + q * 256;
-        const int rr = i / TC, cc = i - rr * TC;
-        const int64_t r = r0 + rr, c = c0 + cc;
-        v[q] = (r < rows && c < cols) ? __ldcs(src + r * ld_src + c) : 0.0f;
-    }
-#pragma unroll
-    for (int q = 0; q < NL; ++q) {
-        const int i = t + q * 256;
-        tile[i / TC][i % TC] = v[q];
-    }
+    load_tile_t<TR, TC>(tile, src, rows, cols, ld_src, r0, c0, vec4);
     __syncthreads();
     const int cc = t / (TR / PER);
     const int j = t - cc * (TR / PER);
@@ -443,7 +472,8 @@ cudaError_t quantize_dt(int64_t rows, int64_t cols, const float* src, int64_t ld
         constexpr int TC = 256 * (16 / sizeof(T)) / 64;
         dim3 grid(static_cast<unsigned>((cols + TC - 1) / TC), static_cast<unsigned>((rows + 63) / 64));
         const int al = ((ld_dst * sizeof(T)) % 16 == 0) && aligned16(dst);
-        k_quantize_transpose<DT><<<grid, 256, 0, st>>>(rows, cols, src, ld_src, d, ld_dst, scale, al);
+        const int v4 = (ld_src % 4 == 0) && aligned16(src);
+        k_quantize_transpose<DT><<<grid, 256, 0, st>>>(rows, cols, src, ld_src, d, ld_dst, scale, al, v4);
     } else {
         const bool vec = (cols % 8 == 0) && (ld_src % 4 == 0) && ((ld_dst * sizeof(T)) % (8 * sizeof(T)) == 0) &&
                          aligned16(src) && ((reinterpret_cast<uintptr_t>(dst) % (8 * sizeof(T))) == 0);
@@ -471,7 +501,8 @@ cudaError_t split_piece(int64_t rows, int64_t cols, const float* src, int64_t ld
     if (transpose) {
         dim3 grid(static_cast<unsigned>((cols + 31) / 32), static_cast<unsigned>((rows + 63) / 64));
         const int al = (ld_dst % 8 == 0) && all_aligned;
-        k_split_transpose<PIECE, SCHEME><<<grid, 256, 0, st>>>(rows, cols, src, ld_src, out, ld_dst, al);
+        const int v4 = (ld_src % 4 == 0) && aligned16(src);
+        k_split_transpose<PIECE, SCHEME><<<grid, 256, 0, st>>>(rows, cols, src, ld_src, out, ld_dst, al, v4);
     } else {
         const bool vec = (cols % 8 == 0) && (ld_src % 4 == 0) && (ld_dst % 8 == 0) && aligned16(src) && all_aligned;
         if (vec)
