@@ -416,6 +416,44 @@ def measure_rows(b, A, B, pk, sm_count):
         ms = _time_ms(g, 2, warm=1)
         res["sgemm_fp32_cuda_cores"] = {"ms": ms, "tflops": flops / (ms * 1e-3) / 1e12,
                                         "error_vs_fp64": _sampled_errors(C, As, Bs, srows)}
+        # the same split-3 products one after another, the pieces of product i+1 formed on a second
+        # stream (CUDA cores) while the refined GEMM of product i runs (tensor cores), two workspaces
+        s3 = b.gemm_split_workspace_bytes(0, 3, N, N, N)
+        ws2 = [ws[:s3], torch.empty(s3, dtype=torch.uint8, device="cuda")]
+        main, side = torch.cuda.current_stream(), torch.cuda.Stream()
+        ready = [torch.cuda.Event() for _ in range(2)]
+        free = [torch.cuda.Event() for _ in range(2)]
+
+        def pipelined(steps):
+            side.wait_stream(main)
+            b.gemm_split_prepare(0, 0, 3, N, N, N, Ad, N, 0, Bd, N, 0, ws2[0], s3, stream=side)
+            ready[0].record(side)
+            for i in range(steps):
+                j = (i + 1) % 2
+                if i >= 1:
+                    side.wait_event(free[j])
+                b.gemm_split_prepare(0, 0, 3, N, N, N, Ad, N, 0, Bd, N, 0, ws2[j], s3, stream=side)
+                ready[j].record(side)
+                main.wait_event(ready[i % 2])
+                b.gemm_split_run(0, 0, 3, N, N, N, 1.0, 0.0, C, N, ws2[i % 2], s3, stream=main)
+                free[i % 2].record(main)
+            main.wait_stream(side)
+
+        pipelined(3)
+        torch.cuda.synchronize()
+        steps = 10
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pipelined(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_p = e0.elapsed_time(e1) / steps
+        res["split3_f16_pipelined"] = {"ms_per_product": ms_p, "effective_tflops": flops / (ms_p * 1e-3) / 1e12,
+                                       "vs_one_call": res["split3_f16"]["ms"] / ms_p,
+                                       "note": "gemm_split_prepare of product i+1 on a second stream beside "
+                                               "gemm_split_run of product i (Sec. VIII's concurrent CUDA cores and "
+                                               "tensor cores)"}
+        del ws2
         e3 = res["split3_f16"]["error_vs_fp64"]["normwise"]
         es = res["sgemm_fp32_cuda_cores"]["error_vs_fp64"]["normwise"]
         res["split3_vs_sgemm"] = {"speedup": res["sgemm_fp32_cuda_cores"]["ms"] / res["split3_f16"]["ms"],

@@ -214,6 +214,30 @@ tc_status gemm_split_bf16x3(int64_t m, int64_t n, int64_t k, float alpha,
                             float beta, float* C, int64_t ldc,
                             void* workspace, size_t workspace_bytes, void* stream);
 
+/* The two halves of gemm_split, gemm_split_scaled and gemm_split_bf16x3, so that
+ * the HBM-bound forming of the next product's pieces (CUDA cores) can run on a
+ * second stream while the tensor cores run the current refined GEMM: the
+ * concurrent CUDA-core / tensor-core use of streams that Sec. VIII proposes.
+ *   scheme: 0 = gemm_split (nprod 2, 3 or 4), 1 = gemm_split_scaled (nprod 2
+ *   or 3), 2 = gemm_split_bf16x3 (piece TC_BF16, nprod 6).
+ *   gemm_split_prepare forms the pieces of A and B (arguments as gemm_split)
+ *   in `workspace`: device memory of gemm_split_workspace_bytes(piece, nprod,
+ *   m, n, k) bytes, 256-byte aligned, owned by the caller; NULL is refused.
+ *   gemm_split_run computes C = alpha * (the scheme's products) + beta * C
+ *   from the pieces a gemm_split_prepare with the same scheme, piece, nprod,
+ *   m, n and k left in `workspace`.
+ * prepare then run on one stream is the one-call entry point, bit for bit.
+ * Ordering across streams is the caller's: a run must start after its prepare
+ * has finished, and a workspace may be prepared again only after the run that
+ * reads it has finished (cudaEventRecord / cudaStreamWaitEvent). */
+tc_status gemm_split_prepare(int32_t scheme, int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k,
+                             const float* A, int64_t lda, int32_t la,
+                             const float* B, int64_t ldb, int32_t lb,
+                             void* workspace, size_t workspace_bytes, void* stream);
+tc_status gemm_split_run(int32_t scheme, int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k,
+                         float alpha, float beta, float* C, int64_t ldc,
+                         const void* workspace, size_t workspace_bytes, void* stream);
+
 /* FP32 GEMM on the CUDA cores (no tensor cores): the paper's sgemm
  * comparison (Sec. VII-A, VII-B).  Any layouts; C row-major. */
 tc_status gemm_sgemm(int64_t m, int64_t n, int64_t k, float alpha,

@@ -91,6 +91,9 @@ SIGNATURES = {
                                  _i64, _vp, _sz, _vp]),
     "gemm_split_bf16x3": (_i32, [_i64, _i64, _i64, _f32, _vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp, _i64, _vp,
                                  _sz, _vp]),
+    "gemm_split_prepare": (_i32, [_i32, _i32, _i32, _i64, _i64, _i64, _vp, _i64, _i32, _vp, _i64, _i32, _vp, _sz,
+                                  _vp]),
+    "gemm_split_run": (_i32, [_i32, _i32, _i32, _i64, _i64, _i64, _f32, _f32, _vp, _i64, _vp, _sz, _vp]),
     "gemm_split": (_i32, [_i32, _i32, _i64, _i64, _i64, _f32, _vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp, _i64,
                           _vp, _sz, _vp]),
     "gemm_sgemm": (_i32, [_i64, _i64, _i64, _f32, _vp, _i64, _i32, _vp, _i64, _i32, _f32, _vp, _i64, _vp]),
@@ -268,6 +271,20 @@ def gemm_split_bf16x3(m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ldc, work
     return _check(load().gemm_split_bf16x3(m, n, k, alpha, _ptr(A), lda, la, _ptr(B), ldb, lb, beta, _ptr(C), ldc,
                                            _ptr(workspace), int(workspace_bytes), _stream(stream)),
                   "gemm_split_bf16x3")
+
+
+def gemm_split_prepare(scheme, piece, nprod, m, n, k, A, lda, la, B, ldb, lb, workspace, workspace_bytes,
+                       stream=None):
+    """The pieces phase of a refined GEMM (scheme 0 gemm_split, 1 scaled, 2 BF16x3) into `workspace`."""
+    return _check(load().gemm_split_prepare(scheme, piece, nprod, m, n, k, _ptr(A), lda, la, _ptr(B), ldb, lb,
+                                            _ptr(workspace), int(workspace_bytes), _stream(stream)),
+                  "gemm_split_prepare")
+
+
+def gemm_split_run(scheme, piece, nprod, m, n, k, alpha, beta, C, ldc, workspace, workspace_bytes, stream=None):
+    """The tensor-core phase of a refined GEMM, on the pieces gemm_split_prepare left in `workspace`."""
+    return _check(load().gemm_split_run(scheme, piece, nprod, m, n, k, alpha, beta, _ptr(C), ldc, _ptr(workspace),
+                                        int(workspace_bytes), _stream(stream)), "gemm_split_run")
 
 
 def gemm_sgemm(m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ldc, stream=None):

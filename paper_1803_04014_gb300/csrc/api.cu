@@ -399,27 +399,38 @@ size_t gemm_split_workspace_bytes(int32_t piece, int32_t nprod, int64_t m, int64
 
 namespace {
 
+// Phases of a refined GEMM: forming the pieces, the tensor-core GEMM on them, or both.
+constexpr int kSplitPhasePieces = 1, kSplitPhaseGemm = 2, kSplitPhaseBoth = 3;
+
 // Refined GEMM of every scheme: form the pieces of A and B (K-major) in the
 // workspace with one HBM-bound pass each, then one tcgen05 launch.
 //   scheme 0: Eq. 1 / Eq. 2, nprod 2-4;  1: scaled residuals, nprod 2-3;
 //   scheme 2: three BF16 pieces, nprod 6.
+// phases selects the pass(es); a single phase needs the caller's workspace, and
+// the GEMM phase reads pieces that an earlier pieces phase left there.
 tc_status split_gemm(const char* name, int scheme, int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k,
                      float alpha, const float* A, int64_t lda, int32_t la, const float* B, int64_t ldb, int32_t lb,
-                     float beta, float* C, int64_t ldc, void* workspace, size_t workspace_bytes, void* stream) {
+                     float beta, float* C, int64_t ldc, void* workspace, size_t workspace_bytes, void* stream,
+                     int phases = kSplitPhaseBoth) {
     if (piece != TC_F16 && piece != TC_BF16) return fail(TC_ERR_INVALID, "%s: piece must be F16 or BF16", name);
     tc_status s = check_dims(m, n, k);
     if (s != TC_OK) return s;
-    if ((la != TC_ROW_MAJOR && la != TC_COL_MAJOR) || (lb != TC_ROW_MAJOR && lb != TC_COL_MAJOR))
+    const bool do_pieces = (phases & kSplitPhasePieces) != 0, do_gemm = (phases & kSplitPhaseGemm) != 0;
+    if (do_pieces && ((la != TC_ROW_MAJOR && la != TC_COL_MAJOR) || (lb != TC_ROW_MAJOR && lb != TC_COL_MAJOR)))
         return fail(TC_ERR_INVALID, "%s: bad layout", name);
+    if (phases != kSplitPhaseBoth && !workspace)
+        return fail(TC_ERR_INVALID, "%s: the pieces live in the caller's workspace: it may not be NULL", name);
     if (m == 0 || n == 0) return TC_OK;
-    if (!C || ldc < n || !aligned(C, 4)) return fail(TC_ERR_INVALID, "%s: bad C / ldc", name);
+    if (do_gemm && (!C || ldc < n || !aligned(C, 4))) return fail(TC_ERR_INVALID, "%s: bad C / ldc", name);
     Device* d;
     if ((s = get_device(&d)) != TC_OK) return s;
     cudaStream_t st = as_stream(stream);
-    if (k == 0) return enqueue(tcg::launch_scale_c(m, n, beta, C, ldc, st), name);
-    if (!A || !B || !aligned(A, 4) || !aligned(B, 4)) return fail(TC_ERR_INVALID, "%s: bad operand pointer", name);
-    if (lda < (la == TC_ROW_MAJOR ? k : m) || ldb < (lb == TC_ROW_MAJOR ? n : k))
-        return fail(TC_ERR_INVALID, "%s: leading dimension too small", name);
+    if (k == 0) return do_gemm ? enqueue(tcg::launch_scale_c(m, n, beta, C, ldc, st), name) : TC_OK;
+    if (do_pieces) {
+        if (!A || !B || !aligned(A, 4) || !aligned(B, 4)) return fail(TC_ERR_INVALID, "%s: bad operand pointer", name);
+        if (lda < (la == TC_ROW_MAJOR ? k : m) || ldb < (lb == TC_ROW_MAJOR ? n : k))
+            return fail(TC_ERR_INVALID, "%s: leading dimension too small", name);
+    }
     const size_t need = gemm_split_workspace_bytes(piece, nprod, m, n, k);
     if (workspace && workspace_bytes < need)
         return fail(TC_ERR_INVALID, "%s: workspace of %zu bytes, need %zu", name, workspace_bytes, need);
@@ -442,14 +453,17 @@ tc_status split_gemm(const char* name, int scheme, int32_t piece, int32_t nprod,
     }
     tc_status out = TC_OK;
     do {
-        // A pieces as m x k (K-major): row-major A directly, column-major A (k x m in memory) transposed
-        e = (la == TC_ROW_MAJOR) ? tcg::launch_split(scheme, piece, m, k, A, lda, false, pa, kp, st)
-                                 : tcg::launch_split(scheme, piece, k, m, A, lda, true, pa, kp, st);
-        if (e != cudaSuccess) { out = cuda_fail(e, "split of A"); break; }
-        // B pieces as n x k (K-major): row-major B (k x n) transposed, column-major B directly
-        e = (lb == TC_ROW_MAJOR) ? tcg::launch_split(scheme, piece, k, n, B, ldb, true, pb, kp, st)
-                                 : tcg::launch_split(scheme, piece, n, k, B, ldb, false, pb, kp, st);
-        if (e != cudaSuccess) { out = cuda_fail(e, "split of B"); break; }
+        if (do_pieces) {
+            // A pieces as m x k (K-major): row-major A directly, column-major A (k x m in memory) transposed
+            e = (la == TC_ROW_MAJOR) ? tcg::launch_split(scheme, piece, m, k, A, lda, false, pa, kp, st)
+                                     : tcg::launch_split(scheme, piece, k, m, A, lda, true, pa, kp, st);
+            if (e != cudaSuccess) { out = cuda_fail(e, "split of A"); break; }
+            // B pieces as n x k (K-major): row-major B (k x n) transposed, column-major B directly
+            e = (lb == TC_ROW_MAJOR) ? tcg::launch_split(scheme, piece, k, n, B, ldb, true, pb, kp, st)
+                                     : tcg::launch_split(scheme, piece, n, k, B, ldb, false, pb, kp, st);
+            if (e != cudaSuccess) { out = cuda_fail(e, "split of B"); break; }
+        }
+        if (!do_gemm) break;
         const CUtensorMapDataType tdt = piece == TC_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
         tcg::TcGemmLaunch p{};
         p.kind = 0;
@@ -511,6 +525,44 @@ tc_status gemm_split_bf16x3(int64_t m, int64_t n, int64_t k, float alpha, const 
                             void* workspace, size_t workspace_bytes, void* stream) {
     return split_gemm("gemm_split_bf16x3", 2, TC_BF16, 6, m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ldc,
                       workspace, workspace_bytes, stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+// The scheme, piece and product count of a two-phase refined GEMM, checked as the one-call
+// entry points check them.
+tc_status split_scheme_ok(const char* name, int32_t scheme, int32_t piece, int32_t nprod) {
+    if (scheme == 0 && (nprod < 2 || nprod > 4)) return fail(TC_ERR_INVALID, "%s: scheme 0 takes nprod 2, 3 or 4", name);
+    if (scheme == 1 && nprod != 2 && nprod != 3) return fail(TC_ERR_INVALID, "%s: scheme 1 takes nprod 2 or 3", name);
+    if (scheme == 2 && (piece != TC_BF16 || nprod != 6))
+        return fail(TC_ERR_INVALID, "%s: scheme 2 takes BF16 pieces and nprod 6", name);
+    if (scheme < 0 || scheme > 2) return fail(TC_ERR_INVALID, "%s: scheme must be 0, 1 or 2", name);
+    return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tc_status gemm_split_prepare(int32_t scheme, int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k,
+                             const float* A, int64_t lda, int32_t la, const float* B, int64_t ldb, int32_t lb,
+                             void* workspace, size_t workspace_bytes, void* stream) {
+    tc_status s = split_scheme_ok("gemm_split_prepare", scheme, piece, nprod);
+    if (s != TC_OK) return s;
+    return split_gemm("gemm_split_prepare", scheme, piece, nprod, m, n, k, 1.0f, A, lda, la, B, ldb, lb, 0.0f, nullptr,
+                      0, workspace, workspace_bytes, stream, kSplitPhasePieces);
+}
+
+tc_status gemm_split_run(int32_t scheme, int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k, float alpha,
+                         float beta, float* C, int64_t ldc, const void* workspace, size_t workspace_bytes,
+                         void* stream) {
+    tc_status s = split_scheme_ok("gemm_split_run", scheme, piece, nprod);
+    if (s != TC_OK) return s;
+    return split_gemm("gemm_split_run", scheme, piece, nprod, m, n, k, alpha, nullptr, 0, TC_ROW_MAJOR, nullptr, 0,
+                      TC_ROW_MAJOR, beta, C, ldc, const_cast<void*>(workspace), workspace_bytes, stream,
+                      kSplitPhaseGemm);
 }
 
 tc_status gemm_sgemm(int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda, int32_t la,

@@ -83,6 +83,12 @@ def test_host_validation_without_gpu(lib):
                                None),
         lambda: lib.gemm_split(2, 3, 8, 8, 8, 1.0, None, 8, 0, None, 8, 0, 0.0, None, 8, None, 0, None),
         lambda: lib.gemm_split(0, 5, 8, 8, 8, 1.0, None, 8, 0, None, 8, 0, 0.0, None, 8, None, 0, None),
+        # the two-phase refinement: a workspace is required, schemes and product counts are checked
+        lambda: lib.gemm_split_prepare(0, 0, 3, 8, 8, 8, None, 8, 0, None, 8, 0, None, 0, None),
+        lambda: lib.gemm_split_run(0, 0, 3, 8, 8, 8, 1.0, 0.0, None, 8, None, 0, None),
+        lambda: lib.gemm_split_run(2, 0, 6, 8, 8, 8, 1.0, 0.0, None, 8, None, 0, None),
+        lambda: lib.gemm_split_run(7, 0, 3, 8, 8, 8, 1.0, 0.0, None, 8, None, 0, None),
+        lambda: lib.gemm_split_prepare(1, 0, 4, 8, 8, 8, None, 8, 0, None, 8, 0, None, 0, None),
         lambda: lib.tc_quantize(9, 4, 4, None, 4, None, 4, 0, None, None),
         lambda: lib.tc_quantize(2, 4, 4, None, 4, None, 4, 0, None, None),   # E4M3 without a scale word
         lambda: lib.tc_split(2, 4, 4, None, 4, 0, None, None, 4, None),

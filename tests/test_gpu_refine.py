@@ -209,3 +209,75 @@ def test_bf16x3_keeps_fp32_accuracy_over_a_wide_range(b):
     e_fp32 = og.normwise_error(host(C), truth, A, B)
     assert e_x3 <= 2.0 * e_fp32, (e_x3, e_fp32)
     assert e_two > 10.0 * e_x3, (e_two, e_x3)
+
+
+# ------------------------------------------------------------------ two-phase refinement (pieces, then GEMM)
+
+_ONE_CALL = {0: "gemm_split", 1: "gemm_split_scaled", 2: "gemm_split_bf16x3"}
+
+
+def _one_call(b, scheme, piece, nprod, m, n, k, alpha, A, la, B, lb, beta, C):
+    lda = k if la == 0 else m
+    ldb = n if lb == 0 else k
+    if scheme == 2:
+        b.gemm_split_bf16x3(m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, n)
+    else:
+        getattr(b, _ONE_CALL[scheme])(piece, nprod, m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, n)
+
+
+@pytest.mark.parametrize("scheme,piece,nprod", [(0, 0, 2), (0, 0, 3), (0, 1, 4), (1, 0, 3), (1, 1, 2), (2, 1, 6)])
+@pytest.mark.parametrize("la,lb", [(0, 0), (1, 1)])
+def test_prepare_then_run_is_the_one_call_bit_for_bit(b, scheme, piece, nprod, la, lb):
+    m, n, k = 300, 264, 520
+    A = _bits_matrix((m, k) if la == 0 else (k, m), seed=701, e_lo=-6, e_hi=6)
+    B = _bits_matrix((k, n) if lb == 0 else (n, k), seed=711, e_lo=-6, e_hi=6)
+    C0 = synth.uniform((m, n), seed=721)
+    Ad, Bd = dev(A), dev(B)
+    want = dev(C0)
+    _one_call(b, scheme, piece, nprod, m, n, k, 1.25, Ad, la, Bd, lb, -0.5, want)
+    need = b.gemm_split_workspace_bytes(piece, nprod, m, n, k)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    got = dev(C0)
+    b.gemm_split_prepare(scheme, piece, nprod, m, n, k, Ad, k if la == 0 else m, la, Bd, n if lb == 0 else k, lb,
+                         ws, need)
+    b.gemm_split_run(scheme, piece, nprod, m, n, k, 1.25, -0.5, got, n, ws, need)
+    b.tc_sync_status()
+    assert torch.equal(got, want)
+
+
+def test_pipelined_prepare_and_run_on_two_streams(b):
+    # the pieces of product i+1 formed on a side stream while product i runs on the main stream,
+    # with two workspaces and events between the streams: every result as the one-call GEMM's
+    m, n, k = 512, 384, 640
+    count = 4
+    ins = [(dev(_bits_matrix((m, k), seed=800 + 2 * i, e_lo=-4, e_hi=4)),
+            dev(_bits_matrix((k, n), seed=801 + 2 * i, e_lo=-4, e_hi=4))) for i in range(count)]
+    want = []
+    for A, B in ins:
+        C = torch.zeros((m, n), dtype=torch.float32, device="cuda")
+        b.gemm_split(0, 3, m, n, k, 1.0, A, k, 0, B, n, 0, 0.0, C, n)
+        want.append(C)
+    need = b.gemm_split_workspace_bytes(0, 3, m, n, k)
+    ws = [torch.empty(need, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    main, side = torch.cuda.current_stream(), torch.cuda.Stream()
+    ready = [torch.cuda.Event() for _ in range(2)]
+    free = [torch.cuda.Event() for _ in range(2)]
+    got = [torch.zeros((m, n), dtype=torch.float32, device="cuda") for _ in range(count)]
+    side.wait_stream(main)
+    b.gemm_split_prepare(0, 0, 3, m, n, k, ins[0][0], k, 0, ins[0][1], n, 0, ws[0], need, stream=side)
+    ready[0].record(side)
+    for i in range(count):
+        if i + 1 < count:
+            j = (i + 1) % 2
+            if i >= 1:
+                side.wait_event(free[j])
+            b.gemm_split_prepare(0, 0, 3, m, n, k, ins[i + 1][0], k, 0, ins[i + 1][1], n, 0, ws[j], need,
+                                 stream=side)
+            ready[j].record(side)
+        main.wait_event(ready[i % 2])
+        b.gemm_split_run(0, 0, 3, m, n, k, 1.0, 0.0, got[i], n, ws[i % 2], need, stream=main)
+        free[i % 2].record(main)
+    torch.cuda.synchronize()
+    b.tc_sync_status()
+    for i in range(count):
+        assert torch.equal(got[i], want[i]), i
