@@ -68,13 +68,15 @@ __device__ __forceinline__ void for_each_mine(int64_t rows, int64_t cols, F&& f)
 
 // GB300 runs FP64 arithmetic at about 1/64 of the FP32 rate, so this kernel
 // is bound by its FP64 instructions before HBM.  Two changes keep the results
-// bit-identical while halving that count: FP32 -> FP64 conversion of normal
+// bit-identical while halving that count (the sums of squares of A and B then
+// move to the FP32 pipe, above, which changes their last bits, not their
+// accuracy): FP32 -> FP64 conversion of normal
 // values by integer bit assembly (IEEE 754 binary32 -> binary64: same sign,
 // exponent rebiased by 1023 - 127, significand shifted up by 29 bits), and
 // the running max of |d| compared as integer bit patterns (the order of
 // non-negative IEEE values is the order of their patterns).  What remains on
 // the FP64 unit is one subtraction and one fused multiply-add per element of
-// C and one fused multiply-add per element of A and B.
+// C, and two additions per 8 elements of A and of B.
 __device__ __forceinline__ double to_f64(float x) {
     const uint32_t u = __float_as_uint(x);
     const uint32_t e = (u >> 23) & 0xFFu;
@@ -90,6 +92,33 @@ __device__ __forceinline__ void acc_diff(double d, double& s, unsigned long long
     s = fma(d, d, s);
     const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(d)) & 0x7FFFFFFFFFFFFFFFull;
     mx_bits = a > mx_bits ? a : mx_bits;
+}
+
+// Sums of squares of FP32 values on the FP32 pipe.  Each square a*a is split
+// exactly into p = RN(a*a) and e = a*a - p (a fused multiply-add), and the
+// p are added with Knuth's error-free two-sum into (hi, lo): hi collects the
+// rounded sums, lo their exact rounding errors and the e terms.  A group of
+// 8 values costs two FP64 additions when it is merged into the FP64 sum,
+// instead of 8 FP64 fused multiply-adds.  The group's only roundings are
+// those of lo (|lo| <= 16 * 2^-24 of the group's sum), below 2^-40 of it in
+// all.  Exactness needs every square and partial sum inside FP32's normal
+// range: 2^-50 <= |a| < 2^60 (or a = 0); any other value (subnormal, huge,
+// infinite, NaN) sends its group of 4 to the FP64 path.  The intrinsics keep
+// the compiler from fusing the steps, which would break the two-sum.
+__device__ __forceinline__ bool square_fits_f32(float a) {
+    const uint32_t u = __float_as_uint(a);
+    const uint32_t eb = (u >> 23) & 0xFFu;
+    return (u & 0x7FFFFFFFu) == 0u || (eb >= 127u - 50u && eb <= 127u + 59u);
+}
+
+__device__ __forceinline__ void add_square_ff(float a, float& hi, float& lo) {
+    const float p = __fmul_rn(a, a);
+    const float e = __fmaf_rn(a, a, -p);              // a*a - p, exact
+    const float s = __fadd_rn(hi, p);
+    const float bv = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv));   // hi + p - s, exact
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
 }
 
 // partial layout: [3][kErrBlocks][2] = (sum, max) for (C - ref), A, B.
@@ -154,17 +183,35 @@ __global__ void __launch_bounds__(kErrThreads) k_err_partials(int64_t m, int64_t
             const float* X = mats[w];
             const int64_t ld = lds[w];
             if (vec) {
+                float hi = 0.0f, lo = 0.0f;   // float-float sum of the current group
+                int in_group = 0;             // groups of 4 values in it
                 for_each_mine<4>(rows[w], cols[w], [&](int64_t r, int64_t c) {
                     const float4 x = __ldcs(reinterpret_cast<const float4*>(X + r * ld + c));
-                    double v = to_f64(x.x);
-                    t = fma(v, v, t);
-                    v = to_f64(x.y);
-                    t = fma(v, v, t);
-                    v = to_f64(x.z);
-                    t = fma(v, v, t);
-                    v = to_f64(x.w);
-                    t = fma(v, v, t);
+                    if (square_fits_f32(x.x) && square_fits_f32(x.y) && square_fits_f32(x.z) &&
+                        square_fits_f32(x.w)) {
+                        add_square_ff(x.x, hi, lo);
+                        add_square_ff(x.y, hi, lo);
+                        add_square_ff(x.z, hi, lo);
+                        add_square_ff(x.w, hi, lo);
+                        if (++in_group == 2) {   // 8 values: merge into the FP64 sum
+                            t += to_f64(hi);
+                            t += to_f64(lo);
+                            hi = lo = 0.0f;
+                            in_group = 0;
+                        }
+                    } else {
+                        double v = to_f64(x.x);
+                        t = fma(v, v, t);
+                        v = to_f64(x.y);
+                        t = fma(v, v, t);
+                        v = to_f64(x.z);
+                        t = fma(v, v, t);
+                        v = to_f64(x.w);
+                        t = fma(v, v, t);
+                    }
                 });
+                t += to_f64(hi);
+                t += to_f64(lo);
             } else {
                 for_each_mine<1>(rows[w], cols[w], [&](int64_t r, int64_t c) {
                     const double x = to_f64(X[r * ld + c]);
