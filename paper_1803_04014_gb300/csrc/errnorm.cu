@@ -75,8 +75,9 @@ __device__ __forceinline__ void for_each_mine(int64_t rows, int64_t cols, F&& f)
 // exponent rebiased by 1023 - 127, significand shifted up by 29 bits), and
 // the running max of |d| compared as integer bit patterns (the order of
 // non-negative IEEE values is the order of their patterns).  What remains on
-// the FP64 unit is one subtraction and one fused multiply-add per element of
-// C, and two additions per 8 elements of A and of B.
+// the FP64 unit is one subtraction per element of C plus two additions per 4
+// elements (their squares on the FP32 pipe, below), and two additions per 8
+// elements of A and of B.
 __device__ __forceinline__ double to_f64(float x) {
     const uint32_t u = __float_as_uint(x);
     const uint32_t e = (u >> 23) & 0xFFu;
@@ -121,6 +122,52 @@ __device__ __forceinline__ void add_square_ff(float a, float& hi, float& lo) {
     lo = __fadd_rn(lo, __fadd_rn(err, e));
 }
 
+// The square of a difference d = c - c64 (an FP64 value) on the FP32 pipe: d
+// splits exactly into hi, its leading 24 significand bits (an FP32 value
+// made by integer bit assembly), and the remaining 29 bits, rounded once to
+// FP32 as lo (|lo| < 2^-23 |hi|, error below 2^-47 |d|).  hi*hi goes into
+// the float-float sum exactly (add_square_ff) and 2*hi*lo is added to its
+// low part; lo*lo (below 2^-46 d^2) is dropped.  Needs 2^-50 <= |d| < 2^60;
+// false (nothing added) for any other d, which the caller sums in FP64.
+__device__ __forceinline__ bool add_diff_square_ff(double d, float& hi_sum, float& lo_sum) {
+    const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(d)) & 0x7FFFFFFFFFFFFFFFull;
+    const uint32_t eb = static_cast<uint32_t>(bits >> 52);
+    if (eb < 1023u - 50u || eb > 1023u + 59u) return false;
+    const uint32_t fe = eb - 1023u + 127u;                                    // FP32 biased exponent of hi
+    const float hi = __uint_as_float((fe << 23) | static_cast<uint32_t>((bits >> 29) & 0x7FFFFFu));
+    const float scale = __uint_as_float((eb - 1075u + 127u) << 23);          // 2^(exponent of d - 52), normal
+    const float lo = __fmul_rn(__uint2float_rn(static_cast<uint32_t>(bits & 0x1FFFFFFFull)), scale);
+    add_square_ff(hi, hi_sum, lo_sum);
+    lo_sum = __fadd_rn(lo_sum, __fmul_rn(__fadd_rn(hi, hi), lo));
+    return true;
+}
+
+// Four differences of C against its reference: the max norm on bit patterns, and
+// their squares through the float-float path when all four allow it (two FP64
+// additions for the four), else in FP64.
+__device__ __forceinline__ void acc_diff4(double d0, double d1, double d2, double d3, double& s,
+                                          unsigned long long& mx_bits) {
+    const double d[4] = {d0, d1, d2, d3};
+    bool fits = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const unsigned long long a = static_cast<unsigned long long>(__double_as_longlong(d[i])) & 0x7FFFFFFFFFFFFFFFull;
+        mx_bits = a > mx_bits ? a : mx_bits;
+        const uint32_t eb = static_cast<uint32_t>(a >> 52);
+        fits = fits && (a == 0ull || (eb >= 1023u - 50u && eb <= 1023u + 59u));
+    }
+    if (fits) {
+        float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) add_diff_square_ff(d[i], hi, lo);   // zeros add nothing
+        s += to_f64(hi);
+        s += to_f64(lo);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) s = fma(d[i], d[i], s);
+    }
+}
+
 // partial layout: [3][kErrBlocks][2] = (sum, max) for (C - ref), A, B.
 // vec: every row of C, ref, A and B starts on a 16-byte boundary and n, the
 // column counts of A and B are multiples of 4 (4-wide loads); else scalar.
@@ -140,20 +187,15 @@ __global__ void __launch_bounds__(kErrThreads) k_err_partials(int64_t m, int64_t
                 const float4 x = __ldcs(reinterpret_cast<const float4*>(C + r * ldc + c));
                 const double2 y0 = __ldcs(reinterpret_cast<const double2*>(R + r * ldr + c));
                 const double2 y1 = __ldcs(reinterpret_cast<const double2*>(R + r * ldr + c + 2));
-                acc_diff(to_f64(x.x) - y0.x, s, mx);
-                acc_diff(to_f64(x.y) - y0.y, s, mx);
-                acc_diff(to_f64(x.z) - y1.x, s, mx);
-                acc_diff(to_f64(x.w) - y1.y, s, mx);
+                acc_diff4(to_f64(x.x) - y0.x, to_f64(x.y) - y0.y, to_f64(x.z) - y1.x, to_f64(x.w) - y1.y, s, mx);
             });
         } else {
             const float* R = static_cast<const float*>(ref);
             for_each_mine<4>(m, n, [&](int64_t r, int64_t c) {
                 const float4 x = __ldcs(reinterpret_cast<const float4*>(C + r * ldc + c));
                 const float4 y = __ldcs(reinterpret_cast<const float4*>(R + r * ldr + c));
-                acc_diff(to_f64(x.x) - to_f64(y.x), s, mx);
-                acc_diff(to_f64(x.y) - to_f64(y.y), s, mx);
-                acc_diff(to_f64(x.z) - to_f64(y.z), s, mx);
-                acc_diff(to_f64(x.w) - to_f64(y.w), s, mx);
+                acc_diff4(to_f64(x.x) - to_f64(y.x), to_f64(x.y) - to_f64(y.y), to_f64(x.z) - to_f64(y.z),
+                          to_f64(x.w) - to_f64(y.w), s, mx);
             });
         }
     } else if (ref_f64) {
