@@ -148,7 +148,8 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--rows", choices=["all", "none"], default="all", help="also measure the other rows (N=1 only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--profile-gemm", choices=["f16", "bf16", "e4m3", "split3", "split3_scaled", "bf16x3", "grouped",
+    p.add_argument("--profile-gemm", choices=["f16", "bf16", "e4m3", "split3", "split3_scaled", "bf16x3",
+                                              "split3_one_launch", "split3_scaled_one_launch", "grouped",
                                               "grouped_rowmajor", "batched16", "batched16_250k", "quantize",
                                               "errnorm"], default=None,
                    help="only run 5 launches of one kernel on one case, nothing timed (cases for ncu captures)")
@@ -396,15 +397,28 @@ def measure_rows(b, A, B, pk, sm_count):
                          "frac_of_peak_effective": tf / peak,
                          "error_vs_fp64": _sampled_errors(C, As, Bs, srows)}
 
-        for nprod in (2, 3, 4):
-            one(f"split{nprod}_f16", nprod,
-                lambda: b.gemm_split(0, nprod, N, N, N, 1.0, Ad, N, 0, Bd, N, 0, 0.0, C, N, ws, ws_bytes))
-        # scaled residuals (hi x hi and the corrections in separate accumulators)
-        for nprod in (2, 3):
-            one(f"split{nprod}_scaled_f16", nprod,
-                lambda: b.gemm_split_scaled(0, nprod, N, N, N, 1.0, Ad, N, 0, Bd, N, 0, 0.0, C, N, ws, ws_bytes))
-        # three BF16 pieces, six products
-        one("bf16x3", 6, lambda: b.gemm_split_bf16x3(N, N, N, 1.0, Ad, N, 0, Bd, N, 0, 0.0, C, N, ws, ws_bytes))
+        # each scheme twice: the two-pass path (split pass into the workspace, then the GEMM on the
+        # pieces; what a call with a workspace runs) and the one launch that streams the FP32 operands
+        # in by TMA and forms the pieces on chip (what a call without a workspace runs)
+        for suffix, env in (("", None), ("_one_launch", "fused")):
+            if env:
+                os.environ["TCGEMM_SPLIT"] = env
+            try:
+                for nprod in (2, 3, 4):
+                    one(f"split{nprod}_f16{suffix}", nprod,
+                        lambda: b.gemm_split(0, nprod, N, N, N, 1.0, Ad, N, 0, Bd, N, 0, 0.0, C, N, ws, ws_bytes))
+                # scaled residuals (hi x hi and the corrections in separate accumulators)
+                for nprod in (2, 3):
+                    one(f"split{nprod}_scaled_f16{suffix}", nprod,
+                        lambda: b.gemm_split_scaled(0, nprod, N, N, N, 1.0, Ad, N, 0, Bd, N, 0, 0.0, C, N, ws,
+                                                    ws_bytes))
+                # three BF16 pieces, six products (two passes only)
+                if not env:
+                    one("bf16x3", 6,
+                        lambda: b.gemm_split_bf16x3(N, N, N, 1.0, Ad, N, 0, Bd, N, 0, 0.0, C, N, ws, ws_bytes))
+            finally:
+                os.environ.pop("TCGEMM_SPLIT", None)
+        res["split3_one_launch_vs_twopass"] = res["split3_f16"]["ms"] / res["split3_f16_one_launch"]["ms"]
         Aq = torch.empty((N, N), dtype=torch.float16, device="cuda")
         Bq = torch.empty((N, N), dtype=torch.float16, device="cuda")
         b.tc_quantize(0, N, N, Ad, N, Aq, N, 0)
@@ -750,6 +764,9 @@ def profile_case(kind):
     A = torch.from_numpy(synth.uniform((N, N), seed=synth.seed_for(1, 0))).cuda()
     B = torch.from_numpy(synth.uniform((N, N), seed=synth.seed_for(1, 1))).cuda()
     C = torch.zeros((N, N), dtype=torch.float32, device="cuda")
+    if kind.endswith("_one_launch"):
+        kind = kind[:-len("_one_launch")]
+        os.environ["TCGEMM_SPLIT"] = "fused"
     if kind in ("split3", "split3_scaled", "bf16x3"):
         ws_bytes = b.gemm_split_workspace_bytes(1, 6 if kind == "bf16x3" else 3, N, N, N)
         ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")

@@ -110,7 +110,9 @@ tc_status tc_split(int32_t piece, int64_t rows, int64_t cols, const float* src, 
  *   workspace: 256-byte aligned device memory of at least
  *   tc_quantize_batch_workspace_bytes(count, jobs) bytes for the job table
  *   and the tile list, not touched by other work until the kernel has
- *   finished on `stream`.  The job array itself is read on the host. */
+ *   finished on `stream`.  The job array itself is read on the host, and the
+ *   job table is uploaded from host memory that the call frees on return: on
+ *   a stream that is being captured the call returns TC_ERR_UNSUPPORTED. */
 typedef struct tc_quantize_job {
     int64_t rows, cols;
     const float* src;
@@ -172,13 +174,24 @@ size_t gemm_split_workspace_bytes(int32_t piece, int32_t nprod, int64_t m, int64
  *     nprod = 2: A_hi B_hi + A_lo B_hi                (Eq. 1)
  *     nprod = 3: + A_hi B_lo                          (Eq. 2 without R_A R_B)
  *     nprod = 4: + A_lo B_lo                          (Eq. 2)
- *   A: m x k FP32, B: k x n FP32, any layout (la, lb); 16-byte aligned.
+ *   A: m x k FP32, B: k x n FP32, any layout (la, lb), 4-byte aligned.
  *   piece: TC_F16 or TC_BF16.
- *   workspace: device memory of gemm_split_workspace_bytes() bytes owned by
- *   the caller, or NULL to let the call take it from the stream-ordered pool
- *   (cudaMallocAsync on `stream`, freed on `stream`).
- * The pieces are formed in registers by one HBM-bound pass and all products
- * accumulate in one TMEM accumulator in one tcgen05 launch. */
+ * Two paths, the same C bit for bit:
+ *   - workspace == NULL: one launch that allocates nothing.  TMA streams the
+ *     FP32 rows of A and B into shared memory, the CUDA cores form the pieces
+ *     of every k-block there while the tensor cores multiply the previous
+ *     ones; the pieces never reach HBM.  Needs A and B 16-byte aligned with
+ *     lda, ldb multiples of 4; other operands fall back to the second path
+ *     with its workspace taken from the stream-ordered pool (cudaMallocAsync
+ *     on `stream`, freed on `stream`).
+ *   - workspace != NULL (device memory of gemm_split_workspace_bytes() bytes
+ *     owned by the caller, 256-byte aligned): a split pass writes the pieces
+ *     there and a second launch multiplies them.  About 1.7x faster than the
+ *     one-launch kernel at m = n = k = 8192 on GB300, whose shared memory then
+ *     carries 288 KB per k-block and CTA against 160 KB here.
+ *   The environment variable TCGEMM_SPLIT=fused or =twopass forces a path.
+ * All products accumulate in TMEM, with partial sums promoted to
+ * round-to-nearest FP32 registers every 128 of K. */
 tc_status gemm_split(int32_t piece, int32_t nprod, int64_t m, int64_t n, int64_t k, float alpha,
                      const float* A, int64_t lda, int32_t la,
                      const float* B, int64_t ldb, int32_t lb,
@@ -313,12 +326,16 @@ tc_status gemm_grouped(int32_t dt, int32_t count, const tc_problem* problems,
  * TCGEMM_GROUPED=mma, the mma.sync kernel's problem table (48 bytes per
  * problem) and 16 bytes per 64 x 64 tile.  A group that fits neither returns
  * TC_ERR_INVALID with the byte counts in tc_last_error().
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, once per device); make that first call before
- *     any stream capture.
+ *   - The first call on a device looks up the array's device address and the
+ *     status word's (cudaGetSymbolAddress, once per device, with that device
+ *     current).  It changes no setting of the device or of its memory pools.
  *   - The schedule is uploaded from pageable host memory, so the call waits on
  *     the host for earlier work on `stream` before it enqueues the kernel;
  *     it does not wait for the kernel.
+ *   - That upload reads host memory the call frees on return, so the call
+ *     cannot be recorded in a CUDA graph: on a stream that is being captured
+ *     it returns TC_ERR_UNSUPPORTED and enqueues nothing.  Use
+ *     gemm_grouped_plan_run for graphs.
  *   - Every call reuses the same array, which keeps the last call's contents
  *     (nothing in it needs to start at zero).  Calls whose work overlaps on
  *     the GPU (different streams, or another thread) race on it: order them
@@ -335,7 +352,9 @@ tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_problem* prob
  *   work until this call's kernel has finished on `stream`.
  * Runs the tcgen05 kernel of gemm_grouped (maps and tiles in the workspace;
  * the mma.sync kernel with TCGEMM_GROUPED=mma); arguments and errors otherwise
- * as gemm_grouped. */
+ * as gemm_grouped.  Like gemm_grouped_noalloc it uploads the schedule from
+ * host memory that it frees on return, so on a stream that is being captured
+ * it returns TC_ERR_UNSUPPORTED and enqueues nothing. */
 size_t gemm_grouped_workspace_bytes(int32_t count, const tc_problem* problems);
 tc_status gemm_grouped_ws(int32_t dt, int32_t count, const tc_problem* problems,
                           const void* a_base, int32_t la, const void* b_base, int32_t lb,

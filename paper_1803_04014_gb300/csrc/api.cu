@@ -402,6 +402,23 @@ namespace {
 // Phases of a refined GEMM: forming the pieces, the tensor-core GEMM on them, or both.
 constexpr int kSplitPhasePieces = 1, kSplitPhaseGemm = 2, kSplitPhaseBoth = 3;
 
+// Path of a one-call refined GEMM.  The one-launch kernel (pieces formed on chip) needs no
+// workspace; the two-pass path (split pass into a workspace, then the tensor-core GEMM on the
+// pieces) is faster on this GPU (its shared memory moves 160 KB per k-block and CTA against the
+// one-launch kernel's 288 KB).  So a call that brings a workspace takes the two-pass path and a
+// call without one takes the one-launch path, which allocates nothing; TCGEMM_SPLIT=fused or
+// =twopass forces either.  The one-launch kernel streams its operands in by TMA: both 16-byte
+// aligned, leading dimensions multiples of 4 (else two passes, with a pooled workspace).
+bool split_use_fused(int scheme, int nprod, const void* workspace, const float* A, int64_t lda, const float* B,
+                     int64_t ldb) {
+    const char* env = getenv("TCGEMM_SPLIT");
+    bool want = workspace == nullptr;
+    if (env && strcmp(env, "fused") == 0) want = true;
+    if (env && strcmp(env, "twopass") == 0) want = false;
+    return want && tcg::split_fused_supported(scheme, nprod) && aligned(A, 16) && aligned(B, 16) && lda % 4 == 0 &&
+           ldb % 4 == 0;
+}
+
 // Refined GEMM of every scheme: form the pieces of A and B (K-major) in the
 // workspace with one HBM-bound pass each, then one tcgen05 launch.
 //   scheme 0: Eq. 1 / Eq. 2, nprod 2-4;  1: scaled residuals, nprod 2-3;
@@ -422,12 +439,12 @@ tc_status split_gemm(const char* name, int scheme, int32_t piece, int32_t nprod,
         return fail(TC_ERR_INVALID, "%s: the pieces live in the caller's workspace: it may not be NULL", name);
     if (m == 0 || n == 0) return TC_OK;
     if (do_gemm && (!C || ldc < n || !aligned(C, 4))) return fail(TC_ERR_INVALID, "%s: bad C / ldc", name);
-    Device* d;
-    if ((s = get_device(&d)) != TC_OK) return s;
-    cudaStream_t st = as_stream(stream);
-    if (k == 0) return do_gemm ? enqueue(tcg::launch_scale_c(m, n, beta, C, ldc, st), name) : TC_OK;
+    // operands, leading dimensions and the workspace are checked before the k = 0 shortcut, so
+    // every call with the same arguments is accepted or refused whatever k is; an empty operand
+    // (k = 0) may be NULL
     if (do_pieces) {
-        if (!A || !B || !aligned(A, 4) || !aligned(B, 4)) return fail(TC_ERR_INVALID, "%s: bad operand pointer", name);
+        if (k > 0 && (!A || !B)) return fail(TC_ERR_INVALID, "%s: null operand", name);
+        if (!aligned(A, 4) || !aligned(B, 4)) return fail(TC_ERR_INVALID, "%s: misaligned operand pointer", name);
         if (lda < (la == TC_ROW_MAJOR ? k : m) || ldb < (lb == TC_ROW_MAJOR ? n : k))
             return fail(TC_ERR_INVALID, "%s: leading dimension too small", name);
     }
@@ -435,13 +452,45 @@ tc_status split_gemm(const char* name, int scheme, int32_t piece, int32_t nprod,
     if (workspace && workspace_bytes < need)
         return fail(TC_ERR_INVALID, "%s: workspace of %zu bytes, need %zu", name, workspace_bytes, need);
     if (workspace && !aligned(workspace, 256)) return fail(TC_ERR_INVALID, "%s: workspace must be 256-byte aligned", name);
+    Device* d;
+    if ((s = get_device(&d)) != TC_OK) return s;
+    cudaStream_t st = as_stream(stream);
+    if (k == 0) return do_gemm ? enqueue(tcg::launch_scale_c(m, n, beta, C, ldc, st), name) : TC_OK;
+    const int np = scheme == 2 ? 3 : 2;
+    if (phases == kSplitPhaseBoth && split_use_fused(scheme, nprod, workspace, A, lda, B, ldb)) {
+        // one launch: the kernel streams FP32 A and B in by TMA and forms the pieces on chip
+        tcg::SplitFusedLaunch f{};
+        f.scheme = scheme;
+        f.nprod = nprod;
+        f.bf16 = piece == TC_BF16 ? 1 : 0;
+        f.m = m; f.n = n; f.k = k;
+        f.alpha = alpha; f.beta = beta;
+        f.a_mn = la == TC_COL_MAJOR ? 1 : 0;
+        f.b_mn = lb == TC_ROW_MAJOR ? 1 : 0;
+        f.C = C; f.ldc = ldc;
+        f.status = d->status;
+        f.sm_count = d->sm_count;
+        f.group_m = gemm_group_m();
+        f.stall_at = take_stall();
+        CUtensorMap ta, tb;
+        // K-major: rows of k elements, boxes of 32 k x 128 rows; MN-major: k rows of m (or n)
+        // elements, boxes of 32 x 32 k-rows
+        if ((s = f.a_mn ? encode_kmajor(&ta, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, A, m, k, 1, lda * 4, k * lda * 4, 32)
+                        : encode_kmajor(&ta, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, A, k, m, 1, lda * 4, m * lda * 4,
+                                        128)) != TC_OK)
+            return s;
+        if ((s = f.b_mn ? encode_kmajor(&tb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B, n, k, 1, ldb * 4, k * ldb * 4, 32)
+                        : encode_kmajor(&tb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, B, k, n, 1, ldb * 4, n * ldb * 4,
+                                        128)) != TC_OK)
+            return s;
+        return enqueue(tcg::launch_split_fused(ta, tb, f, st), name);
+    }
     void* ws = workspace;
     cudaError_t e;
     if (!ws) {
         if ((e = cudaMallocAsync(&ws, need, st)) != cudaSuccess)
             return fail(TC_ERR_OOM, "%s: workspace: %s", name, cudaGetErrorString(e));
     }
-    const int np = scheme == 2 ? 3 : 2;
     const int64_t kp = split_kpad(k);
     uint8_t* wa = static_cast<uint8_t*>(ws);
     uint8_t* wb = wa + (np * m * kp * 2 + 255) / 256 * 256;
@@ -473,8 +522,9 @@ tc_status split_gemm(const char* name, int scheme, int32_t piece, int32_t nprod,
         p.nprod = nprod;
         p.bn = nprod == 2 ? 256 : 128;
         if (scheme == 0) {
-            p.pair = use_pair_tiles(m) ? 1 : 0;
-            p.promote_kb = p.pair ? split_promote_kb() : 0;
+            // the promoted pair kernel for every m, as the one-launch path, so both give the same C
+            p.pair = 1;
+            p.promote_kb = split_promote_kb();
         } else {
             // the scaled and three-piece schemes run on the promoted CTA-pair kernel only
             p.pair = 1;
@@ -902,6 +952,7 @@ static __device__ __align__(256) unsigned char g_grouped_scratch[kNoAllocScratch
 struct NoAllocDevice {
     bool ready = false;
     void* scratch = nullptr;  // device address of g_grouped_scratch on this device
+    int* status = nullptr;    // device address of the status word (a static variable as well)
     int sm_count = 0;
 };
 NoAllocDevice g_noalloc_dev[64];
@@ -917,9 +968,13 @@ tc_status noalloc_setup(NoAllocDevice** out) {
         void* p = nullptr;
         if ((e = cudaGetSymbolAddress(&p, g_grouped_scratch)) != cudaSuccess)
             return cuda_fail(e, "gemm_grouped_noalloc: cudaGetSymbolAddress");
+        void* sw = nullptr;
+        if ((e = cudaGetSymbolAddress(&sw, g_status_word)) != cudaSuccess)
+            return cuda_fail(e, "gemm_grouped_noalloc: cudaGetSymbolAddress(status)");
         if ((e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
             return cuda_fail(e, "gemm_grouped_noalloc: cudaDeviceGetAttribute");
         d.scratch = p;
+        d.status = static_cast<int*>(sw);
         d.ready = true;
     }
     *out = &d;
@@ -929,6 +984,21 @@ tc_status noalloc_setup(NoAllocDevice** out) {
 }  // namespace
 
 namespace {
+
+// The plan-free entry points below copy their schedule from host memory that the call owns and
+// frees on return.  Inside a stream capture that copy would become a graph node reading freed
+// host memory at every replay, so a capturing stream is refused before anything is enqueued.
+tc_status refuse_capture(const char* name, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return cuda_fail(e, name);
+    if (cs != cudaStreamCaptureStatusNone)
+        return fail(TC_ERR_UNSUPPORTED,
+                    "%s: the stream is being captured; this call uploads its schedule from host memory it frees "
+                    "on return and cannot be recorded in a CUDA graph (gemm_grouped_plan_run can)",
+                    name);
+    return TC_OK;
+}
 
 // Host half of a plan-free grouped GEMM on the mma.sync kernel (64 x 64 tiles): checks the
 // call and builds in `host` the problem table (padded to 256 bytes) followed by the tile list,
@@ -1072,6 +1142,7 @@ extern "C" tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_pr
     tc_status s = grouped_mma_host("gemm_grouped_noalloc", dt, count, problems, a_base, la, b_base, lb, c_base, host,
                                    &desc_bytes, &num_tiles, !tc);
     if (s != TC_OK || count == 0) return s;
+    if ((s = refuse_capture("gemm_grouped_noalloc", as_stream(stream))) != TC_OK) return s;
     NoAllocDevice* d;
     if ((s = noalloc_setup(&d)) != TC_OK) return s;
     if (tc) {
@@ -1082,13 +1153,10 @@ extern "C" tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_pr
         if ((s = grouped_tc_host(dt, count, problems, a_base, b_base, lb, kNoAllocScratchBytes, tch, &maps_bytes,
                                  &tc_tiles, &fits)) != TC_OK)
             return s;
-        if (fits) {
-            Device* dev;  // sm_count and the status word (a static variable): nothing is allocated
-            if ((s = get_device(&dev)) != TC_OK) return s;
+        if (fits)
             return grouped_tc_enqueue("gemm_grouped_noalloc", dt, lb, tch, maps_bytes, tc_tiles,
-                                      static_cast<unsigned char*>(d->scratch), c_base, alpha, beta, dev->status,
+                                      static_cast<unsigned char*>(d->scratch), c_base, alpha, beta, d->status,
                                       d->sm_count, as_stream(stream));
-        }
         // more problems than the static table holds maps for: the mma.sync schedule is smaller
         if ((s = grouped_mma_host("gemm_grouped_noalloc", dt, count, problems, a_base, la, b_base, lb, c_base, host,
                                   &desc_bytes, &num_tiles)) != TC_OK)
@@ -1135,6 +1203,7 @@ extern "C" tc_status gemm_grouped_ws(int32_t dt, int32_t count, const tc_problem
     if (s != TC_OK || count == 0) return s;
     if (!workspace || !aligned(workspace, 256))
         return fail(TC_ERR_INVALID, "gemm_grouped_ws: workspace must be a 256-byte aligned device pointer");
+    if ((s = refuse_capture("gemm_grouped_ws", as_stream(stream))) != TC_OK) return s;
     Device* d;
     if ((s = get_device(&d)) != TC_OK) return s;
     if (tc) {
@@ -1202,9 +1271,10 @@ extern "C" tc_status tc_quantize_batch(int32_t dt, int32_t count, const tc_quant
         return fail(TC_ERR_INVALID, "tc_quantize_batch: workspace must be a 256-byte aligned device pointer");
     if (workspace_bytes < need)
         return fail(TC_ERR_INVALID, "tc_quantize_batch: workspace of %zu bytes, need %zu", workspace_bytes, need);
-    Device* d;
-    tc_status s = get_device(&d);
+    tc_status s = refuse_capture("tc_quantize_batch", as_stream(stream));
     if (s != TC_OK) return s;
+    Device* d;
+    if ((s = get_device(&d)) != TC_OK) return s;
     std::vector<unsigned char> host(need, 0);
     auto* hj = reinterpret_cast<tcg::QuantJobDev*>(host.data());
     auto* ht = reinterpret_cast<tcg::QuantTileDev*>(host.data() + desc_bytes);

@@ -31,6 +31,7 @@
 #include <cstring>
 
 #include "launch.h"
+#include "pair_sched.cuh"
 #include "tc_ptx.cuh"
 
 namespace tcg {
@@ -63,35 +64,6 @@ struct Args {
     uint32_t idesc_half;
     int split_tail;  // 0 keeps every unit full-width (TCGEMM_PAIR_TAIL=full)
 };
-
-// product p multiplies A piece prod_a(p) with B piece prod_b(p).  Two pieces:
-// (hi,hi), (lo,hi), (hi,lo), (lo,lo).  Three BF16 pieces (NA = 3): the six
-// products with piece orders adding up to at most 2, largest first:
-// (0,0), (1,0), (0,1), (2,0), (1,1), (0,2).
-template <int NA = 2>
-__host__ __device__ constexpr int prod_a(int p) {
-    return NA == 3 ? (p == 1 || p == 4 ? 1 : (p == 3 ? 2 : 0)) : (p & 1);
-}
-template <int NA = 2>
-__host__ __device__ constexpr int prod_b(int p) {
-    return NA == 3 ? (p == 2 || p == 4 ? 1 : (p == 5 ? 2 : 0)) : (p >> 1);
-}
-static_assert(prod_a<3>(3) == 2 && prod_b<3>(3) == 0 && prod_a<3>(5) == 0 && prod_b<3>(5) == 2 &&
-                  prod_a<3>(4) == 1 && prod_b<3>(4) == 1 && prod_a<3>(2) == 0 && prod_b<3>(2) == 1,
-              "three-piece product table");
-
-__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int group_m, int& mb, int& nb) {
-    const int band = group_m * tiles_n;
-    const int g = t / band;
-    const int first = g * group_m;
-    const int gm = min(tiles_m - first, group_m);
-    const int r = t - g * band;
-    mb = first + r % gm;
-    nb = r / gm;
-}
-
-// Instruction-descriptor bit that reads B as MN-major (its rows run along N).
-constexpr uint32_t kIdescTransposeB = 1u << 16;
 
 // Work unit u of the pair kernel: its tile (mb, nb), the column offset inside the 256-wide tile
 // and the unit's width (256, or 128 for the halves of the last tiles).
@@ -380,17 +352,6 @@ struct PairLayout {
     static constexpr int kBytes = kEpiOffset + 4 * 32 * 33 * 4 + 1024;
     static constexpr int kTmemCols = 512;  // two 256-column accumulators
 };
-
-__device__ __forceinline__ uint32_t cluster_id_x() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t num_clusters_x() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-    return r;
-}
 
 template <int KIND, int STAGES, int NA, int NB, int NPROD, bool B_MN = false>
 __global__ void __launch_bounds__(kThreads, 1)

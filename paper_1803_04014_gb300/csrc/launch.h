@@ -71,6 +71,30 @@ struct TcGemmLaunch {
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmLaunch& p, cudaStream_t st);
 size_t tc_gemm_smem_bytes(int na, int nb, int bn, int* stages_out);
 
+// ---- split_fused.cu: refined GEMM reading FP32 A and B, pieces formed on chip (one launch).
+struct SplitFusedLaunch {
+    int scheme;      // 0: hi, lo (Eq. 1 / Eq. 2); 1: scaled residuals
+    int nprod;       // 2, 3, 4 (scheme 0); 2, 3 (scheme 1)
+    int bf16;        // pieces are BF16 (else FP16)
+    int64_t m, n, k;
+    float alpha, beta;
+    int a_mn;        // 1: A column-major (k x m in memory)
+    int b_mn;        // 1: B row-major (k x n in memory)
+    float* C;
+    int64_t ldc;
+    int* status;
+    int sm_count;
+    int group_m;
+    int stall_at;    // test hook: k-block + 1 to withhold, 0 = off
+};
+// Schemes the one-launch kernel runs (the three-piece BF16 split does not: its pieces and the
+// FP32 staging do not fit in shared memory together).
+bool split_fused_supported(int scheme, int nprod);
+// tmA / tmB: FP32 maps, 128-byte swizzle.  K-major operand: dims {k, rows, 1}, box 32 x 128;
+// MN-major operand: dims {rows, k, 1}, box 32 x 32.
+cudaError_t launch_split_fused(const CUtensorMap& tmA, const CUtensorMap& tmB, const SplitFusedLaunch& p,
+                               cudaStream_t st);
+
 // ---- sgemm.cu
 cudaError_t launch_sgemm(int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda, int la,
                          const float* B, int64_t ldb, int lb, float beta, float* C, int64_t ldc, cudaStream_t st);

@@ -52,8 +52,12 @@ def test_stalled_gemm_times_out_and_the_context_survives(b, monkeypatch, tile, m
     assert normwise_dev(host(C), ref, A, B) <= TOL_NORMWISE
 
 
-@pytest.mark.parametrize("scheme", ["eq2", "scaled", "bf16x3"])
-def test_stalled_refined_gemm_times_out_and_the_context_survives(b, scheme):
+@pytest.mark.parametrize("scheme,path", [("eq2", "fused"), ("eq2", "twopass"), ("scaled", "fused"),
+                                         ("scaled", "twopass"), ("bf16x3", "twopass")])
+def test_stalled_refined_gemm_times_out_and_the_context_survives(b, monkeypatch, scheme, path):
+    # "fused": the one-launch kernel (a piece warp of the first CTA pair withholds its arrival);
+    # "twopass": the promoted GEMM on pieces from a split pass (the producer withholds a k-block)
+    monkeypatch.setenv("TCGEMM_SPLIT", path)
     m, n, k = 512, 256, 640
     A = synth.log_uniform_pow2((m, k), seed=9)
     B = synth.log_uniform_pow2((k, n), seed=10)

@@ -114,3 +114,45 @@ def test_noalloc_rejects_groups_beyond_its_static_scratch(b):
         b.gemm_grouped_noalloc(0, rows, a, 0, a, 0, c, 1.0, 0.0)
     assert e.value.status == b.TC_ERR_INVALID
     assert "static maximum" in str(e.value)
+
+
+def test_plan_free_entry_points_refuse_stream_capture(b):
+    # gemm_grouped_noalloc and gemm_grouped_ws copy their schedule from host memory that the call
+    # frees on return, so a capture would record a copy of freed memory: both refuse a capturing
+    # stream with TC_ERR_UNSUPPORTED before enqueueing anything, and work again afterwards
+    rows, abuf, bbuf, csize = _group(6, 11, 0)
+    ws_bytes = b.gemm_grouped_workspace_bytes(rows)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    c = torch.zeros(csize, dtype=torch.float32, device="cuda")
+    calls = [lambda: b.gemm_grouped_noalloc(0, rows, abuf, 0, bbuf, 0, c, 1.0, 0.0),
+             lambda: b.gemm_grouped_ws(0, rows, abuf, 0, bbuf, 0, c, 1.0, 0.0, ws, ws_bytes)]
+    for call in calls:
+        call()  # the first call on the device, outside any capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    statuses = []
+    with torch.cuda.stream(side):
+        graph.capture_begin()
+        try:
+            c.mul_(1.0)  # keeps the captured graph non-empty
+            for call in calls:
+                try:
+                    call()
+                    statuses.append(b.TC_OK)
+                except b.TcError as e:
+                    statuses.append(e.status)
+        finally:
+            graph.capture_end()
+    assert statuses == [b.TC_ERR_UNSUPPORTED, b.TC_ERR_UNSUPPORTED]
+    c_ref = torch.zeros_like(c)
+    b.gemm_grouped(0, rows, abuf, 0, bbuf, 0, c_ref, 1.0, 0.0)
+    for call in calls:
+        c.zero_()
+        call()
+        b.tc_sync_status()
+        ref, got = host(c_ref), host(c)
+        for (m, n, k, _oa, _ob, oc, _lda, _ldb, _ldc) in rows:
+            sl = slice(oc, oc + m * n)
+            ok, info = elementwise_ok(got[sl], ref[sl], np.full(m * n, float(k)), k)
+            assert ok, (m, n, k, info)
