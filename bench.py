@@ -554,10 +554,18 @@ def measure_rows(b, A, B, pk, sm_count):
         t0 = time.perf_counter()
         for _ in range(5):
             f()
-        ms = (time.perf_counter() - t0) / 5 * 1e3   # the call synchronises and returns host values
+        ms_call = (time.perf_counter() - t0) / 5 * 1e3   # the call synchronises and returns host values
+        # the reduction alone: the asynchronous form, timed with CUDA events on the launching stream
+        ws_bytes = b.tc_error_norm_workspace_bytes()
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+        out4 = torch.empty(4, dtype=torch.float64, device="cuda")
+        g = lambda: b.tc_error_norm_dev(N, N, Cd, N, C64, N, 1, Ad, N, N, N, Bd, N, N, N, out4, ws, ws_bytes)
+        ms = _time_ms(g, 10, warm=3)
         byts = N * N * (4 + 8 + 4 + 4)
         return {"ms": ms, "gbs": byts / (ms * 1e-3) / 1e9, "frac_of_hbm": byts / (ms * 1e-3) / 1e9 / pk["hbm_gbs"],
-                "bytes": byts, "note": "host wall time of the synchronising call (two kernels + 32-byte read-back)"}
+                "bytes": byts, "ms_synchronising_call": ms_call,
+                "note": "ms: CUDA events around tc_error_norm_dev (the two reduction kernels, nothing else); "
+                        "ms_synchronising_call: host wall time of tc_error_norm (plus scratch, read-back and sync)"}
 
     out["error_norm_n8192"] = _row("error_norm_n8192", error_norm)
     torch.cuda.empty_cache()

@@ -405,6 +405,19 @@ tc_status tc_error_norm(int64_t m, int64_t n, const float* C, int64_t ldc,
                         const float* B, int64_t b_rows, int64_t b_cols, int64_t ldb,
                         double* out, void* stream);
 
+/* The same reduction enqueued on `stream` without synchronising: the four
+ * sums land in out_dev, a DEVICE array of 4 doubles (8-byte aligned), and the
+ * per-block partial sums in `workspace`, caller-owned device memory of
+ * tc_error_norm_workspace_bytes() bytes (8-byte aligned).  Nothing is
+ * allocated; the result is bit for bit that of tc_error_norm.  Arguments and
+ * errors otherwise as tc_error_norm. */
+size_t tc_error_norm_workspace_bytes(void);
+tc_status tc_error_norm_dev(int64_t m, int64_t n, const float* C, int64_t ldc,
+                            const void* Cref, int64_t ldr, int32_t ref_is_f64,
+                            const float* A, int64_t a_rows, int64_t a_cols, int64_t lda,
+                            const float* B, int64_t b_rows, int64_t b_cols, int64_t ldb,
+                            double* out_dev, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of GEMM requests (beyond the paper)          */
 /* ------------------------------------------------------------------------ */

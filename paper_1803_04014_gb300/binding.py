@@ -117,6 +117,9 @@ SIGNATURES = {
     "tc_autotune_load": (_i32, [ctypes.c_char_p]),
     "tc_error_norm": (_i32, [_i64, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _i64, _i64, _i64, _vp, _i64, _i64,
                              _i64, ctypes.POINTER(ctypes.c_double), _vp]),
+    "tc_error_norm_workspace_bytes": (_sz, []),
+    "tc_error_norm_dev": (_i32, [_i64, _i64, _vp, _i64, _vp, _i64, _i32, _vp, _i64, _i64, _i64, _vp, _i64, _i64,
+                                 _i64, _vp, _vp, _sz, _vp]),
     "serve_open": (_i32, [ctypes.POINTER(tc_serve_cfg), ctypes.POINTER(_vp)]),
     "serve_submit": (_i32, [_vp, ctypes.POINTER(tc_request), ctypes.POINTER(_u64)]),
     "serve_poll": (_i32, [_vp, _u64, ctypes.POINTER(tc_result)]),
@@ -398,6 +401,18 @@ def tc_error_norm(m, n, C, ldc, Cref, ldr, ref_is_f64, A=None, a_rows=0, a_cols=
     _check(load().tc_error_norm(m, n, _ptr(C), ldc, _ptr(Cref), ldr, int(ref_is_f64), _ptr(A), a_rows, a_cols, lda,
                                 _ptr(B), b_rows, b_cols, ldb, out, _stream(stream)), "tc_error_norm")
     return tuple(out)
+
+
+def tc_error_norm_workspace_bytes() -> int:
+    return int(load().tc_error_norm_workspace_bytes())
+
+
+def tc_error_norm_dev(m, n, C, ldc, Cref, ldr, ref_is_f64, A, a_rows, a_cols, lda, B, b_rows, b_cols, ldb, out_dev,
+                      workspace, workspace_bytes, stream=None):
+    """tc_error_norm into a device array of 4 doubles, enqueued without synchronising."""
+    return _check(load().tc_error_norm_dev(m, n, _ptr(C), ldc, _ptr(Cref), ldr, int(ref_is_f64), _ptr(A), a_rows,
+                                           a_cols, lda, _ptr(B), b_rows, b_cols, ldb, _ptr(out_dev), _ptr(workspace),
+                                           int(workspace_bytes), _stream(stream)), "tc_error_norm_dev")
 
 
 def serve_open(hbm_budget_bytes, max_inflight=16, num_streams=4, queue_capacity=1 << 16):

@@ -192,6 +192,17 @@ int gemm_group_m(int dt = -1, int64_t m = 0, int64_t n = 0, int64_t k = 0) {
     return 8;
 }
 
+// K order of the CTA-pair kernels.  A CTA pair takes every ncl-th tile of the raster, so its
+// i-th tile belongs to round i of tiles in flight together; consecutive rounds of a raster band
+// share the band's A panels.  Walking K downwards in odd rounds starts each round on the k-blocks
+// the round before it left in L2 (DRAM reads of the FP16 GEMM at N = 8192: 1.30 GB against 1.45
+// GB in one direction).  Each tile's order depends only on its place in the raster and the number
+// of CTA pairs, so results stay bitwise reproducible.  TCGEMM_K_ORDER=forward turns it off.
+int gemm_serpentine() {
+    const char* env = getenv("TCGEMM_K_ORDER");
+    return (env && strcmp(env, "forward") == 0) ? 0 : 1;
+}
+
 // Epilogue of the pair GEMM: stage 32 x 32 chunks in shared memory (default) or store rows
 // directly from the accumulator registers (TCGEMM_EPILOGUE=direct).
 int gemm_staged_epilogue() {
@@ -365,6 +376,7 @@ tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, c
     p.group_m = gemm_group_m(dt, m, n, k);
     p.stall_at = take_stall();
     p.staged_epilogue = gemm_staged_epilogue();
+    p.serpentine = gemm_serpentine();
     p.m = m; p.n = n; p.k = k;
     p.alpha = alpha; p.beta = beta;
     p.C = C; p.ldc = ldc;
@@ -472,6 +484,7 @@ tc_status split_gemm(const char* name, int scheme, int32_t piece, int32_t nprod,
         f.sm_count = d->sm_count;
         f.group_m = gemm_group_m();
         f.stall_at = take_stall();
+        f.serpentine = gemm_serpentine();
         CUtensorMap ta, tb;
         // K-major: rows of k elements, boxes of 32 k x 128 rows; MN-major: k rows of m (or n)
         // elements, boxes of 32 x 32 k-rows
@@ -533,6 +546,7 @@ tc_status split_gemm(const char* name, int scheme, int32_t piece, int32_t nprod,
         }
         p.group_m = gemm_group_m();
         p.stall_at = take_stall();
+        p.serpentine = gemm_serpentine();
         p.m = m; p.n = n; p.k = k;
         p.alpha = alpha; p.beta = beta;
         p.C = C; p.ldc = ldc;
@@ -906,21 +920,58 @@ tc_status gemm_grouped(int32_t dt, int32_t count, const tc_problem* problems, co
     return s;
 }
 
+size_t tc_error_norm_workspace_bytes(void) { return static_cast<size_t>(3 * tcg::kErrBlocks * 2) * sizeof(double); }
+
+}  // extern "C"
+
+namespace {
+
+tc_status error_norm_checks(const char* name, int64_t m, int64_t n, const float* C, int64_t ldc, const void* Cref,
+                            int64_t ldr, int64_t a_rows, int64_t a_cols, const float* A, int64_t lda, int64_t b_rows,
+                            int64_t b_cols, const float* B, int64_t ldb) {
+    if (m < 0 || n < 0 || a_rows < 0 || a_cols < 0 || b_rows < 0 || b_cols < 0)
+        return fail(TC_ERR_INVALID, "%s: negative size", name);
+    if (m * n > 0 && (!C || !Cref || ldc < n || ldr < n)) return fail(TC_ERR_INVALID, "%s: bad C / Cref", name);
+    if (A && lda < a_cols) return fail(TC_ERR_INVALID, "%s: lda < a_cols", name);
+    if (B && ldb < b_cols) return fail(TC_ERR_INVALID, "%s: ldb < b_cols", name);
+    return TC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tc_status tc_error_norm_dev(int64_t m, int64_t n, const float* C, int64_t ldc, const void* Cref, int64_t ldr,
+                            int32_t ref_is_f64, const float* A, int64_t a_rows, int64_t a_cols, int64_t lda,
+                            const float* B, int64_t b_rows, int64_t b_cols, int64_t ldb, double* out_dev,
+                            void* workspace, size_t workspace_bytes, void* stream) {
+    tc_status s = error_norm_checks("tc_error_norm_dev", m, n, C, ldc, Cref, ldr, a_rows, a_cols, A, lda, b_rows,
+                                    b_cols, B, ldb);
+    if (s != TC_OK) return s;
+    if (!out_dev || !aligned(out_dev, 8)) return fail(TC_ERR_INVALID, "tc_error_norm_dev: bad out_dev");
+    if (!workspace || !aligned(workspace, 8) || workspace_bytes < tc_error_norm_workspace_bytes())
+        return fail(TC_ERR_INVALID, "tc_error_norm_dev: workspace of %zu bytes, need %zu (8-byte aligned)",
+                    workspace_bytes, tc_error_norm_workspace_bytes());
+    Device* d;
+    if ((s = get_device(&d)) != TC_OK) return s;
+    return enqueue(tcg::launch_error_norm(m, n, C, ldc, Cref, ldr, ref_is_f64 != 0, A, A ? a_rows : 0, a_cols, lda, B,
+                                          B ? b_rows : 0, b_cols, ldb, static_cast<double*>(workspace), out_dev,
+                                          as_stream(stream)),
+                   "tc_error_norm_dev");
+}
+
 tc_status tc_error_norm(int64_t m, int64_t n, const float* C, int64_t ldc, const void* Cref, int64_t ldr,
                         int32_t ref_is_f64, const float* A, int64_t a_rows, int64_t a_cols, int64_t lda,
                         const float* B, int64_t b_rows, int64_t b_cols, int64_t ldb, double* out, void* stream) {
     if (!out) return fail(TC_ERR_INVALID, "tc_error_norm: null out");
-    if (m < 0 || n < 0 || a_rows < 0 || a_cols < 0 || b_rows < 0 || b_cols < 0)
-        return fail(TC_ERR_INVALID, "tc_error_norm: negative size");
-    if (m * n > 0 && (!C || !Cref || ldc < n || ldr < n)) return fail(TC_ERR_INVALID, "tc_error_norm: bad C / Cref");
-    if (A && lda < a_cols) return fail(TC_ERR_INVALID, "tc_error_norm: lda < a_cols");
-    if (B && ldb < b_cols) return fail(TC_ERR_INVALID, "tc_error_norm: ldb < b_cols");
-    Device* d;
-    tc_status s = get_device(&d);
+    tc_status s = error_norm_checks("tc_error_norm", m, n, C, ldc, Cref, ldr, a_rows, a_cols, A, lda, b_rows, b_cols,
+                                    B, ldb);
     if (s != TC_OK) return s;
+    Device* d;
+    if ((s = get_device(&d)) != TC_OK) return s;
     cudaStream_t st = as_stream(stream);
     double* scratch = nullptr;
-    const size_t bytes = (3 * tcg::kErrBlocks * 2 + 4) * sizeof(double);
+    const size_t bytes = tc_error_norm_workspace_bytes() + 4 * sizeof(double);
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), bytes, st);
     if (e != cudaSuccess) return fail(TC_ERR_OOM, "tc_error_norm: scratch: %s", cudaGetErrorString(e));
     double* out_dev = scratch + 3 * tcg::kErrBlocks * 2;

@@ -63,6 +63,7 @@ struct Args {
     int full_units, num_units;
     uint32_t idesc_half;
     int split_tail;  // 0 keeps every unit full-width (TCGEMM_PAIR_TAIL=full)
+    int serpentine;  // pair kernel: every other unit of a CTA pair walks K from the end (L2 reuse)
 };
 
 // Work unit u of the pair kernel: its tile (mb, nb), the column offset inside the 256-wide tile
@@ -428,12 +429,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 unit_coords(a, u, mb, nb, coff, width);
                 // this CTA's half of the unit's B rows (a half-width unit uses the first 64 of the 128 loaded)
                 const int brow = nb * PN + coff + static_cast<int>(rank) * (width >> 1);
-                for (int kb = 0; kb < a.num_kb; ++kb) {
+                // odd rounds of units walk K downwards: a round of units shares A panels with the round
+                // before it (same raster band), and starts on the k-blocks that round left in L2
+                const bool down = a.serpentine && (((u - cid) / ncl) & 1);
+                for (int kb_i = 0; kb_i < a.num_kb; ++kb_i) {
+                    const int kb = down ? a.num_kb - 1 - kb_i : kb_i;
                     if (!wait(empty_bar(stage), phase ^ 1u)) {
                         ok = false;
                         break;
                     }
-                    if (kb == a.stall_kb && u == cid && cid == 0 && rank == 0) {
+                    if (kb_i == a.stall_kb && u == cid && cid == 0 && rank == 0) {
                         // test hook: the even CTA never arms this stage's barrier
                         if (++stage == STAGES) {
                             stage = 0;
@@ -815,12 +820,15 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
             for (int t = cid; ok && t < a.num_tiles; t += ncl) {
                 int mb, nb;
                 tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
-                for (int kb = 0; kb < a.num_kb; ++kb) {
+                // odd rounds of tiles walk K downwards (L2 reuse, as in the pair kernel)
+                const bool down = a.serpentine && (((t - cid) / ncl) & 1);
+                for (int kb_i = 0; kb_i < a.num_kb; ++kb_i) {
+                    const int kb = down ? a.num_kb - 1 - kb_i : kb_i;
                     if (!wait(empty_bar(stage), phase ^ 1u)) {
                         ok = false;
                         break;
                     }
-                    if (kb == a.stall_kb && t == cid && cid == 0 && rank == 0) {
+                    if (kb_i == a.stall_kb && t == cid && cid == 0 && rank == 0) {
                         // test hook: the even CTA never arms this stage's barrier
                         if (++stage == STAGES) {
                             stage = 0;
@@ -1186,6 +1194,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
             const char* env = getenv("TCGEMM_PAIR_TAIL");
             a.split_tail = (env && strcmp(env, "full") == 0) ? 0 : 1;
         }
+        a.serpentine = p.serpentine;
         const int max_clusters = p.sm_count / 2;
         const int clusters = a.num_tiles < max_clusters ? a.num_tiles : max_clusters;
         if (clusters <= 0) return cudaSuccess;

@@ -66,6 +66,7 @@ struct TcGemmLaunch {
                         // box 64 x 64), read by the MMA as MN-major
     int corr_exp;       // pair kernel with promotion, s > 0: products 1.. (the corrections of a scaled
                         // split) accumulate apart and are multiplied by 2^-s in the epilogue
+    int serpentine;     // pair kernels: every other round of tiles of a CTA pair walks K downwards
 };
 // tmA: 3-D map {k, m, na} with a 128 x (128 bytes) box; tmB: {k, n, nb} with a bn x (128 bytes) box.
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmLaunch& p, cudaStream_t st);
@@ -86,6 +87,7 @@ struct SplitFusedLaunch {
     int sm_count;
     int group_m;
     int stall_at;    // test hook: k-block + 1 to withhold, 0 = off
+    int serpentine;  // every other round of tiles of a CTA pair walks K downwards
 };
 // Schemes the one-launch kernel runs (the three-piece BF16 split does not: its pieces and the
 // FP32 staging do not fit in shared memory together).

@@ -74,6 +74,7 @@ struct FusedArgs {
     int* status;
     uint32_t idesc;
     int stall_kb;  // test hook: >= 0 makes the even CTA of the first pair withhold this k-block
+    int serpentine;  // odd rounds of tiles of a CTA pair walk K downwards (as the two-pass kernel)
 };
 
 template <int NA, int NB>
@@ -606,9 +607,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 bool ok = true;
                 const uint32_t fbase = base + L::kFOffset;
                 const int nhalf = 2 * a.num_kb;
+                // half h of a tile covers k from 32 h, or, in the odd rounds of tiles that walk K
+                // downwards, half h % 2 of k-block num_kb - 1 - h / 2
+                auto half_k = [&](int h, bool down) {
+                    const int kb = down ? a.num_kb - 1 - (h >> 1) : (h >> 1);
+                    return 64 * kb + 32 * (h & 1);
+                };
                 for (int t = cid; ok && t < a.num_tiles; t += ncl) {
                     int mb, nb;
                     tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
+                    const bool down = a.serpentine && (((t - cid) / ncl) & 1);
                     const int arow = mb * PM + static_cast<int>(rank) * 128;
                     const int brow = nb * PN + static_cast<int>(rank) * 128;
                     // the next tile of this cluster, whose first halves are prefetched near the end of this one
@@ -619,11 +627,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                         // bytes in flight to cover the latency of loads that miss L2
                         const int hp = h + kPrefetchHalves;
                         if (hp < nhalf) {
-                            prefetch_half(&tmA, a.a_mn != 0, arow, 32 * hp);
-                            prefetch_half(&tmB, a.b_mn != 0, brow, 32 * hp);
+                            prefetch_half(&tmA, a.a_mn != 0, arow, half_k(hp, down));
+                            prefetch_half(&tmB, a.b_mn != 0, brow, half_k(hp, down));
                         } else if (mb2 >= 0) {
-                            prefetch_half(&tmA, a.a_mn != 0, mb2 * PM + static_cast<int>(rank) * 128, 32 * (hp - nhalf));
-                            prefetch_half(&tmB, a.b_mn != 0, nb2 * PN + static_cast<int>(rank) * 128, 32 * (hp - nhalf));
+                            const int k2 = half_k(hp - nhalf, a.serpentine && !down);
+                            prefetch_half(&tmA, a.a_mn != 0, mb2 * PM + static_cast<int>(rank) * 128, k2);
+                            prefetch_half(&tmB, a.b_mn != 0, nb2 * PN + static_cast<int>(rank) * 128, k2);
                         }
                         if (!wait(fempty_bar(fs), fph ^ 1u)) {
                             ok = false;
@@ -631,8 +640,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                         }
                         const uint32_t dst = fbase + fs * kHalfBytes;
                         mbar_arrive_expect_tx(ffull_bar(fs), kHalfBytes);
-                        load_half(&tmA, a.a_mn != 0, dst, ffull_bar(fs), arow, 32 * h);
-                        load_half(&tmB, a.b_mn != 0, dst + kHalfBytes / 2, ffull_bar(fs), brow, 32 * h);
+                        load_half(&tmA, a.a_mn != 0, dst, ffull_bar(fs), arow, half_k(h, down));
+                        load_half(&tmB, a.b_mn != 0, dst + kHalfBytes / 2, ffull_bar(fs), brow, half_k(h, down));
                         issued_phase[fs] = static_cast<int>(fph);
                         if (++fs == L::kFStages) {
                             fs = 0;
@@ -739,6 +748,7 @@ cudaError_t launch_split_fused(const CUtensorMap& tmA, const CUtensorMap& tmB, c
     a.ldc = p.ldc;
     a.status = p.status;
     a.stall_kb = p.stall_at - 1;
+    a.serpentine = p.serpentine;
     a.idesc = make_idesc(256, 256, p.bf16 ? 1u : 0u) | (p.a_mn ? kIdescTransposeA : 0u) |
               (p.b_mn ? kIdescTransposeB : 0u);
     a.corr_scale = 1.0f;

@@ -428,6 +428,52 @@ def test_error_norm_special_values(b, n):
     assert abs(out[1] - want[1]) <= 1e-14 * want[1]
 
 
+def test_error_norm_at_the_edges_of_the_float_float_range(b):
+    # the squares are summed exactly as float-float groups only for 2^-50 <= |x| < 2^60 (values
+    # outside take the FP64 path): put entries of A and B and differences C - C64 at and just past
+    # both edges, mixed into the same groups of 4 and 8 as ordinary values
+    edges = np.array([2.0 ** -50, -(2.0 ** -51), 1.99 * 2.0 ** 59, -(2.0 ** 60), 2.0 ** -49, -(2.0 ** 59)])
+    m, n, k = 8, 24, 16
+    A = synth.uniform((m, k), seed=89)
+    B = synth.uniform((k, n), seed=90)
+    for arr in (A, B):
+        flat = arr.reshape(-1)
+        for i, v in enumerate(edges):
+            flat[3 * i + 1] = np.float32(v)   # spread over several groups, each beside ordinary values
+    C = synth.uniform((m, n), seed=91)
+    C64 = C.astype(np.float64) + synth.normal((m, n), seed=92).astype(np.float64) * 1e-4
+    flatc, flat64 = C.reshape(-1), C64.reshape(-1)
+    for i, v in enumerate(edges):
+        j = 5 * i + 2
+        flatc[j] = 0.0
+        flat64[j] = -float(v)            # C - C64 = v exactly
+    out = b.tc_error_norm(m, n, dev(C), n, dev(C64), n, 1, dev(A), m, k, k, dev(B), k, n, n)
+    want = og.error_sums(C, C64, A, B)
+    for g, w in zip(out, want):
+        assert abs(g - w) <= 1e-12 * abs(w), (g, w)
+    assert out[3] == want[3]
+
+
+def test_error_norm_dev_is_the_host_call_bit_for_bit(b):
+    # the asynchronous form (device output, caller workspace) enqueues the same reduction
+    m, n, k = 300, 260, 72
+    C = synth.uniform((m, n), seed=93)
+    C64 = C.astype(np.float64) + synth.normal((m, n), seed=94).astype(np.float64) * 1e-5
+    A = synth.uniform((m, k), seed=95)
+    B = synth.uniform((k, n), seed=96)
+    args = (m, n, dev(C), n, dev(C64), n, 1, dev(A), m, k, k, dev(B), k, n, n)
+    want = b.tc_error_norm(*args)
+    ws_bytes = b.tc_error_norm_workspace_bytes()
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    out = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+    b.tc_error_norm_dev(*args, out, ws, ws_bytes)
+    got = tuple(host(out).tolist())
+    assert got == want
+    with pytest.raises(b.TcError) as e:
+        b.tc_error_norm_dev(*args, out, ws, ws_bytes - 8)
+    assert e.value.status == b.TC_ERR_INVALID
+
+
 def test_binding_enqueues_on_torchs_current_stream(b):
     # entry points called without a stream go to torch's current stream, including inside a
     # stream context (the binding reads it through torch's raw-stream query when available)

@@ -318,3 +318,59 @@ def test_bf16x3_alpha_beta():
     assert np.allclose(b_ - a, 0.5 * C0.astype(np.float64), rtol=0, atol=1e-14)
     assert np.array_equal(og.gemm_split_bf16x3(A, B, rows=[3, 1], cols=[0, 7]),
                           og.gemm_split_bf16x3(A, B)[[3, 1]][:, [0, 7]])
+
+
+def _int_codes(q, step_exp):
+    """q (FP64 values on a grid of 2^step_exp) -> Python ints q * 2^-step_exp."""
+    scaled = np.asarray(q, np.float64) * 2.0 ** (-step_exp)
+    ints = np.rint(scaled)
+    assert np.array_equal(ints, scaled)       # every value lies on the grid
+    return ints.astype(np.int64).astype(object)
+
+
+@pytest.mark.parametrize("K", [256, 512])
+def test_exact_integer_sums_pin_the_fp64_product_fp16(K):
+    # at the depths of the GPU parity tests: every FP16 value is an integer multiple of 2^-24, so the
+    # exact dot products are integers times 2^-48, summed here in Python integers.  With inputs in
+    # [2^-6, 1) every partial sum needs at most 48 - 32 + 9 + 1 < 53 bits: the FP64 product is exact.
+    # With the tests' uniform[-1,1] inputs it is within the FP64 summation bound K * 2^-53 * sum|ab|.
+    M = N = 12
+    mag = synth.uniform((M, K), seed=20, lo=0.0, hi=1.0) * 0.984375 + 0.015625
+    sgn = np.where(synth.uniform((M, K), seed=21) < 0, -1.0, 1.0)
+    A_narrow = (mag * sgn).astype(np.float32)
+    B_narrow = (synth.uniform((K, N), seed=22, lo=0.0, hi=1.0) * 0.984375 + 0.015625).astype(np.float32)
+    for A, B, exact_expected in ((A_narrow, B_narrow, True),
+                                 (synth.uniform((M, K), seed=23), synth.uniform((K, N), seed=24), False)):
+        got = og.gemm_mixed("f16", A, B)
+        ia = _int_codes(nm.round_to(A, "f16"), -24)
+        ib = _int_codes(nm.round_to(B, "f16"), -24)
+        S = ia.dot(ib)                                   # exact, Python integers
+        absS = np.abs(ia).dot(np.abs(ib))
+        for i in range(M):
+            for j in range(N):
+                exact = Fraction(int(S[i, j]), 2 ** 48)
+                if exact_expected:
+                    assert Fraction(got[i, j]) == exact
+                else:
+                    bound = Fraction(K, 2 ** 53) * Fraction(int(absS[i, j]), 2 ** 48)
+                    assert abs(Fraction(got[i, j]) - exact) <= bound
+
+
+@pytest.mark.parametrize("K", [256, 512])
+def test_exact_integer_sums_pin_the_fp64_product_e4m3(K):
+    # E4M3 codes (after the power-of-two scale) are multiples of 2^-9 below 448, so every partial sum
+    # of K <= 2^20 products is an integer times 2^-18 below 2^38: the FP64 product is exact, and so
+    # is the descale by the power-of-two scales
+    M, N = 10, 14
+    A = synth.uniform((M, K), seed=25) * 3.0
+    B = synth.uniform((K, N), seed=26) * 0.25
+    got = og.gemm_mixed("e4m3", A, B)
+    qa, sa = nm.quantize(A, "e4m3")
+    qb, sb = nm.quantize(B, "e4m3")
+    ia = _int_codes(qa, -9)
+    ib = _int_codes(qb, -9)
+    S = ia.dot(ib)
+    descale = Fraction(1) / (Fraction(float(sa)) * Fraction(float(sb)))
+    for i in range(M):
+        for j in range(N):
+            assert Fraction(got[i, j]) == Fraction(int(S[i, j]), 2 ** 18) * descale
