@@ -470,7 +470,14 @@ def measure_rows(b, A, B, pk, sm_count):
         del ws2
         e3 = res["split3_f16"]["error_vs_fp64"]["normwise"]
         es = res["sgemm_fp32_cuda_cores"]["error_vs_fp64"]["normwise"]
-        res["split3_vs_sgemm"] = {"speedup": res["sgemm_fp32_cuda_cores"]["ms"] / res["split3_f16"]["ms"],
+        # against the FP32 CUDA-core peak itself (152 SMs x 128 lanes x 2 FLOP x 2.07 GHz = 80.5 TFLOP/s), so
+        # the comparison does not rest on how fast the SIMT kernel is
+        fp32_peak = sm_count * 128 * 2 * 2.07e9 / 1e12
+        sg = res["sgemm_fp32_cuda_cores"]
+        sg["frac_of_fp32_peak_at_max_clock"] = sg["tflops"] / fp32_peak
+        res["split3_vs_sgemm"] = {"speedup": sg["ms"] / res["split3_f16"]["ms"],
+                                  "speedup_vs_fp32_peak": (flops / (fp32_peak * 1e12) * 1e3) / res["split3_f16"]["ms"],
+                                  "fp32_peak_tflops_at_max_clock": fp32_peak,
                                   "error_ratio": e3 / es}
         return res
 

@@ -368,11 +368,16 @@ tc_status gemm_grouped_ws(int32_t dt, int32_t count, const tc_problem* problems,
 /* Time gemm_mixed's kernel configurations for this shape on scratch operands
  * and remember the fastest for every later call of the same shape class in
  * this process.  Candidates: 128x256 tiles on single CTAs or 256x256 tiles on
- * CTA pairs (cluster of 2), each with raster bands of 8, 16 or 32 M-tiles.
- * A shape class is (dt, m, n, k) with each size rounded up to a power of two.
- * Allocates and frees stream-ordered scratch (cudaMallocAsync) and
- * synchronises `stream`.  *best_ms (host, may be NULL) receives the winner's
- * time.  TCGEMM_TILE / TCGEMM_GROUP_M, when set, still override the table. */
+ * CTA pairs (cluster of 2), each with raster bands of 4, 8, 16 or 32 M-tiles;
+ * then, for the best of those, a last partial round of pair tiles kept whole
+ * instead of cut into 256x128 halves, and K walked upwards in every round of
+ * tiles instead of downwards in odd rounds.  A shape class is (dt, m, n, k)
+ * with each size rounded up to a power of two.  The candidates are passed to
+ * the launches explicitly: calls of other threads keep their configuration
+ * until the winner is stored at the end.  Allocates and frees stream-ordered
+ * scratch (cudaMallocAsync) and synchronises `stream`.  *best_ms (host, may
+ * be NULL) receives the winner's time.  TCGEMM_TILE, TCGEMM_GROUP_M,
+ * TCGEMM_PAIR_TAIL and TCGEMM_K_ORDER, when set, still override the table. */
 tc_status tc_autotune_gemm(int32_t dt, int64_t m, int64_t n, int64_t k, void* stream, double* best_ms);
 
 /* Time the variants of a grouped plan on its own operands (the tensor-core
@@ -382,7 +387,9 @@ tc_status tc_autotune_gemm(int32_t dt, int64_t m, int64_t n, int64_t k, void* st
 tc_status gemm_grouped_plan_autotune(tc_grouped_plan* plan, const void* a_base, const void* b_base, float* c_base,
                                      void* stream, double* best_ms);
 
-/* Write / read the gemm_mixed autotune table (text, one shape class per line). */
+/* Write / read the gemm_mixed autotune table (text, one shape class per line:
+ * dt log2m log2n log2k pair group_m tail korder ms; lines without the tail and
+ * korder fields are read with both set to 1). */
 tc_status tc_autotune_save(const char* path);
 tc_status tc_autotune_load(const char* path);
 

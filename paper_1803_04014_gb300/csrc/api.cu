@@ -132,14 +132,18 @@ struct TuneKey {
         return dt != o.dt ? dt < o.dt : lm != o.lm ? lm < o.lm : ln != o.ln ? ln < o.ln : lk < o.lk;
     }
 };
+// A kernel configuration of gemm_mixed: 256 x 256 tiles on CTA pairs or 128 x 256 on single CTAs,
+// the raster band height in M-tiles, whether a last partial round of pair tiles is cut into
+// 256 x 128 halves, and whether odd rounds of tiles walk K downwards.
+struct GemmCfg {
+    int pair, group_m, tail, korder;
+};
 struct TuneCfg {
-    int pair, group_m;
+    GemmCfg cfg;
     double ms;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneCfg> g_tune;
-thread_local int g_force_pair = -1;   // set while the autotuner times a candidate
-thread_local int g_force_group = 0;
 
 int ceil_log2(int64_t v) {
     int l = 0;
@@ -149,6 +153,7 @@ int ceil_log2(int64_t v) {
 TuneKey tune_key(int dt, int64_t m, int64_t n, int64_t k) { return {dt, ceil_log2(m), ceil_log2(n), ceil_log2(k)}; }
 
 bool tune_lookup(int dt, int64_t m, int64_t n, int64_t k, TuneCfg* out) {
+    if (dt < 0) return false;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(tune_key(dt, m, n, k));
     if (it == g_tune.end()) return false;
@@ -160,12 +165,11 @@ bool tune_lookup(int dt, int64_t m, int64_t n, int64_t k, TuneCfg* out) {
 // the problem has at most 128 rows.  TCGEMM_TILE=single|pair forces one; the
 // autotune table (tc_autotune_gemm) overrides the default for its shapes.
 bool use_pair_tiles(int64_t m, int dt = -1, int64_t n = 0, int64_t k = 0) {
-    if (g_force_pair >= 0) return g_force_pair != 0;
     const char* env = getenv("TCGEMM_TILE");
     if (env && strcmp(env, "single") == 0) return false;
     if (env && strcmp(env, "pair") == 0) return true;
     TuneCfg c;
-    if (dt >= 0 && tune_lookup(dt, m, n, k, &c)) return c.pair != 0;
+    if (tune_lookup(dt, m, n, k, &c)) return c.cfg.pair != 0;
     return m > 128;
 }
 
@@ -183,13 +187,23 @@ int take_stall() {
 // it read 1.36-1.41 GB from DRAM per FP16 GEMM against 1.53 GB with bands of
 // 16 and 2.4 GB with bands of 2 or 32, at the same speed.
 int gemm_group_m(int dt = -1, int64_t m = 0, int64_t n = 0, int64_t k = 0) {
-    if (g_force_group > 0) return g_force_group;
     const char* env = getenv("TCGEMM_GROUP_M");
     const int v = env ? atoi(env) : 0;
     if (v >= 1 && v <= 1024) return v;
     TuneCfg c;
-    if (dt >= 0 && tune_lookup(dt, m, n, k, &c)) return c.group_m;
+    if (tune_lookup(dt, m, n, k, &c)) return c.cfg.group_m;
     return 8;
+}
+
+// A last round of pair tiles that would keep at most half of the CTA pairs busy runs as 256 x 128
+// halves (TCGEMM_PAIR_TAIL=full keeps whole tiles; the autotune table may choose either).
+int gemm_split_tail(int dt = -1, int64_t m = 0, int64_t n = 0, int64_t k = 0) {
+    const char* env = getenv("TCGEMM_PAIR_TAIL");
+    if (env && strcmp(env, "full") == 0) return 0;
+    if (env && strcmp(env, "split") == 0) return 1;
+    TuneCfg c;
+    if (tune_lookup(dt, m, n, k, &c)) return c.cfg.tail;
+    return 1;
 }
 
 // K order of the CTA-pair kernels.  A CTA pair takes every ncl-th tile of the raster, so its
@@ -198,9 +212,13 @@ int gemm_group_m(int dt = -1, int64_t m = 0, int64_t n = 0, int64_t k = 0) {
 // the round before it left in L2 (DRAM reads of the FP16 GEMM at N = 8192: 1.30 GB against 1.45
 // GB in one direction).  Each tile's order depends only on its place in the raster and the number
 // of CTA pairs, so results stay bitwise reproducible.  TCGEMM_K_ORDER=forward turns it off.
-int gemm_serpentine() {
+int gemm_serpentine(int dt = -1, int64_t m = 0, int64_t n = 0, int64_t k = 0) {
     const char* env = getenv("TCGEMM_K_ORDER");
-    return (env && strcmp(env, "forward") == 0) ? 0 : 1;
+    if (env && strcmp(env, "forward") == 0) return 0;
+    if (env && strcmp(env, "serpentine") == 0) return 1;
+    TuneCfg c;
+    if (tune_lookup(dt, m, n, k, &c)) return c.cfg.korder;
+    return 1;
 }
 
 // Epilogue of the pair GEMM: stage 32 x 32 chunks in shared memory (default) or store rows
@@ -337,9 +355,16 @@ tc_status tc_split_bf16x3(int64_t rows, int64_t cols, const float* src, int64_t 
     return split_entry("tc_split_bf16x3", 2, TC_BF16, rows, cols, src, ld_src, transpose, dst, 3, ld_dst, stream);
 }
 
-tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, const void* A, int64_t lda, int32_t la,
-                     const void* B, int64_t ldb, int32_t lb, float beta, float* C, int64_t ldc, const float* scale_a,
-                     const float* scale_b, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// gemm_mixed with its kernel configuration either resolved from the environment, the autotune
+// table and the defaults (force == NULL), or given explicitly (the autotuner's candidates), so
+// the autotuner changes nothing that another thread's calls see.
+tc_status gemm_mixed_impl(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, const void* A, int64_t lda,
+                          int32_t la, const void* B, int64_t ldb, int32_t lb, float beta, float* C, int64_t ldc,
+                          const float* scale_a, const float* scale_b, void* stream, const GemmCfg* force) {
     if (dt != TC_F16 && dt != TC_BF16 && dt != TC_E4M3) return fail(TC_ERR_INVALID, "gemm_mixed: bad dtype %d", dt);
     tc_status s = check_dims(m, n, k);
     if (s != TC_OK) return s;
@@ -371,12 +396,16 @@ tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, c
     p.ab_format = dt == TC_BF16 ? 1 : 0;
     p.na = p.nb = p.nprod = 1;
     p.bn = 256;
-    p.pair = (b_mn || use_pair_tiles(m, dt, n, k)) ? 1 : 0;   // the MN-major path exists on CTA pairs only
+    const GemmCfg cfg = force ? *force
+                              : GemmCfg{use_pair_tiles(m, dt, n, k) ? 1 : 0, gemm_group_m(dt, m, n, k),
+                                        gemm_split_tail(dt, m, n, k), gemm_serpentine(dt, m, n, k)};
+    p.pair = (b_mn || cfg.pair) ? 1 : 0;   // the MN-major path exists on CTA pairs only
     p.b_mn_major = b_mn ? 1 : 0;
-    p.group_m = gemm_group_m(dt, m, n, k);
+    p.group_m = cfg.group_m;
     p.stall_at = take_stall();
     p.staged_epilogue = gemm_staged_epilogue();
-    p.serpentine = gemm_serpentine();
+    p.split_tail = cfg.tail;
+    p.serpentine = cfg.korder;
     p.m = m; p.n = n; p.k = k;
     p.alpha = alpha; p.beta = beta;
     p.C = C; p.ldc = ldc;
@@ -392,6 +421,16 @@ tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, c
         return s;
     }
     return enqueue(tcg::launch_tc_gemm(ta, tb, p, st), "gemm_mixed launch");
+}
+
+}  // namespace
+
+extern "C" {
+
+tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha, const void* A, int64_t lda, int32_t la,
+                     const void* B, int64_t ldb, int32_t lb, float beta, float* C, int64_t ldc, const float* scale_a,
+                     const float* scale_b, void* stream) {
+    return gemm_mixed_impl(dt, m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ldc, scale_a, scale_b, stream, nullptr);
 }
 
 static int64_t split_kpad(int64_t k) { return (k + 7) / 8 * 8; }
@@ -546,6 +585,7 @@ tc_status split_gemm(const char* name, int scheme, int32_t piece, int32_t nprod,
         }
         p.group_m = gemm_group_m();
         p.stall_at = take_stall();
+        p.split_tail = gemm_split_tail();
         p.serpentine = gemm_serpentine();
         p.m = m; p.n = n; p.k = k;
         p.alpha = alpha; p.beta = beta;
@@ -1406,24 +1446,27 @@ tc_status tc_autotune_gemm(int32_t dt, int64_t m, int64_t n, int64_t k, void* st
     cudaMemsetAsync(C, 0, c_bytes, st);
     const float ones[2] = {1.0f, 1.0f};
     cudaMemcpyAsync(scales, ones, sizeof(ones), cudaMemcpyHostToDevice, st);
-    const int pairs[2] = {0, 1};
-    const int groups[3] = {8, 16, 32};
-    TuneCfg best{-1, 16, 1e30};
-    for (int pi = 0; pi < 2 && s == TC_OK; ++pi) {
-        if (pairs[pi] == 1 && m <= 128) continue;  // a pair tile would leave half of it empty
-        for (int gi = 0; gi < 3 && s == TC_OK; ++gi) {
-            g_force_pair = pairs[pi];
-            g_force_group = groups[gi];
-            double ms = 0;
-            s = time_ms([&] {
-                return gemm_mixed(dt, m, n, k, 1.0f, A, kp, TC_ROW_MAJOR, B, kp, TC_COL_MAJOR, 0.0f, C, n,
-                                  dt == TC_E4M3 ? scales : nullptr, dt == TC_E4M3 ? scales + 1 : nullptr, st);
-            }, st, 2, 5, &ms);
-            g_force_pair = -1;
-            g_force_group = 0;
-            if (s == TC_OK && ms < best.ms) best = {pairs[pi], groups[gi], ms};
-        }
+    // candidates are passed to the launch explicitly: nothing another thread's calls see changes
+    // until the winner is stored in the table at the end
+    auto time_cfg = [&](const GemmCfg& c, double* ms) {
+        return time_ms([&] {
+            return gemm_mixed_impl(dt, m, n, k, 1.0f, A, kp, TC_ROW_MAJOR, B, kp, TC_COL_MAJOR, 0.0f, C, n,
+                                   dt == TC_E4M3 ? scales : nullptr, dt == TC_E4M3 ? scales + 1 : nullptr, st, &c);
+        }, st, 2, 5, ms);
+    };
+    TuneCfg best{{1, 8, 1, 1}, 1e30};
+    auto consider = [&](const GemmCfg& c) {
+        double ms = 0;
+        if (s == TC_OK) s = time_cfg(c, &ms);
+        if (s == TC_OK && ms < best.ms) best = {c, ms};
+    };
+    // tile kind x raster band, then the tail split and the K order of the best of those
+    for (int pair = 0; pair < 2; ++pair) {
+        if (pair == 1 && m <= 128) continue;  // a pair tile would leave half of it empty
+        for (int g : {4, 8, 16, 32}) consider(GemmCfg{pair, g, 1, 1});
     }
+    if (best.cfg.pair) consider(GemmCfg{1, best.cfg.group_m, 0, best.cfg.korder});
+    consider(GemmCfg{best.cfg.pair, best.cfg.group_m, best.cfg.tail, 0});
     cudaFreeAsync(buf, st);
     cudaError_t e2 = cudaStreamSynchronize(st);
     if (s != TC_OK) return s;
@@ -1472,10 +1515,10 @@ tc_status tc_autotune_save(const char* path) {
     FILE* f = fopen(path, "w");
     if (!f) return fail(TC_ERR_INVALID, "tc_autotune_save: cannot open %s", path);
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    fprintf(f, "# tcgemm autotune: dt log2m log2n log2k pair group_m ms\n");
+    fprintf(f, "# tcgemm autotune: dt log2m log2n log2k pair group_m tail korder ms\n");
     for (const auto& kv : g_tune)
-        fprintf(f, "%d %d %d %d %d %d %.6f\n", kv.first.dt, kv.first.lm, kv.first.ln, kv.first.lk, kv.second.pair,
-                kv.second.group_m, kv.second.ms);
+        fprintf(f, "%d %d %d %d %d %d %d %d %.6f\n", kv.first.dt, kv.first.lm, kv.first.ln, kv.first.lk,
+                kv.second.cfg.pair, kv.second.cfg.group_m, kv.second.cfg.tail, kv.second.cfg.korder, kv.second.ms);
     fclose(f);
     return TC_OK;
 }
@@ -1490,11 +1533,26 @@ tc_status tc_autotune_load(const char* path) {
     while (fgets(line, sizeof(line), f)) {
         if (line[0] == '#') continue;
         TuneKey key;
-        TuneCfg cfg;
-        if (sscanf(line, "%d %d %d %d %d %d %lf", &key.dt, &key.lm, &key.ln, &key.lk, &cfg.pair, &cfg.group_m,
-                   &cfg.ms) == 7 &&
-            (cfg.pair == 0 || cfg.pair == 1) && cfg.group_m >= 1 && cfg.group_m <= 1024) {
-            g_tune[key] = cfg;
+        TuneCfg t{{0, 8, 1, 1}, 0.0};
+        int v[8];
+        double ms = 0;
+        // nine fields, or the seven of a table without the tail and K-order columns
+        const int got = sscanf(line, "%d %d %d %d %d %d %d %d %lf", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
+                               &v[7], &ms);
+        if (got == 9) {
+            t.cfg = {v[4], v[5], v[6], v[7]};
+            t.ms = ms;
+        } else if (sscanf(line, "%d %d %d %d %d %d %lf", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &ms) == 7) {
+            t.cfg = {v[4], v[5], 1, 1};
+            t.ms = ms;
+        } else {
+            continue;
+        }
+        key = {v[0], v[1], v[2], v[3]};
+        const GemmCfg& c = t.cfg;
+        if ((c.pair == 0 || c.pair == 1) && c.group_m >= 1 && c.group_m <= 1024 && (c.tail == 0 || c.tail == 1) &&
+            (c.korder == 0 || c.korder == 1)) {
+            g_tune[key] = t;
             ++n;
         }
     }

@@ -1190,10 +1190,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
         a.idesc = make_idesc(256, 256, static_cast<uint32_t>(p.ab_format));
         a.idesc_half = make_idesc(256, 128, static_cast<uint32_t>(p.ab_format));
         a.full_units = a.num_units = a.num_tiles;
-        {
-            const char* env = getenv("TCGEMM_PAIR_TAIL");
-            a.split_tail = (env && strcmp(env, "full") == 0) ? 0 : 1;
-        }
+        a.split_tail = p.split_tail;
         a.serpentine = p.serpentine;
         const int max_clusters = p.sm_count / 2;
         const int clusters = a.num_tiles < max_clusters ? a.num_tiles : max_clusters;

@@ -67,6 +67,8 @@ struct TcGemmLaunch {
     int corr_exp;       // pair kernel with promotion, s > 0: products 1.. (the corrections of a scaled
                         // split) accumulate apart and are multiplied by 2^-s in the epilogue
     int serpentine;     // pair kernels: every other round of tiles of a CTA pair walks K downwards
+    int split_tail;     // pair kernel: a last round of tiles keeping at most half of the pairs busy runs
+                        // as 256 x 128 halves
 };
 // tmA: 3-D map {k, m, na} with a 128 x (128 bytes) box; tmB: {k, n, nb} with a bn x (128 bytes) box.
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmLaunch& p, cudaStream_t st);

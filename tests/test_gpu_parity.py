@@ -655,6 +655,59 @@ def test_autotuned_gemm_still_matches_oracle(b, dt):
     assert normwise_dev(C, ref, A, B) <= TOL_NORMWISE
 
 
+def test_autotuning_on_one_thread_leaves_another_threads_gemms_alone(b):
+    # while one thread times candidate configurations of a shape class, another runs gemm_mixed on
+    # the same class: every result is the one of the configuration before the table was updated or
+    # the one after it (candidates are passed explicitly, never through state other threads read)
+    import threading
+    m, n, k = 1024, 1536, 1536   # > 76 tiles of 256 x 256: candidates differ in K order and tail
+    A = synth.uniform((m, k), seed=511)
+    B = synth.uniform((k, n), seed=512)
+    Ad, Bd = dev(A), dev(B)
+    Aq = torch.empty((m, k), dtype=torch.float16, device="cuda")
+    Bq = torch.empty((n, k), dtype=torch.float16, device="cuda")
+    b.tc_quantize(0, m, k, Ad, k, Aq, k, 0)
+    b.tc_quantize(0, k, n, Bd, n, Bq, k, 1)
+
+    def run(stream):
+        with torch.cuda.stream(stream):
+            C = torch.zeros((m, n), dtype=torch.float32, device="cuda")
+            b.gemm_mixed(0, m, n, k, 1.0, Aq, k, 0, Bq, k, 1, 0.0, C, n)
+        return C
+
+    s_main, s_side = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()   # the roundings above ran on the default stream
+    before = run(s_main)
+    torch.cuda.synchronize()
+    results, errors = [], []
+    stop = threading.Event()
+
+    def worker():
+        try:
+            while not stop.is_set():
+                results.append(run(s_side))
+                s_side.synchronize()
+        except Exception as e:  # surfaced below
+            errors.append(e)
+
+    t = threading.Thread(target=worker)
+    t.start()
+    try:
+        b.tc_autotune_gemm(0, m, n, k, stream=s_main.cuda_stream)
+    finally:
+        stop.set()
+        t.join()
+    after = run(s_main)
+    torch.cuda.synchronize()
+    b.tc_sync_status()
+    assert not errors, errors
+    assert len(results) >= 2
+    for r in results:
+        assert torch.equal(r, before) or torch.equal(r, after)
+    ref = og.gemm_mixed("f16", A, B)
+    assert normwise_dev(host(after), ref, A, B) <= TOL_NORMWISE
+
+
 def test_autotuned_grouped_plan_still_matches_oracle(b):
     probs, abuf, bbuf, csize = _grouped_case(120, seed=503, lb=1)
     desc = [p[:9] for p in probs]
