@@ -136,7 +136,7 @@ struct TuneKey {
 // the raster band height in M-tiles, whether a last partial round of pair tiles is cut into
 // 256 x 128 halves, and whether odd rounds of tiles walk K downwards.
 struct GemmCfg {
-    int pair, group_m, tail, korder;
+    int pair, group_m, tail, korder, cluster;  // cluster: 2 (one CTA pair) or 4 (two pairs sharing A)
 };
 struct TuneCfg {
     GemmCfg cfg;
@@ -212,6 +212,18 @@ int gemm_split_tail(int dt = -1, int64_t m = 0, int64_t n = 0, int64_t k = 0) {
 // the round before it left in L2 (DRAM reads of the FP16 GEMM at N = 8192: 1.30 GB against 1.45
 // GB in one direction).  Each tile's order depends only on its place in the raster and the number
 // of CTA pairs, so results stay bitwise reproducible.  TCGEMM_K_ORDER=forward turns it off.
+// CTAs per cluster of the pair kernel: 2 (one pair per 256 x 256 tile) or 4 (two pairs on adjacent
+// tiles of a row band, A multicast between them).  TCGEMM_CLUSTER=2|4 forces it; else the autotune
+// table; else 2.
+int gemm_cluster(int dt = -1, int64_t m = 0, int64_t n = 0, int64_t k = 0) {
+    const char* env = getenv("TCGEMM_CLUSTER");
+    if (env && strcmp(env, "4") == 0) return 4;
+    if (env && strcmp(env, "2") == 0) return 2;
+    TuneCfg c;
+    if (tune_lookup(dt, m, n, k, &c)) return c.cfg.cluster;
+    return 2;
+}
+
 int gemm_serpentine(int dt = -1, int64_t m = 0, int64_t n = 0, int64_t k = 0) {
     const char* env = getenv("TCGEMM_K_ORDER");
     if (env && strcmp(env, "forward") == 0) return 0;
@@ -398,7 +410,8 @@ tc_status gemm_mixed_impl(int32_t dt, int64_t m, int64_t n, int64_t k, float alp
     p.bn = 256;
     const GemmCfg cfg = force ? *force
                               : GemmCfg{use_pair_tiles(m, dt, n, k) ? 1 : 0, gemm_group_m(dt, m, n, k),
-                                        gemm_split_tail(dt, m, n, k), gemm_serpentine(dt, m, n, k)};
+                                        gemm_split_tail(dt, m, n, k), gemm_serpentine(dt, m, n, k),
+                                        gemm_cluster(dt, m, n, k)};
     p.pair = (b_mn || cfg.pair) ? 1 : 0;   // the MN-major path exists on CTA pairs only
     p.b_mn_major = b_mn ? 1 : 0;
     p.group_m = cfg.group_m;
@@ -406,6 +419,7 @@ tc_status gemm_mixed_impl(int32_t dt, int64_t m, int64_t n, int64_t k, float alp
     p.staged_epilogue = gemm_staged_epilogue();
     p.split_tail = cfg.tail;
     p.serpentine = cfg.korder;
+    p.quad = (p.pair && !b_mn && cfg.cluster == 4) ? 1 : 0;
     p.m = m; p.n = n; p.k = k;
     p.alpha = alpha; p.beta = beta;
     p.C = C; p.ldc = ldc;
@@ -413,7 +427,9 @@ tc_status gemm_mixed_impl(int32_t dt, int64_t m, int64_t n, int64_t k, float alp
     p.status = d->status;
     p.sm_count = d->sm_count;
     CUtensorMap ta, tb;
-    if ((s = encode_kmajor(&ta, tdt, esz, A, k, m, 1, lda * esz, m * lda * esz, 128)) != TC_OK) return s;
+    // the four-CTA kernel loads A in 64-row quarters (each multicast to two CTAs)
+    if ((s = encode_kmajor(&ta, tdt, esz, A, k, m, 1, lda * esz, m * lda * esz, p.quad ? 64 : 128)) != TC_OK)
+        return s;
     if (b_mn) {
         // dims {n, k}: boxes of 64 n (128 bytes) x 64 k rows
         if ((s = encode_kmajor(&tb, tdt, esz, B, n, k, 1, ldb * esz, k * ldb * esz, 64)) != TC_OK) return s;
@@ -1454,7 +1470,7 @@ tc_status tc_autotune_gemm(int32_t dt, int64_t m, int64_t n, int64_t k, void* st
                                    dt == TC_E4M3 ? scales : nullptr, dt == TC_E4M3 ? scales + 1 : nullptr, st, &c);
         }, st, 2, 5, ms);
     };
-    TuneCfg best{{1, 8, 1, 1}, 1e30};
+    TuneCfg best{{1, 8, 1, 1, 2}, 1e30};
     auto consider = [&](const GemmCfg& c) {
         double ms = 0;
         if (s == TC_OK) s = time_cfg(c, &ms);
@@ -1463,10 +1479,14 @@ tc_status tc_autotune_gemm(int32_t dt, int64_t m, int64_t n, int64_t k, void* st
     // tile kind x raster band, then the tail split and the K order of the best of those
     for (int pair = 0; pair < 2; ++pair) {
         if (pair == 1 && m <= 128) continue;  // a pair tile would leave half of it empty
-        for (int g : {4, 8, 16, 32}) consider(GemmCfg{pair, g, 1, 1});
+        for (int g : {4, 8, 16, 32}) consider(GemmCfg{pair, g, 1, 1, 2});
     }
-    if (best.cfg.pair) consider(GemmCfg{1, best.cfg.group_m, 0, best.cfg.korder});
-    consider(GemmCfg{best.cfg.pair, best.cfg.group_m, best.cfg.tail, 0});
+    if (best.cfg.pair) {
+        // clusters of four (A multicast between two pairs; whole tiles only) with each band height
+        for (int g : {4, 8, 16, 32}) consider(GemmCfg{1, g, 1, 1, 4});
+        if (best.cfg.cluster == 2) consider(GemmCfg{1, best.cfg.group_m, 0, best.cfg.korder, 2});
+    }
+    consider(GemmCfg{best.cfg.pair, best.cfg.group_m, best.cfg.tail, 0, best.cfg.cluster});
     cudaFreeAsync(buf, st);
     cudaError_t e2 = cudaStreamSynchronize(st);
     if (s != TC_OK) return s;
@@ -1515,10 +1535,11 @@ tc_status tc_autotune_save(const char* path) {
     FILE* f = fopen(path, "w");
     if (!f) return fail(TC_ERR_INVALID, "tc_autotune_save: cannot open %s", path);
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    fprintf(f, "# tcgemm autotune: dt log2m log2n log2k pair group_m tail korder ms\n");
+    fprintf(f, "# tcgemm autotune: dt log2m log2n log2k pair group_m tail korder cluster ms\n");
     for (const auto& kv : g_tune)
-        fprintf(f, "%d %d %d %d %d %d %d %d %.6f\n", kv.first.dt, kv.first.lm, kv.first.ln, kv.first.lk,
-                kv.second.cfg.pair, kv.second.cfg.group_m, kv.second.cfg.tail, kv.second.cfg.korder, kv.second.ms);
+        fprintf(f, "%d %d %d %d %d %d %d %d %d %.6f\n", kv.first.dt, kv.first.lm, kv.first.ln, kv.first.lk,
+                kv.second.cfg.pair, kv.second.cfg.group_m, kv.second.cfg.tail, kv.second.cfg.korder,
+                kv.second.cfg.cluster, kv.second.ms);
     fclose(f);
     return TC_OK;
 }
@@ -1533,17 +1554,17 @@ tc_status tc_autotune_load(const char* path) {
     while (fgets(line, sizeof(line), f)) {
         if (line[0] == '#') continue;
         TuneKey key;
-        TuneCfg t{{0, 8, 1, 1}, 0.0};
-        int v[8];
+        TuneCfg t{{0, 8, 1, 1, 2}, 0.0};
+        int v[9];
         double ms = 0;
-        // nine fields, or the seven of a table without the tail and K-order columns
-        const int got = sscanf(line, "%d %d %d %d %d %d %d %d %lf", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6],
-                               &v[7], &ms);
-        if (got == 9) {
-            t.cfg = {v[4], v[5], v[6], v[7]};
+        // ten fields, or the seven of a table without the tail, K-order and cluster columns
+        const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %lf", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5],
+                               &v[6], &v[7], &v[8], &ms);
+        if (got == 10) {
+            t.cfg = {v[4], v[5], v[6], v[7], v[8]};
             t.ms = ms;
         } else if (sscanf(line, "%d %d %d %d %d %d %lf", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &ms) == 7) {
-            t.cfg = {v[4], v[5], 1, 1};
+            t.cfg = {v[4], v[5], 1, 1, 2};
             t.ms = ms;
         } else {
             continue;
@@ -1551,7 +1572,7 @@ tc_status tc_autotune_load(const char* path) {
         key = {v[0], v[1], v[2], v[3]};
         const GemmCfg& c = t.cfg;
         if ((c.pair == 0 || c.pair == 1) && c.group_m >= 1 && c.group_m <= 1024 && (c.tail == 0 || c.tail == 1) &&
-            (c.korder == 0 || c.korder == 1)) {
+            (c.korder == 0 || c.korder == 1) && (c.cluster == 2 || c.cluster == 4)) {
             g_tune[key] = t;
             ++n;
         }

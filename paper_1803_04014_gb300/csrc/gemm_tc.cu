@@ -1195,6 +1195,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
         const int max_clusters = p.sm_count / 2;
         const int clusters = a.num_tiles < max_clusters ? a.num_tiles : max_clusters;
         if (clusters <= 0) return cudaSuccess;
+        if (p.quad && p.na == 1 && p.nb == 1 && !p.b_mn_major) return launch_tc_gemm_quad(tmA, tmB, p, st);
         if (p.kind == 1) {
             if (p.na == 1 && p.nb == 1) return run_pair<1, 6, 1, 1, 1>(tmA, tmB, a, max_clusters, st);
             return cudaErrorInvalidValue;

@@ -69,9 +69,14 @@ struct TcGemmLaunch {
     int serpentine;     // pair kernels: every other round of tiles of a CTA pair walks K downwards
     int split_tail;     // pair kernel: a last round of tiles keeping at most half of the pairs busy runs
                         // as 256 x 128 halves
+    int quad;           // one product, K-major B: clusters of four CTAs (two pairs) sharing A by TMA
+                        // multicast (gemm_quad.cu); tmA then has a 64-row box
 };
 // tmA: 3-D map {k, m, na} with a 128 x (128 bytes) box; tmB: {k, n, nb} with a bn x (128 bytes) box.
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmLaunch& p, cudaStream_t st);
+// ---- gemm_quad.cu: the pair GEMM on clusters of four CTAs, A multicast between the two pairs.
+cudaError_t launch_tc_gemm_quad(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmLaunch& p,
+                                cudaStream_t st);
 size_t tc_gemm_smem_bytes(int na, int nb, int bn, int* stages_out);
 
 // ---- split_fused.cu: refined GEMM reading FP32 A and B, pieces formed on chip (one launch).

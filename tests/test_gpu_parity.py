@@ -4,6 +4,8 @@ Rounding, scaling and splitting are compared bit for bit; GEMMs element by
 element within the FP32 accumulation bound and normwise within 1e-5 of the
 oracle's result on the same rounded inputs.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -655,10 +657,38 @@ def test_autotuned_gemm_still_matches_oracle(b, dt):
     assert normwise_dev(C, ref, A, B) <= TOL_NORMWISE
 
 
+@pytest.mark.parametrize("dt", [0, 1, 2])
+@pytest.mark.parametrize("mnk", [(512, 512, 512), (300, 770, 208), (1024, 1280, 1008), (2304, 2560, 640),
+                                 (256, 256, 64)])
+def test_gemm_on_clusters_of_four_sharing_a_by_multicast(b, monkeypatch, dt, mnk):
+    # TCGEMM_CLUSTER=4: two CTA pairs per cluster take adjacent tiles of a row band and multicast
+    # their A quarters to each other.  Shapes: one unit, ragged m/n/k with an odd number of tile
+    # columns (the second pair of the last unit has no tile), several rounds of units (odd rounds
+    # walk K downwards), a single tile.  Same tolerance as the pair kernel; with K walked upwards
+    # everywhere and whole tiles, equal to the pair kernel bit for bit (the products of a tile are
+    # issued in the same order)
+    m, n, k = mnk
+    A = synth.uniform((m, k), seed=521)
+    B = synth.uniform((k, n), seed=522)
+    C0 = synth.uniform((m, n), seed=523)
+    monkeypatch.setenv("TCGEMM_CLUSTER", "4")
+    got = _run_mixed(b, dt, A, B, beta=0.5, C0=C0)
+    ref = og.gemm_mixed(DT_NAME[dt], A, B, 1.0, 0.5, C0)
+    ok, info = elementwise_ok(got, ref, _mag(dt, A, B, 1.0, 0.5, C0), k)
+    assert ok, info
+    monkeypatch.setenv("TCGEMM_K_ORDER", "forward")
+    quad_fwd = _run_mixed(b, dt, A, B, beta=0.5, C0=C0)
+    monkeypatch.setenv("TCGEMM_CLUSTER", "2")
+    monkeypatch.setenv("TCGEMM_PAIR_TAIL", "full")
+    pair_fwd = _run_mixed(b, dt, A, B, beta=0.5, C0=C0)
+    assert np.array_equal(quad_fwd, pair_fwd)
+
+
 def test_autotuning_on_one_thread_leaves_another_threads_gemms_alone(b):
-    # while one thread times candidate configurations of a shape class, another runs gemm_mixed on
-    # the same class: every result is the one of the configuration before the table was updated or
-    # the one after it (candidates are passed explicitly, never through state other threads read)
+    # while one thread times candidate configurations of a shape class, another issues gemm_mixed on
+    # the same class: each call resolves its configuration when it is issued, and every result is
+    # the one of the configuration before the table was updated or the one after it (candidates are
+    # passed explicitly, never through state other threads read)
     import threading
     m, n, k = 1024, 1536, 1536   # > 76 tiles of 256 x 256: candidates differ in K order and tail
     A = synth.uniform((m, k), seed=511)
@@ -668,42 +698,41 @@ def test_autotuning_on_one_thread_leaves_another_threads_gemms_alone(b):
     Bq = torch.empty((n, k), dtype=torch.float16, device="cuda")
     b.tc_quantize(0, m, k, Ad, k, Aq, k, 0)
     b.tc_quantize(0, k, n, Bd, n, Bq, k, 1)
-
-    def run(stream):
-        with torch.cuda.stream(stream):
-            C = torch.zeros((m, n), dtype=torch.float32, device="cuda")
-            b.gemm_mixed(0, m, n, k, 1.0, Aq, k, 0, Bq, k, 1, 0.0, C, n)
-        return C
-
-    s_main, s_side = torch.cuda.Stream(), torch.cuda.Stream()
-    torch.cuda.synchronize()   # the roundings above ran on the default stream
-    before = run(s_main)
+    s_tune, s_call = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = [torch.zeros((m, n), dtype=torch.float32, device="cuda") for _ in range(65)]
     torch.cuda.synchronize()
-    results, errors = [], []
-    stop = threading.Event()
 
-    def worker():
+    def call(C):
+        with torch.cuda.stream(s_call):
+            b.gemm_mixed(0, m, n, k, 1.0, Aq, k, 0, Bq, k, 1, 0.0, C, n)
+
+    call(outs[0])                      # the configuration before tuning
+    errors = []
+
+    def tuner():
         try:
-            while not stop.is_set():
-                results.append(run(s_side))
-                s_side.synchronize()
+            b.tc_autotune_gemm(0, m, n, k, stream=s_tune.cuda_stream)
         except Exception as e:  # surfaced below
             errors.append(e)
 
-    t = threading.Thread(target=worker)
+    t = threading.Thread(target=tuner)
     t.start()
-    try:
-        b.tc_autotune_gemm(0, m, n, k, stream=s_main.cuda_stream)
-    finally:
-        stop.set()
-        t.join()
-    after = run(s_main)
+    issued_during = 0
+    i = 1
+    while i < len(outs) - 1 and t.is_alive():
+        call(outs[i])
+        issued_during += 1 if t.is_alive() else 0
+        i += 1
+        time.sleep(0.0005)
+    t.join()
+    call(outs[-1])                     # the configuration after tuning
     torch.cuda.synchronize()
     b.tc_sync_status()
     assert not errors, errors
-    assert len(results) >= 2
-    for r in results:
-        assert torch.equal(r, before) or torch.equal(r, after)
+    assert issued_during >= 1
+    before, after = outs[0], outs[-1]
+    for C in outs[1:i]:
+        assert torch.equal(C, before) or torch.equal(C, after)
     ref = og.gemm_mixed("f16", A, B)
     assert normwise_dev(host(after), ref, A, B) <= TOL_NORMWISE
 

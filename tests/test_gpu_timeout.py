@@ -33,9 +33,12 @@ def _operands(b, m, n, k, seed):
     return A, B, Aq, Bq
 
 
-@pytest.mark.parametrize("tile,mnk", [("single", (128, 256, 512)), ("pair", (512, 512, 512))])
+@pytest.mark.parametrize("tile,mnk", [("single", (128, 256, 512)), ("pair", (512, 512, 512)),
+                                      ("quad", (512, 1024, 512))])
 def test_stalled_gemm_times_out_and_the_context_survives(b, monkeypatch, tile, mnk):
-    monkeypatch.setenv("TCGEMM_TILE", tile)
+    # "quad": clusters of four CTAs (two pairs sharing A by multicast)
+    monkeypatch.setenv("TCGEMM_TILE", "pair" if tile == "quad" else tile)
+    monkeypatch.setenv("TCGEMM_CLUSTER", "4" if tile == "quad" else "2")
     m, n, k = mnk
     A, B, Aq, Bq = _operands(b, m, n, k, seed=5)
     b.tc_sync_status()
