@@ -486,6 +486,13 @@ tc_status serve_drain(tc_server* s, int64_t timeout_ms);
  * out[3] peak requests in flight, out[4] times admission waited for budget. */
 tc_status serve_stats(tc_server* s, int64_t* out5);
 
+/* Where the scheduler thread's time went, cumulative since serve_open: out6 =
+ * {retire ns (completion-event queries and arena release), admit ns (queue to
+ * workspace, event and stream), launch ns (the library calls that enqueue the
+ * kernels), launch groups (single requests and batches), event queries,
+ * completed requests}.  out6: host array of 6. */
+tc_status serve_timing(tc_server* s, int64_t* out6);
+
 /* Drain, stop the scheduler, free the arena and streams. */
 tc_status serve_close(tc_server* s);
 

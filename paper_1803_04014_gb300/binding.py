@@ -125,6 +125,7 @@ SIGNATURES = {
     "serve_poll": (_i32, [_vp, _u64, ctypes.POINTER(tc_result)]),
     "serve_drain": (_i32, [_vp, _i64]),
     "serve_stats": (_i32, [_vp, ctypes.POINTER(_i64)]),
+    "serve_timing": (_i32, [_vp, ctypes.POINTER(_i64)]),
     "serve_close": (_i32, [_vp]),
 }
 
@@ -442,6 +443,14 @@ def serve_poll(server, ticket):
         return None
     return {"status": res.status, "t_submit_us": res.t_submit_us, "t_start_us": res.t_start_us,
             "t_done_us": res.t_done_us}
+
+
+def serve_timing(server):
+    """Cumulative scheduler time by phase (ns), launch groups, event queries and completed requests."""
+    out = (_i64 * 6)()
+    _check(load().serve_timing(server, out), "serve_timing")
+    keys = ("retire_ns", "admit_ns", "launch_ns", "launch_groups", "event_queries", "completed")
+    return dict(zip(keys, (int(v) for v in out)))
 
 
 def serve_drain(server, timeout_ms=60_000):

@@ -173,3 +173,30 @@ def test_full_queue_reports_busy_and_tickets_are_forgotten_after_poll(b):
             b.serve_poll(srv, first)          # already reported, forgotten
     finally:
         b.serve_close(srv)
+
+
+def test_scheduler_timing_counters(b):
+    # serve_timing reports where the scheduler thread spent its time; after a drained stream every
+    # request is counted as completed and each phase took some time
+    reqs = _requests(24, seed=synth.seed_for(4, 30))
+    srv = b.serve_open(1 << 30, max_inflight=8, num_streams=4)
+    keep = []
+    try:
+        tickets = []
+        for (mode, A, B, C0) in reqs:
+            (m, k), n = A.shape, B.shape[1]
+            Ad, Bd, Cd = dev(A), dev(B), dev(C0)
+            keep.append((Ad, Bd, Cd))
+            t = None
+            while t is None:
+                t = b.serve_submit(srv, mode, m, n, k, Ad, k, Bd, n, Cd, n)
+            tickets.append(t)
+        b.serve_drain(srv, 60_000)
+        for t in tickets:
+            assert _wait(b, srv, t)["status"] == b.TC_OK
+        tm = b.serve_timing(srv)
+    finally:
+        b.serve_close(srv)
+    assert tm["completed"] == len(reqs)
+    assert tm["launch_ns"] > 0 and tm["admit_ns"] > 0 and tm["retire_ns"] > 0
+    assert 1 <= tm["launch_groups"] <= len(reqs)
