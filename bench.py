@@ -71,7 +71,7 @@ def kernel_sources_sha():
     """Hash of the GEMM kernel's code (comments and blank space removed, so editing a comment
     keeps a committed profile valid while any change of code invalidates it)."""
     h = hashlib.sha256()
-    for name in ("gemm_tc.cu", "tc_ptx.cuh"):
+    for name in ("gemm_tc.cu", "pair_sched.cuh", "tc_ptx.cuh"):
         with open(os.path.join(ROOT, "paper_1803_04014_gb300", "csrc", name)) as f:
             text = f.read()
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
@@ -80,8 +80,31 @@ def kernel_sources_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per GEMM launch from the committed ncu summary, if it matches the current kernel source."""
+# the untuned configuration of gemm_mixed at the headline size (tc_autotune_gemm's first candidate)
+DEFAULT_GEMM_CFG = {"pair": 1, "group_m": 8, "tail": 1, "korder": 1, "cluster": 2, "bn": 256}
+
+
+def kernel_name(cfg):
+    if not cfg["pair"]:
+        return f"k_tc_gemm (tcgen05.mma.cta_group::1, 128x{cfg['bn']} tiles per CTA)"
+    if cfg["cluster"] == 4:
+        return "k_tc_gemm_quad (clusters of two CTA pairs, A multicast between them)"
+    return "k_tc_gemm_pair (tcgen05.mma.cta_group::2, 256x256 tiles per CTA pair)"
+
+
+def headline_config(tune_table):
+    """The configuration gemm_mixed runs the headline FP16 GEMM in: the tuner's row for it, else
+    the untuned one."""
+    for r in tune_table:
+        if len(r) == 11 and r[0] == "0":
+            return {"pair": int(r[4]), "group_m": int(r[5]), "tail": int(r[6]), "korder": int(r[7]),
+                    "cluster": int(r[8]), "bn": int(r[9]) if r[4] == "0" else 256}
+    return dict(DEFAULT_GEMM_CFG)
+
+
+def profiled_traffic(cfg):
+    """DRAM bytes per GEMM launch from the committed ncu summary, if it was taken of the current
+    kernel source in the configuration the headline runs."""
     path = os.path.join(ROOT, "profiles", "gemm_mixed_f16_n8192.md")
     try:
         text = open(path).read()
@@ -89,7 +112,10 @@ def profiled_traffic():
         return None
     m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     m_s = re.search(r"kernel_sources_sha256:\s*([0-9a-f]+)", text)
+    m_c = re.search(r"kernel_config:\s*(.+)", text)
     if not m_b or not m_s or m_s.group(1) != kernel_sources_sha():
+        return None
+    if not m_c or dict(kv.split("=") for kv in m_c.group(1).split()) != {k: str(v) for k, v in cfg.items()}:
         return None
     return float(m_b.group(1))
 
@@ -148,6 +174,9 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--rows", choices=["all", "none"], default="all", help="also measure the other rows (N=1 only)")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="run the headline GEMM in its untuned configuration (for launch lists taken under a "
+                        "profiler, where the tuner's timings are not the program's)")
     p.add_argument("--profile-gemm", choices=["f16", "bf16", "e4m3", "split3", "split3_scaled", "bf16x3",
                                               "split3_one_launch", "split3_scaled_one_launch", "grouped",
                                               "grouped_rowmajor", "batched16", "batched16_250k", "quantize",
@@ -837,10 +866,13 @@ def main():
     pk = peaks()
     # pick the tile kernel (single CTA / CTA pair) and raster band for this shape before timing
     _progress("autotune")
-    tune_ms = b.tc_autotune_gemm(b.TC_F16, N, N, N)
-    with tempfile.NamedTemporaryFile(mode="r", suffix=".txt") as tf:
-        b.tc_autotune_save(tf.name)
-        tune_table = [l.split() for l in open(tf.name).read().splitlines() if l and not l.startswith("#")]
+    tune_ms, tune_table = None, []
+    if not args.no_autotune:
+        tune_ms = b.tc_autotune_gemm(b.TC_F16, N, N, N)
+        with tempfile.NamedTemporaryFile(mode="r", suffix=".txt") as tf:
+            b.tc_autotune_save(tf.name)
+            tune_table = [l.split() for l in open(tf.name).read().splitlines() if l and not l.startswith("#")]
+    gemm_cfg = headline_config(tune_table)
 
     A, B, C0 = workload_inputs()
     f32 = torch.float32
@@ -1057,8 +1089,9 @@ def main():
         "error_vs_fp64": {"normwise_rel_sampled": err_vs_fp64, "parity_vs_oracle_rel": parity_dev,
                           "sample": f"{len(srows)}x{len(scols)} entries"},
         "roofline": {"bound": "tensor", "achieved": gemm_tflops, "peak": peak, "unit": "TFLOP/s",
-                     "frac": gemm_tflops / peak, "traffic": profiled_traffic(),
-                     "kernel": "k_tc_gemm_pair (tcgen05.mma.cta_group::2, 256x256 tiles per CTA pair)",
+                     "frac": gemm_tflops / peak, "traffic": profiled_traffic(gemm_cfg),
+                     "kernel": kernel_name(gemm_cfg),
+                     "kernel_config": gemm_cfg,
                      "peak_source": f"{pk['source']} bf16 sustained (kernel timed inside the step loop)",
                      "frac_of_burst": gemm_tflops / pk["bf16_tflops"], "burst_peak": pk["bf16_tflops"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * N * N * 4,
@@ -1069,7 +1102,8 @@ def main():
                 "serial_ms_per_step": e2e_serial_ms, "serial_windows_ms_per_step": serial_windows,
                 "serial_value": world * flops / (e2e_serial_ms * 1e-3) / 1e12},
         "autotune": {"best_ms": tune_ms, "table": [" ".join(r) for r in tune_table],
-                     "fields": "dt log2m log2n log2k pair group_m ms"},
+                     "fields": "dt log2m log2n log2k pair group_m tail korder cluster bn ms",
+                     "skipped": bool(args.no_autotune)},
         "gpu_launches": 3 * K,
         "gpu_launches_note": "per step: 2 rounding kernels + 1 persistent GEMM",
         "clocks": clocks,

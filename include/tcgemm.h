@@ -157,7 +157,12 @@ tc_status tc_split_bf16x3(int64_t rows, int64_t cols, const float* src, int64_t 
  *   beta == 0: C is not read.  k == 0: C = beta*C.
  * Runs a persistent tcgen05 kernel: TMA-fed shared-memory ring, one thread
  * issuing the MMAs into a double-buffered TMEM accumulator, four epilogue
- * warps. */
+ * warps.  Untuned tiles: 256 x 256 on CTA pairs; 128 x 64 (else 128 x 128)
+ * on single CTAs when that many tiles fit on the SMs at once; single CTAs
+ * whenever m <= 128.  The kernel is launched with programmatic stream
+ * serialization: it may run its set-up while the previous kernel of the
+ * stream finishes and waits for it before touching A, B, C or the scales
+ * (TCGEMM_PDL=0 turns this off). */
 tc_status gemm_mixed(int32_t dt, int64_t m, int64_t n, int64_t k, float alpha,
                      const void* A, int64_t lda, int32_t la,
                      const void* B, int64_t ldb, int32_t lb,
@@ -367,17 +372,21 @@ tc_status gemm_grouped_ws(int32_t dt, int32_t count, const tc_problem* problems,
 
 /* Time gemm_mixed's kernel configurations for this shape on scratch operands
  * and remember the fastest for every later call of the same shape class in
- * this process.  Candidates: 128x256 tiles on single CTAs or 256x256 tiles on
- * CTA pairs (cluster of 2), each with raster bands of 4, 8, 16 or 32 M-tiles;
- * then, for the best of those, a last partial round of pair tiles kept whole
- * instead of cut into 256x128 halves, and K walked upwards in every round of
- * tiles instead of downwards in odd rounds.  A shape class is (dt, m, n, k)
- * with each size rounded up to a power of two.  The candidates are passed to
- * the launches explicitly: calls of other threads keep their configuration
- * until the winner is stored at the end.  Allocates and frees stream-ordered
- * scratch (cudaMallocAsync) and synchronises `stream`.  *best_ms (host, may
- * be NULL) receives the winner's time.  TCGEMM_TILE, TCGEMM_GROUP_M,
- * TCGEMM_PAIR_TAIL and TCGEMM_K_ORDER, when set, still override the table. */
+ * this process.  Candidates: 128 x 64, 128 x 128 and 128 x 256 tiles on single
+ * CTAs and 256 x 256 tiles on CTA pairs (cluster of 2), then raster bands of 4,
+ * 8, 16 or 32 M-tiles for the best of those; if pairs win, clusters of four
+ * CTAs (two pairs sharing A by TMA multicast) with each band height, and a
+ * last partial round of pair tiles kept whole instead of cut into 256 x 128
+ * halves; last, K walked upwards in every round of tiles instead of downwards
+ * in odd rounds.  The untuned configuration (see gemm_mixed) is timed first
+ * and a candidate replaces it only if more than 2 % faster.  A shape class is
+ * (dt, m, n, k) with each size rounded up to a power of two.  The candidates
+ * are passed to the launches explicitly: calls of other threads keep their
+ * configuration until the winner is stored at the end.  Allocates and frees
+ * stream-ordered scratch (cudaMallocAsync) and synchronises `stream`.
+ * *best_ms (host, may be NULL) receives the winner's time.  TCGEMM_TILE,
+ * TCGEMM_BN, TCGEMM_GROUP_M, TCGEMM_PAIR_TAIL, TCGEMM_K_ORDER and
+ * TCGEMM_CLUSTER, when set, still override the table. */
 tc_status tc_autotune_gemm(int32_t dt, int64_t m, int64_t n, int64_t k, void* stream, double* best_ms);
 
 /* Time the variants of a grouped plan on its own operands (the tensor-core
@@ -388,8 +397,10 @@ tc_status gemm_grouped_plan_autotune(tc_grouped_plan* plan, const void* a_base, 
                                      void* stream, double* best_ms);
 
 /* Write / read the gemm_mixed autotune table (text, one shape class per line:
- * dt log2m log2n log2k pair group_m tail korder ms; lines without the tail and
- * korder fields are read with both set to 1). */
+ * dt log2m log2n log2k pair group_m tail korder cluster bn ms; lines without
+ * the bn field are read with bn = 256, lines of the older form
+ * "dt log2m log2n log2k pair group_m ms" with tail = korder = 1, cluster = 2
+ * and bn = 256). */
 tc_status tc_autotune_save(const char* path);
 tc_status tc_autotune_load(const char* path);
 

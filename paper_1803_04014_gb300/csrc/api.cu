@@ -132,11 +132,13 @@ struct TuneKey {
         return dt != o.dt ? dt < o.dt : lm != o.lm ? lm < o.lm : ln != o.ln ? ln < o.ln : lk < o.lk;
     }
 };
-// A kernel configuration of gemm_mixed: 256 x 256 tiles on CTA pairs or 128 x 256 on single CTAs,
+// A kernel configuration of gemm_mixed: 256 x 256 tiles on CTA pairs or 128 x bn on single CTAs,
 // the raster band height in M-tiles, whether a last partial round of pair tiles is cut into
-// 256 x 128 halves, and whether odd rounds of tiles walk K downwards.
+// 256 x 128 halves, whether odd rounds of tiles walk K downwards, and the CTAs per cluster of the
+// pair kernel: 2 (one pair per tile) or 4 (two pairs on adjacent tiles of a row band, A multicast
+// between them).
 struct GemmCfg {
-    int pair, group_m, tail, korder, cluster;  // cluster: 2 (one CTA pair) or 4 (two pairs sharing A)
+    int pair, group_m, tail, korder, cluster, bn;
 };
 struct TuneCfg {
     GemmCfg cfg;
@@ -161,17 +163,78 @@ bool tune_lookup(int dt, int64_t m, int64_t n, int64_t k, TuneCfg* out) {
     return true;
 }
 
-// Tile choice of the tensor-core GEMM: 256 x 256 tiles on CTA pairs unless
-// the problem has at most 128 rows.  TCGEMM_TILE=single|pair forces one; the
-// autotune table (tc_autotune_gemm) overrides the default for its shapes.
-bool use_pair_tiles(int64_t m, int dt = -1, int64_t n = 0, int64_t k = 0) {
-    const char* env = getenv("TCGEMM_TILE");
-    if (env && strcmp(env, "single") == 0) return false;
-    if (env && strcmp(env, "pair") == 0) return true;
-    TuneCfg c;
-    if (tune_lookup(dt, m, n, k, &c)) return c.cfg.pair != 0;
-    return m > 128;
+// Untuned configuration of gemm_mixed for an m x n output.
+//   Tiles: 256 x 256 on CTA pairs, unless 128 x 64 (else 128 x 128) tiles on single CTAs number no
+//   more than the SMs: a problem that small is bound by the latency of each CTA's loads and
+//   epilogue, not by tensor throughput, and narrow tiles spread it over the most SMs (graph-replayed
+//   FP16 GEMMs with beta = 0.5: N = 256 6.3 us against 8.5 on one CTA pair, N = 1024 9.9 against
+//   12.3).  Problems of at most 128 rows always take single CTAs (a pair tile would be half empty).
+//   Raster bands of 8 M-tiles: the tiles in flight then span 8 M-tiles and about 10 N-tiles, the
+//   smallest A-band plus B-panel working set (DRAM reads of the FP16 GEMM at N = 8192: 1.36-1.41 GB
+//   against 1.53 GB with bands of 16 and 2.4 GB with bands of 2 or 32, at the same speed).
+//   A last round of pair tiles that would keep at most half of the CTA pairs busy runs as
+//   256 x 128 halves.
+//   K order: a CTA pair takes every ncl-th tile of the raster, so its i-th tile belongs to round i
+//   of tiles in flight together; consecutive rounds of a raster band share the band's A panels.
+//   Walking K downwards in odd rounds starts each round on the k-blocks the round before it left in
+//   L2 (DRAM reads at N = 8192: 1.30 GB against 1.45 GB in one direction).  Each tile's order
+//   depends only on its place in the raster and the number of CTA pairs, so results stay bitwise
+//   reproducible.
+//   Clusters of two CTAs.
+GemmCfg default_gemm_cfg(int64_t m, int64_t n, int sm_count) {
+    GemmCfg c{1, 8, 1, 1, 2, 256};
+    auto tiles = [&](int64_t bn) { return ((m + 127) / 128) * ((n + bn - 1) / bn); };
+    if (tiles(64) <= sm_count) {
+        c.pair = 0;
+        c.bn = 64;
+    } else if (tiles(128) <= sm_count) {
+        c.pair = 0;
+        c.bn = 128;
+    } else if (m <= 128) {
+        c.pair = 0;
+    }
+    return c;
 }
+
+// Environment overrides of a configuration: TCGEMM_TILE=single|pair, TCGEMM_BN=64|128|256 (single
+// CTAs), TCGEMM_GROUP_M, TCGEMM_PAIR_TAIL=full|split, TCGEMM_K_ORDER=forward|serpentine and
+// TCGEMM_CLUSTER=2|4.
+int env_choice(const char* name, const char* a, int va, const char* b, int vb, int dflt) {
+    const char* env = getenv(name);
+    if (env && strcmp(env, a) == 0) return va;
+    if (env && strcmp(env, b) == 0) return vb;
+    return dflt;
+}
+GemmCfg apply_env(GemmCfg c) {
+    const int pair = env_choice("TCGEMM_TILE", "single", 0, "pair", 1, c.pair);
+    if (pair != c.pair) c.bn = 256;
+    c.pair = pair;
+    if (const char* env = getenv("TCGEMM_BN")) {
+        const int v = atoi(env);
+        if (v == 64 || v == 128 || v == 256) c.bn = v;
+    }
+    if (const char* env = getenv("TCGEMM_GROUP_M")) {
+        const int v = atoi(env);
+        if (v >= 1 && v <= 1024) c.group_m = v;
+    }
+    c.tail = env_choice("TCGEMM_PAIR_TAIL", "full", 0, "split", 1, c.tail);
+    c.korder = env_choice("TCGEMM_K_ORDER", "forward", 0, "serpentine", 1, c.korder);
+    c.cluster = env_choice("TCGEMM_CLUSTER", "2", 2, "4", 4, c.cluster);
+    return c;
+}
+
+// The configuration a gemm_mixed call runs: the environment's overrides of the autotune table's
+// entry for the shape class, else of the untuned configuration.
+GemmCfg gemm_cfg_for(int dt, int64_t m, int64_t n, int64_t k, int sm_count) {
+    TuneCfg t;
+    return apply_env(tune_lookup(dt, m, n, k, &t) ? t.cfg : default_gemm_cfg(m, n, sm_count));
+}
+
+// Raster band, tail split and K order of the refined GEMMs (CTA pairs): the untuned values unless
+// overridden by the environment.
+int gemm_group_m() { return apply_env(GemmCfg{1, 8, 1, 1, 2, 256}).group_m; }
+int gemm_split_tail() { return apply_env(GemmCfg{1, 8, 1, 1, 2, 256}).tail; }
+int gemm_serpentine() { return apply_env(GemmCfg{1, 8, 1, 1, 2, 256}).korder; }
 
 // Pending failure-injection request of this thread (tc_debug_stall_next_gemm).
 thread_local int g_stall_next = 0;  // k-block + 1, 0 = none
@@ -179,58 +242,6 @@ int take_stall() {
     const int v = g_stall_next;
     g_stall_next = 0;
     return v;
-}
-
-// Tile raster band of the tensor-core GEMM in M-tiles (TCGEMM_GROUP_M, then the
-// autotune table, default 8).  The tiles in flight then span 8 M-tiles and
-// about 10 N-tiles, the smallest A-band plus B-panel working set: at N = 8192
-// it read 1.36-1.41 GB from DRAM per FP16 GEMM against 1.53 GB with bands of
-// 16 and 2.4 GB with bands of 2 or 32, at the same speed.
-int gemm_group_m(int dt = -1, int64_t m = 0, int64_t n = 0, int64_t k = 0) {
-    const char* env = getenv("TCGEMM_GROUP_M");
-    const int v = env ? atoi(env) : 0;
-    if (v >= 1 && v <= 1024) return v;
-    TuneCfg c;
-    if (tune_lookup(dt, m, n, k, &c)) return c.cfg.group_m;
-    return 8;
-}
-
-// A last round of pair tiles that would keep at most half of the CTA pairs busy runs as 256 x 128
-// halves (TCGEMM_PAIR_TAIL=full keeps whole tiles; the autotune table may choose either).
-int gemm_split_tail(int dt = -1, int64_t m = 0, int64_t n = 0, int64_t k = 0) {
-    const char* env = getenv("TCGEMM_PAIR_TAIL");
-    if (env && strcmp(env, "full") == 0) return 0;
-    if (env && strcmp(env, "split") == 0) return 1;
-    TuneCfg c;
-    if (tune_lookup(dt, m, n, k, &c)) return c.cfg.tail;
-    return 1;
-}
-
-// K order of the CTA-pair kernels.  A CTA pair takes every ncl-th tile of the raster, so its
-// i-th tile belongs to round i of tiles in flight together; consecutive rounds of a raster band
-// share the band's A panels.  Walking K downwards in odd rounds starts each round on the k-blocks
-// the round before it left in L2 (DRAM reads of the FP16 GEMM at N = 8192: 1.30 GB against 1.45
-// GB in one direction).  Each tile's order depends only on its place in the raster and the number
-// of CTA pairs, so results stay bitwise reproducible.  TCGEMM_K_ORDER=forward turns it off.
-// CTAs per cluster of the pair kernel: 2 (one pair per 256 x 256 tile) or 4 (two pairs on adjacent
-// tiles of a row band, A multicast between them).  TCGEMM_CLUSTER=2|4 forces it; else the autotune
-// table; else 2.
-int gemm_cluster(int dt = -1, int64_t m = 0, int64_t n = 0, int64_t k = 0) {
-    const char* env = getenv("TCGEMM_CLUSTER");
-    if (env && strcmp(env, "4") == 0) return 4;
-    if (env && strcmp(env, "2") == 0) return 2;
-    TuneCfg c;
-    if (tune_lookup(dt, m, n, k, &c)) return c.cfg.cluster;
-    return 2;
-}
-
-int gemm_serpentine(int dt = -1, int64_t m = 0, int64_t n = 0, int64_t k = 0) {
-    const char* env = getenv("TCGEMM_K_ORDER");
-    if (env && strcmp(env, "forward") == 0) return 0;
-    if (env && strcmp(env, "serpentine") == 0) return 1;
-    TuneCfg c;
-    if (tune_lookup(dt, m, n, k, &c)) return c.cfg.korder;
-    return 1;
 }
 
 // Epilogue of the pair GEMM: stage 32 x 32 chunks in shared memory (default) or store rows
@@ -408,11 +419,9 @@ tc_status gemm_mixed_impl(int32_t dt, int64_t m, int64_t n, int64_t k, float alp
     p.ab_format = dt == TC_BF16 ? 1 : 0;
     p.na = p.nb = p.nprod = 1;
     p.bn = 256;
-    const GemmCfg cfg = force ? *force
-                              : GemmCfg{use_pair_tiles(m, dt, n, k) ? 1 : 0, gemm_group_m(dt, m, n, k),
-                                        gemm_split_tail(dt, m, n, k), gemm_serpentine(dt, m, n, k),
-                                        gemm_cluster(dt, m, n, k)};
+    const GemmCfg cfg = force ? *force : gemm_cfg_for(dt, m, n, k, d->sm_count);
     p.pair = (b_mn || cfg.pair) ? 1 : 0;   // the MN-major path exists on CTA pairs only
+    if (!p.pair) p.bn = cfg.bn;
     p.b_mn_major = b_mn ? 1 : 0;
     p.group_m = cfg.group_m;
     p.stall_at = take_stall();
@@ -1470,23 +1479,33 @@ tc_status tc_autotune_gemm(int32_t dt, int64_t m, int64_t n, int64_t k, void* st
                                    dt == TC_E4M3 ? scales : nullptr, dt == TC_E4M3 ? scales + 1 : nullptr, st, &c);
         }, st, 2, 5, ms);
     };
-    TuneCfg best{{1, 8, 1, 1, 2}, 1e30};
-    auto consider = [&](const GemmCfg& c) {
-        double ms = 0;
-        if (s == TC_OK) s = time_cfg(c, &ms);
-        if (s == TC_OK && ms < best.ms) best = {c, ms};
+    // The untuned configuration is timed first and stays unless a candidate beats it by more than
+    // 2 %: single timings of one configuration scatter by about that much, and a pick made on noise
+    // would trade the default's lower DRAM traffic (serpentine K order) for nothing.
+    const GemmCfg dflt = default_gemm_cfg(m, n, d->sm_count);
+    TuneCfg best{dflt, 1e30};
+    auto same = [](const GemmCfg& x, const GemmCfg& y) {
+        return x.pair == y.pair && x.group_m == y.group_m && x.tail == y.tail && x.korder == y.korder &&
+               x.cluster == y.cluster && (x.pair || x.bn == y.bn);
     };
-    // tile kind x raster band, then the tail split and the K order of the best of those
-    for (int pair = 0; pair < 2; ++pair) {
-        if (pair == 1 && m <= 128) continue;  // a pair tile would leave half of it empty
-        for (int g : {4, 8, 16, 32}) consider(GemmCfg{pair, g, 1, 1, 2});
-    }
+    auto consider = [&](const GemmCfg& c) {
+        if (s != TC_OK || (best.ms < 1e30 && same(c, dflt))) return;
+        double ms = 0;
+        s = time_cfg(c, &ms);
+        if (s == TC_OK && (same(c, dflt) ? ms < best.ms : ms < 0.98 * best.ms)) best = {c, ms};
+    };
+    consider(dflt);
+    // tile kind and width (single CTAs 128 x 64 / 128 x 128 / 128 x 256, or pairs), then the raster
+    // band of the best of those; for pairs then clusters of four (A multicast between two pairs,
+    // whole tiles only) with each band, and the tail split; last the K order
+    for (int bn : {64, 128, 256}) consider(GemmCfg{0, 8, 1, 1, 2, bn});
+    if (m > 128) consider(GemmCfg{1, 8, 1, 1, 2, 256});  // a pair tile would leave half of it empty
+    for (int g : {4, 8, 16, 32}) consider(GemmCfg{best.cfg.pair, g, 1, 1, 2, best.cfg.bn});
     if (best.cfg.pair) {
-        // clusters of four (A multicast between two pairs; whole tiles only) with each band height
-        for (int g : {4, 8, 16, 32}) consider(GemmCfg{1, g, 1, 1, 4});
-        if (best.cfg.cluster == 2) consider(GemmCfg{1, best.cfg.group_m, 0, best.cfg.korder, 2});
+        for (int g : {4, 8, 16, 32}) consider(GemmCfg{1, g, 1, 1, 4, 256});
+        if (best.cfg.cluster == 2) consider(GemmCfg{1, best.cfg.group_m, 0, best.cfg.korder, 2, 256});
     }
-    consider(GemmCfg{best.cfg.pair, best.cfg.group_m, best.cfg.tail, 0, best.cfg.cluster});
+    consider(GemmCfg{best.cfg.pair, best.cfg.group_m, best.cfg.tail, 0, best.cfg.cluster, best.cfg.bn});
     cudaFreeAsync(buf, st);
     cudaError_t e2 = cudaStreamSynchronize(st);
     if (s != TC_OK) return s;
@@ -1535,11 +1554,11 @@ tc_status tc_autotune_save(const char* path) {
     FILE* f = fopen(path, "w");
     if (!f) return fail(TC_ERR_INVALID, "tc_autotune_save: cannot open %s", path);
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    fprintf(f, "# tcgemm autotune: dt log2m log2n log2k pair group_m tail korder cluster ms\n");
+    fprintf(f, "# tcgemm autotune: dt log2m log2n log2k pair group_m tail korder cluster bn ms\n");
     for (const auto& kv : g_tune)
-        fprintf(f, "%d %d %d %d %d %d %d %d %d %.6f\n", kv.first.dt, kv.first.lm, kv.first.ln, kv.first.lk,
+        fprintf(f, "%d %d %d %d %d %d %d %d %d %d %.6f\n", kv.first.dt, kv.first.lm, kv.first.ln, kv.first.lk,
                 kv.second.cfg.pair, kv.second.cfg.group_m, kv.second.cfg.tail, kv.second.cfg.korder,
-                kv.second.cfg.cluster, kv.second.ms);
+                kv.second.cfg.cluster, kv.second.cfg.bn, kv.second.ms);
     fclose(f);
     return TC_OK;
 }
@@ -1554,25 +1573,43 @@ tc_status tc_autotune_load(const char* path) {
     while (fgets(line, sizeof(line), f)) {
         if (line[0] == '#') continue;
         TuneKey key;
-        TuneCfg t{{0, 8, 1, 1, 2}, 0.0};
-        int v[9];
-        double ms = 0;
-        // ten fields, or the seven of a table without the tail, K-order and cluster columns
-        const int got = sscanf(line, "%d %d %d %d %d %d %d %d %d %lf", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5],
-                               &v[6], &v[7], &v[8], &ms);
-        if (got == 10) {
-            t.cfg = {v[4], v[5], v[6], v[7], v[8]};
-            t.ms = ms;
-        } else if (sscanf(line, "%d %d %d %d %d %d %lf", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &ms) == 7) {
-            t.cfg = {v[4], v[5], 1, 1, 2};
-            t.ms = ms;
+        TuneCfg t{{0, 8, 1, 1, 2, 256}, 0.0};
+        // whitespace-separated fields: integers, then the time; eleven of them, ten in a table
+        // without the tile width (256), seven in one without the tail, K-order, cluster and
+        // tile-width columns
+        int v[10];
+        int nf = 0;
+        bool bad = false;
+        char* save = nullptr;
+        for (char* tok = strtok_r(line, " \t\r\n", &save); tok; tok = strtok_r(nullptr, " \t\r\n", &save)) {
+            if (nf < 10 && strchr(tok, '.') == nullptr) {
+                char* end = nullptr;
+                const long x = strtol(tok, &end, 10);
+                if (*end != '\0' || x < -1000000 || x > 1000000) bad = true;
+                v[nf++] = static_cast<int>(x);
+            } else {
+                char* end = nullptr;
+                t.ms = strtod(tok, &end);
+                if (*end != '\0' || strtok_r(nullptr, " \t\r\n", &save) != nullptr) bad = true;
+                ++nf;
+                break;
+            }
+        }
+        if (bad) continue;
+        if (nf == 11) {
+            t.cfg = {v[4], v[5], v[6], v[7], v[8], v[9]};
+        } else if (nf == 10) {
+            t.cfg = {v[4], v[5], v[6], v[7], v[8], 256};
+        } else if (nf == 7) {
+            t.cfg = {v[4], v[5], 1, 1, 2, 256};
         } else {
             continue;
         }
         key = {v[0], v[1], v[2], v[3]};
         const GemmCfg& c = t.cfg;
         if ((c.pair == 0 || c.pair == 1) && c.group_m >= 1 && c.group_m <= 1024 && (c.tail == 0 || c.tail == 1) &&
-            (c.korder == 0 || c.korder == 1) && (c.cluster == 2 || c.cluster == 4)) {
+            (c.korder == 0 || c.korder == 1) && (c.cluster == 2 || c.cluster == 4) &&
+            (c.bn == 64 || c.bn == 128 || c.bn == 256)) {
             g_tune[key] = t;
             ++n;
         }

@@ -148,6 +148,9 @@ __global__ void __launch_bounds__(kQuadThreads, 1)
     cluster_sync();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // the set-up above overlaps the previous kernel of the stream; operands and C only from here on
+    griddep_wait();
+    griddep_launch_dependents();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -351,7 +354,7 @@ cudaError_t run_quad(const CUtensorMap& tmA, const CUtensorMap& tmB, const QuadA
     cfg.blockDim = dim3(kQuadThreads, 1, 1);
     cfg.dynamicSmemBytes = L::kBytes;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 4;
     attr[0].val.clusterDim.y = 1;
@@ -366,6 +369,7 @@ cudaError_t run_quad(const CUtensorMap& tmA, const CUtensorMap& tmB, const QuadA
         clusters = resident;
         cfg.gridDim = dim3(4 * clusters, 1, 1);
     }
+    add_pdl(cfg);
     return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, args);
 }
 

@@ -97,7 +97,8 @@ template <int KIND, int BN, int STAGES, int NA, int NB, int NPROD>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const Args a) {
     using L = Layout<BN, STAGES, NA, NB>;
-    static_assert(L::kTmemCols == 256 || L::kTmemCols == 512, "TMEM columns must be a power of two");
+    static_assert(L::kTmemCols == 128 || L::kTmemCols == 256 || L::kTmemCols == 512,
+                  "TMEM columns must be a power of two");
     constexpr int kElemBytes = (KIND == 1) ? 1 : 2;
     constexpr int BK = kRowBytes / kElemBytes;  // elements per k-block
     constexpr int kSteps = 4;                   // 4 MMAs of 32 bytes of K per k-block
@@ -141,6 +142,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // the set-up above overlaps the previous kernel of the stream; operands and C only from here on
+    griddep_wait();
+    griddep_launch_dependents();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -260,17 +264,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int t = blockIdx.x; t < a.num_tiles; t += gridDim.x) {
             int mb, nb;
             tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
-            const bool ok = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, a.status);
-            if (!__all_sync(0xffffffffu, ok)) break;
-            tc_fence_after();
             const int row = mb * BM + quarter * 32 + lane;
             const int col0 = nb * BN;
+            float* crow = a.C + static_cast<int64_t>(row) * a.ldc + col0;
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                    static_cast<uint32_t>(acc * BN);
-            float* crow = a.C + static_cast<int64_t>(row) * a.ldc + col0;
-#pragma unroll 1
-            for (int c = 0; c < BN; c += 32) {
-                if (col0 + c >= a.n) break;  // uniform across the warp
+            // old C of a whole 32-column chunk of this thread's row (the vector path's chunks only);
+            // the first two chunks are read before the accumulator is waited for, so their latency
+            // hides behind the main loop, and each later one two chunks ahead of its use
+            auto load_old = [&](int c, float4 (&o)[8]) {
+                if (c < BN && beta != 0.0f && vec_ok && row < a.m && col0 + c + 32 <= a.n) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) o[j] = *reinterpret_cast<const float4*>(crow + c + 4 * j);
+                }
+            };
+            auto store_chunk = [&](int c, const float4 (&o)[8]) {
                 float v[32];
                 tmem_load_32(taddr + c, v);
                 if (row < a.m) {
@@ -279,20 +287,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (ncols == 32 && vec_ok) {
 #pragma unroll
                         for (int j = 0; j < 8; ++j) {
-                            float4 o;
+                            float4 r;
                             if (beta != 0.0f) {
-                                const float4 old = *reinterpret_cast<const float4*>(p + 4 * j);
-                                o.x = fmaf(alpha, v[4 * j + 0], beta * old.x);
-                                o.y = fmaf(alpha, v[4 * j + 1], beta * old.y);
-                                o.z = fmaf(alpha, v[4 * j + 2], beta * old.z);
-                                o.w = fmaf(alpha, v[4 * j + 3], beta * old.w);
+                                r.x = fmaf(alpha, v[4 * j + 0], beta * o[j].x);
+                                r.y = fmaf(alpha, v[4 * j + 1], beta * o[j].y);
+                                r.z = fmaf(alpha, v[4 * j + 2], beta * o[j].z);
+                                r.w = fmaf(alpha, v[4 * j + 3], beta * o[j].w);
                             } else {
-                                o.x = alpha * v[4 * j + 0];
-                                o.y = alpha * v[4 * j + 1];
-                                o.z = alpha * v[4 * j + 2];
-                                o.w = alpha * v[4 * j + 3];
+                                r.x = alpha * v[4 * j + 0];
+                                r.y = alpha * v[4 * j + 1];
+                                r.z = alpha * v[4 * j + 2];
+                                r.w = alpha * v[4 * j + 3];
                             }
-                            *reinterpret_cast<float4*>(p + 4 * j) = o;
+                            *reinterpret_cast<float4*>(p + 4 * j) = r;
                         }
                     } else {
 #pragma unroll
@@ -301,6 +308,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                 }
+            };
+            float4 o0[8], o1[8];
+            load_old(0, o0);
+            load_old(32, o1);
+            const bool ok = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, a.status);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+#pragma unroll
+            for (int c = 0; c < BN; c += 64) {
+                if (col0 + c >= a.n) break;  // uniform across the warp
+                store_chunk(c, o0);
+                load_old(c + 64, o0);
+                if (c + 32 >= BN || col0 + c + 32 >= a.n) break;
+                store_chunk(c + 32, o1);
+                load_old(c + 96, o1);
             }
             tc_fence_before();
             __syncwarp();
@@ -324,8 +346,16 @@ cudaError_t run(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args& args
     auto kern = k_tc_gemm<KIND, BN, STAGES, NA, NB, NPROD>;
     cudaError_t e = kernel_setup(reinterpret_cast<const void*>(kern), L::kBytes, nullptr, 0, nullptr);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kThreads, L::kBytes, st>>>(tmA, tmB, args);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = L::kBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    cfg.attrs = attr;
+    cfg.numAttrs = 0;
+    add_pdl(cfg);
+    return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, args);
 }
 
 
@@ -414,6 +444,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     cluster_sync();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // the set-up above overlaps the previous kernel of the stream; operands and C only from here on
+    griddep_wait();
+    griddep_launch_dependents();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -561,9 +594,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int u = cid; u < a.num_units; u += ncl) {
             int mb, nb, coff, width;
             unit_coords(a, u, mb, nb, coff, width);
-            const bool ok = wait(tfull_bar(acc), acc_phase);
-            if (!__all_sync(0xffffffffu, ok)) break;
-            tc_fence_after();
             const int row = mb * PM + static_cast<int>(rank) * 128 + quarter * 32 + lane;
             const int col0 = nb * PN + coff;
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
@@ -575,22 +605,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float* stg = reinterpret_cast<float*>(base_ptr + L::kEpiOffset) + (warp - 2) * (32 * 33);
                 const int r0 = row - lane;
                 const int cc = (lane & 7) * 4;
-#pragma unroll 1
-                for (int c = 0; c < width; c += 32) {
-                    if (col0 + c >= a.n) break;
+                // old C of chunk c, in the store pattern (rows r0 + 4q + lane / 8, columns cc..cc+3):
+                // the first two chunks are read before the accumulator is waited for, so their latency
+                // hides behind the main loop, and each later one two chunks ahead of its use
+                auto load_old = [&](int c, float4 (&o)[8]) {
+                    if (beta == 0.0f || c >= width || col0 + c >= a.n) return;
                     const int nc = min(32, a.n - (col0 + c));
-                    // old C of this chunk first: its global-memory latency overlaps the TMEM load
-                    float4 old[8];
-                    if (beta != 0.0f) {
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const int grow = r0 + q * 4 + (lane >> 3);
-                            old[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                            if (grow < a.m && vec_ok && cc + 4 <= nc)
-                                old[q] = *reinterpret_cast<const float4*>(a.C + static_cast<int64_t>(grow) * a.ldc +
-                                                                          col0 + c + cc);
-                        }
+                    for (int q = 0; q < 8; ++q) {
+                        const int grow = r0 + q * 4 + (lane >> 3);
+                        o[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (grow < a.m && vec_ok && cc + 4 <= nc)
+                            o[q] = *reinterpret_cast<const float4*>(a.C + static_cast<int64_t>(grow) * a.ldc +
+                                                                    col0 + c + cc);
                     }
+                };
+                auto store_chunk = [&](int c, const float4 (&old)[8]) {
+                    const int nc = min(32, a.n - (col0 + c));
                     float v[32];
                     tmem_load_32(taddr + c, v);
 #pragma unroll
@@ -620,6 +651,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                     __syncwarp();
+                };
+                float4 o0[8], o1[8];
+                load_old(0, o0);
+                load_old(32, o1);
+                const bool ok = wait(tfull_bar(acc), acc_phase);
+                if (!__all_sync(0xffffffffu, ok)) break;
+                tc_fence_after();
+#pragma unroll 1
+                for (int c = 0; c < width; c += 64) {
+                    if (col0 + c >= a.n) break;
+                    store_chunk(c, o0);
+                    load_old(c + 64, o0);
+                    if (c + 32 >= width || col0 + c + 32 >= a.n) break;
+                    store_chunk(c + 32, o1);
+                    load_old(c + 96, o1);
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -628,6 +674,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (acc == 0) acc_phase ^= 1u;
                 continue;
             }
+            const bool ok = wait(tfull_bar(acc), acc_phase);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
 #pragma unroll 1
             for (int c = 0; c < width; c += 32) {
                 if (col0 + c >= a.n) break;
@@ -691,7 +740,7 @@ cudaError_t run_pair(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args&
     cfg.blockDim = dim3(kThreads, 1, 1);
     cfg.dynamicSmemBytes = L::kBytes;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
@@ -716,6 +765,7 @@ cudaError_t run_pair(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args&
         clusters = a.num_units;
         cfg.gridDim = dim3(2 * clusters, 1, 1);
     }
+    add_pdl(cfg);
     return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, a);
 }
 
@@ -808,6 +858,9 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
     cluster_sync();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // the set-up above overlaps the previous kernel of the stream; operands and C only from here on
+    griddep_wait();
+    griddep_launch_dependents();
 
     if (warp == 0) {
         if (lane == 0) {
@@ -1134,7 +1187,7 @@ cudaError_t run_pair_promote(const CUtensorMap& tmA, const CUtensorMap& tmB, con
     cfg.blockDim = dim3(kPromoteThreads, 1, 1);
     cfg.dynamicSmemBytes = L::kBytes;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
@@ -1148,6 +1201,7 @@ cudaError_t run_pair_promote(const CUtensorMap& tmA, const CUtensorMap& tmB, con
         clusters = resident;
         cfg.gridDim = dim3(2 * clusters, 1, 1);
     }
+    add_pdl(cfg);
     return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, args);
 }
 }  // namespace
@@ -1251,11 +1305,17 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
     const int grid = a.num_tiles < p.sm_count ? a.num_tiles : p.sm_count;
     if (grid <= 0) return cudaSuccess;
 
+    // one product: 128 x 256 tiles, or 128 x 128 / 128 x 64 for problems too small to fill the SMs
+    // with wide tiles (same 192 KB of stages, deeper rings)
     if (p.kind == 1) {
         if (p.na == 1 && p.nb == 1 && p.bn == 256) return run<1, 256, 4, 1, 1, 1>(tmA, tmB, a, grid, st);
+        if (p.na == 1 && p.nb == 1 && p.bn == 128) return run<1, 128, 6, 1, 1, 1>(tmA, tmB, a, grid, st);
+        if (p.na == 1 && p.nb == 1 && p.bn == 64) return run<1, 64, 8, 1, 1, 1>(tmA, tmB, a, grid, st);
         return cudaErrorInvalidValue;
     }
     if (p.na == 1 && p.nb == 1 && p.bn == 256) return run<0, 256, 4, 1, 1, 1>(tmA, tmB, a, grid, st);
+    if (p.na == 1 && p.nb == 1 && p.bn == 128) return run<0, 128, 6, 1, 1, 1>(tmA, tmB, a, grid, st);
+    if (p.na == 1 && p.nb == 1 && p.bn == 64) return run<0, 64, 8, 1, 1, 1>(tmA, tmB, a, grid, st);
     if (p.na == 2 && p.nb == 1 && p.nprod == 2 && p.bn == 256) return run<0, 256, 3, 2, 1, 2>(tmA, tmB, a, grid, st);
     if (p.na == 2 && p.nb == 2 && p.nprod == 3 && p.bn == 128) return run<0, 128, 3, 2, 2, 3>(tmA, tmB, a, grid, st);
     if (p.na == 2 && p.nb == 2 && p.nprod == 4 && p.bn == 128) return run<0, 128, 3, 2, 2, 4>(tmA, tmB, a, grid, st);

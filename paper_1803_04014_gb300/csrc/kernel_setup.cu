@@ -5,6 +5,8 @@
 // calculator) are host-side calls of a few microseconds each.  A served
 // stream of small GEMMs launches thousands of kernels per second, so the
 // answers are computed once per (kernel, device) and kept.
+#include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -21,6 +23,14 @@ struct Entry {
 std::mutex g_mu;
 std::map<std::pair<const void*, int>, Entry> g_cache;
 }  // namespace
+
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* env = getenv("TCGEMM_PDL");
+        return !(env && strcmp(env, "0") == 0);
+    }();
+    return on;
+}
 
 cudaError_t kernel_setup(const void* kern, int smem_bytes, const cudaLaunchConfig_t* cluster_cfg, int block_threads,
                          int* resident) {

@@ -42,6 +42,19 @@ cudaError_t launch_quantize_jobs(int dt, const QuantJobDev* jobs, const QuantTil
 cudaError_t kernel_setup(const void* kern, int smem_bytes, const cudaLaunchConfig_t* cluster_cfg, int block_threads,
                          int* resident);
 
+// Programmatic stream serialization for a GEMM launch: the kernel may be placed on SMs and run its
+// set-up (barriers, TMEM allocation, tensor-map prefetch) while the kernel before it in the stream
+// finishes; it waits for that kernel (griddepcontrol.wait) before touching any operand.  On unless
+// TCGEMM_PDL=0.  add_pdl appends the attribute to cfg.attrs, which must have room for one more.
+bool pdl_enabled();
+inline void add_pdl(cudaLaunchConfig_t& cfg) {
+    if (!pdl_enabled()) return;
+    cudaLaunchAttribute& at = cfg.attrs[cfg.numAttrs];
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    ++cfg.numAttrs;
+}
+
 // ---- gemm_tc.cu
 struct TcGemmLaunch {
     int kind;           // 0: 16-bit inputs (F16/BF16), 1: E4M3

@@ -355,6 +355,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     cluster_sync();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // the set-up above overlaps the previous kernel of the stream; operands and C only from here on
+    griddep_wait();
+    griddep_launch_dependents();
 
     const int wg = warp >> 2;
     if (wg == 1 || wg == 2) {
@@ -707,7 +710,7 @@ cudaError_t run_fused(const CUtensorMap& tmA, const CUtensorMap& tmB, const Fuse
     cfg.blockDim = dim3(kFusedThreads, 1, 1);
     cfg.dynamicSmemBytes = L::kBytes;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
@@ -721,6 +724,7 @@ cudaError_t run_fused(const CUtensorMap& tmA, const CUtensorMap& tmB, const Fuse
         clusters = resident;
         cfg.gridDim = dim3(2 * clusters, 1, 1);
     }
+    add_pdl(cfg);
     return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, args);
 }
 

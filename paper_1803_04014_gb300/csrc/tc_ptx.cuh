@@ -21,6 +21,14 @@ __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may start
+// while the kernel before it in the stream is still running; griddep_wait blocks until that kernel
+// has completed and its memory is visible, so everything before it may touch only this CTA's own
+// shared memory, TMEM and kernel parameters.  griddep_launch_dependents lets the next such kernel
+// start placing its CTAs on SMs this grid leaves free.  Both are no-ops for a normal launch.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ uint64_t global_timer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -143,20 +143,26 @@ def test_serve_rejects_bad_config(lib):
 def test_autotune_table_save_and_load(lib, tmp_path):
     from paper_1803_04014_gb300 import binding as b
     good = tmp_path / "tune.txt"
-    # lines of the current format (pair, group_m, tail, korder, cluster) and one of the older
-    # seven-field format, which reads as tail = 1, korder = 1, cluster = 2
-    good.write_text("# comment\n0 13 13 13 1 16 0 1 4 0.65\n1 10 10 10 0 8 0.01\n2 12 12 12 1 4 1 0 2 0.2\n")
+    # lines of the current format (pair, group_m, tail, korder, cluster, bn), of the ten-field
+    # format without bn (read as bn = 256) and of the older seven-field format (tail = 1,
+    # korder = 1, cluster = 2, bn = 256)
+    good.write_text("# comment\n0 13 13 13 1 16 0 1 4 256 0.65\n1 10 10 10 0 8 0.01\n2 12 12 12 1 4 1 0 2 0.2\n"
+                    "0 8 8 8 0 8 1 1 2 64 0.004\n")
     b.tc_autotune_load(good)
     out = tmp_path / "out.txt"
     b.tc_autotune_save(out)
     lines = [l for l in out.read_text().splitlines() if not l.startswith("#")]
-    assert any(l.startswith("0 13 13 13 1 16 0 1 4 ") for l in lines)
-    assert any(l.startswith("1 10 10 10 0 8 1 1 2 ") for l in lines)
-    assert any(l.startswith("2 12 12 12 1 4 1 0 2 ") for l in lines)
-    for text in ("0 13 13 13 7 16 0.5\n",             # pair must be 0 or 1
-                 "0 13 13 13 1 16 2 1 2 0.5\n",       # tail must be 0 or 1
-                 "0 13 13 13 1 16 1 5 2 0.5\n",       # korder must be 0 or 1
-                 "0 13 13 13 1 16 1 1 3 0.5\n"):      # cluster must be 2 or 4
+    assert any(l.startswith("0 13 13 13 1 16 0 1 4 256 ") for l in lines)
+    assert any(l.startswith("1 10 10 10 0 8 1 1 2 256 ") for l in lines)
+    assert any(l.startswith("2 12 12 12 1 4 1 0 2 256 ") for l in lines)
+    assert any(l.startswith("0 8 8 8 0 8 1 1 2 64 ") for l in lines)
+    for text in ("0 13 13 13 7 16 0.5\n",               # pair must be 0 or 1
+                 "0 13 13 13 1 16 2 1 2 0.5\n",         # tail must be 0 or 1
+                 "0 13 13 13 1 16 1 5 2 0.5\n",         # korder must be 0 or 1
+                 "0 13 13 13 1 16 1 1 3 0.5\n",         # cluster must be 2 or 4
+                 "0 13 13 13 0 16 1 1 2 96 0.5\n",      # bn must be 64, 128 or 256
+                 "0 13 13 13 0 16 1 1 2 64 0.5 7\n",    # nothing after the time
+                 "0 13 13 x 0 16 1 1 2 64 0.5\n"):      # fields are numbers
         bad = tmp_path / "bad.txt"
         bad.write_text(text)
         with pytest.raises(b.TcError):

@@ -507,8 +507,8 @@ def test_gemm_tile_kernels(b, monkeypatch, tile, dt, mnk):
 @pytest.mark.parametrize("dt", [0, 1, 2])
 @pytest.mark.parametrize("mnk", [(256, 256, 256), (1024, 1024, 1024), (1536, 1400, 208)])
 def test_gemm_default_tiles_at_small_sizes(b, dt, mnk):
-    # the small square sizes of the sweep with the default tile choice (CTA pairs, grids of
-    # 1, 16 and 36 pairs)
+    # small sizes with the untuned tile choice: 8 and 128 single-CTA tiles of 128 x 64, and 132
+    # of 128 x 128
     m, n, k = mnk
     A = synth.uniform((m, k), seed=151)
     B = synth.uniform((k, n), seed=152)
