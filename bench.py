@@ -177,7 +177,7 @@ def parse_args():
     p.add_argument("--no-autotune", action="store_true",
                    help="run the headline GEMM in its untuned configuration (for launch lists taken under a "
                         "profiler, where the tuner's timings are not the program's)")
-    p.add_argument("--profile-gemm", choices=["f16", "bf16", "e4m3", "split3", "split3_scaled", "bf16x3",
+    p.add_argument("--profile-gemm", choices=["f16", "f16_n1024", "bf16", "e4m3", "split3", "split3_scaled", "bf16x3",
                                               "split3_one_launch", "split3_scaled_one_launch", "grouped",
                                               "grouped_rowmajor", "batched16", "batched16_250k", "quantize",
                                               "errnorm"], default=None,
@@ -804,6 +804,21 @@ def profile_case(kind):
             b.gemm_batched_strided(0, batch, 16, 16, 16, 1.0, Ab, 256, 0, Bb, 256, 0, 0.0, Cb, 256)
         b.tc_sync_status()
         print(json.dumps({"profile_case": kind, "batch": batch, "launches": 5}))
+        return 0
+    if kind == "f16_n1024":
+        # a sweep size that single CTAs with 128 x 64 tiles cover in one round (128 tiles); operands
+        # stay in L2, as they do when such GEMMs follow one another
+        n_ = 1024
+        X = torch.empty((n_, n_), dtype=torch.float32, device="cuda").uniform_(-1, 1)
+        Aq = torch.empty((n_, n_), dtype=torch.float16, device="cuda")
+        Bq = torch.empty((n_, n_), dtype=torch.float16, device="cuda")
+        b.tc_quantize(0, n_, n_, X, n_, Aq, n_, 0)
+        b.tc_quantize(0, n_, n_, X, n_, Bq, n_, 1)
+        C = torch.empty((n_, n_), dtype=torch.float32, device="cuda").uniform_(-1, 1)
+        for _ in range(10):
+            b.gemm_mixed(0, n_, n_, n_, 1.0, Aq, n_, 0, Bq, n_, 1, 0.5, C, n_)
+        b.tc_sync_status()
+        print(json.dumps({"profile_case": kind, "n": n_, "launches": 10}))
         return 0
     A = torch.from_numpy(synth.uniform((N, N), seed=synth.seed_for(1, 0))).cuda()
     B = torch.from_numpy(synth.uniform((N, N), seed=synth.seed_for(1, 1))).cuda()
