@@ -641,8 +641,11 @@ def measure_serve(b, count=50000, budget=40 << 30):
     for rho, fixed in ((0.5, None), (0.95, None), (None, 20000.0)):
         r = _serve_stream(b, count, budget, rho=rho, fixed_rate=fixed, capacity=capacity)
         loads.append({"rho": rho, "offered_rate_per_s": r["offered_rate_per_s"], "p50_ms": r["p50_ms"],
-                      "p99_ms": r["p99_ms"], "tflops": r["tflops"], "wall_s": r["wall_s"]})
+                      "p99_ms": r["p99_ms"], "p999_ms": r["p999_ms"], "max_ms": r["max_ms"], "tflops": r["tflops"],
+                      "wall_s": r["wall_s"]})
     main["capacity_per_s"] = capacity.get("rate")
+    main["capacity_burst_host_us_per_request"] = capacity.get("burst_us_per_request")
+    main["server"] = {"max_inflight": 128, "num_streams": 16, "hbm_budget_bytes": budget}
     main["loads"] = loads
     return main
 
@@ -654,33 +657,52 @@ def _serve_stream(b, count, budget, rho=0.8, fixed_rate=None, capacity=None):
     Bpool = torch.empty((S, S), dtype=torch.float32, device="cuda").uniform_(-1, 1)
     slots = 64
     Cpool = torch.empty((slots, S * S), dtype=torch.float32, device="cuda")
-    srv = b.serve_open(budget, max_inflight=32, num_streams=8)
+    srv = b.serve_open(budget, max_inflight=128, num_streams=16)
     deadline = time.perf_counter() + 90.0   # one stream takes a few seconds; fail fast if it stalls
 
     def check_deadline():
         if time.perf_counter() > deadline:
             raise TimeoutError(f"served stream still running after 90 s: {b.serve_stats(srv)}")
 
+    # device addresses of the operand pools and the C slots, taken once (a client holds its buffers'
+    # addresses; indexing a torch tensor per request costs microseconds of Python)
+    a_ptr, b_ptr = Apool.data_ptr(), Bpool.data_ptr()
+    c_ptrs = [Cpool[j].data_ptr() for j in range(slots)]
     try:
         def submit(i, m, n, k, mode):
             while True:
-                t = b.serve_submit(srv, mode, m, n, k, Apool, S, Bpool, S, Cpool[i % slots], n)
+                t = b.serve_submit(srv, mode, m, n, k, a_ptr, S, b_ptr, S, c_ptrs[i % slots], n)
                 if t is not None:
                     return t
                 check_deadline()
 
-        # capacity: a closed burst of 1000 requests (measured once, on the first stream)
+        # capacity: a closed burst of 2000 requests (measured once, on the first stream), after an
+        # unmeasured burst of 2000 others (first launches of each kernel and configuration)
         if capacity is None or "rate" not in capacity:
-            nb = 1000
+            nb = 2000
+            _, sizes, modes = synth.serve_stream(nb, seed=synth.seed_for(4, 2), rate_per_s=1.0)
+            warm = [submit(i, *map(int, sizes[i]), int(modes[i])) for i in range(nb)]
+            b.serve_drain(srv, 120_000)
+            for t in warm:
+                b.serve_poll(srv, t)
             _, sizes, modes = synth.serve_stream(nb, seed=synth.seed_for(4, 1), rate_per_s=1.0)
+            tm0 = b.serve_timing(srv)
             t0 = time.perf_counter()
             tickets = [submit(i, *map(int, sizes[i]), int(modes[i])) for i in range(nb)]
+            t1 = time.perf_counter()
             b.serve_drain(srv, 120_000)
             burst_s = time.perf_counter() - t0
+            tm1 = b.serve_timing(srv)
             for t in tickets:
                 b.serve_poll(srv, t)
             if capacity is not None:
                 capacity["rate"] = nb / burst_s
+                # host microseconds per request: the client's submit call, and the scheduler thread's
+                # three phases (retire, admit, launch: the launch groups' API calls)
+                capacity["burst_us_per_request"] = {
+                    "client_submit": (t1 - t0) / nb * 1e6,
+                    **{k[:-3]: (tm1[k] - tm0[k]) / 1e3 / nb for k in ("retire_ns", "admit_ns", "launch_ns")},
+                    "requests_per_launch_group": nb / max(1, tm1["launch_groups"] - tm0["launch_groups"])}
             cap = nb / burst_s
         else:
             cap = capacity["rate"]
@@ -688,6 +710,7 @@ def _serve_stream(b, count, budget, rho=0.8, fixed_rate=None, capacity=None):
         arrival, sizes, modes = synth.serve_stream(count, seed=synth.seed_for(4, 0), rate_per_s=rate)
         lat, flop = [], 0.0
         pending = collections.deque()
+        tm_s = b.serve_timing(srv)
         start = time.perf_counter()
         next_poll = 0.0
         for i in range(count):
@@ -717,11 +740,16 @@ def _serve_stream(b, count, budget, rho=0.8, fixed_rate=None, capacity=None):
             r = b.serve_poll(srv, t)
             lat.append((r["t_done_us"] - r["t_submit_us"]) / 1e3)
         st = b.serve_stats(srv)
+        tm = {k: v - tm_s[k] for k, v in b.serve_timing(srv).items()}
+        st["scheduler_us_per_request"] = {k[:-3]: tm[k] / 1e3 / max(1, tm["completed"])
+                                          for k in ("retire_ns", "admit_ns", "launch_ns")}
+        st["requests_per_launch_group"] = tm["completed"] / max(1, tm["launch_groups"])
     finally:
         b.serve_close(srv)
     lat = np.array(lat)
     return {"requests": count, "offered_rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "tflops": flop / wall / 1e12, "wall_s": wall,
+            "p99_ms": float(np.percentile(lat, 99)), "p999_ms": float(np.percentile(lat, 99.9)),
+            "max_ms": float(lat.max()), "tflops": flop / wall / 1e12, "wall_s": wall,
             "modes": "f16, bf16, e4m3 (scaled), split-3 uniform", "sizes": "m,n,k log-uniform [32,4096], multiple of 16",
             "stats": st}
 

@@ -106,7 +106,7 @@ tc_status tc_split(int32_t piece, int64_t rows, int64_t cols, const float* src, 
  * rounds the rows x cols FP32 matrix at src (row-major, ld_src) into dst
  * (ld_dst), transposed (dst cols x rows) if transpose != 0.  For a batch of
  * small operands, where a launch per operand costs more than the rounding.
- *   dt: TC_F16 or TC_BF16 (E4M3 needs a scale per tensor: use tc_quantize).
+ *   dt: TC_F16 or TC_BF16 (E4M3 needs a scale per tensor: tc_quantize_batch_e4m3).
  *   workspace: 256-byte aligned device memory of at least
  *   tc_quantize_batch_workspace_bytes(count, jobs) bytes for the job table
  *   and the tile list, not touched by other work until the kernel has
@@ -124,6 +124,17 @@ typedef struct tc_quantize_job {
 size_t tc_quantize_batch_workspace_bytes(int32_t count, const tc_quantize_job* jobs);
 tc_status tc_quantize_batch(int32_t dt, int32_t count, const tc_quantize_job* jobs,
                             void* workspace, size_t workspace_bytes, void* stream);
+
+/* Many FP32 -> E4M3 roundings (as tc_quantize with dt = TC_E4M3, each job
+ * with its own per-tensor scale): job j's scale s_j is the largest power of
+ * two with max|src_j| * s_j <= 448 (1 for an empty or all-zero job), stored
+ * as a device float at scale_out[j] (a host array of count device pointers,
+ * 4-byte aligned), and dst_j = RNE_satfinite(src_j * s_j).  Two launches: a
+ * max-|x| pass over every job, then the rounding.  Codes and scales equal
+ * tc_quantize's bit for bit.  Jobs, workspace (same size function) and the
+ * capture rule as tc_quantize_batch; dst needs 1-byte alignment only. */
+tc_status tc_quantize_batch_e4m3(int32_t count, const tc_quantize_job* jobs, float* const* scale_out,
+                                 void* workspace, size_t workspace_bytes, void* stream);
 
 /* Scaled residual split (Ootomo and Yokota, 2022, refining Sec. V):
  *   hi = RNE(x), lo = RNE((x - hi) * 2^s), s = 11 for TC_F16, 8 for TC_BF16.

@@ -111,6 +111,7 @@ SIGNATURES = {
                                _sz, _vp]),
     "tc_quantize_batch_workspace_bytes": (_sz, [_i32, ctypes.POINTER(tc_quantize_job)]),
     "tc_quantize_batch": (_i32, [_i32, _i32, ctypes.POINTER(tc_quantize_job), _vp, _sz, _vp]),
+    "tc_quantize_batch_e4m3": (_i32, [_i32, ctypes.POINTER(tc_quantize_job), ctypes.POINTER(_vp), _vp, _sz, _vp]),
     "tc_autotune_gemm": (_i32, [_i32, _i64, _i64, _i64, _vp, ctypes.POINTER(ctypes.c_double)]),
     "gemm_grouped_plan_autotune": (_i32, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     "tc_autotune_save": (_i32, [ctypes.c_char_p]),
@@ -140,6 +141,9 @@ def library_path() -> str:
 def load(build_if_needed: bool = True) -> ctypes.CDLL:
     """Load libtcgemm.so (building it first if allowed); raises if it cannot be loaded."""
     global _LIB
+    lib = _LIB
+    if lib is not None:   # set once, under the lock, fully configured
+        return lib
     with _LOCK:
         if _LIB is None:
             path = _build.build() if build_if_needed else _build.LIB
@@ -371,6 +375,15 @@ def tc_quantize_batch(dt, jobs, workspace, workspace_bytes, stream=None):
     arr = jobs if isinstance(jobs, ctypes.Array) else quantize_jobs_array(jobs)
     return _check(load().tc_quantize_batch(dt, len(arr), arr, _ptr(workspace), int(workspace_bytes),
                                            _stream(stream)), "tc_quantize_batch")
+
+
+def tc_quantize_batch_e4m3(jobs, scales, workspace, workspace_bytes, stream=None):
+    """E4M3 roundings of many tensors, job j's scale into the device float scales[j] (tensors or
+    device addresses)."""
+    arr = jobs if isinstance(jobs, ctypes.Array) else quantize_jobs_array(jobs)
+    ptrs = (_vp * len(arr))(*[_ptr(x) for x in scales])
+    return _check(load().tc_quantize_batch_e4m3(len(arr), arr, ptrs, _ptr(workspace), int(workspace_bytes),
+                                                _stream(stream)), "tc_quantize_batch_e4m3")
 
 
 def tc_autotune_gemm(dt, m, n, k, stream=None):

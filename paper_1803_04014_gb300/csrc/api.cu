@@ -1358,59 +1358,165 @@ int64_t quant_job_tiles(const tc_quantize_job& j) {
 extern "C" size_t tc_quantize_batch_workspace_bytes(int32_t count, const tc_quantize_job* jobs) {
     if (count <= 0 || !jobs) return 0;
     int64_t tiles = 0;
+    // an empty job of an E4M3 batch still takes one tile (it stores the job's scale)
     for (int32_t j = 0; j < count; ++j)
-        if (jobs[j].rows > 0 && jobs[j].cols > 0) tiles += quant_job_tiles(jobs[j]);
+        tiles += (jobs[j].rows > 0 && jobs[j].cols > 0) ? quant_job_tiles(jobs[j]) : 1;
     return (size_t(count) * sizeof(tcg::QuantJobDev) + 255) / 256 * 256 + size_t(tiles) * sizeof(tcg::QuantTileDev);
 }
 
-extern "C" tc_status tc_quantize_batch(int32_t dt, int32_t count, const tc_quantize_job* jobs, void* workspace,
-                                       size_t workspace_bytes, void* stream) {
-    if (dt != TC_F16 && dt != TC_BF16) return fail(TC_ERR_UNSUPPORTED, "tc_quantize_batch: F16 or BF16 only");
-    if (count < 0 || (count > 0 && !jobs)) return fail(TC_ERR_INVALID, "tc_quantize_batch: bad job array");
-    if (count == 0) return TC_OK;
+namespace {
+
+// Checks of a batch of roundings and its job table and tile list built in `host` (job table padded
+// to 256 bytes, then the tiles).
+tc_status quantize_batch_build(const char* name, int32_t dt, int32_t count, const tc_quantize_job* jobs,
+                               float* const* scale_out, std::vector<unsigned char>& host, size_t* desc_bytes_out,
+                               int64_t* ntiles_out) {
+    if (count < 0 || (count > 0 && !jobs)) return fail(TC_ERR_INVALID, "%s: bad job array", name);
+    if (dt == TC_E4M3 && count > 0 && !scale_out) return fail(TC_ERR_INVALID, "%s: null scale array", name);
+    const int esz = elem_size(dt);
     const size_t desc_bytes = (size_t(count) * sizeof(tcg::QuantJobDev) + 255) / 256 * 256;
     int64_t ntiles = 0;
     for (int32_t j = 0; j < count; ++j) {
         const tc_quantize_job& J = jobs[j];
-        if (J.rows < 0 || J.cols < 0) return fail(TC_ERR_INVALID, "tc_quantize_batch: job %d negative size", j);
-        if (J.rows == 0 || J.cols == 0) continue;
-        if (!J.src || !J.dst) return fail(TC_ERR_INVALID, "tc_quantize_batch: job %d null pointer", j);
+        if (J.rows < 0 || J.cols < 0) return fail(TC_ERR_INVALID, "%s: job %d negative size", name, j);
+        if (dt == TC_E4M3 && (!scale_out[j] || !aligned(scale_out[j], 4)))
+            return fail(TC_ERR_INVALID, "%s: job %d null or misaligned scale", name, j);
+        if (J.rows == 0 || J.cols == 0) {
+            if (dt == TC_E4M3) ++ntiles;
+            continue;
+        }
+        if (!J.src || !J.dst) return fail(TC_ERR_INVALID, "%s: job %d null pointer", name, j);
         if (J.ld_src < J.cols || J.ld_dst < (J.transpose ? J.rows : J.cols))
-            return fail(TC_ERR_INVALID, "tc_quantize_batch: job %d leading dimension too small", j);
-        if (!aligned(J.src, 4) || !aligned(J.dst, 2))
-            return fail(TC_ERR_INVALID, "tc_quantize_batch: job %d misaligned pointer", j);
+            return fail(TC_ERR_INVALID, "%s: job %d leading dimension too small", name, j);
+        if (!aligned(J.src, 4) || !aligned(J.dst, esz))
+            return fail(TC_ERR_INVALID, "%s: job %d misaligned pointer", name, j);
         ntiles += quant_job_tiles(J);
     }
-    if (ntiles > 0x7FFFFFFF) return fail(TC_ERR_INVALID, "tc_quantize_batch: too many tiles");
-    const size_t need = desc_bytes + size_t(ntiles) * sizeof(tcg::QuantTileDev);
-    if (!workspace || !aligned(workspace, 256))
-        return fail(TC_ERR_INVALID, "tc_quantize_batch: workspace must be a 256-byte aligned device pointer");
-    if (workspace_bytes < need)
-        return fail(TC_ERR_INVALID, "tc_quantize_batch: workspace of %zu bytes, need %zu", workspace_bytes, need);
-    tc_status s = refuse_capture("tc_quantize_batch", as_stream(stream));
-    if (s != TC_OK) return s;
-    Device* d;
-    if ((s = get_device(&d)) != TC_OK) return s;
-    std::vector<unsigned char> host(need, 0);
+    if (ntiles > 0x7FFFFFFF) return fail(TC_ERR_INVALID, "%s: too many tiles", name);
+    host.assign(desc_bytes + size_t(ntiles) * sizeof(tcg::QuantTileDev), 0);
     auto* hj = reinterpret_cast<tcg::QuantJobDev*>(host.data());
     auto* ht = reinterpret_cast<tcg::QuantTileDev*>(host.data() + desc_bytes);
     int64_t t = 0;
     for (int32_t j = 0; j < count; ++j) {
         const tc_quantize_job& J = jobs[j];
-        hj[j] = {J.src, J.dst, J.rows, J.cols, J.ld_src, J.ld_dst, J.transpose ? 1 : 0,
-                 (aligned(J.dst, 16) && J.ld_dst % 8 == 0) ? 1 : 0};
-        if (J.rows == 0 || J.cols == 0) continue;
+        // 8-element chunks of dst start on 16 bytes (16-bit types) or 8 bytes (E4M3)
+        const bool vec = aligned(J.dst, 8 * esz) && J.ld_dst % 8 == 0;
+        hj[j] = {J.src, J.dst, J.rows, J.cols, J.ld_src, J.ld_dst, J.transpose ? 1 : 0, vec ? 1 : 0,
+                 dt == TC_E4M3 ? scale_out[j] : nullptr, 0u, 0u};
+        if (J.rows == 0 || J.cols == 0) {
+            if (dt == TC_E4M3) ht[t++] = {j, 0, 0, 0};
+            continue;
+        }
         for (int64_t r = 0; r < J.rows; r += tcg::kQuantTileRows)
             for (int64_t c = 0; c < J.cols; c += tcg::kQuantTileCols) ht[t++] = {j, 0, r, c};
     }
+    *desc_bytes_out = desc_bytes;
+    *ntiles_out = ntiles;
+    return TC_OK;
+}
+
+// Shared body of tc_quantize_batch and tc_quantize_batch_e4m3: the host table, one upload, the
+// launches.
+tc_status quantize_batch_impl(const char* name, int32_t dt, int32_t count, const tc_quantize_job* jobs,
+                              float* const* scale_out, void* workspace, size_t workspace_bytes, void* stream) {
+    std::vector<unsigned char> host;
+    size_t desc_bytes = 0;
+    int64_t ntiles = 0;
+    tc_status s = quantize_batch_build(name, dt, count, jobs, scale_out, host, &desc_bytes, &ntiles);
+    if (s != TC_OK || count == 0) return s;
+    if (!workspace || !aligned(workspace, 256))
+        return fail(TC_ERR_INVALID, "%s: workspace must be a 256-byte aligned device pointer", name);
+    if (workspace_bytes < host.size())
+        return fail(TC_ERR_INVALID, "%s: workspace of %zu bytes, need %zu", name, workspace_bytes, host.size());
+    if ((s = refuse_capture(name, as_stream(stream))) != TC_OK) return s;
+    Device* d;
+    if ((s = get_device(&d)) != TC_OK) return s;
     cudaStream_t st = as_stream(stream);
-    cudaError_t e = cudaMemcpyAsync(workspace, host.data(), need, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "tc_quantize_batch: upload");
+    cudaError_t e = cudaMemcpyAsync(workspace, host.data(), host.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, name);
     auto* dev = static_cast<unsigned char*>(workspace);
-    return enqueue(tcg::launch_quantize_jobs(dt, reinterpret_cast<const tcg::QuantJobDev*>(dev),
+    return enqueue(tcg::launch_quantize_jobs(dt, reinterpret_cast<tcg::QuantJobDev*>(dev),
                                              reinterpret_cast<const tcg::QuantTileDev*>(dev + desc_bytes),
                                              static_cast<int32_t>(ntiles), st),
-                   "tc_quantize_batch launch");
+                   name);
+}
+
+}  // namespace
+
+namespace tcgserve {
+
+tc_status round_and_grouped_ws(int32_t dt, int32_t njobs, const tc_quantize_job* jobs, int32_t count,
+                               const tc_problem* problems, const void* ab_base, float* c_base, float alpha,
+                               float beta, void* desc, size_t desc_bytes, void* stream) {
+    const char* name = "serve batch";
+    if (dt != TC_F16 && dt != TC_BF16) return fail(TC_ERR_UNSUPPORTED, "%s: F16 or BF16 only", name);
+    std::vector<unsigned char> q;
+    size_t q_table = 0;
+    int64_t q_tiles = 0;
+    tc_status s = quantize_batch_build(name, dt, njobs, jobs, nullptr, q, &q_table, &q_tiles);
+    if (s != TC_OK) return s;
+    const size_t q_bytes = (q.size() + 255) / 256 * 256;
+    std::vector<unsigned char> g;
+    size_t g_table = 0;
+    int64_t g_tiles = 0;
+    const bool tc = grouped_use_tensor_cores(TC_ROW_MAJOR);
+    if ((s = grouped_mma_host(name, dt, count, problems, ab_base, TC_ROW_MAJOR, ab_base, TC_ROW_MAJOR, c_base, g,
+                              &g_table, &g_tiles, !tc)) != TC_OK)
+        return s;
+    int32_t tc_tiles = 0;
+    if (tc && count > 0) {
+        bool fits = false;
+        if ((s = grouped_tc_host(dt, count, problems, ab_base, ab_base, TC_ROW_MAJOR,
+                                 desc_bytes > q_bytes ? desc_bytes - q_bytes : 0, g, &g_table, &tc_tiles, &fits)) !=
+            TC_OK)
+            return s;
+        if (!fits) return fail(TC_ERR_INVALID, "%s: descriptor space of %zu bytes is too small", name, desc_bytes);
+    }
+    if (!desc || !aligned(desc, 256) || q_bytes + g.size() > desc_bytes)
+        return fail(TC_ERR_INVALID, "%s: descriptor space of %zu bytes is too small", name, desc_bytes);
+    cudaStream_t st = as_stream(stream);
+    if ((s = refuse_capture(name, st)) != TC_OK) return s;
+    Device* d;
+    if ((s = get_device(&d)) != TC_OK) return s;
+    // both tables in one upload: the rounding's at desc, the grouped GEMM's 256-byte aligned after it
+    q.resize(q_bytes, 0);
+    q.insert(q.end(), g.begin(), g.end());
+    cudaError_t e = cudaMemcpyAsync(desc, q.data(), q.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, name);
+    auto* dev = static_cast<unsigned char*>(desc);
+    if (q_tiles > 0 &&
+        (s = enqueue(tcg::launch_quantize_jobs(dt, reinterpret_cast<tcg::QuantJobDev*>(dev),
+                                               reinterpret_cast<const tcg::QuantTileDev*>(dev + q_table),
+                                               static_cast<int32_t>(q_tiles), st),
+                     name)) != TC_OK)
+        return s;
+    if (count == 0) return TC_OK;
+    unsigned char* gdev = dev + q_bytes;
+    if (tc)
+        return enqueue(tcg::launch_grouped_tc(dt, reinterpret_cast<const tcg::GroupedTcTile*>(gdev + g_table),
+                                              tc_tiles, reinterpret_cast<const CUtensorMap*>(gdev), c_base, alpha,
+                                              beta, d->status, d->sm_count, st, -1, true),
+                       name);
+    return enqueue(tcg::launch_grouped(dt, TC_ROW_MAJOR, reinterpret_cast<const tcg::GroupedProblemDev*>(gdev),
+                                       reinterpret_cast<const tcg::GroupedTileDev*>(gdev + g_table),
+                                       static_cast<int32_t>(g_tiles), ab_base, ab_base, c_base, alpha, beta,
+                                       d->sm_count, st),
+                   name);
+}
+
+}  // namespace tcgserve
+
+extern "C" tc_status tc_quantize_batch(int32_t dt, int32_t count, const tc_quantize_job* jobs, void* workspace,
+                                       size_t workspace_bytes, void* stream) {
+    if (dt != TC_F16 && dt != TC_BF16)
+        return fail(TC_ERR_UNSUPPORTED, "tc_quantize_batch: F16 or BF16 only (E4M3: tc_quantize_batch_e4m3)");
+    return quantize_batch_impl("tc_quantize_batch", dt, count, jobs, nullptr, workspace, workspace_bytes, stream);
+}
+
+extern "C" tc_status tc_quantize_batch_e4m3(int32_t count, const tc_quantize_job* jobs, float* const* scale_out,
+                                            void* workspace, size_t workspace_bytes, void* stream) {
+    return quantize_batch_impl("tc_quantize_batch_e4m3", TC_E4M3, count, jobs, scale_out, workspace,
+                               workspace_bytes, stream);
 }
 
 // ------------------------------------------------------------ autotuning

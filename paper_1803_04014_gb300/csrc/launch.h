@@ -18,20 +18,27 @@ cudaError_t launch_quantize(int dt, int64_t rows, int64_t cols, const float* src
 cudaError_t launch_split(int scheme, int piece, int64_t rows, int64_t cols, const float* src, int64_t ld_src,
                          bool transpose, void* const* dst, int64_t ld_dst, cudaStream_t st);
 cudaError_t launch_scale_c(int64_t m, int64_t n, float beta, float* C, int64_t ldc, cudaStream_t st);
-// A batch of FP16/BF16 conversions: job j converts rows x cols FP32 at src (ld_src) into dst
-// (ld_dst), transposed if asked; vec = every 8-element chunk of dst starts on 16 bytes.
+// A batch of conversions: job j converts rows x cols FP32 at src (ld_src) into dst (ld_dst),
+// transposed if asked; vec = every 8-element chunk of dst starts on 8 elements' worth of aligned
+// bytes (16 for FP16/BF16, 8 for E4M3).  E4M3 jobs: amax (uploaded as 0) gathers max |x| as FP32
+// bits, and scale receives the job's power-of-two scale.
 struct QuantJobDev {
     const float* src;
     void* dst;
     int64_t rows, cols, ld_src, ld_dst;
     int32_t transpose, vec;
+    float* scale;
+    uint32_t amax, pad;
 };
 struct QuantTileDev {  // 64 source rows x 32 source columns of one job
     int32_t job, pad;
     int64_t r0, c0;
 };
+static_assert(sizeof(QuantJobDev) <= 80 && sizeof(QuantTileDev) <= 32, "the serving loop's descriptor bound");
 constexpr int kQuantTileRows = 64, kQuantTileCols = 32;
-cudaError_t launch_quantize_jobs(int dt, const QuantJobDev* jobs, const QuantTileDev* tiles, int32_t ntiles,
+// dt F16 / BF16: one launch.  E4M3: a max-|x| pass over every tile into the jobs' amax words, then
+// the rounding (which also writes each job's scale); every job needs at least one tile.
+cudaError_t launch_quantize_jobs(int dt, QuantJobDev* jobs, const QuantTileDev* tiles, int32_t ntiles,
                                  cudaStream_t st);
 
 // ---- kernel_setup.cu

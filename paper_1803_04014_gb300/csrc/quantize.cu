@@ -378,12 +378,46 @@ __global__ void __launch_bounds__(256) k_split_transpose(int64_t rows, int64_t c
     }
 }
 
-// Many independent FP32 -> FP16/BF16 conversions in one launch (a batch of
-// small operands, where one launch per operand would cost more than the
+// max |x| of every tile of a batch of E4M3 jobs into the job's amax word (FP32 bits; the words
+// are uploaded as 0, and non-negative floats order like their bit patterns).  fmaxf drops NaN, as
+// k_absmax does, so a job's scale is the one tc_quantize gives it.
+__global__ void __launch_bounds__(256) k_absmax_jobs(QuantJobDev* __restrict__ jobs,
+                                                     const QuantTileDev* __restrict__ tiles, int32_t ntiles) {
+    constexpr int TC = 32;
+    __shared__ float wmax[8];
+    for (int32_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+        const QuantTileDev td = tiles[ti];
+        const QuantJobDev J = jobs[td.job];
+        float m = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = threadIdx.x + q * 256;
+            const int rr = i / TC, cc = i - rr * TC;
+            const int64_t r = td.r0 + rr, c = td.c0 + cc;
+            if (r < J.rows && c < J.cols) m = fmaxf(m, fabsf(__ldg(J.src + r * J.ld_src + c)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        __syncthreads();  // the previous tile's wmax readers are done
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            m = threadIdx.x < 8 ? wmax[threadIdx.x] : 0.0f;
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (threadIdx.x == 0 && m > 0.0f) atomicMax(&jobs[td.job].amax, __float_as_uint(m));
+        }
+    }
+}
+
+// Many independent FP32 -> FP16/BF16/E4M3 conversions in one launch (a batch
+// of small operands, where one launch per operand would cost more than the
 // conversion).  The host cuts every job into 64 x 32 tiles of its source; a
 // block converts one tile through shared memory and writes it either in the
-// source's layout (rows of 32 elements, four 16-byte chunks each) or
-// transposed (rows of 64 elements, eight chunks each).
+// source's layout (rows of 32 elements, four chunks of 8 each) or transposed
+// (rows of 64 elements, eight chunks each).  E4M3 jobs take the scale from
+// the job's amax word (k_absmax_jobs ran before), and the job's first tile
+// stores it.
 template <int DT>
 __global__ void __launch_bounds__(256) k_quantize_jobs(const QuantJobDev* __restrict__ jobs,
                                                        const QuantTileDev* __restrict__ tiles, int32_t ntiles) {
@@ -393,6 +427,11 @@ __global__ void __launch_bounds__(256) k_quantize_jobs(const QuantJobDev* __rest
     for (int32_t ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
         const QuantTileDev td = tiles[ti];
         const QuantJobDev J = jobs[td.job];
+        float s = 1.0f;
+        if constexpr (DT == kDtE4M3) {
+            s = ldexpf(1.0f, e4m3_scale_exp(__uint_as_float(J.amax)));
+            if (td.r0 == 0 && td.c0 == 0 && threadIdx.x == 0) *J.scale = s;
+        }
         const float* __restrict__ src = J.src;
         T* __restrict__ dst = static_cast<T*>(J.dst);
         const int64_t r0 = td.r0, c0 = td.c0;
@@ -420,23 +459,30 @@ __global__ void __launch_bounds__(256) k_quantize_jobs(const QuantJobDev* __rest
             const int64_t c = c0 + cc;
             avail = (c < J.cols) ? J.rows - (r0 + j * 8) : 0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) o[q] = Narrow<DT>::cvt(tile[j * 8 + q][cc], 1.0f);
+            for (int q = 0; q < 8; ++q) o[q] = Narrow<DT>::cvt(tile[j * 8 + q][cc], s);
             d = dst + c * J.ld_dst + r0 + j * 8;
         } else {
             const int rr = t >> 2, q4 = t & 3;  // destination row r0 + rr, elements c0 + 8 q4 ..
             const int64_t r = r0 + rr;
             avail = (r < J.rows) ? J.cols - (c0 + q4 * 8) : 0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) o[q] = Narrow<DT>::cvt(tile[rr][q4 * 8 + q], 1.0f);
+            for (int q = 0; q < 8; ++q) o[q] = Narrow<DT>::cvt(tile[rr][q4 * 8 + q], s);
             d = dst + r * J.ld_dst + c0 + q4 * 8;
         }
         if (avail >= 8 && J.vec) {
-            uint4 w;
-            w.x = o[0] | (uint32_t(o[1]) << 16);
-            w.y = o[2] | (uint32_t(o[3]) << 16);
-            w.z = o[4] | (uint32_t(o[5]) << 16);
-            w.w = o[6] | (uint32_t(o[7]) << 16);
-            *reinterpret_cast<uint4*>(d) = w;
+            if constexpr (sizeof(T) == 2) {
+                uint4 w;
+                w.x = o[0] | (uint32_t(o[1]) << 16);
+                w.y = o[2] | (uint32_t(o[3]) << 16);
+                w.z = o[4] | (uint32_t(o[5]) << 16);
+                w.w = o[6] | (uint32_t(o[7]) << 16);
+                *reinterpret_cast<uint4*>(d) = w;
+            } else {
+                uint2 w;
+                w.x = o[0] | (uint32_t(o[1]) << 8) | (uint32_t(o[2]) << 16) | (uint32_t(o[3]) << 24);
+                w.y = o[4] | (uint32_t(o[5]) << 8) | (uint32_t(o[6]) << 16) | (uint32_t(o[7]) << 24);
+                *reinterpret_cast<uint2*>(d) = w;
+            }
         } else {
 #pragma unroll
             for (int q = 0; q < 8; ++q)
@@ -561,14 +607,20 @@ cudaError_t launch_split(int scheme, int piece, int64_t rows, int64_t cols, cons
                            : split_piece<kDtBF16, kSplitPlain>(rows, cols, src, ld_src, transpose, dst, ld_dst, st);
 }
 
-cudaError_t launch_quantize_jobs(int dt, const QuantJobDev* jobs, const QuantTileDev* tiles, int32_t ntiles,
+cudaError_t launch_quantize_jobs(int dt, QuantJobDev* jobs, const QuantTileDev* tiles, int32_t ntiles,
                                  cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
     const unsigned grid = static_cast<unsigned>(ntiles < 152 * 16 ? ntiles : 152 * 16);
-    if (dt == kDtF16)
+    if (dt == kDtF16) {
         k_quantize_jobs<kDtF16><<<grid, 256, 0, st>>>(jobs, tiles, ntiles);
-    else
+    } else if (dt == kDtBF16) {
         k_quantize_jobs<kDtBF16><<<grid, 256, 0, st>>>(jobs, tiles, ntiles);
+    } else {
+        k_absmax_jobs<<<grid, 256, 0, st>>>(jobs, tiles, ntiles);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_quantize_jobs<kDtE4M3><<<grid, 256, 0, st>>>(jobs, tiles, ntiles);
+    }
     return cudaGetLastError();
 }
 

@@ -9,12 +9,15 @@
 //      free and their workspace fits in the HBM budget (a first-fit arena
 //      carved out of one allocation made at serve_open),
 //   3. launches the admitted requests on S streams in turn, so requests that
-//      arrive while others run overlap them on the GPU.  Small FP16/BF16
-//      requests (m n k <= 2^28, each of m, n, k <= 4096) admitted together
-//      are batched: their roundings run as one tc_quantize_batch launch and
-//      their GEMMs as one grouped launch (gemm_grouped_ws), grouped by mode,
-//      alpha and beta; every other request gets its own launches.  Launches
-//      happen outside the lock that submit and poll take.
+//      arrive while others run overlap them on the GPU.  Small requests
+//      (m n k <= 2^28, each of m, n, k <= 4096) admitted together are batched
+//      by mode, alpha and beta: FP16/BF16 roundings run as one
+//      tc_quantize_batch launch and their GEMMs as one grouped launch
+//      (gemm_grouped_ws); E4M3 roundings as one tc_quantize_batch_e4m3 (a
+//      max-|x| launch and a rounding launch), then a gemm_mixed each.  Small
+//      split-3 requests (m n k <= 2^29) run as the one-launch refined GEMM,
+//      larger ones in two passes; every other request gets its own launches.
+//      Launches happen outside the lock that submit and poll take.
 // Whether a request is batched, and its kernels and tile shapes, depend only
 // on (mode, m, n, k) and its C alignment, so its result is bitwise the same
 // alone and in any mix.
@@ -42,6 +45,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "serve_batch.h"
 #include "tcgemm.h"
 
 namespace {
@@ -60,20 +64,43 @@ constexpr int64_t kBatchDim = 4096;
 constexpr size_t kDescBytes = size_t(4) << 20;    // per stream: job tables and tile lists of batches
 constexpr size_t kMaxBatch = 64;
 
-bool batched(const tc_request& r) {
-    return (r.mode == TC_MODE_F16 || r.mode == TC_MODE_BF16) && r.m <= kBatchDim && r.n <= kBatchDim &&
-           r.k <= kBatchDim && r.m * r.n * r.k <= kBatchWork && r.ldc <= 0x7FFFFFFF &&
+bool small_request(const tc_request& r) {
+    return r.m <= kBatchDim && r.n <= kBatchDim && r.k <= kBatchDim && r.m * r.n * r.k <= kBatchWork &&
+           r.ldc <= 0x7FFFFFFF &&
            ((reinterpret_cast<uintptr_t>(r.A) | reinterpret_cast<uintptr_t>(r.B) |
              reinterpret_cast<uintptr_t>(r.C)) & 3u) == 0;
 }
 
+// Requests whose roundings run in a batch: small FP16/BF16 requests (their GEMMs also run as one
+// grouped launch) and small E4M3 requests (one max-|x| pass and one rounding launch for all of
+// them, then a GEMM each).
+bool batched(const tc_request& r) {
+    return (r.mode == TC_MODE_F16 || r.mode == TC_MODE_BF16 || r.mode == TC_MODE_E4M3) && small_request(r);
+}
+
+// Split-3 requests small enough that launches, not the GPU, bound them run as one launch that forms
+// the pieces on chip (gemm_split without a workspace); larger ones in two passes through a
+// workspace, which take less GPU time.  Both give the same bits.
+constexpr int64_t kFusedSplitWork = int64_t(1) << 29;
+bool split_one_launch(const tc_request& r) {
+    return r.mode == TC_MODE_SPLIT3 && r.m * r.n * r.k <= kFusedSplitWork && r.lda % 4 == 0 && r.ldb % 4 == 0 &&
+           ((reinterpret_cast<uintptr_t>(r.A) | reinterpret_cast<uintptr_t>(r.B)) & 15u) == 0;
+}
+
 // Workspace a request needs in the arena (quantised copies or split pieces).
 size_t request_bytes(const tc_request& r) {
+    if (batched(r) && r.mode == TC_MODE_E4M3) {
+        // A (m x kp) and K-major B (n x kp), kp a multiple of 16, then the two scales
+        const int64_t kp = pad_k(r.k, 16);
+        return round_up(static_cast<size_t>(r.m * kp), kAlign) + round_up(static_cast<size_t>(r.n * kp), kAlign) +
+               kAlign;
+    }
     if (batched(r)) {
         // row-major A (m x kp) and B (k x np), both 16-byte aligned rows
         return round_up(static_cast<size_t>(r.m * pad_k(r.k, 8) * 2), kAlign) +
                round_up(static_cast<size_t>(r.k * pad_k(r.n, 8) * 2), kAlign);
     }
+    if (split_one_launch(r)) return 0;
     switch (r.mode) {
         case TC_MODE_F16:
         case TC_MODE_BF16: {
@@ -177,6 +204,9 @@ tc_status launch_request(const tc_request& r, void* ws, cudaStream_t st) {
                               r.C, r.ldc, scales, scales + 1, st);
         }
         case TC_MODE_SPLIT3:
+            if (split_one_launch(r))
+                return gemm_split(TC_F16, 3, r.m, r.n, r.k, r.alpha, r.A, r.lda, TC_ROW_MAJOR, r.B, r.ldb,
+                                  TC_ROW_MAJOR, r.beta, r.C, r.ldc, nullptr, 0, st);
             return gemm_split(TC_F16, 3, r.m, r.n, r.k, r.alpha, r.A, r.lda, TC_ROW_MAJOR, r.B, r.ldb, TC_ROW_MAJOR,
                               r.beta, r.C, r.ldc, ws, gemm_split_workspace_bytes(TC_F16, 3, r.m, r.n, r.k), st);
         default:
@@ -185,12 +215,41 @@ tc_status launch_request(const tc_request& r, void* ws, cudaStream_t st) {
 }
 
 // One launch pair for `members` (same mode, alpha, beta; all batched): their A and B
-// rounded into their workspaces by one tc_quantize_batch, their GEMMs by one
-// gemm_grouped_ws with the arena as the A and B base.  Job tables and tile lists go to
+// rounded into their workspaces as tc_quantize_batch does, their GEMMs as one
+// gemm_grouped_ws with the arena as the A and B base, both schedules in one upload to
 // `desc` (kDescBytes of device memory of this stream: stream order keeps an earlier
-// batch's kernels ahead of the next upload).
+// batch's kernels ahead of the next upload).  E4M3 members: tc_quantize_batch_e4m3, then
+// a gemm_mixed each.
+tc_status launch_batch_e4m3(const std::vector<Req*>& members, uint8_t* desc, cudaStream_t st) {
+    std::vector<tc_quantize_job> jobs;
+    std::vector<float*> scales;
+    for (Req* q : members) {
+        const tc_request& r = q->r;
+        const int64_t kp = pad_k(r.k, 16);
+        uint8_t* aq = static_cast<uint8_t*>(q->ws);
+        uint8_t* bq = aq + round_up(static_cast<size_t>(r.m * kp), kAlign);
+        float* sc = reinterpret_cast<float*>(bq + round_up(static_cast<size_t>(r.n * kp), kAlign));
+        jobs.push_back({r.m, r.k, static_cast<const float*>(r.A), r.lda, aq, kp, 0, 0});
+        jobs.push_back({r.k, r.n, static_cast<const float*>(r.B), r.ldb, bq, kp, 1, 0});
+        scales.push_back(sc);
+        scales.push_back(sc + 1);
+    }
+    const size_t qbytes = tc_quantize_batch_workspace_bytes(static_cast<int32_t>(jobs.size()), jobs.data());
+    if (qbytes > kDescBytes) return TC_ERR_INVALID;
+    tc_status s = tc_quantize_batch_e4m3(static_cast<int32_t>(jobs.size()), jobs.data(), scales.data(), desc, qbytes,
+                                         st);
+    for (size_t i = 0; s == TC_OK && i < members.size(); ++i) {
+        const tc_request& r = members[i]->r;
+        const int64_t kp = pad_k(r.k, 16);
+        s = gemm_mixed(TC_E4M3, r.m, r.n, r.k, r.alpha, jobs[2 * i].dst, kp, TC_ROW_MAJOR, jobs[2 * i + 1].dst, kp,
+                       TC_COL_MAJOR, r.beta, r.C, r.ldc, scales[2 * i], scales[2 * i + 1], st);
+    }
+    return s;
+}
+
 tc_status launch_batch(const std::vector<Req*>& members, uint8_t* arena_base, uint8_t* desc, cudaStream_t st) {
     const tc_request& r0 = members.front()->r;
+    if (r0.mode == TC_MODE_E4M3) return launch_batch_e4m3(members, desc, st);
     const int32_t dt = r0.mode == TC_MODE_F16 ? TC_F16 : TC_BF16;
     std::vector<tc_quantize_job> jobs;
     std::vector<tc_problem> probs;
@@ -216,24 +275,20 @@ tc_status launch_batch(const std::vector<Req*>& members, uint8_t* arena_base, ui
         p.ldc = static_cast<int32_t>(r.ldc);
         probs.push_back(p);
     }
-    const size_t qbytes = round_up(tc_quantize_batch_workspace_bytes(static_cast<int32_t>(jobs.size()), jobs.data()),
-                                   kAlign);
-    const size_t gbytes = gemm_grouped_workspace_bytes(static_cast<int32_t>(probs.size()), probs.data());
-    if (qbytes + gbytes > kDescBytes) return TC_ERR_INVALID;
-    tc_status s = tc_quantize_batch(dt, static_cast<int32_t>(jobs.size()), jobs.data(), desc, qbytes, st);
-    if (s != TC_OK) return s;
-    return gemm_grouped_ws(dt, static_cast<int32_t>(probs.size()), probs.data(), arena_base, TC_ROW_MAJOR,
-                           arena_base, TC_ROW_MAJOR, reinterpret_cast<float*>(c_lo), r0.alpha, r0.beta, desc + qbytes,
-                           kDescBytes - qbytes, st);
+    return tcgserve::round_and_grouped_ws(dt, static_cast<int32_t>(jobs.size()), jobs.data(),
+                                          static_cast<int32_t>(probs.size()), probs.data(), arena_base,
+                                          reinterpret_cast<float*>(c_lo), r0.alpha, r0.beta, desc, kDescBytes, st);
 }
 
-// Descriptor bytes a batch member adds (job table entries, tiles, then the larger of the two
-// grouped layouts: tensor maps and 128 x 256 tiles, or problem entry and 64 x 64 tiles; an upper bound).
+// Descriptor bytes a batch member adds (two rounding jobs of at most 80 bytes and their 64 x 32 tiles
+// of at most 32, then for FP16/BF16 the larger of the two grouped layouts: tensor maps and 128 x 256
+// tiles, or problem entry and 64 x 64 tiles; an upper bound).
 size_t batch_desc_bytes(const tc_request& r) {
     auto tiles = [](int64_t rows, int64_t cols, int64_t tr, int64_t tc) { return ((rows + tr - 1) / tr) * ((cols + tc - 1) / tc); };
+    if (r.mode == TC_MODE_E4M3) return 2 * 80 + size_t(tiles(r.m, r.k, 64, 32) + tiles(r.k, r.n, 64, 32)) * 32;
     const size_t mma = 64 + size_t(tiles(r.m, r.n, 64, 64)) * 16;
     const size_t tc = 2 * 128 + size_t(tiles(r.m, r.n, 128, 256)) * 48;
-    return 2 * 64 + size_t(tiles(r.m, r.k, 64, 32) + tiles(r.k, r.n, 64, 32)) * 32 + std::max(mma, tc);
+    return 2 * 80 + size_t(tiles(r.m, r.k, 64, 32) + tiles(r.k, r.n, 64, 32)) * 32 + std::max(mma, tc);
 }
 
 // The driver's stream-write entry point, if it has one.

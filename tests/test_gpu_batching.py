@@ -52,6 +52,51 @@ def test_quantize_batch_bit_exact(b, dt):
         b.tc_quantize_batch(2, jobs, ws, need)          # E4M3 needs a per-tensor scale
 
 
+def test_quantize_batch_e4m3_matches_per_tensor_rounding(b):
+    # each job's scale and codes equal tc_quantize's (and the oracle's) bit for bit: ragged sizes,
+    # both layouts, padded and unaligned destinations, an empty job, an all-zero job, magnitudes
+    # far apart (each job gets its own scale), one job with inf and NaN (NaN ignored by the max,
+    # inf gives scale 1)
+    shapes = [(1, 1, 0, 0, 1.0), (37, 70, 0, 2, 1e-6), (64, 32, 1, 0, 3e4), (130, 33, 1, 5, 1.0),
+              (300, 257, 0, 8, 0.02), (65, 129, 1, 8, 7.0), (0, 16, 0, 0, 1.0), (16, 16, 0, 0, 0.0),
+              (200, 1000, 1, 3, 1.0), (40, 48, 0, 0, 1.0)]
+    jobs, dsts, scales, srcs = [], [], [], []
+    for i, (rows, cols, tr, pad, mag) in enumerate(shapes):
+        X = synth.log_uniform_pow2((rows, cols), seed=synth.seed_for(6, 60 + i)) * np.float32(mag)
+        if i == 9:
+            X[3, 5], X[7, 9] = np.inf, np.nan
+        srcs.append(X)
+        Xd = dev(X) if X.size else torch.empty((max(rows, 1), max(cols, 1)), device="cuda")
+        drows, dcols = (cols, rows) if tr else (rows, cols)
+        ld = max(dcols + pad, 1)
+        D = torch.full((max(drows, 1), ld), 0x55, dtype=torch.uint8, device="cuda")
+        jobs.append((rows, cols, Xd, max(cols, 1), D, ld, tr))
+        dsts.append(D)
+        scales.append(torch.full((1,), -1.0, device="cuda"))
+    need = b.tc_quantize_batch_workspace_bytes(jobs)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    b.tc_quantize_batch_e4m3(jobs, scales, ws, need)
+    b.tc_sync_status()
+    for (rows, cols, Xd, lds, D, ld, tr), X, sc in zip(jobs, srcs, scales):
+        # the same rounding one tensor at a time
+        D1 = torch.full_like(D, 0x55)
+        s1 = torch.full((1,), -1.0, device="cuda")
+        b.tc_quantize(2, rows, cols, Xd, lds, D1, ld, tr, s1)
+        b.tc_sync_status()
+        assert float(host(sc)[0]) == float(host(s1)[0])
+        assert torch.equal(D, D1)
+        if rows and cols and np.all(np.isfinite(X)):
+            want, s = nm.quantize(X, "e4m3")
+            assert float(host(sc)[0]) == s
+            got = nm.e4m3_value(host(D))[:, :(rows if tr else cols)]
+            assert np.array_equal(got, want.T if tr else want)   # the oracle's values carry the scale
+    assert float(host(scales[6])[0]) == 1.0 and float(host(scales[7])[0]) == 1.0
+    with pytest.raises(b.TcError):
+        b.tc_quantize_batch_e4m3(jobs, scales, ws, need - 16)
+    with pytest.raises(b.TcError):
+        b.tc_quantize_batch_e4m3(jobs, scales[:-1] + [0], ws, need)   # a null scale pointer
+
+
 @pytest.mark.parametrize("impl", ["tc", "mma"])
 @pytest.mark.parametrize("lb", [0, 1])
 def test_grouped_ws_matches_oracle_and_runs_concurrently(b, lb, impl, monkeypatch):
