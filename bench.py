@@ -177,7 +177,7 @@ def parse_args():
     p.add_argument("--no-autotune", action="store_true",
                    help="run the headline GEMM in its untuned configuration (for launch lists taken under a "
                         "profiler, where the tuner's timings are not the program's)")
-    p.add_argument("--profile-gemm", choices=["f16", "f16_n1024", "bf16", "e4m3", "split3", "split3_scaled", "bf16x3",
+    p.add_argument("--profile-gemm", choices=["f16", "f16_n1024", "sgemm", "bf16", "e4m3", "split3", "split3_scaled", "bf16x3",
                                               "split3_one_launch", "split3_scaled_one_launch", "grouped",
                                               "grouped_rowmajor", "batched16", "batched16_250k", "quantize",
                                               "errnorm"], default=None,
@@ -832,6 +832,16 @@ def profile_case(kind):
             b.gemm_batched_strided(0, batch, 16, 16, 16, 1.0, Ab, 256, 0, Bb, 256, 0, 0.0, Cb, 256)
         b.tc_sync_status()
         print(json.dumps({"profile_case": kind, "batch": batch, "launches": 5}))
+        return 0
+    if kind == "sgemm":
+        # the FP32 CUDA-core GEMM at N = 8192, row-major A and B
+        A = torch.from_numpy(synth.uniform((N, N), seed=synth.seed_for(1, 0))).cuda()
+        B = torch.from_numpy(synth.uniform((N, N), seed=synth.seed_for(1, 1))).cuda()
+        C = torch.empty((N, N), dtype=torch.float32, device="cuda")
+        for _ in range(5):
+            b.gemm_sgemm(N, N, N, 1.0, A, N, 0, B, N, 0, 0.0, C, N)
+        b.tc_sync_status()
+        print(json.dumps({"profile_case": kind, "n": N, "launches": 5}))
         return 0
     if kind == "f16_n1024":
         # a sweep size that single CTAs with 128 x 64 tiles cover in one round (128 tiles); operands
