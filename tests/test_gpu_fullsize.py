@@ -130,8 +130,17 @@ def test_refinement_sampled(b, N):
             if piece == 0:
                 # the accuracy bar: within 2x of the FP32 CUDA-core GEMM's error
                 assert _sampled_normwise(got, truth, A_r, B_c) <= 2.0 * e_fp32
+            # the one-launch path (no workspace: pieces formed on chip) gives the same C bit for bit
+            two_pass = C.clone()
+            b.gemm_split(piece, nprod, N, N, N, 1.0, Ad, N, 0, Bd, N, 0, 0.0, C, N)
+            b.tc_sync_status()
+            assert torch.equal(C, two_pass), (piece, nprod)
     b.gemm_split_scaled(0, 3, N, N, N, 1.0, Ad, N, 0, Bd, N, 0, 0.0, C, N, ws, wsb)
     got = sample()
+    two_pass = C.clone()
+    b.gemm_split_scaled(0, 3, N, N, N, 1.0, Ad, N, 0, Bd, N, 0, 0.0, C, N)
+    b.tc_sync_status()
+    assert torch.equal(C, two_pass)
     ref = og.gemm_split_scaled("f16", 3, A, B, rows=rows, cols=cols)
     ok, info = elementwise_ok(got, ref, np.abs(A_r) @ np.abs(B_c), 3 * N)
     assert ok, info
