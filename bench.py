@@ -296,6 +296,34 @@ def _graph_ms_per_launch(fn, reps, replays=10):
     return ms
 
 
+def _graph_ms_per_launch_cold(fns, replays=5):
+    """Device time per launch of one launch of each of `fns` (each on its own operands, together
+    larger than L2) captured in one CUDA graph: every launch finds its operands outside L2."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for f in fns[:3]:
+            f()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for f in fns:
+            f()
+    graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(replays):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (replays * len(fns))
+    del graph
+    return ms
+
+
 def _rate_stats(flop, times_ms):
     """Mean (total work over total time), harmonic mean, median and spread of per-launch TFLOP/s."""
     rates = [flop / (t * 1e-3) / 1e12 for t in times_ms]
@@ -393,13 +421,27 @@ def measure_rows(b, A, B, pk, sm_count):
                     gms = _graph_ms_per_launch(g, 50)
                     row[name]["graph_us_per_launch"] = gms * 1e3
                     row[name]["graph_tflops"] = 2.0 * n_ ** 3 / (gms * 1e-3) / 1e12
+                    # the same with cold L2: one launch per copy of the operands, the copies together
+                    # above 160 MB (more than L2), so every launch reads A, B and C from DRAM
+                    set_bytes = n_ * n_ * (2 * Aq.element_size() + 4)
+                    nsets = max(8, min(400, -(-160 * 2 ** 20 // set_bytes)))
+                    sets = [(Aq.clone(), Bq.clone(), Cs.clone()) for _ in range(nsets)]
+                    fns = [(lambda a_, b_, c_: (lambda: b.gemm_mixed(
+                        dt, n_, n_, n_, 1.0, a_, n_, 0, b_, n_, 1, 0.5, c_, n_,
+                        sc[0:1] if dt == 2 else None, sc[1:2] if dt == 2 else None)))(*t) for t in sets]
+                    cms = _graph_ms_per_launch_cold(fns)
+                    row[name]["graph_cold_us_per_launch"] = cms * 1e3
+                    row[name]["graph_cold_tflops"] = 2.0 * n_ ** 3 / (cms * 1e-3) / 1e12
+                    row[name]["graph_cold_operand_sets"] = nsets
+                    del sets, fns
                 del Aq, Bq
             res[str(n_)] = row
             del Xa, Xb, Cs
             torch.cuda.empty_cache()
         res["note"] = ("burst peak (x2 for E4M3); inputs uniform[-1,1] rounded on the GPU; tflops from launches "
                        "submitted one by one (host-bound below N = 2048), graph_* from 50 launches replayed from "
-                       "one CUDA graph")
+                       "one CUDA graph (operands warm in L2), graph_cold_* from one launch per copy of the "
+                       "operands, the copies together above 160 MB (operands from DRAM)")
         return res
 
     out["gemm_square_sweep"] = _row("gemm_square_sweep", sweep)
