@@ -74,10 +74,13 @@ __device__ __forceinline__ void for_each_mine(int64_t rows, int64_t cols, F&& f)
 // values by integer bit assembly (IEEE 754 binary32 -> binary64: same sign,
 // exponent rebiased by 1023 - 127, significand shifted up by 29 bits), and
 // the running max of |d| compared as integer bit patterns (the order of
-// non-negative IEEE values is the order of their patterns).  What remains on
-// the FP64 unit is one subtraction per element of C plus two additions per 4
-// elements (their squares on the FP32 pipe, below), and two additions per 8
-// elements of A and of B.
+// non-negative IEEE values is the order of their patterns).  The difference
+// c - c64 of an FP64 reference is taken on integers where that is exact
+// (abs_diff_bits, below), so what remains on the FP64 unit is, per group of 4
+// elements of C and of 8 of A and of B, the two additions that merge the
+// group's float-float sum of squares (FP32 pipe, below) into the FP64 sum.
+// Launch bounds hold the kernel at 32 registers: 8 of the fixed grid's 1024
+// blocks per SM, so the grid runs as one wave.
 __device__ __forceinline__ double to_f64(float x) {
     const uint32_t u = __float_as_uint(x);
     const uint32_t e = (u >> 23) & 0xFFu;
@@ -142,6 +145,57 @@ __device__ __forceinline__ bool add_diff_square_ff(double d, float& hi_sum, floa
     return true;
 }
 
+// The same split from the bit pattern of |d| (sign bit clear): hi*hi and 2*hi*lo into the float-float
+// sum exactly as add_diff_square_ff does for d.  The caller has checked 2^-50 <= |d| < 2^60.
+__device__ __forceinline__ void add_diff_square_ff_bits(unsigned long long bits, float& hi_sum, float& lo_sum) {
+    const uint32_t eb = static_cast<uint32_t>(bits >> 52);
+    const uint32_t fe = eb - 1023u + 127u;
+    const float hi = __uint_as_float((fe << 23) | static_cast<uint32_t>((bits >> 29) & 0x7FFFFFu));
+    const float scale = __uint_as_float((eb - 1075u + 127u) << 23);
+    const float lo = __fmul_rn(__uint2float_rn(static_cast<uint32_t>(bits & 0x1FFFFFFFull)), scale);
+    add_square_ff(hi, hi_sum, lo_sum);
+    lo_sum = __fadd_rn(lo_sum, __fmul_rn(__fadd_rn(hi, hi), lo));
+}
+
+// |c - r| for an FP32 c and an FP64 r without FP64 arithmetic (the FP64 unit is the scarce one):
+// the two significands, aligned to the smaller exponent, are subtracted as 64-bit integers, which
+// is exact; the result is the bit pattern of |c - r| when both are normal with the same sign and
+// exponents at most 1 apart, the difference has at most 53 significant bits (so the FP64
+// subtraction would have been exact and gives the same bits) and 2^-50 <= |c - r| < 2^60 or
+// c == r.  Returns false otherwise; the caller then takes the FP64 path.
+__device__ __forceinline__ bool abs_diff_bits(float c, double r, unsigned long long& out) {
+    const uint32_t cu = __float_as_uint(c);
+    const unsigned long long ru = static_cast<unsigned long long>(__double_as_longlong(r));
+    const uint32_t ce = (cu >> 23) & 0xFFu;
+    const uint32_t re = static_cast<uint32_t>(ru >> 52) & 0x7FFu;
+    if (ce == 0u || ce == 0xFFu || re == 0u || re == 0x7FFu || (cu >> 31) != static_cast<uint32_t>(ru >> 63))
+        return false;
+    const int ec = static_cast<int>(ce) + (1023 - 127);   // c's exponent with the FP64 bias
+    const int em = min(ec, static_cast<int>(re));
+    if (ec - em > 1 || static_cast<int>(re) - em > 1) return false;
+    const long long mc = static_cast<long long>((1ull << 52) | (static_cast<unsigned long long>(cu & 0x7FFFFFu) << 29))
+                         << (ec - em);
+    const long long mr = static_cast<long long>((1ull << 52) | (ru & 0xFFFFFFFFFFFFFull)) << (static_cast<int>(re) - em);
+    const long long diff = mc - mr;   // |c - r| = |diff| * 2^(em - 1075), exactly
+    if (diff == 0) {
+        out = 0ull;
+        return true;
+    }
+    const unsigned long long ad = static_cast<unsigned long long>(diff < 0 ? -diff : diff);
+    const int p = 63 - __clzll(static_cast<long long>(ad));   // leading bit, at most 54
+    if (p > 52) return false;
+    const int e = p + em - 1075;                              // exponent of |c - r|
+    if (e < -50 || e > 59) return false;
+    out = (static_cast<unsigned long long>(e + 1023) << 52) | ((ad << (52 - p)) & 0xFFFFFFFFFFFFFull);
+    return true;
+}
+
+// Four differences of C against an FP64 reference: the integer path for all four when each allows
+// it (the same max and the same float-float terms as acc_diff4 below, bit for bit, with no FP64
+// subtraction), else acc_diff4 on the FP64 differences.
+__device__ __forceinline__ void acc_diff4_f64ref(float4 x, double2 y0, double2 y1, double& s,
+                                                 unsigned long long& mx_bits);
+
 // Four differences of C against its reference: the max norm on bit patterns, and
 // their squares through the float-float path when all four allow it (two FP64
 // additions for the four), else in FP64.
@@ -168,10 +222,29 @@ __device__ __forceinline__ void acc_diff4(double d0, double d1, double d2, doubl
     }
 }
 
+__device__ __forceinline__ void acc_diff4_f64ref(float4 x, double2 y0, double2 y1, double& s,
+                                                 unsigned long long& mx_bits) {
+    unsigned long long a0, a1, a2, a3;
+    if (abs_diff_bits(x.x, y0.x, a0) && abs_diff_bits(x.y, y0.y, a1) && abs_diff_bits(x.z, y1.x, a2) &&
+        abs_diff_bits(x.w, y1.y, a3)) {
+        const unsigned long long a[4] = {a0, a1, a2, a3};
+        float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            mx_bits = a[i] > mx_bits ? a[i] : mx_bits;
+            if (a[i] != 0ull) add_diff_square_ff_bits(a[i], hi, lo);
+        }
+        s += to_f64(hi);
+        s += to_f64(lo);
+        return;
+    }
+    acc_diff4(to_f64(x.x) - y0.x, to_f64(x.y) - y0.y, to_f64(x.z) - y1.x, to_f64(x.w) - y1.y, s, mx_bits);
+}
+
 // partial layout: [3][kErrBlocks][2] = (sum, max) for (C - ref), A, B.
 // vec: every row of C, ref, A and B starts on a 16-byte boundary and n, the
 // column counts of A and B are multiples of 4 (4-wide loads); else scalar.
-__global__ void __launch_bounds__(kErrThreads) k_err_partials(int64_t m, int64_t n, const float* __restrict__ C,
+__global__ void __launch_bounds__(kErrThreads, 8) k_err_partials(int64_t m, int64_t n, const float* __restrict__ C,
                                                               int64_t ldc, const void* __restrict__ ref, int64_t ldr,
                                                               int ref_f64, const float* __restrict__ A, int64_t ar,
                                                               int64_t ac, int64_t lda, const float* __restrict__ B,
@@ -187,7 +260,7 @@ __global__ void __launch_bounds__(kErrThreads) k_err_partials(int64_t m, int64_t
                 const float4 x = __ldcs(reinterpret_cast<const float4*>(C + r * ldc + c));
                 const double2 y0 = __ldcs(reinterpret_cast<const double2*>(R + r * ldr + c));
                 const double2 y1 = __ldcs(reinterpret_cast<const double2*>(R + r * ldr + c + 2));
-                acc_diff4(to_f64(x.x) - y0.x, to_f64(x.y) - y0.y, to_f64(x.z) - y1.x, to_f64(x.w) - y1.y, s, mx);
+                acc_diff4_f64ref(x, y0, y1, s, mx);
             });
         } else {
             const float* R = static_cast<const float*>(ref);

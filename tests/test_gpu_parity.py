@@ -456,6 +456,44 @@ def test_error_norm_at_the_edges_of_the_float_float_range(b):
     assert out[3] == want[3]
 
 
+def test_error_norm_differences_taken_on_integers(b):
+    # C - C64 is taken as an integer difference of aligned significands when both are normal with one
+    # sign and exponents at most 1 apart, the result has at most 53 bits and lies in the float-float
+    # range; everything else goes through the FP64 subtraction.  Pairs on both sides of each of those
+    # lines, each in a group of 4 with ordinary values
+    m, n = 8, 32
+    C = synth.uniform((m, n), seed=97)
+    C64 = C.astype(np.float64) + synth.normal((m, n), seed=98).astype(np.float64) * 1e-6
+    pairs = [
+        (1.0, 1.0 - 2.0 ** -30),          # exponents 1 apart
+        (1.0, 1.0),                       # equal: difference 0
+        (1.5, 0.75 + 2.0 ** -40),         # exponents 1 apart, 53 significant bits
+        (1.75, 0.5 + 2.0 ** -53),         # exponents 1 apart, 54 significant bits: FP64 path
+        (3.0, 0.7),                       # exponents 2 apart: FP64 path
+        (1e-6, -1e-6),                    # opposite signs: FP64 path
+        (1.0, 1.0 - 2.0 ** -50),          # difference 2^-50, the range's lower edge
+        (1.0, 1.0 - 2.0 ** -52),          # difference 2^-52: FP64 path
+        (-2.5, -2.5 + 2.0 ** -20),        # negative, same sign
+        (2.0 ** 100, 2.0 ** 100 * (1 - 2.0 ** -45)),   # large values, difference 2^55
+        (-(2.0 ** -100), -(2.0 ** -100) * (1 + 2.0 ** -20)),  # tiny values, difference 2^-120: FP64 path
+    ]
+    for i, (c, r) in enumerate(pairs):
+        row, col = divmod(4 * i + 1 + (i % 3), n)
+        C[row, col] = np.float32(c)
+        C64[row, col] = r
+    out = b.tc_error_norm(m, n, dev(C), n, dev(C64), n, 1)
+    want = og.error_sums(C, C64, np.zeros(1), np.zeros(1))
+    assert abs(out[0] - want[0]) <= 1e-12 * abs(want[0]), (out[0], want[0])
+    assert out[3] == want[3]
+    # the same against the FP64 path alone (rows of odd length: scalar loads, FP64 differences)
+    Cs = np.zeros((m, n + 1), np.float32)
+    Cs[:, :n] = C
+    Rs = np.zeros((m, n + 1))
+    Rs[:, :n] = C64
+    outs = b.tc_error_norm(m, n + 1, dev(Cs), n + 1, dev(Rs), n + 1, 1)
+    assert abs(outs[0] - want[0]) <= 1e-12 * abs(want[0]) and outs[3] == want[3]
+
+
 def test_error_norm_dev_is_the_host_call_bit_for_bit(b):
     # the asynchronous form (device output, caller workspace) enqueues the same reduction
     m, n, k = 300, 260, 72
