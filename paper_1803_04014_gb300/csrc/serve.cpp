@@ -87,6 +87,13 @@ bool split_one_launch(const tc_request& r) {
            ((reinterpret_cast<uintptr_t>(r.A) | reinterpret_cast<uintptr_t>(r.B)) & 15u) == 0;
 }
 
+// Tensor-core work of a request, in FP16 multiply-adds: E4M3 runs at twice the rate, split-3 issues
+// three products.
+double request_work(const tc_request& r) {
+    const double mnk = static_cast<double>(r.m) * static_cast<double>(r.n) * static_cast<double>(r.k);
+    return r.mode == TC_MODE_E4M3 ? 0.5 * mnk : r.mode == TC_MODE_SPLIT3 ? 3.0 * mnk : mnk;
+}
+
 // Workspace a request needs in the arena (quantised copies or split pieces).
 size_t request_bytes(const tc_request& r) {
     if (batched(r) && r.mode == TC_MODE_E4M3) {
@@ -326,6 +333,9 @@ struct tc_server {
     std::vector<uint32_t> issued_seq;
     volatile uint32_t* done_seq = nullptr;
     std::vector<double> last_progress_us;
+    // per stream: the tensor-core work of its admitted, unretired requests, to give each new launch
+    // group the least-loaded stream (a request queued behind a long one on its stream waits for it)
+    std::vector<double> stream_work;
     std::unordered_map<uint64_t, Req*> by_ticket;
     std::vector<cudaEvent_t> event_pool;
     uint64_t next_ticket = 1;
@@ -380,6 +390,8 @@ struct tc_server {
                     q->t_done = now_us();
                     if (e != cudaSuccess && q->status == TC_OK) q->status = TC_ERR_CUDA;
                     q->state = State::Done;
+                    stream_work[si] -= request_work(q->r);
+                    if (fifo.size() == 1) stream_work[si] = 0.0;  // no rounding residue on an idle stream
                     arena.release(q->ws, q->ws_bytes);
                     q->ws = nullptr;
                     if (q->ev) event_pool.push_back(q->ev);
@@ -436,13 +448,21 @@ struct tc_server {
                     }
                     if (into) {
                         into->qs.push_back(q);
+                        stream_work[into->si] += request_work(q->r);
                         continue;
                     }
                     open_batches.push_back(admitted.size());
                     batch_bytes[admitted.size()] = batch_desc_bytes(q->r);
                 }
-                admitted.push_back({{q}, next_stream});
-                next_stream = (next_stream + 1) % streams.size();
+                // the stream with the least work in flight; ties go round-robin
+                size_t si = next_stream;
+                for (size_t j = 1; j < streams.size(); ++j) {
+                    const size_t c = (next_stream + j) % streams.size();
+                    if (stream_work[c] < stream_work[si]) si = c;
+                }
+                next_stream = (si + 1) % streams.size();
+                stream_work[si] += request_work(q->r);
+                admitted.push_back({{q}, si});
             }
             const double tl0 = now_us();
             t_admit_ns += static_cast<int64_t>((tl0 - ta0) * 1e3);
@@ -546,6 +566,7 @@ tc_status serve_open(const tc_serve_cfg* cfg, tc_server** out) {
     s->running.resize(s->streams.size());
     s->issued_seq.assign(s->streams.size(), 0);
     s->last_progress_us.assign(s->streams.size(), now_us());
+    s->stream_work.assign(s->streams.size(), 0.0);
     // completion numbers written by the streams into pinned, mapped host memory, where the driver
     // supports stream writes (else completion events)
     void* seq_mem = nullptr;
