@@ -12,7 +12,9 @@
 // by element.
 //
 // Every output element is the FP32 FMA chain acc = fma(a_k, b_k, acc) over k
-// in increasing order, then alpha * acc (+ beta * C).
+// in increasing order, then alpha * acc (+ beta * C).  The accumulators of two
+// adjacent columns are updated by one packed FP32 FMA (__ffma2_rn: two
+// independent round-to-nearest FMAs), which halves the FMA instructions issued.
 #include "launch.h"
 
 namespace tcg {
@@ -104,11 +106,12 @@ __global__ void __launch_bounds__(kThreads, MINB)
         sb.load(B, ldb, n, k, n0, k0, vec_b && full_n && kfull, tid);
     };
 
-    float acc[RM][RN];
+    // accumulators in column pairs: one packed FP32 FMA (two lanes of RN FMA) per pair and k
+    float2 acc[RM][RN / 2];
 #pragma unroll
     for (int i = 0; i < RM; ++i)
 #pragma unroll
-        for (int j = 0; j < RN; ++j) acc[i][j] = 0.0f;
+        for (int j = 0; j < RN / 2; ++j) acc[i][j] = make_float2(0.0f, 0.0f);
 
     const int nk = (k + SK - 1) / SK;
     load(0);
@@ -120,7 +123,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
         if (s + 1 < nk) load((s + 1) * SK);
 #pragma unroll
         for (int kk = 0; kk < SK; ++kk) {
-            float av[RM], bv[RN];
+            float av[RM];
+            float2 bv[RN / 2];
 #pragma unroll
             for (int i = 0; i < RM / 4; ++i) {
                 const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][kk][64 * i + ty * 4]);
@@ -132,15 +136,15 @@ __global__ void __launch_bounds__(kThreads, MINB)
 #pragma unroll
             for (int j = 0; j < RN / 4; ++j) {
                 const float4 b4 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 * j + tx * 4]);
-                bv[4 * j + 0] = b4.x;
-                bv[4 * j + 1] = b4.y;
-                bv[4 * j + 2] = b4.z;
-                bv[4 * j + 3] = b4.w;
+                bv[2 * j + 0] = make_float2(b4.x, b4.y);
+                bv[2 * j + 1] = make_float2(b4.z, b4.w);
             }
 #pragma unroll
-            for (int i = 0; i < RM; ++i)
+            for (int i = 0; i < RM; ++i) {
+                const float2 a2 = make_float2(av[i], av[i]);
 #pragma unroll
-                for (int j = 0; j < RN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                for (int j = 0; j < RN / 2; ++j) acc[i][j] = __ffma2_rn(a2, bv[j], acc[i][j]);
+            }
         }
         if (s + 1 < nk) {
             sa.store(As[buf ^ 1], tid);
@@ -150,6 +154,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
     }
 
     const bool vec_c = (ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
+    auto el = [&](int i, int j) { return (j & 1) ? acc[i][j >> 1].y : acc[i][j >> 1].x; };
 #pragma unroll
     for (int i = 0; i < RM; ++i) {
         const int r = m0 + 64 * (i / 4) + ty * 4 + (i % 4);
@@ -159,21 +164,21 @@ __global__ void __launch_bounds__(kThreads, MINB)
             const int c = n0 + jh * 64 + tx * 4;
             float* p = C + static_cast<int64_t>(r) * ldc + c;
             if (vec_c && c + 4 <= n) {
-                float4 o = make_float4(alpha * acc[i][4 * jh + 0], alpha * acc[i][4 * jh + 1],
-                                       alpha * acc[i][4 * jh + 2], alpha * acc[i][4 * jh + 3]);
+                float4 o = make_float4(alpha * el(i, 4 * jh + 0), alpha * el(i, 4 * jh + 1),
+                                       alpha * el(i, 4 * jh + 2), alpha * el(i, 4 * jh + 3));
                 if (beta != 0.0f) {
                     const float4 old = *reinterpret_cast<const float4*>(p);
-                    o.x = fmaf(alpha, acc[i][4 * jh + 0], beta * old.x);
-                    o.y = fmaf(alpha, acc[i][4 * jh + 1], beta * old.y);
-                    o.z = fmaf(alpha, acc[i][4 * jh + 2], beta * old.z);
-                    o.w = fmaf(alpha, acc[i][4 * jh + 3], beta * old.w);
+                    o.x = fmaf(alpha, el(i, 4 * jh + 0), beta * old.x);
+                    o.y = fmaf(alpha, el(i, 4 * jh + 1), beta * old.y);
+                    o.z = fmaf(alpha, el(i, 4 * jh + 2), beta * old.z);
+                    o.w = fmaf(alpha, el(i, 4 * jh + 3), beta * old.w);
                 }
                 *reinterpret_cast<float4*>(p) = o;
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (c + j >= n) continue;
-                    p[j] = (beta != 0.0f) ? fmaf(alpha, acc[i][4 * jh + j], beta * p[j]) : alpha * acc[i][4 * jh + j];
+                    p[j] = (beta != 0.0f) ? fmaf(alpha, el(i, 4 * jh + j), beta * p[j]) : alpha * el(i, 4 * jh + j);
                 }
             }
         }
@@ -202,12 +207,15 @@ cudaError_t run_sgemm(int64_t m, int64_t n, int64_t k, float alpha, const float*
 
 }  // namespace
 
-// 128 x 128 tiles, 8 x 8 per thread, K steps of 16, two blocks per SM (128 registers).  Measured at
-// N = 8192 over the four layouts (TFLOP/s): this 51.7-54.4; one block per SM 50.3-54.6; 128 x 256
-// tiles (8 x 16 per thread, K steps of 8) 52.2-55.8; 256 x 128 52.9-53.9; K steps of 8 48.0-54.0.
-// ncu on this one: FMA pipe 68 % of peak, issue slots 77 % busy, FMAs 86 % of the instructions.
+// 128 x 128 tiles, 8 x 8 per thread, two blocks per SM (128 registers); K steps of 16, or of 8 for
+// row-major A with row-major B, whose staging at 16 spills (140 bytes).  Measured at N = 8192 over
+// the four layouts with packed FMAs (TFLOP/s): K steps of 16 53.1 / 60.3 / 60.6 / 61.5 (A, B
+// row/row, row/col, col/row, col/col), of 8 57.4 / 59.8 / 61.4 / 57.5; with one FMA per instruction
+// 51.7-54.4, and 128 x 256, 256 x 128 tiles or one block per SM were within 2 % of that.  All are
+// bit-identical (the same FMA chain per element).
 cudaError_t launch_sgemm(int64_t m, int64_t n, int64_t k, float alpha, const float* A, int64_t lda, int la,
                          const float* B, int64_t ldb, int lb, float beta, float* C, int64_t ldc, cudaStream_t st) {
+    if (la == 0 && lb == 0) return run_sgemm<8, 8, 8, 2>(m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ldc, st);
     return run_sgemm<8, 8, 16, 2>(m, n, k, alpha, A, lda, la, B, ldb, lb, beta, C, ldc, st);
 }
 
