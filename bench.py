@@ -434,6 +434,11 @@ def measure_rows(b, A, B, pk, sm_count):
                     row[name]["graph_cold_tflops"] = 2.0 * n_ ** 3 / (cms * 1e-3) / 1e12
                     row[name]["graph_cold_operand_sets"] = nsets
                     del sets, fns
+                    if n_ == 256:
+                        # the 256^3 configuration itself: C = A B (beta = 0, C not read)
+                        g0 = lambda: b.gemm_mixed(dt, n_, n_, n_, 1.0, Aq, n_, 0, Bq, n_, 1, 0.0, Cs, n_,
+                                                  sc[0:1] if dt == 2 else None, sc[1:2] if dt == 2 else None)
+                        row[name]["graph_us_per_launch_beta0"] = _graph_ms_per_launch(g0, 50) * 1e3
                 del Aq, Bq
             res[str(n_)] = row
             del Xa, Xb, Cs
