@@ -487,7 +487,14 @@ typedef struct tc_result {
 typedef struct tc_server tc_server;
 
 /* Start a server on the current device: allocates the budget arena and the
- * streams, starts the scheduler thread. */
+ * streams, starts the scheduler thread.  The scheduler admits queued requests
+ * in arrival order while the in-flight count and the budget allow, batches
+ * small FP16/BF16 requests (rounding + grouped GEMM) and small E4M3 requests
+ * (rounding) admitted together, runs small split-3 requests as the one-launch
+ * refined GEMM, and gives each launch group the stream with the least
+ * admitted, unretired tensor-core work.  A request's kernels depend only on
+ * its mode, sizes and pointer alignment, so its result is bitwise the same
+ * alone and in any mix. */
 tc_status serve_open(const tc_serve_cfg* cfg, tc_server** out);
 
 /* Queue a request (non-blocking).  TC_ERR_BUSY if the queue is full,
