@@ -651,6 +651,40 @@ def measure_rows(b, A, B, pk, sm_count):
                         "ms_synchronising_call: host wall time of tc_error_norm (plus scratch, read-back and sync)"}
 
     out["error_norm_n8192"] = _row("error_norm_n8192", error_norm)
+
+    # the paper's precision experiment (Sec. VII-B): the max norm of e = C_x - C_single, C_single the
+    # FP32 CUDA-core GEMM, for x = FP16 inputs (no refinement), Eq. 1 (R_A) and Eq. 2 (R_A and R_B)
+    def precision_vs_paper():
+        res = {"definition": "max |C_x - C_single|, C_single = gemm_sgemm (FP32 CUDA cores), beta = 0; "
+                             "x = gemm_mixed FP16 (none), gemm_split FP16 pieces with 2 products (R_A, Eq. 1) "
+                             "and 4 products (R_A and R_B, Eq. 2)",
+               "paper": {"pm16_n4096": {"none": 8.32, "ra_rb": 0.24, "factor": 35},
+                         "pm1_n8192": {"ra_reduction": 0.30, "ra_rb_factor": 10}}}
+        cases = [("pm1", n_, 1.0) for n_ in (1024, 2048, 4096, 8192)] + [("pm16", 4096, 16.0)]
+        for tag, n_, scale in cases:
+            A_ = torch.from_numpy(synth.uniform((n_, n_), seed=synth.seed_for(0, 0)) * np.float32(scale)).cuda()
+            B_ = torch.from_numpy(synth.uniform((n_, n_), seed=synth.seed_for(0, 1)) * np.float32(scale)).cuda()
+            Cs = torch.empty((n_, n_), dtype=torch.float32, device="cuda")
+            Cx = torch.empty_like(Cs)
+            b.gemm_sgemm(n_, n_, n_, 1.0, A_, n_, 0, B_, n_, 0, 0.0, Cs, n_)
+            Aq = torch.empty((n_, n_), dtype=torch.float16, device="cuda")
+            Bq = torch.empty((n_, n_), dtype=torch.float16, device="cuda")
+            b.tc_quantize(0, n_, n_, A_, n_, Aq, n_, 0)
+            b.tc_quantize(0, n_, n_, B_, n_, Bq, n_, 1)
+            row = {}
+            b.gemm_mixed(0, n_, n_, n_, 1.0, Aq, n_, 0, Bq, n_, 1, 0.0, Cx, n_)
+            row["none"] = b.tc_error_norm(n_, n_, Cx, n_, Cs, n_, 0)[3]
+            for name, nprod in (("ra", 2), ("ra_rb", 4)):
+                b.gemm_split(0, nprod, n_, n_, n_, 1.0, A_, n_, 0, B_, n_, 0, 0.0, Cx, n_)
+                row[name] = b.tc_error_norm(n_, n_, Cx, n_, Cs, n_, 0)[3]
+            row["ra_reduction"] = 1.0 - row["ra"] / row["none"]
+            row["ra_rb_factor"] = row["none"] / row["ra_rb"]
+            res[f"{tag}_n{n_}"] = row
+            del A_, B_, Cs, Cx, Aq, Bq
+            torch.cuda.empty_cache()
+        return res
+
+    out["precision_vs_paper"] = _row("precision_vs_paper", precision_vs_paper)
     torch.cuda.empty_cache()
     out["serve"] = _row("serve", serve_row_in_child)
     return out
