@@ -281,3 +281,39 @@ def test_pipelined_prepare_and_run_on_two_streams(b):
     b.tc_sync_status()
     for i in range(count):
         assert torch.equal(got[i], want[i]), i
+
+
+# ------------------------------------------------------------------ the paper's precision claims, on the GPU
+
+def test_paper_precision_claims_hold_on_the_gpu_path(b, golden_dir):
+    # Sec. VII-B: with e = C_x - C_single (C_single the FP32 CUDA-core GEMM), the refinement with R_A
+    # alone removes about 30 % of max |e|, and R_A with R_B at least the paper's factors (10x for
+    # uniform [-1, 1] inputs, 35x for [-16, 16]); the same bounds as the oracle's pins of these claims
+    import json
+    import os
+    with open(os.path.join(golden_dir, "paper_numbers.json")) as f:
+        paper = json.load(f)
+    n = 1024
+    for scale, key in ((1.0, "refinement_uniform_pm1_n8192"), (16.0, "refinement_uniform_pm16_n4096")):
+        A = dev(synth.uniform((n, n), seed=synth.seed_for(0, 0)) * np.float32(scale))
+        B = dev(synth.uniform((n, n), seed=synth.seed_for(0, 1)) * np.float32(scale))
+        Cs = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        Cx = torch.empty_like(Cs)
+        b.gemm_sgemm(n, n, n, 1.0, A, n, 0, B, n, 0, 0.0, Cs, n)
+        Aq = torch.empty((n, n), dtype=torch.float16, device="cuda")
+        Bq = torch.empty((n, n), dtype=torch.float16, device="cuda")
+        b.tc_quantize(0, n, n, A, n, Aq, n, 0)
+        b.tc_quantize(0, n, n, B, n, Bq, n, 1)
+        b.gemm_mixed(0, n, n, n, 1.0, Aq, n, 0, Bq, n, 1, 0.0, Cx, n)
+        e0 = b.tc_error_norm(n, n, Cx, n, Cs, n, 0)[3]
+        b.gemm_split(0, 2, n, n, n, 1.0, A, n, 0, B, n, 0, 0.0, Cx, n)
+        e2 = b.tc_error_norm(n, n, Cx, n, Cs, n, 0)[3]
+        b.gemm_split(0, 4, n, n, n, 1.0, A, n, 0, B, n, 0, 0.0, Cx, n)
+        e4 = b.tc_error_norm(n, n, Cx, n, Cs, n, 0)[3]
+        b.tc_sync_status()
+        ref = paper[key]
+        if scale == 1.0:
+            assert abs((1.0 - e2 / e0) - ref["emax_reduction_RA_only_fraction"]) < 0.12, (e0, e2)
+            assert e0 > ref["emax_reduction_RA_RB_factor"] * e4, (e0, e4)
+        else:
+            assert e0 > ref["reduction_factor"] * e4, (e0, e4)
