@@ -824,6 +824,33 @@ bool grouped_use_tensor_cores(int32_t lb) {
     return !(env && strcmp(env, "mma") == 0);
 }
 
+// Tensor-core tiles of one problem: 128 x 256, or, for n <= 128, tall 256-row tiles that cover
+// M-blocks tm and tm + 1 with one B tile (an odd last M-block stays 128 rows high).  Tall tiles
+// unless TCGEMM_GROUPED_TALL=0.
+bool grouped_tall_tiles() {
+    const char* env = getenv("TCGEMM_GROUPED_TALL");
+    return !(env && strcmp(env, "0") == 0);
+}
+
+int64_t grouped_tc_tile_count(const tc_problem& p, bool tall_on) {
+    const int64_t tm = (p.m + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM;
+    const int64_t tn = (p.n + tcg::kGroupedTcTileN - 1) / tcg::kGroupedTcTileN;
+    return (tall_on && p.n <= tcg::kGroupedTcTileN / 2 ? (tm + 1) / 2 : tm) * tn;
+}
+
+template <class Emit>
+void grouped_tc_tiles(const tc_problem& p, int32_t g, bool tall_on, Emit&& emit) {
+    const bool tall = tall_on && p.n <= tcg::kGroupedTcTileN / 2;
+    const int tm = (p.m + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM;
+    const int tn = (p.n + tcg::kGroupedTcTileN - 1) / tcg::kGroupedTcTileN;
+    for (int i = 0; i < tm;) {
+        const int rows = (tall && i + 1 < tm) ? 2 * tcg::kGroupedTcTileM : tcg::kGroupedTcTileM;
+        for (int j = 0; j < tn; ++j)
+            emit(tcg::GroupedTcTile{g, i, j, p.m, p.n, p.k, p.ldc, (p.k + 63) / 64, p.off_c, rows, 0});
+        i += rows / tcg::kGroupedTcTileM;
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -888,16 +915,11 @@ tc_status gemm_grouped_plan_create(int32_t dt, int32_t count, const tc_problem* 
             e = cudaMemcpy(plan->d_tiles, tl.data(), tl.size() * sizeof(tl[0]), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess && count > 0 && grouped_use_tensor_cores(lb)) {
-        // the same problem order, cut into 128 x 256 tiles
+        // the same problem order, cut into 128 x 256 (and tall 256 x 256) tiles
         std::vector<tcg::GroupedTcTile> tc;
-        for (const P& o : order) {
-            const tc_problem& p = problems[o.g];
-            const int tm = (p.m + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM;
-            const int tn = (p.n + tcg::kGroupedTcTileN - 1) / tcg::kGroupedTcTileN;
-            for (int i = 0; i < tm; ++i)
-                for (int j = 0; j < tn; ++j)
-                    tc.push_back({o.g, i, j, p.m, p.n, p.k, p.ldc, (p.k + 63) / 64, p.off_c, 0});
-        }
+        const bool tall = grouped_tall_tiles();
+        for (const P& o : order)
+            grouped_tc_tiles(problems[o.g], o.g, tall, [&](const tcg::GroupedTcTile& t) { tc.push_back(t); });
         plan->use_tc = true;
         plan->tc_tiles = static_cast<int32_t>(tc.size());
         plan->host_probs.assign(problems, problems + count);
@@ -1204,11 +1226,12 @@ tc_status grouped_tc_host(int32_t dt, int32_t count, const tc_problem* problems,
     std::vector<P> order;
     order.reserve(count);
     int64_t ntiles = 0;
+    const bool tall = grouped_tall_tiles();
     for (int32_t g = 0; g < count; ++g) {
         const tc_problem& p = problems[g];
         const int64_t tm = (p.m + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM;
         const int64_t tn = (p.n + tcg::kGroupedTcTileN - 1) / tcg::kGroupedTcTileN;
-        ntiles += tm * tn;
+        ntiles += grouped_tc_tile_count(p, tall);
         order.push_back({2 * p.k * (p.m * tn + p.n * tm) + 4 * int64_t(p.m) * p.n, g});
     }
     if (ntiles > 0x7FFFFFFF) return fail(TC_ERR_INVALID, "grouped: too many tiles");
@@ -1222,13 +1245,8 @@ tc_status grouped_tc_host(int32_t dt, int32_t count, const tc_problem* problems,
     if (st != TC_OK) return st;
     auto* tl = reinterpret_cast<tcg::GroupedTcTile*>(host.data() + maps_bytes);
     size_t t = 0;
-    for (const P& o : order) {
-        const tc_problem& p = problems[o.g];
-        const int tm = (p.m + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM;
-        const int tn = (p.n + tcg::kGroupedTcTileN - 1) / tcg::kGroupedTcTileN;
-        for (int i = 0; i < tm; ++i)
-            for (int j = 0; j < tn; ++j) tl[t++] = {o.g, i, j, p.m, p.n, p.k, p.ldc, (p.k + 63) / 64, p.off_c, 0};
-    }
+    for (const P& o : order)
+        grouped_tc_tiles(problems[o.g], o.g, tall, [&](const tcg::GroupedTcTile& x) { tl[t++] = x; });
     *maps_bytes_out = maps_bytes;
     *tiles_out = static_cast<int32_t>(ntiles);
     return TC_OK;

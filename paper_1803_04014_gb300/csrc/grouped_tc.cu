@@ -4,7 +4,10 @@
 // The workload moves far more bytes than it computes (about 34 FLOP/byte for
 // m, n, k <= 256), so the kernel is built to keep HBM streaming:
 //   * one persistent CTA per SM walks a longest-first list of output tiles of
-//     128 x 256 (every problem of the benchmark is one or two tiles);
+//     128 x 256, or 256 x n for a problem with n <= 128 (a "tall" tile: both
+//     128-row blocks against one B tile, so B is fetched once and the tile
+//     pays one round of pipeline and epilogue latency instead of two; every
+//     problem of the benchmark is one or two tiles);
 //   * every problem has its own pair of TMA tensor maps (A: k x m, B: k x n,
 //     K-major) in device memory, so each tile is fetched by TMA with the box
 //     cut to the problem (rows beyond m or n are zero-filled, not read);
@@ -12,9 +15,11 @@
 //     tile boundaries, so the loads of the next tile overlap the MMAs and the
 //     epilogue of the current one;
 //   * one thread issues tcgen05.mma 128 x N x 16 (N = the problem's n rounded up
-//     to 16, at most 256) into a double-buffered TMEM accumulator;
+//     to 16, at most 256) into a double-buffered TMEM accumulator (a tall
+//     tile: two MMAs per step, rows 128-255 into columns 128... of the buffer);
 //   * eight epilogue warps read the accumulator and store C with alpha/beta,
-//     the two warps of each TMEM lane quarter taking alternate 32-column chunks;
+//     the two warps of each TMEM lane quarter taking alternate 32-column chunks
+//     (of a tall tile: one warp rows 0-127, the other rows 128-255);
 //     each chunk (32 rows x 32 columns) is transposed through a 4 KB swizzled
 //     shared-memory slot of the warp so that C leaves as whole row segments.
 //     (Storing the chunks by TMA instead was measured slower: the stores queue
@@ -34,6 +39,8 @@ constexpr int kRow = 128;                    // bytes per k-block row (64 x 16-b
 constexpr int kABytes = GM * kRow;           // 16 KB
 constexpr int kBBytes = GN * kRow;           // 32 KB (largest B box)
 constexpr int kStages = 4;
+// A stage holds a 128-row tile's A box and B box (B at kABytes), or a tall tile's two A boxes
+// (rows tm * 128 ... and (tm + 1) * 128 ...) and a B box of at most 128 rows (B at 2 * kABytes).
 constexpr int kStage = kABytes + kBBytes;
 constexpr int kBarOff = kStages * kStage;
 constexpr int kNumBars = 2 * kStages + 5;
@@ -71,7 +78,7 @@ __device__ __forceinline__ GroupedTcTile load_tile(const GroupedTcTile* tiles, i
         r.prob = x.x; r.tm = x.y; r.tn = x.z; r.m = x.w;
         r.n = y.x; r.k = y.y; r.ldc = y.z; r.nk = y.w;
         r.off_c = (static_cast<int64_t>(static_cast<uint32_t>(z.y)) << 32) | static_cast<uint32_t>(z.x);
-        r.pad = 0;
+        r.rows = z.z;
     } else {
         r = GroupedTcTile{};
     }
@@ -88,6 +95,14 @@ __host__ __device__ __forceinline__ int mma_n(int n) {
 __host__ __device__ __forceinline__ int mma_n_mn(int n) {
     const int r = (n + 63) / 64 * 64;
     return r < GN ? r : GN;
+}
+
+// A tall tile (256 rows: M-blocks tm and tm + 1 against one B tile) is taken as one only when its
+// MMA N is at most 128: its B box then fits beside the two A boxes in a stage, and its two 128-row
+// accumulators share one 256-column buffer (rows 128-255 in columns 128...).  Any other tile
+// record is a 128-row tile.
+__device__ __forceinline__ bool tall_tile(const GroupedTcTile& t, bool b_mn) {
+    return t.rows > GM && (b_mn ? mma_n_mn(t.n) : mma_n(t.n)) <= GN / 2;
 }
 
 // B_MN: B_g is row-major (k x n, maps[2g+1] dims {n, k}, boxes of 64 n x 64 k) and is read by
@@ -157,8 +172,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                     prefetch_tmap(a.maps + 2 * nxt.prob + 1);
                 }
                 const int nk = tile.nk;
+                const bool tall = tall_tile(tile, B_MN);
+                const int boff = tall ? 2 * kABytes : kABytes;
                 const int nslabs = B_MN ? mma_n_mn(tile.n) / 64 : 0;
-                const uint32_t bytes = static_cast<uint32_t>(kABytes + (B_MN ? nslabs * 64 : mma_n(tile.n)) * kRow);
+                const uint32_t bytes = static_cast<uint32_t>((tall ? 2 : 1) * kABytes +
+                                                             (B_MN ? nslabs * 64 : mma_n(tile.n)) * kRow);
                 for (int kb = 0; kb < nk; ++kb) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, a.status)) {
                         ok = false;
@@ -167,12 +185,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                     const uint32_t sbase = base + stage * kStage;
                     mbar_arrive_expect_tx(full_bar(stage), bytes);
                     tma_load_3d(sbase, mA, full_bar(stage), kb * 64, tile.tm * GM, 0);
+                    if (tall) tma_load_3d(sbase + kABytes, mA, full_bar(stage), kb * 64, (tile.tm + 1) * GM, 0);
                     if constexpr (B_MN) {
                         for (int sl = 0; sl < nslabs; ++sl)
-                            tma_load_3d(sbase + kABytes + sl * 64 * kRow, mB, full_bar(stage), tile.tn * GN + sl * 64,
+                            tma_load_3d(sbase + boff + sl * 64 * kRow, mB, full_bar(stage), tile.tn * GN + sl * 64,
                                         kb * 64, 0);
                     } else {
-                        tma_load_3d(sbase + kABytes, mB, full_bar(stage), kb * 64, tile.tn * GN, 0);
+                        tma_load_3d(sbase + boff, mB, full_bar(stage), kb * 64, tile.tn * GN, 0);
                     }
                     issued_phase[stage] = static_cast<int>(phase);
                     if (++stage == kStages) {
@@ -203,6 +222,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                 const int nk = tile.nk;
                 const uint32_t idesc = B_MN ? (make_idesc(GM, mma_n_mn(tile.n), a.ab_format) | (1u << 16))
                                             : make_idesc(GM, mma_n(tile.n), a.ab_format);
+                const bool tall = tall_tile(tile, B_MN);
+                const int boff = tall ? 2 * kABytes : kABytes;
                 if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, a.status)) {
                     ok = false;
                     break;
@@ -219,9 +240,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
                         // MN-major B: 16 k-rows of 128 bytes per step, 64-n slabs 8 KB apart
-                        const uint64_t bdesc = B_MN ? sw128_mnmajor_desc(sbase + kABytes + ks * 2048, 64 * kRow, 1024)
-                                                    : sw128_kmajor_desc(sbase + kABytes + ks * 32);
+                        const uint64_t bdesc = B_MN ? sw128_mnmajor_desc(sbase + boff + ks * 2048, 64 * kRow, 1024)
+                                                    : sw128_kmajor_desc(sbase + boff + ks * 32);
                         mma_f16(d_tmem, sw128_kmajor_desc(sbase + ks * 32), bdesc, idesc, (kb | ks) != 0 ? 1u : 0u);
+                        if (tall)   // rows 128-255 against the same B, into columns 128... of the buffer
+                            mma_f16(d_tmem + static_cast<uint32_t>(GN / 2), sw128_kmajor_desc(sbase + kABytes + ks * 32),
+                                    bdesc, idesc, (kb | ks) != 0 ? 1u : 0u);
                     }
                     issued_any = true;
                     mma_commit(empty_bar(stage));
@@ -244,6 +268,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
     } else {
         // ---------------- epilogue (warps 2..9): lanes 32*(warp%4).., every other 32-column chunk
         // (chunks half, half + 2, ...), so both warps of a lane quarter share any width of tile
+        // A tall tile's rows go to the halves: half h stores rows 128 h .. 128 h + 127, every chunk.
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
         const float alpha = a.alpha, beta = a.beta;
@@ -257,22 +282,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
             const bool ok = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, a.status);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
-            const int row = tile.tm * GM + quarter * 32 + lane;
+            const bool tall = tall_tile(P, B_MN);
+            const int c_first = tall ? 0 : half * 32, c_step = tall ? 32 : 64;
+            const int row0 = tile.tm * GM + (tall ? half * GM : 0);
+            const int row = row0 + quarter * 32 + lane;
             const int col0 = tile.tn * GN;
             const int ncols_tile = max(0, min(GN, P.n - col0));
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                   static_cast<uint32_t>(acc * GN);
+                                   static_cast<uint32_t>(acc * GN + (tall ? half * (GN / 2) : 0));
             float* crow = a.c_base + P.off_c + static_cast<int64_t>(row) * P.ldc + col0;
             const bool vec_ok = ((P.ldc & 3) == 0) && (((P.off_c + col0) & 3) == 0) &&
                                 ((reinterpret_cast<uintptr_t>(a.c_base) & 15u) == 0);
             uint8_t* slot_ptr = base_ptr + kEpiOff + (warp - 2) * kEpiWarpBytes;
-            const int r0 = tile.tm * GM + quarter * 32;
+            const int r0 = row0 + quarter * 32;
             // a warp whose 32 rows all lie past the last row of C_g has nothing to read or store
             const int ncols_warp = r0 < P.m ? ncols_tile : 0;
             if (a.staged_epilogue) {
                 // each warp owns rows r0..r0+31 of the tile; stage 32 x 32 chunks and store whole row segments
 #pragma unroll 1
-                for (int c = half * 32; c < ncols_warp; c += 64) {
+                for (int c = c_first; c < ncols_warp; c += c_step) {
                     const int nc = min(32, ncols_tile - c);
                     // lane l writes 16-byte group g = l % 8 (columns 4g..4g+3) of rows q*4 + l/8, q = 0..7
                     const int g = lane & 7;
@@ -332,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                 continue;
             }
 #pragma unroll 1
-            for (int c = half * 32; c < ncols_warp; c += 64) {
+            for (int c = c_first; c < ncols_warp; c += c_step) {
                 float v[32];
                 tmem_load_32(taddr + c, v);
                 if (row < P.m) {

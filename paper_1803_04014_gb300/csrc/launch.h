@@ -146,7 +146,8 @@ cudaError_t launch_grouped(int dt, int lb, const GroupedProblemDev* probs, const
 constexpr int kGroupedTileM = 64;
 constexpr int kGroupedTileN = 64;
 
-// ---- grouped_tc.cu: tcgen05 grouped GEMM, K-major A and B, 128 x 256 output tiles.
+// ---- grouped_tc.cu: tcgen05 grouped GEMM, K-major A and B, 128 x 256 output tiles (256 x n tall
+// tiles for n <= 128).
 // maps: per problem g, maps[2g] = A (dims {k, m, 1}, box 64 x 128) and maps[2g+1] =
 // B (dims {k, n, 1}, box 64 x grouped_tc_box_rows(n)), both 128-byte swizzled.
 constexpr int kGroupedTcTileM = 128;
@@ -155,7 +156,8 @@ constexpr int kGroupedTcTileN = 256;
 struct alignas(16) GroupedTcTile {
     int32_t prob, tm, tn, m;  // problem, tile coordinates, problem rows
     int32_t n, k, ldc, nk;    // problem columns, depth, C row stride, k-blocks of 64
-    int64_t off_c, pad;       // element offset of C_g
+    int64_t off_c;            // element offset of C_g
+    int32_t rows, pad;        // rows of the tile: 128, or 256 for a tall tile (M-blocks tm and tm + 1); 0 = 128
 };
 int grouped_tc_box_rows(int n);
 constexpr int kGroupedTcMapsPerProblem = 2;

@@ -681,6 +681,45 @@ def test_grouped_tc_large_problems_and_new_bases(b):
         b.gemm_grouped_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("lb", [1, 0])
+@pytest.mark.parametrize("epi", ["staged", "direct"])
+def test_grouped_tall_tiles_match_128_row_tiles(b, monkeypatch, lb, epi):
+    # tall 256-row tiles (problems with n <= 128: M-blocks tm and tm + 1 share one B tile and one
+    # accumulator buffer) against 128 x 256 tiles only: each element is the same MMA chain, so the
+    # bits agree.  Problems with 1 to 5 M-blocks (an odd last block stays 128 rows), one row into the
+    # second block, n at, below and past 128 (those stay 128-row tiles) and past 256.
+    monkeypatch.setenv("TCGEMM_GROUPED_EPI", epi)
+    sizes = [(129, 40, 64), (256, 256, 256), (300, 520, 200), (513, 100, 72), (640, 264, 136), (200, 16, 8),
+             (96, 96, 96), (384, 250, 192), (257, 128, 64), (384, 112, 520)]
+    rows, a_parts, b_parts = [], [], []
+    oa = ob = oc = 0
+    for i, (m, n, k) in enumerate(sizes):
+        A = synth.uniform((m, k), seed=600 + i)
+        B = synth.uniform((k, n), seed=700 + i)
+        lda = (k + 7) // 8 * 8
+        Ap = np.zeros((m, lda), np.float32); Ap[:, :k] = A
+        if lb == 1:
+            ldb = lda
+            Bp = np.zeros((n, ldb), np.float32); Bp[:, :k] = B.T
+        else:
+            ldb = (n + 7) // 8 * 8
+            Bp = np.zeros((k, ldb), np.float32); Bp[:, :n] = B
+        rows.append((m, n, k, oa, ob, oc, lda, ldb, n))
+        a_parts.append(Ap.ravel()); b_parts.append(Bp.ravel())
+        oa += Ap.size; ob += Bp.size; oc += m * n
+    Ad = dev(np.concatenate(a_parts), torch.float16)
+    Bd = dev(np.concatenate(b_parts), torch.float16)
+    C0 = dev(synth.uniform((oc,), seed=777))
+    out = {}
+    for tall in ("1", "0"):
+        monkeypatch.setenv("TCGEMM_GROUPED_TALL", tall)
+        C = C0.clone()
+        b.gemm_grouped(0, rows, Ad, 0, Bd, lb, C, 1.25, 0.5)
+        b.tc_sync_status()
+        out[tall] = C
+    assert torch.equal(out["1"], out["0"])
+
+
 # ------------------------------------------------------------------ autotuner
 
 @pytest.mark.parametrize("dt", [0, 2])
