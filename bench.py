@@ -81,7 +81,7 @@ def kernel_sources_sha():
 
 
 # the untuned configuration of gemm_mixed at the headline size (tc_autotune_gemm's first candidate)
-DEFAULT_GEMM_CFG = {"pair": 1, "group_m": 8, "tail": 1, "korder": 1, "cluster": 2, "bn": 256}
+DEFAULT_GEMM_CFG = {"pair": 1, "group_m": 8, "tail": 2, "korder": 1, "cluster": 2, "bn": 256}
 
 
 def kernel_name(cfg):
@@ -453,6 +453,42 @@ def measure_rows(b, A, B, pk, sm_count):
     out["gemm_f16_n8192"] = _row("gemm_f16_n8192", lambda: mixed(0, "f16"))
     out["gemm_bf16_n8192"] = _row("gemm_bf16_n8192", lambda: mixed(1, "bf16"))
     out["gemm_e4m3_n8192"] = _row("gemm_e4m3_n8192", lambda: mixed(2, "e4m3"))
+
+    def vs_cublas():
+        # the same rounded operands through cuBLAS (torch.matmul, FP16/BF16 in, FP32 accumulate, C
+        # written in the input type) and through gemm_mixed (FP32 C, beta = 0 and 0.5): 200
+        # launches back to back per case, three rounds in a fixed interleaved order, median.  A
+        # comparison only: cuBLAS is not on the path.
+        res = {"note": "cuBLAS writes C in the input type and does not read it; gemm_mixed writes FP32 C "
+                       "(and reads it at beta = 0.5). 200 back-to-back launches per case, median of 3 rounds; "
+                       "both under the same power cap"}
+        for dt, tdt, name in ((0, torch.float16, "f16"), (1, torch.bfloat16, "bf16")):
+            Aq = torch.empty((N, N), dtype=tdt, device="cuda")
+            Bq = torch.empty((N, N), dtype=tdt, device="cuda")
+            b.tc_quantize(dt, N, N, Ad, N, Aq, N, 0)
+            b.tc_quantize(dt, N, N, Bd, N, Bq, N, 1)
+            Cf = torch.zeros((N, N), dtype=torch.float32, device="cuda")
+            Ch = torch.empty((N, N), dtype=tdt, device="cuda")
+            Bt = Bq.t()   # k x n view of the K-major copy
+            cases = {
+                "gemm_mixed_beta0": lambda: b.gemm_mixed(dt, N, N, N, 1.0, Aq, N, 0, Bq, N, 1, 0.0, Cf, N),
+                "gemm_mixed_beta0.5": lambda: b.gemm_mixed(dt, N, N, N, 1.0, Aq, N, 0, Bq, N, 1, 0.5, Cf, N),
+                "cublas": lambda: torch.matmul(Aq, Bt, out=Ch),
+            }
+            times = {k: [] for k in cases}
+            for _ in range(3):
+                for k, f in cases.items():
+                    times[k].append(_time_ms(f, 200, warm=10))
+            b.tc_sync_status()
+            r = {k: {"ms": float(np.median(v)), "tflops": flops / (float(np.median(v)) * 1e-3) / 1e12}
+                 for k, v in times.items()}
+            r["ratio_beta0_to_cublas"] = r["gemm_mixed_beta0"]["tflops"] / r["cublas"]["tflops"]
+            res[name] = r
+            del Aq, Bq, Cf, Ch, Bt
+            torch.cuda.empty_cache()
+        return res
+
+    out["gemm_vs_cublas_n8192"] = _row("gemm_vs_cublas_n8192", vs_cublas)
     del Ad, Bd
     torch.cuda.empty_cache()
 

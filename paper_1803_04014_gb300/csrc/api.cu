@@ -4,6 +4,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -40,11 +41,18 @@ struct Device {
     int sm_count = 0;
     int cc_major = 0, cc_minor = 0;
     int* status = nullptr;  // device status word (first error wins)
+    unsigned* kflags = nullptr;          // kKpartRegions regions of flags for parts of K
+    std::atomic<unsigned> kregion{0};    // next region (launches take them in turn)
 };
 
 std::mutex g_mu;
 Device g_dev[64];
 static __device__ __align__(256) int g_status_word[64];  // one copy per device; word 0 is used
+// Flags of the pair kernel's parts of K (static, zero at module load; every launch leaves its region
+// zero).  Launches take the regions in turn, so launches in flight at the same time on different
+// streams use different flags unless kKpartRegions of them are.
+constexpr int kKpartRegions = 64;
+static __device__ __align__(256) unsigned g_kpart_flags[kKpartRegions * tcg::kKpartRegionWords];
 
 tc_status get_device(Device** out) {
     int dev = 0;
@@ -63,6 +71,10 @@ tc_status get_device(Device** out) {
         if ((e = cudaGetSymbolAddress(&sw, g_status_word)) != cudaSuccess)
             return cuda_fail(e, "cudaGetSymbolAddress(status)");
         d.status = static_cast<int*>(sw);
+        void* kf = nullptr;
+        if ((e = cudaGetSymbolAddress(&kf, g_kpart_flags)) != cudaSuccess)
+            return cuda_fail(e, "cudaGetSymbolAddress(flags)");
+        d.kflags = static_cast<unsigned*>(kf);
         // keep freed stream-ordered workspace cached in the pool instead of returning it each sync
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
@@ -73,6 +85,13 @@ tc_status get_device(Device** out) {
     }
     *out = &d;
     return TC_OK;
+}
+
+// The flags region of one launch of the pair kernel with parts of K.
+unsigned* kpart_region(Device* d) {
+    if (!d->kflags) return nullptr;
+    const unsigned r = d->kregion.fetch_add(1u, std::memory_order_relaxed) % kKpartRegions;
+    return d->kflags + static_cast<size_t>(r) * tcg::kKpartRegionWords;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -172,8 +191,9 @@ bool tune_lookup(int dt, int64_t m, int64_t n, int64_t k, TuneCfg* out) {
 //   Raster bands of 8 M-tiles: the tiles in flight then span 8 M-tiles and about 10 N-tiles, the
 //   smallest A-band plus B-panel working set (DRAM reads of the FP16 GEMM at N = 8192: 1.36-1.41 GB
 //   against 1.53 GB with bands of 16 and 2.4 GB with bands of 2 or 32, at the same speed).
-//   A last round of pair tiles that would keep at most half of the CTA pairs busy runs as
-//   256 x 128 halves.
+//   A last round of pair tiles that would keep at most half of the CTA pairs busy runs as two units
+//   per tile over parts of K (tail 2): an MMA takes about as long at N = 128 as at N = 256, so
+//   256 x 128 halves (tail 1) take as long as whole tiles.
 //   K order: a CTA pair takes every ncl-th tile of the raster, so its i-th tile belongs to round i
 //   of tiles in flight together; consecutive rounds of a raster band share the band's A panels.
 //   Walking K downwards in odd rounds starts each round on the k-blocks the round before it left in
@@ -182,7 +202,7 @@ bool tune_lookup(int dt, int64_t m, int64_t n, int64_t k, TuneCfg* out) {
 //   reproducible.
 //   Clusters of two CTAs.
 GemmCfg default_gemm_cfg(int64_t m, int64_t n, int sm_count) {
-    GemmCfg c{1, 8, 1, 1, 2, 256};
+    GemmCfg c{1, 8, 2, 1, 2, 256};
     auto tiles = [&](int64_t bn) { return ((m + 127) / 128) * ((n + bn - 1) / bn); };
     if (tiles(64) <= sm_count) {
         c.pair = 0;
@@ -197,7 +217,8 @@ GemmCfg default_gemm_cfg(int64_t m, int64_t n, int sm_count) {
 }
 
 // Environment overrides of a configuration: TCGEMM_TILE=single|pair, TCGEMM_BN=64|128|256 (single
-// CTAs), TCGEMM_GROUP_M, TCGEMM_PAIR_TAIL=full|split, TCGEMM_K_ORDER=forward|serpentine and
+// CTAs), TCGEMM_GROUP_M, TCGEMM_PAIR_TAIL=full|halves|split (split: parts of K),
+// TCGEMM_K_ORDER=forward|serpentine and
 // TCGEMM_CLUSTER=2|4.
 int env_choice(const char* name, const char* a, int va, const char* b, int vb, int dflt) {
     const char* env = getenv(name);
@@ -217,7 +238,8 @@ GemmCfg apply_env(GemmCfg c) {
         const int v = atoi(env);
         if (v >= 1 && v <= 1024) c.group_m = v;
     }
-    c.tail = env_choice("TCGEMM_PAIR_TAIL", "full", 0, "split", 1, c.tail);
+    c.tail = env_choice("TCGEMM_PAIR_TAIL", "full", 0, "split", 2, c.tail);
+    c.tail = env_choice("TCGEMM_PAIR_TAIL", "halves", 1, "kparts", 2, c.tail);
     c.korder = env_choice("TCGEMM_K_ORDER", "forward", 0, "serpentine", 1, c.korder);
     c.cluster = env_choice("TCGEMM_CLUSTER", "2", 2, "4", 4, c.cluster);
     return c;
@@ -232,9 +254,9 @@ GemmCfg gemm_cfg_for(int dt, int64_t m, int64_t n, int64_t k, int sm_count) {
 
 // Raster band, tail split and K order of the refined GEMMs (CTA pairs): the untuned values unless
 // overridden by the environment.
-int gemm_group_m() { return apply_env(GemmCfg{1, 8, 1, 1, 2, 256}).group_m; }
-int gemm_split_tail() { return apply_env(GemmCfg{1, 8, 1, 1, 2, 256}).tail; }
-int gemm_serpentine() { return apply_env(GemmCfg{1, 8, 1, 1, 2, 256}).korder; }
+int gemm_group_m() { return apply_env(GemmCfg{1, 8, 2, 1, 2, 256}).group_m; }
+int gemm_split_tail() { return apply_env(GemmCfg{1, 8, 2, 1, 2, 256}).tail; }
+int gemm_serpentine() { return apply_env(GemmCfg{1, 8, 2, 1, 2, 256}).korder; }
 
 // Pending failure-injection request of this thread (tc_debug_stall_next_gemm).
 thread_local int g_stall_next = 0;  // k-block + 1, 0 = none
@@ -301,6 +323,8 @@ tc_status tc_sync_status(void* stream) {
         return cuda_fail(e, "read status");
     if (word != 0) {
         cudaMemset(d->status, 0, sizeof(int));
+        // a kernel that gave up may have left flags of parts of K raised
+        cudaMemset(d->kflags, 0, sizeof(unsigned) * kKpartRegions * tcg::kKpartRegionWords);
         return fail(TC_ERR_TIMEOUT, "a kernel gave up on a bounded wait (device status %d)", word);
     }
     return TC_OK;
@@ -427,6 +451,7 @@ tc_status gemm_mixed_impl(int32_t dt, int64_t m, int64_t n, int64_t k, float alp
     p.stall_at = take_stall();
     p.staged_epilogue = gemm_staged_epilogue();
     p.split_tail = cfg.tail;
+    p.kpart_flags = kpart_region(d);
     p.serpentine = cfg.korder;
     p.quad = (p.pair && !b_mn && cfg.cluster == 4) ? 1 : 0;
     p.m = m; p.n = n; p.k = k;
@@ -611,6 +636,7 @@ tc_status split_gemm(const char* name, int scheme, int32_t piece, int32_t nprod,
         p.group_m = gemm_group_m();
         p.stall_at = take_stall();
         p.split_tail = gemm_split_tail();
+        p.kpart_flags = kpart_region(d);
         p.serpentine = gemm_serpentine();
         p.m = m; p.n = n; p.k = k;
         p.alpha = alpha; p.beta = beta;
@@ -1622,12 +1648,13 @@ tc_status tc_autotune_gemm(int32_t dt, int64_t m, int64_t n, int64_t k, void* st
     // tile kind and width (single CTAs 128 x 64 / 128 x 128 / 128 x 256, or pairs), then the raster
     // band of the best of those; for pairs then clusters of four (A multicast between two pairs,
     // whole tiles only) with each band, and the tail split; last the K order
-    for (int bn : {64, 128, 256}) consider(GemmCfg{0, 8, 1, 1, 2, bn});
-    if (m > 128) consider(GemmCfg{1, 8, 1, 1, 2, 256});  // a pair tile would leave half of it empty
-    for (int g : {4, 8, 16, 32}) consider(GemmCfg{best.cfg.pair, g, 1, 1, 2, best.cfg.bn});
+    for (int bn : {64, 128, 256}) consider(GemmCfg{0, 8, 2, 1, 2, bn});
+    if (m > 128) consider(GemmCfg{1, 8, 2, 1, 2, 256});  // a pair tile would leave half of it empty
+    for (int g : {4, 8, 16, 32}) consider(GemmCfg{best.cfg.pair, g, 2, 1, 2, best.cfg.bn});
     if (best.cfg.pair) {
         for (int g : {4, 8, 16, 32}) consider(GemmCfg{1, g, 1, 1, 4, 256});
-        if (best.cfg.cluster == 2) consider(GemmCfg{1, best.cfg.group_m, 0, best.cfg.korder, 2, 256});
+        if (best.cfg.cluster == 2)
+            for (int tail : {0, 1, 2}) consider(GemmCfg{1, best.cfg.group_m, tail, best.cfg.korder, 2, 256});
     }
     consider(GemmCfg{best.cfg.pair, best.cfg.group_m, best.cfg.tail, 0, best.cfg.cluster, best.cfg.bn});
     cudaFreeAsync(buf, st);
@@ -1731,7 +1758,7 @@ tc_status tc_autotune_load(const char* path) {
         }
         key = {v[0], v[1], v[2], v[3]};
         const GemmCfg& c = t.cfg;
-        if ((c.pair == 0 || c.pair == 1) && c.group_m >= 1 && c.group_m <= 1024 && (c.tail == 0 || c.tail == 1) &&
+        if ((c.pair == 0 || c.pair == 1) && c.group_m >= 1 && c.group_m <= 1024 && (c.tail >= 0 && c.tail <= 2) &&
             (c.korder == 0 || c.korder == 1) && (c.cluster == 2 || c.cluster == 4) &&
             (c.bn == 64 || c.bn == 128 || c.bn == 256)) {
             g_tune[key] = t;

@@ -57,28 +57,51 @@ struct Args {
     int staged_epilogue;  // pair kernel: transpose 32 x 32 chunks through shared memory before storing
     float corr_scale;     // scaled split: 2^-s applied to the correction accumulator
     // pair kernel: work units are the first full_units tiles of the raster (256 x 256) followed by
-    // the remaining tiles cut into two 256 x 128 halves each, num_units in all; idesc_half is the
-    // instruction descriptor of the half-width MMA.  Cutting the last, partial round of tiles in
-    // two lets twice as many CTA pairs share it.
+    // the remaining tiles cut in two each, num_units in all.  Cutting the last, partial round of
+    // tiles in two lets twice as many CTA pairs share it.
+    //   split_tail 1: two 256 x 128 halves (idesc_half is the half-width MMA's descriptor);
+    //   split_tail 2: two parts of K, k-blocks [0, kb_split) and [kb_split, num_kb).  The first
+    //     part's epilogue stores alpha * P_1 + beta * C into C and raises one flag per epilogue
+    //     warp in kflags; the second part's warp waits for its flag and stores alpha * P_2 + C.
+    //     An MMA takes about as long at N = 128 as at N = 256, so halves of N take as long as
+    //     whole tiles, and parts of K less.
     int full_units, num_units;
     uint32_t idesc_half;
-    int split_tail;  // 0 keeps every unit full-width (TCGEMM_PAIR_TAIL=full)
+    int split_tail;  // 0 keeps every unit whole (TCGEMM_PAIR_TAIL=full)
+    int kb_split;
+    unsigned* kflags;
     int serpentine;  // pair kernel: every other unit of a CTA pair walks K from the end (L2 reuse)
 };
 
-// Work unit u of the pair kernel: its tile (mb, nb), the column offset inside the 256-wide tile
-// and the unit's width (256, or 128 for the halves of the last tiles).
-__device__ __forceinline__ void unit_coords(const Args& a, int u, int& mb, int& nb, int& coff, int& width) {
+// Work unit u of the pair kernel: its tile (mb, nb), the column offset inside the 256-wide tile,
+// the unit's width (256, or 128 for the halves of the last tiles), its k-blocks [kb0, kb1) and its
+// part of K (0: all of it; 1, 2: the first or second part of a tile of the last round).
+struct Unit {
+    int mb, nb, coff, width, kb0, kb1, kpart;
+};
+__device__ __forceinline__ Unit unit_coords(const Args& a, int u) {
+    Unit w{0, 0, 0, 256, 0, a.num_kb, 0};
     int t = u;
-    coff = 0;
-    width = 256;
     if (u >= a.full_units) {
         const int h = u - a.full_units;
         t = a.full_units + (h >> 1);
-        coff = (h & 1) * 128;
-        width = 128;
+        if (a.split_tail == 2) {
+            w.kpart = 1 + (h & 1);
+            if (h & 1) w.kb0 = a.kb_split;
+            else w.kb1 = a.kb_split;
+        } else {
+            w.coff = (h & 1) * 128;
+            w.width = 128;
+        }
     }
-    tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
+    tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, w.mb, w.nb);
+    return w;
+}
+
+// Flag of epilogue warp (rank, quarter) of the unit's tile, for parts of K of the pair kernel.
+__device__ __forceinline__ unsigned* kpart_flag(const Args& a, int u, uint32_t rank, int quarter) {
+    const int j = (u - a.full_units) >> 1;
+    return a.kflags + (j * 2 + static_cast<int>(rank)) * 4 + quarter;
 }
 
 template <int BN, int STAGES, int NA, int NB>
@@ -379,8 +402,8 @@ struct PairLayout {
     static constexpr int kBarOffset = STAGES * kStageBytes;
     static constexpr int kNumBars = 2 * STAGES + 5;
     static constexpr int kSlotOffset = kBarOffset + 8 * kNumBars;
-    static constexpr int kEpiOffset = kSlotOffset + 16;          // 4 warps x 32 x 33 floats of store staging
-    static constexpr int kBytes = kEpiOffset + 4 * 32 * 33 * 4 + 1024;
+    static constexpr int kEpiOffset = (kSlotOffset + 16 + 127) / 128 * 128;  // 4 warps x 4 KB of store staging
+    static constexpr int kBytes = kEpiOffset + 4 * kChunkSlotBytes + 1024;
     static constexpr int kTmemCols = 512;  // two 256-column accumulators
 };
 
@@ -458,15 +481,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int s = 0; s < STAGES; ++s) issued_phase[s] = -1;
             bool ok = true;
             for (int u = cid; ok && u < a.num_units; u += ncl) {
-                int mb, nb, coff, width;
-                unit_coords(a, u, mb, nb, coff, width);
+                const Unit w = unit_coords(a, u);
+                const int mb = w.mb;
                 // this CTA's half of the unit's B rows (a half-width unit uses the first 64 of the 128 loaded)
-                const int brow = nb * PN + coff + static_cast<int>(rank) * (width >> 1);
+                const int brow = w.nb * PN + w.coff + static_cast<int>(rank) * (w.width >> 1);
                 // odd rounds of units walk K downwards: a round of units shares A panels with the round
                 // before it (same raster band), and starts on the k-blocks that round left in L2
                 const bool down = a.serpentine && (((u - cid) / ncl) & 1);
-                for (int kb_i = 0; kb_i < a.num_kb; ++kb_i) {
-                    const int kb = down ? a.num_kb - 1 - kb_i : kb_i;
+                for (int kb_i = 0; kb_i < w.kb1 - w.kb0; ++kb_i) {
+                    const int kb = down ? w.kb1 - 1 - kb_i : w.kb0 + kb_i;
                     if (!wait(empty_bar(stage), phase ^ 1u)) {
                         ok = false;
                         break;
@@ -533,8 +556,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * PN);
-                const uint32_t idesc = u < a.full_units ? a.idesc : a.idesc_half;
-                for (int kb = 0; kb < a.num_kb; ++kb) {
+                const Unit w = unit_coords(a, u);
+                const uint32_t idesc = w.width == 256 ? a.idesc : a.idesc_half;
+                for (int kb = 0; kb < w.kb1 - w.kb0; ++kb) {
                     if (!wait(full_bar(stage), phase)) {
                         ok = false;
                         break;
@@ -585,26 +609,43 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int quarter = warp & 3;
         float alpha = a.alpha;
         if constexpr (KIND == 1) alpha = alpha * (1.0f / *a.scale_a) * (1.0f / *a.scale_b);
-        const float beta = a.beta;
+        const float beta_in = a.beta;
+        // flag of the first part of K set: a bounded poll with acquire by every lane
+        auto wait_flag = [&](const unsigned* f) {
+            const bool ok = poll_flag_acquire(f, abort_flag, a.status);
+            if (!ok) st_shared_cluster_u32(peer_abort, 1u);
+            return __all_sync(0xffffffffu, ok);
+        };
+        // this warp's stores of the first part of K are visible before its flag is raised
+        auto raise_flag = [&](int u) {
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) st_release_gpu(kpart_flag(a, u, rank, quarter), 1u);
+        };
         const bool vec_ok = ((a.ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15u) == 0);
         const uint32_t leader_tempty0 = mapa_shared(tempty_bar(0), 0);
         const uint32_t leader_tempty1 = mapa_shared(tempty_bar(1), 0);
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int u = cid; u < a.num_units; u += ncl) {
-            int mb, nb, coff, width;
-            unit_coords(a, u, mb, nb, coff, width);
-            const int row = mb * PM + static_cast<int>(rank) * 128 + quarter * 32 + lane;
-            const int col0 = nb * PN + coff;
+            const Unit w = unit_coords(a, u);
+            const int width = w.width;
+            const int row = w.mb * PM + static_cast<int>(rank) * 128 + quarter * 32 + lane;
+            const int col0 = w.nb * PN + w.coff;
+            // the second part of K adds its product to what the first part's warp stored: wait for
+            // that warp's flag before reading C (beta = 1 for this unit)
+            const float beta = w.kpart == 2 ? 1.0f : beta_in;
+            if (w.kpart == 2 && !wait_flag(kpart_flag(a, u, rank, quarter))) break;
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                    static_cast<uint32_t>(acc * PN);
             float* crow = a.C + static_cast<int64_t>(row) * a.ldc + col0;
             if (a.staged_epilogue) {
                 // rows r0..r0+31 of this warp: each 32 x 32 chunk goes through shared memory and is
                 // written as four 128-byte row segments per store instruction
-                float* stg = reinterpret_cast<float*>(base_ptr + L::kEpiOffset) + (warp - 2) * (32 * 33);
+                uint8_t* slot = base_ptr + L::kEpiOffset + (warp - 2) * kChunkSlotBytes;
                 const int r0 = row - lane;
-                const int cc = (lane & 7) * 4;
+                const int g = lane & 7;
+                const int cc = g * 4;
                 // old C of chunk c, in the store pattern (rows r0 + 4q + lane / 8, columns cc..cc+3):
                 // the first two chunks are read before the accumulator is waited for, so their latency
                 // hides behind the main loop, and each later one two chunks ahead of its use
@@ -616,8 +657,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int grow = r0 + q * 4 + (lane >> 3);
                         o[q] = make_float4(0.f, 0.f, 0.f, 0.f);
                         if (grow < a.m && vec_ok && cc + 4 <= nc)
-                            o[q] = *reinterpret_cast<const float4*>(a.C + static_cast<int64_t>(grow) * a.ldc +
-                                                                    col0 + c + cc);
+                            o[q] = __ldcg(reinterpret_cast<const float4*>(a.C + static_cast<int64_t>(grow) * a.ldc +
+                                                                          col0 + c + cc));
                     }
                 };
                 auto store_chunk = [&](int c, const float4 (&old)[8]) {
@@ -625,7 +666,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     float v[32];
                     tmem_load_32(taddr + c, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = v[j];
+                    for (int q = 0; q < 8; ++q)
+                        *reinterpret_cast<float4*>(slot + chunk_slot_off(lane, q)) =
+                            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                     __syncwarp();
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
@@ -633,7 +676,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int grow = r0 + rr;
                         if (grow < a.m) {
                             float* p = a.C + static_cast<int64_t>(grow) * a.ldc + col0 + c + cc;
-                            const float* sv = stg + rr * 33 + cc;
+                            const float4 s4 = *reinterpret_cast<const float4*>(slot + chunk_slot_off(rr, g));
+                            const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
                             if (vec_ok && cc + 4 <= nc) {
                                 float4 o = make_float4(alpha * sv[0], alpha * sv[1], alpha * sv[2], alpha * sv[3]);
                                 if (beta != 0.0f) {
@@ -646,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                             } else {
                                 for (int e = 0; e < 4; ++e)
                                     if (cc + e < nc)
-                                        p[e] = (beta != 0.0f) ? fmaf(alpha, sv[e], beta * p[e]) : alpha * sv[e];
+                                        p[e] = (beta != 0.0f) ? fmaf(alpha, sv[e], beta * __ldcg(p + e)) : alpha * sv[e];
                             }
                         }
                     }
@@ -672,6 +716,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (lane == 0) mbar_arrive_cluster(acc == 0 ? leader_tempty0 : leader_tempty1);
                 acc ^= 1;
                 if (acc == 0) acc_phase ^= 1u;
+                if (w.kpart == 1) raise_flag(u);
+                if (w.kpart == 2 && lane == 0) *kpart_flag(a, u, rank, quarter) = 0u;  // ready for the next launch
                 continue;
             }
             const bool ok = wait(tfull_bar(acc), acc_phase);
@@ -690,7 +736,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int j = 0; j < 8; ++j) {
                             float4 o;
                             if (beta != 0.0f) {
-                                const float4 old = *reinterpret_cast<const float4*>(p + 4 * j);
+                                const float4 old = __ldcg(reinterpret_cast<const float4*>(p + 4 * j));
                                 o.x = fmaf(alpha, v[4 * j + 0], beta * old.x);
                                 o.y = fmaf(alpha, v[4 * j + 1], beta * old.y);
                                 o.z = fmaf(alpha, v[4 * j + 2], beta * old.z);
@@ -706,7 +752,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     } else {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
-                            if (j < ncols) p[j] = (beta != 0.0f) ? fmaf(alpha, v[j], beta * p[j]) : alpha * v[j];
+                            if (j < ncols) p[j] = (beta != 0.0f) ? fmaf(alpha, v[j], beta * __ldcg(p + j)) : alpha * v[j];
                         }
                     }
                 }
@@ -716,6 +762,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) mbar_arrive_cluster(acc == 0 ? leader_tempty0 : leader_tempty1);
             acc ^= 1;
             if (acc == 0) acc_phase ^= 1u;
+            if (w.kpart == 1) raise_flag(u);
+            if (w.kpart == 2 && lane == 0) *kpart_flag(a, u, rank, quarter) = 0u;
         }
     }
 
@@ -759,6 +807,8 @@ cudaError_t run_pair(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args&
     // half the pairs) is cut into half-width units
     const int rem = a.num_tiles % clusters;
     a.full_units = a.num_tiles;
+    // parts of K need two k-blocks and a flag per epilogue warp of each cut tile; else halves of N
+    if (a.split_tail == 2 && (a.num_kb < 2 || !a.kflags || 8 * rem > kKpartRegionWords)) a.split_tail = 1;
     if (rem > 0 && 2 * rem <= clusters && a.split_tail) a.full_units = a.num_tiles - rem;
     a.num_units = a.full_units + 2 * (a.num_tiles - a.full_units);
     if (clusters > a.num_units) {
@@ -1246,6 +1296,9 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
         a.full_units = a.num_units = a.num_tiles;
         a.split_tail = p.split_tail;
         a.serpentine = p.serpentine;
+        // the first part of K is the shorter, so that its epilogue overlaps the second's main loop
+        a.kb_split = a.num_kb * 7 / 16 > 0 ? a.num_kb * 7 / 16 : 1;
+        a.kflags = p.kpart_flags;
         const int max_clusters = p.sm_count / 2;
         const int clusters = a.num_tiles < max_clusters ? a.num_tiles : max_clusters;
         if (clusters <= 0) return cudaSuccess;

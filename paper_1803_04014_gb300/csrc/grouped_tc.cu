@@ -46,17 +46,11 @@ constexpr int kBarOff = kStages * kStage;
 constexpr int kNumBars = 2 * kStages + 5;
 constexpr int kSlotOff = kBarOff + 8 * kNumBars;
 constexpr int kEpiWarps = 8;                         // two warps per TMEM lane quarter, 128 columns each
-constexpr int kEpiWarpBytes = 32 * 32 * 4;           // one 32 x 32 FP32 chunk, 128-byte rows
+constexpr int kEpiWarpBytes = kChunkSlotBytes;       // one 32 x 32 FP32 chunk, 128-byte rows
 constexpr int kEpiOff = (kSlotOff + 16 + 127) / 128 * 128;
 constexpr int kSmem = kEpiOff + kEpiWarps * kEpiWarpBytes + 1024;
 static_assert(kSmem <= 232448, "shared memory per CTA");
 
-// Byte offset of the 16-byte group `g` (columns 4g..4g+3) of row `r` in a chunk slot: the
-// group index is XORed with the row mod 8, so a warp's 16-byte accesses are free of bank
-// conflicts both when each lane writes its own row and when 8 lanes read one row.
-__device__ __forceinline__ uint32_t slot_off(int r, int g) {
-    return static_cast<uint32_t>(r * 128 + ((g ^ (r & 7)) << 4));
-}
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 struct Args {
@@ -322,7 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                     tmem_load_32(taddr + c, v);
 #pragma unroll
                     for (int q = 0; q < 8; ++q)
-                        *reinterpret_cast<float4*>(slot_ptr + slot_off(lane, q)) =
+                        *reinterpret_cast<float4*>(slot_ptr + chunk_slot_off(lane, q)) =
                             make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                     __syncwarp();
 #pragma unroll
@@ -331,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                         const int grow = r0 + rr;
                         if (grow < P.m) {
                             float* p = a.c_base + P.off_c + static_cast<int64_t>(grow) * P.ldc + col0 + c + cc;
-                            const float4 sv = *reinterpret_cast<const float4*>(slot_ptr + slot_off(rr, g));
+                            const float4 sv = *reinterpret_cast<const float4*>(slot_ptr + chunk_slot_off(rr, g));
                             if (vec_ok && cc + 4 <= nc) {
                                 float4 o = make_float4(alpha * sv.x, alpha * sv.y, alpha * sv.z, alpha * sv.w);
                                 if (beta != 0.0f) {

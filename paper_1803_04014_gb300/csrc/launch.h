@@ -88,10 +88,14 @@ struct TcGemmLaunch {
                         // split) accumulate apart and are multiplied by 2^-s in the epilogue
     int serpentine;     // pair kernels: every other round of tiles of a CTA pair walks K downwards
     int split_tail;     // pair kernel: a last round of tiles keeping at most half of the pairs busy runs
-                        // as 256 x 128 halves
+                        // as two units per tile: 1 = 256 x 128 halves, 2 = two parts of K (which need
+                        // kpart_flags; else halves)
+    unsigned* kpart_flags;  // kKpartRegionWords zero words of device memory, zero again when the kernel ends
     int quad;           // one product, K-major B: clusters of four CTAs (two pairs) sharing A by TMA
                         // multicast (gemm_quad.cu); tmA then has a 64-row box
 };
+// Flags of one launch of the pair kernel with parts of K: 8 per cut tile (at most 128 tiles).
+constexpr int kKpartRegionWords = 1024;
 // tmA: 3-D map {k, m, na} with a 128 x (128 bytes) box; tmB: {k, n, nb} with a bn x (128 bytes) box.
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmLaunch& p, cudaStream_t st);
 // ---- gemm_quad.cu: the pair GEMM on clusters of four CTAs, A multicast between the two pairs.

@@ -92,6 +92,29 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
+// Bounded poll of a flag in global memory that another CTA of the grid raises with a release
+// store: true once it reads non-zero (with acquire at GPU scope), false on the abort flag or after
+// kWaitLimitNs (then the status word says so).
+__device__ __forceinline__ bool poll_flag_acquire(const unsigned* f, volatile int* abort_flag, int* status) {
+    const uint64_t t0 = global_timer_ns();
+    for (uint32_t it = 0;; ++it) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+        if (v != 0u) return true;
+        if (*abort_flag) return false;
+        if ((it & 15u) == 15u && global_timer_ns() - t0 > kWaitLimitNs) {
+            *abort_flag = 1;
+            raise_status(status, TC_DEV_TIMEOUT);
+            return false;
+        }
+        __nanosleep(128);
+    }
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned* f, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
+}
+
 // try_wait with cluster-scope acquire: for barriers that threads of the peer
 // CTA complete with a release.cluster arrive after writing shared memory the
 // waiter's MMAs then read.
@@ -120,6 +143,15 @@ __device__ __forceinline__ bool mbar_wait_acq_cluster(uint32_t bar, uint32_t par
             return false;
         }
     }
+}
+
+// Epilogue staging of one 32 x 32 FP32 accumulator chunk per warp: 32 rows of 128 bytes.  Byte
+// offset of the 16-byte group `g` (columns 4g..4g+3) of row `r`: the group index is XORed with the
+// row mod 8, so a warp's 16-byte accesses are free of bank conflicts both when each lane writes
+// its own row and when 8 lanes read one row.
+constexpr int kChunkSlotBytes = 32 * 32 * 4;
+__device__ __forceinline__ uint32_t chunk_slot_off(int r, int g) {
+    return static_cast<uint32_t>(r * 128 + ((g ^ (r & 7)) << 4));
 }
 
 // Register budget of the executing warpgroup (all four warps execute it).

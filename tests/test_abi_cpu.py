@@ -147,7 +147,7 @@ def test_autotune_table_save_and_load(lib, tmp_path):
     # format without bn (read as bn = 256) and of the older seven-field format (tail = 1,
     # korder = 1, cluster = 2, bn = 256)
     good.write_text("# comment\n0 13 13 13 1 16 0 1 4 256 0.65\n1 10 10 10 0 8 0.01\n2 12 12 12 1 4 1 0 2 0.2\n"
-                    "0 8 8 8 0 8 1 1 2 64 0.004\n")
+                    "0 8 8 8 0 8 1 1 2 64 0.004\n0 11 11 11 1 8 2 1 2 256 0.1\n")
     b.tc_autotune_load(good)
     out = tmp_path / "out.txt"
     b.tc_autotune_save(out)
@@ -156,8 +156,9 @@ def test_autotune_table_save_and_load(lib, tmp_path):
     assert any(l.startswith("1 10 10 10 0 8 1 1 2 256 ") for l in lines)
     assert any(l.startswith("2 12 12 12 1 4 1 0 2 256 ") for l in lines)
     assert any(l.startswith("0 8 8 8 0 8 1 1 2 64 ") for l in lines)
+    assert any(l.startswith("0 11 11 11 1 8 2 1 2 256 ") for l in lines)   # tail 2: parts of K
     for text in ("0 13 13 13 7 16 0.5\n",               # pair must be 0 or 1
-                 "0 13 13 13 1 16 2 1 2 0.5\n",         # tail must be 0 or 1
+                 "0 13 13 13 1 16 3 1 2 0.5\n",         # tail must be 0, 1 or 2
                  "0 13 13 13 1 16 1 5 2 0.5\n",         # korder must be 0 or 1
                  "0 13 13 13 1 16 1 1 3 0.5\n",         # cluster must be 2 or 4
                  "0 13 13 13 0 16 1 1 2 96 0.5\n",      # bn must be 64, 128 or 256

@@ -561,7 +561,9 @@ def test_gemm_default_tiles_at_small_sizes(b, dt, mnk):
 @pytest.mark.parametrize("mnk", [(2560, 2560, 192), (2304, 2600, 320), (256, 2560, 128)])
 def test_gemm_pair_full_and_half_width_units(b, monkeypatch, dt, mnk):
     # 100 and 99 tiles of 256 x 256 over 76 CTA pairs: the tiles of the partial last round run as
-    # 256 x 128 halves after the full tiles; 10 tiles: every tile runs as two halves
+    # two units each after the full tiles; 10 tiles: every tile runs as two units.  By default the
+    # units are parts of K (the first stores alpha P1 + beta C, the second adds alpha P2 to it
+    # after its flag), with TCGEMM_PAIR_TAIL=halves 256 x 128 halves.
     monkeypatch.setenv("TCGEMM_TILE", "pair")
     m, n, k = mnk
     A = synth.uniform((m, k), seed=131)
@@ -571,6 +573,52 @@ def test_gemm_pair_full_and_half_width_units(b, monkeypatch, dt, mnk):
     ref = og.gemm_mixed(DT_NAME[dt], A, B, 1.0, -0.5, C0)
     ok, info = elementwise_ok(C, ref, _mag(dt, A, B, 1.0, -0.5, C0), k)
     assert ok, info
+    # parts of K add in a fixed order: the same bits every run
+    assert np.array_equal(_run_mixed(b, dt, A, B, 1.0, -0.5, C0), C)
+    # halves of N run the whole K chain of each element: the bits of whole tiles
+    monkeypatch.setenv("TCGEMM_PAIR_TAIL", "halves")
+    halves = _run_mixed(b, dt, A, B, 1.0, -0.5, C0)
+    ok, info = elementwise_ok(halves, ref, _mag(dt, A, B, 1.0, -0.5, C0), k)
+    assert ok, info
+    monkeypatch.setenv("TCGEMM_PAIR_TAIL", "full")
+    assert np.array_equal(_run_mixed(b, dt, A, B, 1.0, -0.5, C0), halves)
+
+
+@pytest.mark.parametrize("epi", ["staged", "direct"])
+@pytest.mark.parametrize("beta", [0.0, 0.75])
+@pytest.mark.parametrize("case", ["f16", "e4m3", "f16_row_major_b"])
+def test_gemm_pair_parts_of_k(b, monkeypatch, epi, beta, case):
+    # parts of K on 24 cut tiles (100 tiles over 76 CTA pairs), K = 16 k-blocks (the first part 7);
+    # m and n ragged so that some epilogue warps of cut tiles hold no rows of C and the last tiles
+    # hold a few columns; both epilogues, beta 0 (the second part still reads what the first
+    # stored) and 0.75, E4M3 with its scales and a row-major B read as MN-major
+    monkeypatch.setenv("TCGEMM_TILE", "pair")
+    monkeypatch.setenv("TCGEMM_EPILOGUE", epi)
+    m, n, k = 2500, 2520, 1024
+    dt = 2 if case == "e4m3" else 0
+    A = synth.uniform((m, k), seed=141)
+    B = synth.uniform((k, n), seed=142)
+    C0 = synth.uniform((m, n), seed=143)
+    if case == "f16_row_major_b":
+        Aq = torch.empty((m, k), dtype=torch.float16, device="cuda")
+        Bq = torch.empty((k, n), dtype=torch.float16, device="cuda")
+        b.tc_quantize(0, m, k, dev(A), k, Aq, k, 0)
+        b.tc_quantize(0, k, n, dev(B), n, Bq, n, 0)
+        C = dev(C0)
+        b.gemm_mixed(0, m, n, k, 1.5, Aq, k, 0, Bq, n, 0, beta, C, n)
+        b.tc_sync_status()
+        got = host(C)
+        C = dev(C0)
+        b.gemm_mixed(0, m, n, k, 1.5, Aq, k, 0, Bq, n, 0, beta, C, n)
+        b.tc_sync_status()
+        again = host(C)
+    else:
+        got = _run_mixed(b, dt, A, B, 1.5, beta, C0)
+        again = _run_mixed(b, dt, A, B, 1.5, beta, C0)
+    ref = og.gemm_mixed(DT_NAME[dt], A, B, 1.5, beta, C0)
+    ok, info = elementwise_ok(got, ref, _mag(dt, A, B, 1.5, beta, C0), k)
+    assert ok, info
+    assert np.array_equal(got, again)
 
 
 @pytest.mark.parametrize("tile", ["single", "pair"])
