@@ -70,6 +70,9 @@ struct Args {
     int split_tail;  // 0 keeps every unit whole (TCGEMM_PAIR_TAIL=full)
     int kb_split;
     unsigned* kflags;
+    // pair kernel with promotion: parts of K only (split_tail 2), cut between chunks: the first part
+    // takes chunks [0, chunk_split)
+    int chunk_split;
     int serpentine;  // pair kernel: every other unit of a CTA pair walks K from the end (L2 reuse)
 };
 
@@ -95,6 +98,23 @@ __device__ __forceinline__ Unit unit_coords(const Args& a, int u) {
         }
     }
     tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, w.mb, w.nb);
+    return w;
+}
+
+// Work unit u of the pair kernel with promotion: its tile, its chunks [c0, c1) of CHUNK_KB k-blocks
+// and its part of K (0: all of it; 1, 2: first or second part of a tile of the last round).
+struct PromoteUnit {
+    int t, c0, c1, kpart;
+};
+__device__ __forceinline__ PromoteUnit promote_unit(const Args& a, int u, int nchunks) {
+    PromoteUnit w{u, 0, nchunks, 0};
+    if (u >= a.full_units) {
+        const int h = u - a.full_units;
+        w.t = a.full_units + (h >> 1);
+        w.kpart = 1 + (h & 1);
+        if (h & 1) w.c0 = a.chunk_split;
+        else w.c1 = a.chunk_split;
+    }
     return w;
 }
 
@@ -920,18 +940,21 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
 #pragma unroll
             for (int s = 0; s < STAGES; ++s) issued_phase[s] = -1;
             bool ok = true;
-            for (int t = cid; ok && t < a.num_tiles; t += ncl) {
+            for (int u = cid; ok && u < a.num_units; u += ncl) {
+                const PromoteUnit w = promote_unit(a, u, nchunks);
                 int mb, nb;
-                tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
-                // odd rounds of tiles walk K downwards (L2 reuse, as in the pair kernel)
-                const bool down = a.serpentine && (((t - cid) / ncl) & 1);
-                for (int kb_i = 0; kb_i < a.num_kb; ++kb_i) {
-                    const int kb = down ? a.num_kb - 1 - kb_i : kb_i;
+                tile_coords(w.t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
+                // odd rounds of tiles walk K downwards (L2 reuse, as in the pair kernel); a part of K
+                // walks its own k-blocks
+                const bool down = a.serpentine && w.kpart == 0 && (((u - cid) / ncl) & 1);
+                const int ukb0 = w.c0 * CHUNK_KB, ukb1 = min(a.num_kb, w.c1 * CHUNK_KB);
+                for (int kb_i = 0; kb_i < ukb1 - ukb0; ++kb_i) {
+                    const int kb = down ? ukb1 - 1 - kb_i : ukb0 + kb_i;
                     if (!wait(empty_bar(stage), phase ^ 1u)) {
                         ok = false;
                         break;
                     }
-                    if (kb_i == a.stall_kb && t == cid && cid == 0 && rank == 0) {
+                    if (kb_i == a.stall_kb && u == cid && cid == 0 && rank == 0) {
                         // test hook: the even CTA never arms this stage's barrier
                         if (++stage == STAGES) {
                             stage = 0;
@@ -982,6 +1005,7 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
             bool issued_any = false;
             const uint32_t h_tmem = tmem_base;
             const uint32_t y_tmem = tmem_base + static_cast<uint32_t>(PN);
+            int ukb0 = 0;  // first k-block of the unit: the correction accumulator restarts there
             auto advance = [&](int& s_, uint32_t& ph_) {
                 if (++s_ == STAGES) {
                     s_ = 0;
@@ -996,7 +1020,7 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
                     for (int p = 1; p < NPROD; ++p) {
                         const uint32_t a_addr = sbase + prod_a<NA>(p) * L::kHalfTile + ks * 32;
                         const uint32_t b_addr = sbase + (NA + prod_b<NA>(p)) * L::kHalfTile + ks * 32;
-                        const uint32_t accumulate = (kb != 0 || ks != 0 || p != 1) ? 1u : 0u;
+                        const uint32_t accumulate = (kb != ukb0 || ks != 0 || p != 1) ? 1u : 0u;
                         mma_pair_f16(y_tmem, sw128_kmajor_desc(a_addr), sw128_kmajor_desc(b_addr), a.idesc,
                                      accumulate);
                     }
@@ -1012,13 +1036,15 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
                 }
                 mma_commit_pair_mc(empty_bar(s_), 0x3);
             };
-            for (int t = cid; ok && t < a.num_tiles; t += ncl) {
-                for (int c = 0; ok && c < nchunks; ++c) {
+            for (int u = cid; ok && u < a.num_units; u += ncl) {
+                const PromoteUnit w = promote_unit(a, u, nchunks);
+                ukb0 = w.c0 * CHUNK_KB;
+                for (int c = w.c0; ok && c < w.c1; ++c) {
                     const int kb0 = c * CHUNK_KB;
                     const int kb_end = min(a.num_kb, kb0 + CHUNK_KB);
                     const int ahead = min(kb_end - kb0, kAhead);
-                    if (c == 0) {
-                        // Y restarts with this tile: wait until the previous tile's Y and H are drained
+                    if (c == w.c0) {
+                        // Y restarts with this unit: wait until the previous unit's Y and H are drained
                         if (!wait(cempty_bar(0), h_phase ^ 1u)) {
                             ok = false;
                             break;
@@ -1075,8 +1101,9 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
             uint32_t buf_phase = 0;
             bool ok = true;
             bool issued_any = false;
-            for (int t = cid; ok && t < a.num_tiles; t += ncl) {
-                for (int c = 0; ok && c < nchunks; ++c) {
+            for (int u = cid; ok && u < a.num_units; u += ncl) {
+                const PromoteUnit w = promote_unit(a, u, nchunks);
+                for (int c = w.c0; ok && c < w.c1; ++c) {
                     if (!wait(cempty_bar(buf), buf_phase ^ 1u)) {
                         ok = false;
                         break;
@@ -1131,22 +1158,30 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
         const int half = (warp - 2) >> 2;  // columns [128*half, 128*half + 128)
         float alpha = a.alpha;
         if constexpr (KIND == 1) alpha = alpha * (1.0f / *a.scale_a) * (1.0f / *a.scale_b);
-        const float beta = a.beta;
+        const float beta_in = a.beta;
         const bool vec_ok = ((a.ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15u) == 0);
+        // flags of parts of K: one per epilogue warp of each cut tile (as in the pair kernel)
+        auto part_flag = [&](int u) {
+            const int j = (u - a.full_units) >> 1;
+            return a.kflags + (j * 2 + static_cast<int>(rank)) * 8 + (warp - 2);
+        };
         const uint32_t leader_cempty0 = mapa_shared(cempty_bar(0), 0);
         const uint32_t leader_cempty1 = mapa_shared(cempty_bar(1), 0);
         int buf = 0;
         uint32_t buf_phase = 0;
         bool ok = true;
-        for (int t = cid; ok && t < a.num_tiles; t += ncl) {
+        for (int u = cid; ok && u < a.num_units; u += ncl) {
+            const PromoteUnit pu = promote_unit(a, u, nchunks);
             int mb, nb;
-            tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
+            tile_coords(pu.t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
+            // the second part of K adds its sum to what the first part's warp stored (beta = 1)
+            const float beta = pu.kpart == 2 ? 1.0f : beta_in;
             const int row = mb * PM + static_cast<int>(rank) * 128 + quarter * 32 + lane;
             const int col0 = nb * PN + half * 128;
             float acc[128];
 #pragma unroll
             for (int j = 0; j < 128; ++j) acc[j] = 0.0f;
-            for (int c = 0; c < nchunks; ++c) {
+            for (int c = pu.c0; c < pu.c1; ++c) {
                 // SCALED: one H buffer whose phase flips every chunk; else two buffers in turn
                 const int cb = SCALED ? 0 : buf;
                 const bool w = wait(cfull_bar(cb), buf_phase);
@@ -1164,8 +1199,8 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
 #pragma unroll
                     for (int j = 0; j < 32; ++j) acc[q * 32 + j] += v[j];
                 }
-                if (SCALED && c == nchunks - 1) {
-                    // the correction accumulator, complete with the tile's last chunk
+                if (SCALED && c == pu.c1 - 1) {
+                    // the correction accumulator, complete with the unit's last chunk
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         float v[32];
@@ -1185,6 +1220,11 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
                 }
             }
             if (!ok) break;
+            if (pu.kpart == 2) {
+                const bool fl = poll_flag_acquire(part_flag(u), abort_flag, a.status);
+                if (!fl) st_shared_cluster_u32(peer_abort, 1u);
+                if (!__all_sync(0xffffffffu, fl)) break;
+            }
             if (row < a.m && col0 < a.n) {
                 float* p = a.C + static_cast<int64_t>(row) * a.ldc + col0;
                 const int ncols = min(128, a.n - col0);
@@ -1193,7 +1233,7 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
                     for (int j = 0; j < 32; ++j) {
                         float4 o;
                         if (beta != 0.0f) {
-                            const float4 old = *reinterpret_cast<const float4*>(p + 4 * j);
+                            const float4 old = __ldcg(reinterpret_cast<const float4*>(p + 4 * j));
                             o.x = fmaf(alpha, acc[4 * j + 0], beta * old.x);
                             o.y = fmaf(alpha, acc[4 * j + 1], beta * old.y);
                             o.z = fmaf(alpha, acc[4 * j + 2], beta * old.z);
@@ -1209,9 +1249,16 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
                 } else {
 #pragma unroll
                     for (int j = 0; j < 128; ++j) {
-                        if (j < ncols) p[j] = (beta != 0.0f) ? fmaf(alpha, acc[j], beta * p[j]) : alpha * acc[j];
+                        if (j < ncols) p[j] = (beta != 0.0f) ? fmaf(alpha, acc[j], beta * __ldcg(p + j)) : alpha * acc[j];
                     }
                 }
+            }
+            if (pu.kpart == 1) {   // this warp's stores are visible before its flag is raised
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) st_release_gpu(part_flag(u), 1u);
+            } else if (pu.kpart == 2 && lane == 0) {
+                *part_flag(u) = 0u;   // ready for the next launch
             }
         }
     }
@@ -1232,6 +1279,7 @@ cudaError_t run_pair_promote(const CUtensorMap& tmA, const CUtensorMap& tmB, con
     using L = PairLayout<STAGES, NA, NB>;
     static_assert(L::kBytes <= 227 * 1024, "shared memory of the promoted pair kernel");
     auto kern = k_tc_gemm_pair_promote<KIND, STAGES, NA, NB, NPROD, CHUNK_KB, SCALED>;
+    Args a = args;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2 * clusters, 1, 1);
     cfg.blockDim = dim3(kPromoteThreads, 1, 1);
@@ -1251,8 +1299,23 @@ cudaError_t run_pair_promote(const CUtensorMap& tmA, const CUtensorMap& tmB, con
         clusters = resident;
         cfg.gridDim = dim3(2 * clusters, 1, 1);
     }
+    // a last round that would keep at most half of the pairs busy runs as two parts of K per tile
+    // (cut between chunks, the first part the shorter), as in the pair kernel
+    const int rem = a.num_tiles % clusters;
+    const int nchunks = (a.num_kb + CHUNK_KB - 1) / CHUNK_KB;
+    a.full_units = a.num_units = a.num_tiles;
+    if (a.split_tail == 2 && a.kflags && nchunks >= 2 && rem > 0 && 2 * rem <= clusters &&
+        16 * rem <= kKpartRegionWords) {
+        a.full_units = a.num_tiles - rem;
+        a.num_units = a.full_units + 2 * rem;
+        a.chunk_split = nchunks * 7 / 16 > 0 ? nchunks * 7 / 16 : 1;
+    }
+    if (clusters > a.num_units) {
+        clusters = a.num_units;
+        cfg.gridDim = dim3(2 * clusters, 1, 1);
+    }
     add_pdl(cfg);
-    return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, args);
+    return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, a);
 }
 }  // namespace
 
