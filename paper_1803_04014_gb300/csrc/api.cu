@@ -574,6 +574,8 @@ tc_status split_gemm(const char* name, int scheme, int32_t piece, int32_t nprod,
         f.group_m = gemm_group_m();
         f.stall_at = take_stall();
         f.serpentine = gemm_serpentine();
+        f.split_tail = gemm_split_tail();
+        f.kpart_flags = kpart_region(d);
         CUtensorMap ta, tb;
         // K-major: rows of k elements, boxes of 32 k x 128 rows; MN-major: k rows of m (or n)
         // elements, boxes of 32 x 32 k-rows

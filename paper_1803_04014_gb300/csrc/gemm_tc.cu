@@ -101,23 +101,6 @@ __device__ __forceinline__ Unit unit_coords(const Args& a, int u) {
     return w;
 }
 
-// Work unit u of the pair kernel with promotion: its tile, its chunks [c0, c1) of CHUNK_KB k-blocks
-// and its part of K (0: all of it; 1, 2: first or second part of a tile of the last round).
-struct PromoteUnit {
-    int t, c0, c1, kpart;
-};
-__device__ __forceinline__ PromoteUnit promote_unit(const Args& a, int u, int nchunks) {
-    PromoteUnit w{u, 0, nchunks, 0};
-    if (u >= a.full_units) {
-        const int h = u - a.full_units;
-        w.t = a.full_units + (h >> 1);
-        w.kpart = 1 + (h & 1);
-        if (h & 1) w.c0 = a.chunk_split;
-        else w.c1 = a.chunk_split;
-    }
-    return w;
-}
-
 // Flag of epilogue warp (rank, quarter) of the unit's tile, for parts of K of the pair kernel.
 __device__ __forceinline__ unsigned* kpart_flag(const Args& a, int u, uint32_t rank, int quarter) {
     const int j = (u - a.full_units) >> 1;
@@ -941,7 +924,7 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
             for (int s = 0; s < STAGES; ++s) issued_phase[s] = -1;
             bool ok = true;
             for (int u = cid; ok && u < a.num_units; u += ncl) {
-                const PromoteUnit w = promote_unit(a, u, nchunks);
+                const ChunkUnit w = chunk_unit(a.full_units, a.chunk_split, nchunks, u);
                 int mb, nb;
                 tile_coords(w.t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
                 // odd rounds of tiles walk K downwards (L2 reuse, as in the pair kernel); a part of K
@@ -1037,7 +1020,7 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
                 mma_commit_pair_mc(empty_bar(s_), 0x3);
             };
             for (int u = cid; ok && u < a.num_units; u += ncl) {
-                const PromoteUnit w = promote_unit(a, u, nchunks);
+                const ChunkUnit w = chunk_unit(a.full_units, a.chunk_split, nchunks, u);
                 ukb0 = w.c0 * CHUNK_KB;
                 for (int c = w.c0; ok && c < w.c1; ++c) {
                     const int kb0 = c * CHUNK_KB;
@@ -1102,7 +1085,7 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
             bool ok = true;
             bool issued_any = false;
             for (int u = cid; ok && u < a.num_units; u += ncl) {
-                const PromoteUnit w = promote_unit(a, u, nchunks);
+                const ChunkUnit w = chunk_unit(a.full_units, a.chunk_split, nchunks, u);
                 for (int c = w.c0; ok && c < w.c1; ++c) {
                     if (!wait(cempty_bar(buf), buf_phase ^ 1u)) {
                         ok = false;
@@ -1171,7 +1154,7 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
         uint32_t buf_phase = 0;
         bool ok = true;
         for (int u = cid; ok && u < a.num_units; u += ncl) {
-            const PromoteUnit pu = promote_unit(a, u, nchunks);
+            const ChunkUnit pu = chunk_unit(a.full_units, a.chunk_split, nchunks, u);
             int mb, nb;
             tile_coords(pu.t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
             // the second part of K adds its sum to what the first part's warp stored (beta = 1)
@@ -1295,20 +1278,17 @@ cudaError_t run_pair_promote(const CUtensorMap& tmA, const CUtensorMap& tmB, con
     int resident = 0;
     const cudaError_t e = kernel_setup(reinterpret_cast<const void*>(kern), L::kBytes, &cfg, 0, &resident);
     if (e != cudaSuccess) return e;
+    // a last round that would keep at most half of the pairs busy runs as two parts of K per tile,
+    // cut between chunks as the one-launch kernel cuts them (decided on the nominal grid, so that
+    // both paths give the same bits)
+    const ChunkPlan cp = plan_chunk_parts(a.num_tiles, clusters, (a.num_kb + CHUNK_KB - 1) / CHUNK_KB,
+                                          a.split_tail == 2 && a.kflags != nullptr, kKpartRegionWords / 16);
+    a.full_units = cp.full_units;
+    a.num_units = cp.num_units;
+    a.chunk_split = cp.chunk_split;
     if (resident > 0 && clusters > resident) {
         clusters = resident;
         cfg.gridDim = dim3(2 * clusters, 1, 1);
-    }
-    // a last round that would keep at most half of the pairs busy runs as two parts of K per tile
-    // (cut between chunks, the first part the shorter), as in the pair kernel
-    const int rem = a.num_tiles % clusters;
-    const int nchunks = (a.num_kb + CHUNK_KB - 1) / CHUNK_KB;
-    a.full_units = a.num_units = a.num_tiles;
-    if (a.split_tail == 2 && a.kflags && nchunks >= 2 && rem > 0 && 2 * rem <= clusters &&
-        16 * rem <= kKpartRegionWords) {
-        a.full_units = a.num_tiles - rem;
-        a.num_units = a.full_units + 2 * rem;
-        a.chunk_split = nchunks * 7 / 16 > 0 ? nchunks * 7 / 16 : 1;
     }
     if (clusters > a.num_units) {
         clusters = a.num_units;

@@ -119,6 +119,8 @@ struct SplitFusedLaunch {
     int group_m;
     int stall_at;    // test hook: k-block + 1 to withhold, 0 = off
     int serpentine;  // every other round of tiles of a CTA pair walks K downwards
+    int split_tail;  // 2: a partial last round of tiles runs as two parts of K (as the two-pass kernel)
+    unsigned* kpart_flags;  // kKpartRegionWords zero words (see TcGemmLaunch)
 };
 // Schemes the one-launch kernel runs (the three-piece BF16 split does not: its pieces and the
 // FP32 staging do not fit in shared memory together).

@@ -36,6 +36,43 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
     nb = r / gm;
 }
 
+// Work units of the refined (promoting) pair kernels.  The two-pass kernel (gemm_tc.cu) and the
+// one-launch kernel (split_fused.cu) cut the same tiles at the same chunk, so that they give the
+// same bits: units u < full_units are tiles u with every chunk; unit full_units + 2 j + h is part
+// h + 1 of tile full_units + j, chunks [0, chunk_split) (h = 0) or [chunk_split, nchunks) (h = 1).
+// A part walks its k-blocks upwards; the second part adds its sum to what the first stored.
+struct ChunkUnit {
+    int t, c0, c1, kpart;
+};
+__host__ __device__ __forceinline__ ChunkUnit chunk_unit(int full_units, int chunk_split, int nchunks, int u) {
+    ChunkUnit w{u, 0, nchunks, 0};
+    if (u >= full_units) {
+        const int h = u - full_units;
+        w.t = full_units + (h >> 1);
+        w.kpart = 1 + (h & 1);
+        if (h & 1) w.c0 = chunk_split;
+        else w.c1 = chunk_split;
+    }
+    return w;
+}
+
+// The cut: a last round of tiles that would keep at most half of `clusters` CTA pairs busy (or a
+// grid of fewer tiles than half of them), at most max_cut tiles, K at least two chunks.  The first
+// part is the shorter (7/16 of the chunks), so that its epilogue overlaps the second's main loop.
+struct ChunkPlan {
+    int full_units, num_units, chunk_split;
+};
+inline ChunkPlan plan_chunk_parts(int num_tiles, int clusters, int nchunks, bool enabled, int max_cut) {
+    ChunkPlan p{num_tiles, num_tiles, 0};
+    const int rem = clusters > 0 ? num_tiles % clusters : 0;
+    if (enabled && nchunks >= 2 && rem > 0 && 2 * rem <= clusters && rem <= max_cut) {
+        p.full_units = num_tiles - rem;
+        p.num_units = p.full_units + 2 * rem;
+        p.chunk_split = nchunks * 7 / 16 > 0 ? nchunks * 7 / 16 : 1;
+    }
+    return p;
+}
+
 // Instruction-descriptor bits that read A (bit 15) or B (bit 16) as MN-major
 // (rows of the shared-memory tile run along M or N instead of K).
 constexpr uint32_t kIdescTransposeA = 1u << 15;

@@ -75,6 +75,10 @@ struct FusedArgs {
     uint32_t idesc;
     int stall_kb;  // test hook: >= 0 makes the even CTA of the first pair withhold this k-block
     int serpentine;  // odd rounds of tiles of a CTA pair walk K downwards (as the two-pass kernel)
+    // work units (chunk_unit): tiles, then two parts of K of each tile of a cut last round; the
+    // second part's epilogue warp waits for the first part's flag in kflags (8 per CTA and tile)
+    int full_units, num_units, chunk_split;
+    unsigned* kflags;
 };
 
 template <int NA, int NB>
@@ -234,7 +238,7 @@ __device__ __forceinline__ void convert_half(uint32_t src_base, uint32_t dst_bas
 template <int SCHEME, int NA, int NB, int STAGES, int FSTAGES, int PSTAGE_BYTES, int FOFFSET, bool A_MN, bool B_MN>
 __device__ __forceinline__ void form_pieces(const FusedArgs& a, int xw, int lane, uint32_t rank, int cid, int ncl,
                                             uint32_t base, uint32_t bars, volatile int* abort_flag,
-                                            uint32_t peer_abort) {
+                                            uint32_t peer_abort, int64_t total_kb) {
     auto full_bar = [&](int s) { return bars + 8u * s; };
     auto empty_bar = [&](int s) { return bars + 8u * (STAGES + s); };
     auto ffull_bar = [&](int s) { return bars + 8u * (2 * STAGES + s); };
@@ -250,8 +254,6 @@ __device__ __forceinline__ void form_pieces(const FusedArgs& a, int xw, int lane
     int ps = 0, fs = 0;
     uint32_t pph = 0, fph = 0;
     const uint32_t fbase = base + FOFFSET;
-    const int64_t total_kb =
-        cid < a.num_tiles ? static_cast<int64_t>((a.num_tiles - cid + ncl - 1) / ncl) * a.num_kb : 0;
     for (int64_t done_kb = 0; done_kb < total_kb; ++done_kb) {
         if (!wait(empty_bar(ps), pph ^ 1u)) return;
         const uint32_t pbase = base + ps * PSTAGE_BYTES;
@@ -367,22 +369,29 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         const int quarter = warp & 3;  // TMEM lanes [32*quarter, +32)
         const int half = e >> 2;       // columns [128*half, +128)
         const float alpha = a.alpha;
-        const float beta = a.beta;
+        const float beta_in = a.beta;
         const bool vec_ok = ((a.ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15u) == 0);
+        auto part_flag = [&](int u) {
+            const int j = (u - a.full_units) >> 1;
+            return a.kflags + (j * 2 + static_cast<int>(rank)) * 8 + e;
+        };
         const uint32_t leader_cempty0 = mapa_shared(cempty_bar(0), 0);
         const uint32_t leader_cempty1 = mapa_shared(cempty_bar(1), 0);
         int buf = 0;
         uint32_t buf_phase = 0;
-        for (int t = cid; t < a.num_tiles; t += ncl) {
+        for (int u = cid; u < a.num_units; u += ncl) {
+            const ChunkUnit pu = chunk_unit(a.full_units, a.chunk_split, nchunks, u);
             int mb, nb;
-            tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
+            tile_coords(pu.t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
+            // the second part of K adds its sum to what the first part's warp stored (beta = 1)
+            const float beta = pu.kpart == 2 ? 1.0f : beta_in;
             const int row = mb * PM + static_cast<int>(rank) * 128 + quarter * 32 + lane;
             const int col0 = nb * PN + half * 128;
             float acc[128];
 #pragma unroll
             for (int j = 0; j < 128; ++j) acc[j] = 0.0f;
             bool ok = true;
-            for (int c = 0; c < nchunks; ++c) {
+            for (int c = pu.c0; c < pu.c1; ++c) {
                 const int cb = SCALED ? 0 : buf;
                 const bool w = wait(cfull_bar(cb), buf_phase);
                 if (!__all_sync(0xffffffffu, w)) {
@@ -399,7 +408,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
 #pragma unroll
                     for (int j = 0; j < 32; ++j) acc[q * 32 + j] += v[j];
                 }
-                if (SCALED && c == nchunks - 1) {
+                if (SCALED && c == pu.c1 - 1) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         float v[32];
@@ -419,6 +428,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 }
             }
             if (!ok) break;
+            if (pu.kpart == 2) {
+                const bool fl = poll_flag_acquire(part_flag(u), abort_flag, a.status);
+                if (!fl) st_shared_cluster_u32(peer_abort, 1u);
+                if (!__all_sync(0xffffffffu, fl)) break;
+            }
             if (row < a.m && col0 < a.n) {
                 float* p = a.C + static_cast<int64_t>(row) * a.ldc + col0;
                 const int ncols = min(128, a.n - col0);
@@ -427,7 +441,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                     for (int j = 0; j < 32; ++j) {
                         float4 o;
                         if (beta != 0.0f) {
-                            const float4 old = *reinterpret_cast<const float4*>(p + 4 * j);
+                            const float4 old = __ldcg(reinterpret_cast<const float4*>(p + 4 * j));
                             o.x = fmaf(alpha, acc[4 * j + 0], beta * old.x);
                             o.y = fmaf(alpha, acc[4 * j + 1], beta * old.y);
                             o.z = fmaf(alpha, acc[4 * j + 2], beta * old.z);
@@ -443,9 +457,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 } else {
 #pragma unroll
                     for (int j = 0; j < 128; ++j) {
-                        if (j < ncols) p[j] = (beta != 0.0f) ? fmaf(alpha, acc[j], beta * p[j]) : alpha * acc[j];
+                        if (j < ncols) p[j] = (beta != 0.0f) ? fmaf(alpha, acc[j], beta * __ldcg(p + j)) : alpha * acc[j];
                     }
                 }
+            }
+            if (pu.kpart == 1) {   // this warp's stores are visible before its flag is raised
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) st_release_gpu(part_flag(u), 1u);
+            } else if (pu.kpart == 2 && lane == 0) {
+                *part_flag(u) = 0u;   // ready for the next launch
             }
         }
     } else if (wg == 0) {
@@ -480,13 +501,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                     uint32_t h_phase = 0;
                     const uint32_t h_tmem = tmem_base;
                     const uint32_t y_tmem = tmem_base + static_cast<uint32_t>(PN);
+                    int ukb0 = 0;  // first k-block of the unit: the correction accumulator restarts there
                     auto corrections = [&](int kb, int s_) {
                         const uint32_t sbase = base + s_ * L::kPStageBytes;
 #pragma unroll
                         for (int ks = 0; ks < kSteps; ++ks) {
 #pragma unroll
                             for (int p = 1; p < NPROD; ++p) {
-                                const uint32_t accumulate = (kb != 0 || ks != 0 || p != 1) ? 1u : 0u;
+                                const uint32_t accumulate = (kb != ukb0 || ks != 0 || p != 1) ? 1u : 0u;
                                 mma_pair_f16(y_tmem, adesc(sbase, prod_a<NA>(p), ks), bdesc(sbase, prod_b<NA>(p), ks),
                                              idesc, accumulate);
                             }
@@ -501,13 +523,15 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                         }
                         mma_commit_pair_mc(empty_bar(s_), 0x3);
                     };
-                    for (int t = cid; ok && t < a.num_tiles; t += ncl) {
-                        for (int c = 0; ok && c < nchunks; ++c) {
+                    for (int u = cid; ok && u < a.num_units; u += ncl) {
+                        const ChunkUnit w = chunk_unit(a.full_units, a.chunk_split, nchunks, u);
+                        ukb0 = w.c0 * CHUNK_KB;
+                        for (int c = w.c0; ok && c < w.c1; ++c) {
                             const int kb0 = c * CHUNK_KB;
                             const int kb_end = min(a.num_kb, kb0 + CHUNK_KB);
                             const int ahead = min(kb_end - kb0, kAhead);
-                            if (c == 0) {
-                                // Y restarts with this tile: the previous tile's Y and H must be drained
+                            if (c == w.c0) {
+                                // Y restarts with this unit: the previous unit's Y and H must be drained
                                 if (!wait(cempty_bar(0), h_phase ^ 1u)) {
                                     ok = false;
                                     break;
@@ -556,8 +580,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 } else {
                     int buf = 0;
                     uint32_t buf_phase = 0;
-                    for (int t = cid; ok && t < a.num_tiles; t += ncl) {
-                        for (int c = 0; ok && c < nchunks; ++c) {
+                    for (int u = cid; ok && u < a.num_units; u += ncl) {
+                        const ChunkUnit w = chunk_unit(a.full_units, a.chunk_split, nchunks, u);
+                        for (int c = w.c0; ok && c < w.c1; ++c) {
                             if (!wait(cempty_bar(buf), buf_phase ^ 1u)) {
                                 ok = false;
                                 break;
@@ -609,31 +634,43 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 for (int s = 0; s < L::kFStages; ++s) issued_phase[s] = -1;
                 bool ok = true;
                 const uint32_t fbase = base + L::kFOffset;
-                const int nhalf = 2 * a.num_kb;
-                // half h of a tile covers k from 32 h, or, in the odd rounds of tiles that walk K
-                // downwards, half h % 2 of k-block num_kb - 1 - h / 2
-                auto half_k = [&](int h, bool down) {
-                    const int kb = down ? a.num_kb - 1 - (h >> 1) : (h >> 1);
-                    return 64 * kb + 32 * (h & 1);
+                // half i (0 <= i < 2 (kb1 - kb0)) of a unit with k-blocks [kb0, kb1) covers k from
+                // 64 kb0 + 32 i, or, in the odd rounds of whole tiles that walk K downwards, half i % 2
+                // of k-block kb1 - 1 - i / 2
+                auto half_k = [&](const ChunkUnit& w_, int i, bool down) {
+                    const int kb0 = w_.c0 * CHUNK_KB, kb1 = min(a.num_kb, w_.c1 * CHUNK_KB);
+                    const int kb = down ? kb1 - 1 - (i >> 1) : kb0 + (i >> 1);
+                    return 64 * kb + 32 * (i & 1);
                 };
-                for (int t = cid; ok && t < a.num_tiles; t += ncl) {
+                auto unit_down = [&](const ChunkUnit& w_, int u_) {
+                    return a.serpentine && w_.kpart == 0 && (((u_ - cid) / ncl) & 1);
+                };
+                for (int u = cid; ok && u < a.num_units; u += ncl) {
+                    const ChunkUnit w = chunk_unit(a.full_units, a.chunk_split, nchunks, u);
                     int mb, nb;
-                    tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
-                    const bool down = a.serpentine && (((t - cid) / ncl) & 1);
+                    tile_coords(w.t, a.tiles_m, a.tiles_n, a.group_m, mb, nb);
+                    const bool down = unit_down(w, u);
+                    const int nhalf = 2 * (min(a.num_kb, w.c1 * CHUNK_KB) - w.c0 * CHUNK_KB);
                     const int arow = mb * PM + static_cast<int>(rank) * 128;
                     const int brow = nb * PN + static_cast<int>(rank) * 128;
-                    // the next tile of this cluster, whose first halves are prefetched near the end of this one
+                    // the next unit of this cluster, whose first halves are prefetched near the end of this one
                     int mb2 = -1, nb2 = -1;
-                    if (t + ncl < a.num_tiles) tile_coords(t + ncl, a.tiles_m, a.tiles_n, a.group_m, mb2, nb2);
+                    ChunkUnit w2{0, 0, 0, 0};
+                    bool down2 = false;
+                    if (u + ncl < a.num_units) {
+                        w2 = chunk_unit(a.full_units, a.chunk_split, nchunks, u + ncl);
+                        tile_coords(w2.t, a.tiles_m, a.tiles_n, a.group_m, mb2, nb2);
+                        down2 = unit_down(w2, u + ncl);
+                    }
                     for (int h = 0; h < nhalf; ++h) {
                         // L2 prefetch kPrefetchHalves ahead: the ring of three halves alone keeps too few
                         // bytes in flight to cover the latency of loads that miss L2
                         const int hp = h + kPrefetchHalves;
                         if (hp < nhalf) {
-                            prefetch_half(&tmA, a.a_mn != 0, arow, half_k(hp, down));
-                            prefetch_half(&tmB, a.b_mn != 0, brow, half_k(hp, down));
-                        } else if (mb2 >= 0) {
-                            const int k2 = half_k(hp - nhalf, a.serpentine && !down);
+                            prefetch_half(&tmA, a.a_mn != 0, arow, half_k(w, hp, down));
+                            prefetch_half(&tmB, a.b_mn != 0, brow, half_k(w, hp, down));
+                        } else if (mb2 >= 0 && hp - nhalf < 2 * (min(a.num_kb, w2.c1 * CHUNK_KB) - w2.c0 * CHUNK_KB)) {
+                            const int k2 = half_k(w2, hp - nhalf, down2);
                             prefetch_half(&tmA, a.a_mn != 0, mb2 * PM + static_cast<int>(rank) * 128, k2);
                             prefetch_half(&tmB, a.b_mn != 0, nb2 * PN + static_cast<int>(rank) * 128, k2);
                         }
@@ -643,8 +680,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                         }
                         const uint32_t dst = fbase + fs * kHalfBytes;
                         mbar_arrive_expect_tx(ffull_bar(fs), kHalfBytes);
-                        load_half(&tmA, a.a_mn != 0, dst, ffull_bar(fs), arow, half_k(h, down));
-                        load_half(&tmB, a.b_mn != 0, dst + kHalfBytes / 2, ffull_bar(fs), brow, half_k(h, down));
+                        load_half(&tmA, a.a_mn != 0, dst, ffull_bar(fs), arow, half_k(w, h, down));
+                        load_half(&tmB, a.b_mn != 0, dst + kHalfBytes / 2, ffull_bar(fs), brow, half_k(w, h, down));
                         issued_phase[fs] = static_cast<int>(fph);
                         if (++fs == L::kFStages) {
                             fs = 0;
@@ -665,19 +702,24 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         setmaxnreg_dec<kXformRegs>();
         // ---------------- piece formation (warps 12-19)
         const int xw = warp - 12;
+        int64_t total_kb = 0;   // k-blocks of this cluster's units
+        for (int u = cid; u < a.num_units; u += ncl) {
+            const ChunkUnit w = chunk_unit(a.full_units, a.chunk_split, nchunks, u);
+            total_kb += min(a.num_kb, w.c1 * CHUNK_KB) - w.c0 * CHUNK_KB;
+        }
         constexpr int FS = L::kFStages, PB = L::kPStageBytes, FO = L::kFOffset;
         if (!a.a_mn && !a.b_mn)
             form_pieces<SCHEME, NA, NB, STAGES, FS, PB, FO, false, false>(a, xw, lane, rank, cid, ncl, base, bars,
-                                                                         abort_flag, peer_abort);
+                                                                         abort_flag, peer_abort, total_kb);
         else if (!a.a_mn && a.b_mn)
             form_pieces<SCHEME, NA, NB, STAGES, FS, PB, FO, false, true>(a, xw, lane, rank, cid, ncl, base, bars,
-                                                                        abort_flag, peer_abort);
+                                                                        abort_flag, peer_abort, total_kb);
         else if (a.a_mn && !a.b_mn)
             form_pieces<SCHEME, NA, NB, STAGES, FS, PB, FO, true, false>(a, xw, lane, rank, cid, ncl, base, bars,
-                                                                        abort_flag, peer_abort);
+                                                                        abort_flag, peer_abort, total_kb);
         else
             form_pieces<SCHEME, NA, NB, STAGES, FS, PB, FO, true, true>(a, xw, lane, rank, cid, ncl, base, bars,
-                                                                       abort_flag, peer_abort);
+                                                                       abort_flag, peer_abort, total_kb);
     }
 
     tc_fence_before();
@@ -696,6 +738,13 @@ cudaError_t run_fused(const CUtensorMap& tmA, const CUtensorMap& tmB, const Fuse
     constexpr int NB = NPROD == 2 ? 1 : NA;
     using L = FusedLayout<NA, NB>;
     auto kern = k_split_fused<SCHEME, NPROD, CHUNK_KB>;
+    FusedArgs a = args;
+    // the same cut as the two-pass kernel's (decided on the nominal grid)
+    const ChunkPlan cp = plan_chunk_parts(a.num_tiles, clusters, (a.num_kb + CHUNK_KB - 1) / CHUNK_KB,
+                                          a.kflags != nullptr, kKpartRegionWords / 16);
+    a.full_units = cp.full_units;
+    a.num_units = cp.num_units;
+    a.chunk_split = cp.chunk_split;
     // the setmaxnreg split assumes the launch's 96 registers per thread; refuse anything less
     static int checked_regs = 0;
     if (checked_regs == 0) {
@@ -724,8 +773,12 @@ cudaError_t run_fused(const CUtensorMap& tmA, const CUtensorMap& tmB, const Fuse
         clusters = resident;
         cfg.gridDim = dim3(2 * clusters, 1, 1);
     }
+    if (clusters > a.num_units) {
+        clusters = a.num_units;
+        cfg.gridDim = dim3(2 * clusters, 1, 1);
+    }
     add_pdl(cfg);
-    return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, args);
+    return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, a);
 }
 
 }  // namespace
@@ -753,6 +806,7 @@ cudaError_t launch_split_fused(const CUtensorMap& tmA, const CUtensorMap& tmB, c
     a.status = p.status;
     a.stall_kb = p.stall_at - 1;
     a.serpentine = p.serpentine;
+    a.kflags = p.split_tail == 2 ? p.kpart_flags : nullptr;
     a.idesc = make_idesc(256, 256, p.bf16 ? 1u : 0u) | (p.a_mn ? kIdescTransposeA : 0u) |
               (p.b_mn ? kIdescTransposeB : 0u);
     a.corr_scale = 1.0f;
