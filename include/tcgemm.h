@@ -170,7 +170,12 @@ tc_status tc_split_bf16x3(int64_t rows, int64_t cols, const float* src, int64_t 
  * issuing the MMAs into a double-buffered TMEM accumulator, four epilogue
  * warps.  Untuned tiles: 256 x 256 on CTA pairs; 128 x 64 (else 128 x 128)
  * on single CTAs when that many tiles fit on the SMs at once; single CTAs
- * whenever m <= 128.  The kernel is launched with programmatic stream
+ * whenever m <= 128.  On CTA pairs, a last round of tiles that would keep at
+ * most half of the pairs busy runs as two parts of K per tile: the first
+ * part stores alpha*P1 + beta*C, the second, once the first has signalled
+ * through a device flag, alpha*P2 + C (a fixed order: the same bits every
+ * run; TCGEMM_PAIR_TAIL=full keeps whole tiles, =halves cuts them into
+ * 256 x 128 halves).  The kernel is launched with programmatic stream
  * serialization: it may run its set-up while the previous kernel of the
  * stream finishes and waits for it before touching A, B, C or the scales
  * (TCGEMM_PDL=0 turns this off). */
@@ -387,9 +392,9 @@ tc_status gemm_grouped_ws(int32_t dt, int32_t count, const tc_problem* problems,
  * CTAs and 256 x 256 tiles on CTA pairs (cluster of 2), then raster bands of 4,
  * 8, 16 or 32 M-tiles for the best of those; if pairs win, clusters of four
  * CTAs (two pairs sharing A by TMA multicast) with each band height, and a
- * last partial round of pair tiles kept whole instead of cut into 256 x 128
- * halves; last, K walked upwards in every round of tiles instead of downwards
- * in odd rounds.  The untuned configuration (see gemm_mixed) is timed first
+ * last partial round of pair tiles kept whole (tail 0) or cut into 256 x 128
+ * halves (tail 1) instead of two parts of K (tail 2); last, K walked upwards
+ * in every round of tiles instead of downwards in odd rounds.  The untuned configuration (see gemm_mixed) is timed first
  * and a candidate replaces it only if more than 2 % faster.  A shape class is
  * (dt, m, n, k) with each size rounded up to a power of two.  The candidates
  * are passed to the launches explicitly: calls of other threads keep their
@@ -408,7 +413,8 @@ tc_status gemm_grouped_plan_autotune(tc_grouped_plan* plan, const void* a_base, 
                                      void* stream, double* best_ms);
 
 /* Write / read the gemm_mixed autotune table (text, one shape class per line:
- * dt log2m log2n log2k pair group_m tail korder cluster bn ms; lines without
+ * dt log2m log2n log2k pair group_m tail korder cluster bn ms, tail 0, 1 or 2
+ * as in tc_autotune_gemm; lines without
  * the bn field are read with bn = 256, lines of the older form
  * "dt log2m log2n log2k pair group_m ms" with tail = korder = 1, cluster = 2
  * and bn = 256). */
