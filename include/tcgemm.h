@@ -171,11 +171,12 @@ tc_status tc_split_bf16x3(int64_t rows, int64_t cols, const float* src, int64_t 
  * warps.  Untuned tiles: 256 x 256 on CTA pairs; 128 x 64 (else 128 x 128)
  * on single CTAs when that many tiles fit on the SMs at once; single CTAs
  * whenever m <= 128.  On CTA pairs, a last round of tiles that would keep at
- * most half of the pairs busy runs as two parts of K per tile: the first
- * part stores alpha*P1 + beta*C, the second, once the first has signalled
+ * most half of the pairs busy runs as two units per tile: with K of at least
+ * 48 k-blocks (3072 FP16/BF16, 6144 E4M3 elements) two parts of K, the first
+ * storing alpha*P1 + beta*C, the second, once the first has signalled
  * through a device flag, alpha*P2 + C (a fixed order: the same bits every
- * run; TCGEMM_PAIR_TAIL=full keeps whole tiles, =halves cuts them into
- * 256 x 128 halves).  The kernel is launched with programmatic stream
+ * run); with a shorter K two 256 x 128 halves.  TCGEMM_PAIR_TAIL=full keeps
+ * whole tiles, =halves always cuts halves.  The kernel is launched with programmatic stream
  * serialization: it may run its set-up while the previous kernel of the
  * stream finishes and waits for it before touching A, B, C or the scales
  * (TCGEMM_PDL=0 turns this off). */

@@ -41,6 +41,7 @@ constexpr int BM = 128;
 constexpr int kRowBytes = 128;
 constexpr int kATileBytes = BM * kRowBytes;
 constexpr int kThreads = 192;
+constexpr int kKpartMinKb = 48;  // shortest K (in k-blocks) cut into parts
 
 struct Args {
     int m, n, k;
@@ -810,8 +811,10 @@ cudaError_t run_pair(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args&
     // half the pairs) is cut into half-width units
     const int rem = a.num_tiles % clusters;
     a.full_units = a.num_tiles;
-    // parts of K need two k-blocks and a flag per epilogue warp of each cut tile; else halves of N
-    if (a.split_tail == 2 && (a.num_kb < 2 || !a.kflags || 8 * rem > kKpartRegionWords)) a.split_tail = 1;
+    // parts of K need a flag per epilogue warp of each cut tile and a K long enough that the first
+    // part's epilogue (about 16 k-blocks' time) ends before the second part's main loop; else halves
+    // of N (a short K would chain the two parts' epilogues: 23 us against 11.5 us at m = n = k = 1024)
+    if (a.split_tail == 2 && (a.num_kb < kKpartMinKb || !a.kflags || 8 * rem > kKpartRegionWords)) a.split_tail = 1;
     if (rem > 0 && 2 * rem <= clusters && a.split_tail) a.full_units = a.num_tiles - rem;
     a.num_units = a.full_units + 2 * (a.num_tiles - a.full_units);
     if (clusters > a.num_units) {
@@ -1339,8 +1342,8 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
         a.full_units = a.num_units = a.num_tiles;
         a.split_tail = p.split_tail;
         a.serpentine = p.serpentine;
-        // the first part of K is the shorter, so that its epilogue overlaps the second's main loop
-        a.kb_split = a.num_kb * 7 / 16 > 0 ? a.num_kb * 7 / 16 : 1;
+        // the first part of K is 16 k-blocks shorter, so that its epilogue overlaps the second's main loop
+        a.kb_split = (a.num_kb - 16) / 2 > 0 ? (a.num_kb - 16) / 2 : 1;
         a.kflags = p.kpart_flags;
         const int max_clusters = p.sm_count / 2;
         const int clusters = a.num_tiles < max_clusters ? a.num_tiles : max_clusters;

@@ -57,18 +57,20 @@ __host__ __device__ __forceinline__ ChunkUnit chunk_unit(int full_units, int chu
 }
 
 // The cut: a last round of tiles that would keep at most half of `clusters` CTA pairs busy (or a
-// grid of fewer tiles than half of them), at most max_cut tiles, K at least two chunks.  The first
-// part is the shorter (7/16 of the chunks), so that its epilogue overlaps the second's main loop.
+// grid of fewer tiles than half of them), at most max_cut tiles, K at least 16 chunks.  The first
+// part is 4 chunks shorter, so that its epilogue (a few k-blocks' time at three or more products
+// per k-step) ends before the second part's main loop; with a shorter K the two parts' epilogues
+// would follow one another.
 struct ChunkPlan {
     int full_units, num_units, chunk_split;
 };
 inline ChunkPlan plan_chunk_parts(int num_tiles, int clusters, int nchunks, bool enabled, int max_cut) {
     ChunkPlan p{num_tiles, num_tiles, 0};
     const int rem = clusters > 0 ? num_tiles % clusters : 0;
-    if (enabled && nchunks >= 2 && rem > 0 && 2 * rem <= clusters && rem <= max_cut) {
+    if (enabled && nchunks >= 16 && rem > 0 && 2 * rem <= clusters && rem <= max_cut) {
         p.full_units = num_tiles - rem;
         p.num_units = p.full_units + 2 * rem;
-        p.chunk_split = nchunks * 7 / 16 > 0 ? nchunks * 7 / 16 : 1;
+        p.chunk_split = (nchunks - 4) / 2;
     }
     return p;
 }

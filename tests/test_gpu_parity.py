@@ -561,9 +561,8 @@ def test_gemm_default_tiles_at_small_sizes(b, dt, mnk):
 @pytest.mark.parametrize("mnk", [(2560, 2560, 192), (2304, 2600, 320), (256, 2560, 128)])
 def test_gemm_pair_full_and_half_width_units(b, monkeypatch, dt, mnk):
     # 100 and 99 tiles of 256 x 256 over 76 CTA pairs: the tiles of the partial last round run as
-    # two units each after the full tiles; 10 tiles: every tile runs as two units.  By default the
-    # units are parts of K (the first stores alpha P1 + beta C, the second adds alpha P2 to it
-    # after its flag), with TCGEMM_PAIR_TAIL=halves 256 x 128 halves.
+    # two units each after the full tiles; 10 tiles: every tile runs as two units.  K is short here,
+    # so the units are 256 x 128 halves (parts of K from 48 k-blocks: test_gemm_pair_parts_of_k).
     monkeypatch.setenv("TCGEMM_TILE", "pair")
     m, n, k = mnk
     A = synth.uniform((m, k), seed=131)
@@ -573,7 +572,6 @@ def test_gemm_pair_full_and_half_width_units(b, monkeypatch, dt, mnk):
     ref = og.gemm_mixed(DT_NAME[dt], A, B, 1.0, -0.5, C0)
     ok, info = elementwise_ok(C, ref, _mag(dt, A, B, 1.0, -0.5, C0), k)
     assert ok, info
-    # parts of K add in a fixed order: the same bits every run
     assert np.array_equal(_run_mixed(b, dt, A, B, 1.0, -0.5, C0), C)
     # halves of N run the whole K chain of each element: the bits of whole tiles
     monkeypatch.setenv("TCGEMM_PAIR_TAIL", "halves")
@@ -588,14 +586,15 @@ def test_gemm_pair_full_and_half_width_units(b, monkeypatch, dt, mnk):
 @pytest.mark.parametrize("beta", [0.0, 0.75])
 @pytest.mark.parametrize("case", ["f16", "e4m3", "f16_row_major_b"])
 def test_gemm_pair_parts_of_k(b, monkeypatch, epi, beta, case):
-    # parts of K on 24 cut tiles (100 tiles over 76 CTA pairs), K = 16 k-blocks (the first part 7);
-    # m and n ragged so that some epilogue warps of cut tiles hold no rows of C and the last tiles
-    # hold a few columns; both epilogues, beta 0 (the second part still reads what the first
-    # stored) and 0.75, E4M3 with its scales and a row-major B read as MN-major
+    # parts of K on 24 cut tiles (100 tiles over 76 CTA pairs), K = 48 k-blocks (the first part 16,
+    # 16 shorter than the second: the shortest K cut into parts); m and n ragged so that some
+    # epilogue warps of cut tiles hold no rows of C and the last tiles hold a few columns; both
+    # epilogues, beta 0 (the second part still reads what the first stored) and 0.75, E4M3 (k-blocks
+    # of 128) with its scales and a row-major B read as MN-major.  The bits are the same every run.
     monkeypatch.setenv("TCGEMM_TILE", "pair")
     monkeypatch.setenv("TCGEMM_EPILOGUE", epi)
-    m, n, k = 2500, 2520, 1024
     dt = 2 if case == "e4m3" else 0
+    m, n, k = 2500, 2520, 6144 if dt == 2 else 3072
     A = synth.uniform((m, k), seed=141)
     B = synth.uniform((k, n), seed=142)
     C0 = synth.uniform((m, n), seed=143)
