@@ -396,8 +396,10 @@ cudaError_t run(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args& args
 // on the even CTA's "full" barrier; the MMA commits are multicast to the
 // "empty"/"accumulator full" barriers of both CTAs; both epilogues arrive on
 // the even CTA's "accumulator empty" barrier.  A last round of tiles that would
-// leave more than half of the pairs idle runs as 256 x 128 half-width units
-// (unit_coords).
+// leave more than half of the pairs idle runs as two units per tile
+// (unit_coords): two parts of K, the second adding to what the first stored
+// once the first's epilogue warps have raised their flags, or, for a short K,
+// two 256 x 128 halves.
 
 template <int STAGES, int NA, int NB>
 struct PairLayout {
@@ -808,7 +810,7 @@ cudaError_t run_pair(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args&
         cfg.gridDim = dim3(2 * clusters, 1, 1);
     }
     // a last round that would leave more than half of the pairs idle (or a grid of fewer tiles than
-    // half the pairs) is cut into half-width units
+    // half the pairs) is cut into two units per tile
     const int rem = a.num_tiles % clusters;
     a.full_units = a.num_tiles;
     // parts of K need a flag per epilogue warp of each cut tile and a K long enough that the first
