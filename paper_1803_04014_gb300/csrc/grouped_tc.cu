@@ -73,6 +73,7 @@ __device__ __forceinline__ GroupedTcTile load_tile(const GroupedTcTile* tiles, i
         r.n = y.x; r.k = y.y; r.ldc = y.z; r.nk = y.w;
         r.off_c = (static_cast<int64_t>(static_cast<uint32_t>(z.y)) << 32) | static_cast<uint32_t>(z.x);
         r.rows = z.z;
+        r.flags = z.w;
     } else {
         r = GroupedTcTile{};
     }
@@ -285,7 +286,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
             const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                    static_cast<uint32_t>(acc * GN + (tall ? half * (GN / 2) : 0));
             float* crow = a.c_base + P.off_c + static_cast<int64_t>(row) * P.ldc + col0;
-            const bool vec_ok = ((P.ldc & 3) == 0) && (((P.off_c + col0) & 3) == 0) &&
+            // a transposed problem (C^T = B^T A^T): tile row r is column r of C_g, tile column c its
+            // row c; the chunks are staged transposed, so the stores are C_g row segments again
+            const bool swapped = (P.flags & kGroupedTcSwapped) != 0;
+            const bool vec_ok = ((P.ldc & 3) == 0) && (((P.off_c + (swapped ? 0 : col0)) & 3) == 0) &&
                                 ((reinterpret_cast<uintptr_t>(a.c_base) & 15u) == 0);
             uint8_t* slot_ptr = base_ptr + kEpiOff + (warp - 2) * kEpiWarpBytes;
             const int r0 = row0 + quarter * 32;
@@ -295,7 +299,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                 // each warp owns rows r0..r0+31 of the tile; stage 32 x 32 chunks and store whole row segments
 #pragma unroll 1
                 for (int c = c_first; c < ncols_warp; c += c_step) {
-                    const int nc = min(32, ncols_tile - c);
+                    // the chunk as C_g rows: rows crow0 + 0..31, columns ccol0 + 0..31, of which nrows
+                    // and nc exist (a transposed tile's chunk is 32 of its columns by 32 of its rows)
+                    const int crow0 = swapped ? col0 + c : r0;
+                    const int ccol0 = swapped ? r0 : col0 + c;
+                    const int nrows = swapped ? min(32, P.n - (col0 + c)) : min(32, P.m - r0);
+                    const int nc = swapped ? min(32, P.m - r0) : min(32, ncols_tile - c);
                     // lane l writes 16-byte group g = l % 8 (columns 4g..4g+3) of rows q*4 + l/8, q = 0..7
                     const int g = lane & 7;
                     const int cc = g * 4;
@@ -304,27 +313,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                     if (beta != 0.0f) {
 #pragma unroll
                         for (int q = 0; q < 8; ++q) {
-                            const int grow = r0 + q * 4 + (lane >> 3);
+                            const int rr = q * 4 + (lane >> 3);
                             old[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                            if (grow < P.m && vec_ok && cc + 4 <= nc)
-                                old[q] = *reinterpret_cast<const float4*>(a.c_base + P.off_c +
-                                                                          static_cast<int64_t>(grow) * P.ldc + col0 +
-                                                                          c + cc);
+                            if (rr < nrows && vec_ok && cc + 4 <= nc)
+                                old[q] = *reinterpret_cast<const float4*>(
+                                    a.c_base + P.off_c + static_cast<int64_t>(crow0 + rr) * P.ldc + ccol0 + cc);
                         }
                     }
                     float v[32];
                     tmem_load_32(taddr + c, v);
+                    if (swapped) {
+                        // lane l holds column l of the C chunk: value i goes to row i, column l
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        *reinterpret_cast<float4*>(slot_ptr + chunk_slot_off(lane, q)) =
-                            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                        for (int i = 0; i < 32; ++i)
+                            *reinterpret_cast<float*>(slot_ptr + chunk_slot_off(i, lane >> 2) + (lane & 3) * 4) = v[i];
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            *reinterpret_cast<float4*>(slot_ptr + chunk_slot_off(lane, q)) =
+                                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    }
                     __syncwarp();
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int rr = q * 4 + (lane >> 3);
-                        const int grow = r0 + rr;
-                        if (grow < P.m) {
-                            float* p = a.c_base + P.off_c + static_cast<int64_t>(grow) * P.ldc + col0 + c + cc;
+                        if (rr < nrows) {
+                            float* p = a.c_base + P.off_c + static_cast<int64_t>(crow0 + rr) * P.ldc + ccol0 + cc;
                             const float4 sv = *reinterpret_cast<const float4*>(slot_ptr + chunk_slot_off(rr, g));
                             if (vec_ok && cc + 4 <= nc) {
                                 float4 o = make_float4(alpha * sv.x, alpha * sv.y, alpha * sv.z, alpha * sv.w);
@@ -357,6 +371,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
             for (int c = c_first; c < ncols_warp; c += c_step) {
                 float v[32];
                 tmem_load_32(taddr + c, v);
+                if (swapped) {
+                    // lane l holds C_g column `row` for the chunk's 32 rows: one row per step, the
+                    // warp's 32 lanes writing 32 consecutive columns of it
+                    if (row < P.m) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if (col0 + c + j < P.n) {
+                                float* q = a.c_base + P.off_c + static_cast<int64_t>(col0 + c + j) * P.ldc + row;
+                                *q = (beta != 0.0f) ? fmaf(alpha, v[j], beta * *q) : alpha * v[j];
+                            }
+                        }
+                    }
+                    continue;
+                }
                 if (row < P.m) {
                     const int nc = min(32, ncols_tile - c);
                     float* p = crow + c;

@@ -163,8 +163,11 @@ struct alignas(16) GroupedTcTile {
     int32_t prob, tm, tn, m;  // problem, tile coordinates, problem rows
     int32_t n, k, ldc, nk;    // problem columns, depth, C row stride, k-blocks of 64
     int64_t off_c;            // element offset of C_g
-    int32_t rows, pad;        // rows of the tile: 128, or 256 for a tall tile (M-blocks tm and tm + 1); 0 = 128
+    int32_t rows, flags;      // rows of the tile: 128, or 256 for a tall tile (M-blocks tm and tm + 1); 0 = 128
 };
+// flags bit 0: the problem runs transposed, C_g^T = B_g^T A_g^T (maps[2g] is then B_g's, maps[2g+1]
+// A_g's; m and n of the record are n_g and m_g), its tiles stored to C_g transposed.
+constexpr int32_t kGroupedTcSwapped = 1;
 int grouped_tc_box_rows(int n);
 constexpr int kGroupedTcMapsPerProblem = 2;
 // staged: 1 = epilogue through shared memory, 0 = direct row stores, -1 = TCGEMM_GROUPED_EPI or staged
