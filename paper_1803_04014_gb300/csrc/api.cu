@@ -794,14 +794,15 @@ struct tc_grouped_plan {
 
 namespace {
 
-// Problems with a K-major B_g and m < n <= 256 run transposed on the tensor cores: C_g^T = B_g^T A_g^T,
-// so that the n rows of the transposed tile fill the accumulator's lanes (and the epilogue warps that
-// read them) where the m rows would fill a few; both operands are then K-major A operands of each
-// other, and the tile count does not grow (one tile, or two for m > 128).  Unless
-// TCGEMM_GROUPED_SWAP=0.  (10 000-problem mix with m, n, k uniform over 16..256: 2-2.5 % faster;
-// problems with m <= 48 and n >= 128 alone: 3.3 -> 3.9 TB/s.)
+// Problems with m < n <= 256 run transposed on the tensor cores: C_g^T = B_g^T A_g^T, so that the n
+// rows of the transposed tile fill the accumulator's lanes (and the epilogue warps that read them)
+// where the m rows would fill a few.  B_g (K-major, or row-major and then read as an MN-major A
+// operand) takes the A operand's place and A_g the K-major B operand's; the tile count does not grow
+// (one tile, or two for m > 128).  Unless TCGEMM_GROUPED_SWAP=0.  (10 000-problem mix with m, n, k
+// uniform over 16..256: 2-3 % faster; problems with m <= 48 and n >= 128 alone: 3.3 -> 3.9 TB/s.)
 bool grouped_swap(const tc_problem& p, int32_t lb) {
-    if (lb != TC_COL_MAJOR || !(p.m < p.n && p.n <= tcg::kGroupedTcTileN)) return false;
+    (void)lb;
+    if (!(p.m < p.n && p.n <= tcg::kGroupedTcTileN)) return false;
     const char* env = getenv("TCGEMM_GROUPED_SWAP");
     return !(env && strcmp(env, "0") == 0);
 }
@@ -816,9 +817,12 @@ tc_status encode_grouped_maps(int32_t dt, int32_t lb, int32_t count, const tc_pr
     constexpr int kM = tcg::kGroupedTcMapsPerProblem;
     for (int32_t g = 0; g < count; ++g) {
         const tc_problem& p = problems[g];
-        if (grouped_swap(p, lb)) {   // B_g (n x k) as the A operand, A_g (m x k) as the B operand
-            tc_status s = encode_kmajor(&maps[kM * g], tdt, 2, b + p.off_b * 2, p.k, p.n, 1, int64_t(p.ldb) * 2,
-                                        int64_t(p.n) * p.ldb * 2, tcg::kGroupedTcTileM);
+        if (grouped_swap(p, lb)) {   // B_g as the A operand, A_g (m x k) as the K-major B operand
+            tc_status s = lb == TC_ROW_MAJOR   // k x n: dims {n, k}, boxes of 64 n x 64 k (MN-major A)
+                              ? encode_kmajor(&maps[kM * g], tdt, 2, b + p.off_b * 2, p.n, p.k, 1, int64_t(p.ldb) * 2,
+                                              int64_t(p.k) * p.ldb * 2, 64)
+                              : encode_kmajor(&maps[kM * g], tdt, 2, b + p.off_b * 2, p.k, p.n, 1, int64_t(p.ldb) * 2,
+                                              int64_t(p.n) * p.ldb * 2, tcg::kGroupedTcTileM);
             if (s == TC_OK)
                 s = encode_kmajor(&maps[kM * g + 1], tdt, 2, a + p.off_a * 2, p.k, p.m, 1, int64_t(p.lda) * 2,
                                   int64_t(p.m) * p.lda * 2, tcg::grouped_tc_box_rows(p.m));

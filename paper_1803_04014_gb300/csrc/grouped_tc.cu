@@ -167,11 +167,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                     prefetch_tmap(a.maps + 2 * nxt.prob + 1);
                 }
                 const int nk = tile.nk;
-                const bool tall = tall_tile(tile, B_MN);
+                // a transposed problem with a row-major B_g: its A operand (B_g^T) is MN-major, its
+                // B operand (A_g) K-major
+                const bool a_mn = B_MN && (tile.flags & kGroupedTcSwapped);
+                const bool b_mn = B_MN && !a_mn;
+                const bool tall = tall_tile(tile, b_mn);
                 const int boff = tall ? 2 * kABytes : kABytes;
-                const int nslabs = B_MN ? mma_n_mn(tile.n) / 64 : 0;
+                const int nslabs = b_mn ? mma_n_mn(tile.n) / 64 : 0;
                 const uint32_t bytes = static_cast<uint32_t>((tall ? 2 : 1) * kABytes +
-                                                             (B_MN ? nslabs * 64 : mma_n(tile.n)) * kRow);
+                                                             (b_mn ? nslabs * 64 : mma_n(tile.n)) * kRow);
                 for (int kb = 0; kb < nk; ++kb) {
                     if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, a.status)) {
                         ok = false;
@@ -179,9 +183,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                     }
                     const uint32_t sbase = base + stage * kStage;
                     mbar_arrive_expect_tx(full_bar(stage), bytes);
-                    tma_load_3d(sbase, mA, full_bar(stage), kb * 64, tile.tm * GM, 0);
-                    if (tall) tma_load_3d(sbase + kABytes, mA, full_bar(stage), kb * 64, (tile.tm + 1) * GM, 0);
-                    if constexpr (B_MN) {
+                    for (int blk = 0; blk < (tall ? 2 : 1); ++blk) {
+                        const int row_a = (tile.tm + blk) * GM;
+                        if (a_mn) {   // 128 rows of A as two slabs of 64 (rows of B_g^T) x 64 k
+                            tma_load_3d(sbase + blk * kABytes, mA, full_bar(stage), row_a, kb * 64, 0);
+                            tma_load_3d(sbase + blk * kABytes + 64 * kRow, mA, full_bar(stage), row_a + 64, kb * 64, 0);
+                        } else {
+                            tma_load_3d(sbase + blk * kABytes, mA, full_bar(stage), kb * 64, row_a, 0);
+                        }
+                    }
+                    if (b_mn) {
                         for (int sl = 0; sl < nslabs; ++sl)
                             tma_load_3d(sbase + boff + sl * 64 * kRow, mB, full_bar(stage), tile.tn * GN + sl * 64,
                                         kb * 64, 0);
@@ -215,9 +226,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                 const GroupedTcTile tile = nxt;
                 nxt = load_tile(a.tiles, t + gridDim.x, a.num_tiles);
                 const int nk = tile.nk;
-                const uint32_t idesc = B_MN ? (make_idesc(GM, mma_n_mn(tile.n), a.ab_format) | (1u << 16))
-                                            : make_idesc(GM, mma_n(tile.n), a.ab_format);
-                const bool tall = tall_tile(tile, B_MN);
+                const bool a_mn = B_MN && (tile.flags & kGroupedTcSwapped);
+                const bool b_mn = B_MN && !a_mn;
+                // bit 15 of the instruction descriptor: A MN-major; bit 16: B MN-major
+                const uint32_t idesc = b_mn ? (make_idesc(GM, mma_n_mn(tile.n), a.ab_format) | (1u << 16))
+                                            : (make_idesc(GM, mma_n(tile.n), a.ab_format) | (a_mn ? (1u << 15) : 0u));
+                const bool tall = tall_tile(tile, b_mn);
                 const int boff = tall ? 2 * kABytes : kABytes;
                 if (!mbar_wait(tempty_bar(acc), acc_phase ^ 1u, abort_flag, a.status)) {
                     ok = false;
@@ -234,13 +248,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
                     const uint32_t sbase = base + stage * kStage;
 #pragma unroll
                     for (int ks = 0; ks < 4; ++ks) {
-                        // MN-major B: 16 k-rows of 128 bytes per step, 64-n slabs 8 KB apart
-                        const uint64_t bdesc = B_MN ? sw128_mnmajor_desc(sbase + boff + ks * 2048, 64 * kRow, 1024)
+                        // MN-major operand: 16 k-rows of 128 bytes per step, 64-row slabs 8 KB apart
+                        const uint64_t bdesc = b_mn ? sw128_mnmajor_desc(sbase + boff + ks * 2048, 64 * kRow, 1024)
                                                     : sw128_kmajor_desc(sbase + boff + ks * 32);
-                        mma_f16(d_tmem, sw128_kmajor_desc(sbase + ks * 32), bdesc, idesc, (kb | ks) != 0 ? 1u : 0u);
+                        auto adesc = [&](int blk) {
+                            const uint32_t at = sbase + blk * kABytes;
+                            return a_mn ? sw128_mnmajor_desc(at + ks * 2048, 64 * kRow, 1024)
+                                        : sw128_kmajor_desc(at + ks * 32);
+                        };
+                        mma_f16(d_tmem, adesc(0), bdesc, idesc, (kb | ks) != 0 ? 1u : 0u);
                         if (tall)   // rows 128-255 against the same B, into columns 128... of the buffer
-                            mma_f16(d_tmem + static_cast<uint32_t>(GN / 2), sw128_kmajor_desc(sbase + kABytes + ks * 32),
-                                    bdesc, idesc, (kb | ks) != 0 ? 1u : 0u);
+                            mma_f16(d_tmem + static_cast<uint32_t>(GN / 2), adesc(1), bdesc, idesc,
+                                    (kb | ks) != 0 ? 1u : 0u);
                     }
                     issued_any = true;
                     mma_commit(empty_bar(stage));
@@ -277,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grouped_tc(const Args a) {
             const bool ok = mbar_wait(tfull_bar(acc), acc_phase, abort_flag, a.status);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
-            const bool tall = tall_tile(P, B_MN);
+            const bool tall = tall_tile(P, B_MN && !(P.flags & kGroupedTcSwapped));
             const int c_first = tall ? 0 : half * 32, c_step = tall ? 32 : 64;
             const int row0 = tile.tm * GM + (tall ? half * GM : 0);
             const int row = row0 + quarter * 32 + lane;

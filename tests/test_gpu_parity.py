@@ -728,12 +728,14 @@ def test_grouped_tc_large_problems_and_new_bases(b):
         b.gemm_grouped_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("lb", [1, 0])
 @pytest.mark.parametrize("epi", ["staged", "direct"])
 @pytest.mark.parametrize("beta", [0.0, -0.75])
-def test_grouped_transposed_problems(b, monkeypatch, epi, beta):
-    # K-major B and m < n <= 256: the problem runs as C^T = B^T A^T (tall when m <= 128 < n) and its
-    # tiles are stored to C transposed.  Against the oracle, and against the untransposed run
-    # (TCGEMM_GROUPED_SWAP=0) within the same bound; odd m, n and ldc (scalar stores), m = 1, m = n.
+def test_grouped_transposed_problems(b, monkeypatch, lb, epi, beta):
+    # m < n <= 256: the problem runs as C^T = B^T A^T (tall when m <= 128 < n) and its tiles are
+    # stored to C transposed; with a row-major B, B^T is an MN-major A operand.  Against the oracle,
+    # and against the untransposed run (TCGEMM_GROUPED_SWAP=0) within the same bound; odd m, n and
+    # ldc (scalar stores), m = 1, m = n.
     monkeypatch.setenv("TCGEMM_GROUPED_EPI", epi)
     sizes = [(32, 256, 32), (16, 200, 96), (100, 240, 64), (129, 250, 40), (200, 256, 128), (1, 17, 16),
              (7, 9, 24), (64, 64, 64), (250, 256, 200), (120, 130, 8), (300, 100, 64), (48, 512, 32)]
@@ -744,9 +746,14 @@ def test_grouped_transposed_problems(b, monkeypatch, epi, beta):
         B = synth.uniform((k, n), seed=900 + i)
         lda = (k + 7) // 8 * 8
         Ap = np.zeros((m, lda), np.float32); Ap[:, :k] = A
-        Bp = np.zeros((n, lda), np.float32); Bp[:, :k] = B.T
+        if lb == 1:
+            ldb = lda
+            Bp = np.zeros((n, ldb), np.float32); Bp[:, :k] = B.T
+        else:
+            ldb = (n + 7) // 8 * 8
+            Bp = np.zeros((k, ldb), np.float32); Bp[:, :n] = B
         ldc = n + (i % 3)   # padded rows of C: 0, 1 or 2 extra floats
-        rows.append((m, n, k, oa, ob, oc, lda, lda, ldc))
+        rows.append((m, n, k, oa, ob, oc, lda, ldb, ldc))
         a_parts.append(Ap.ravel()); b_parts.append(Bp.ravel())
         data.append((m, n, k, oc, ldc, A, B))
         oa += Ap.size; ob += Bp.size; oc += m * ldc
@@ -757,13 +764,13 @@ def test_grouped_transposed_problems(b, monkeypatch, epi, beta):
     for swap in ("1", "0"):
         monkeypatch.setenv("TCGEMM_GROUPED_SWAP", swap)
         C = dev(C0)
-        b.gemm_grouped(0, rows, Ad, 0, Bd, 1, C, 1.25, beta)
+        b.gemm_grouped(0, rows, Ad, 0, Bd, lb, C, 1.25, beta)
         b.tc_sync_status()
         out[swap] = host(C)
     # the same bits every run
     monkeypatch.setenv("TCGEMM_GROUPED_SWAP", "1")
     C = dev(C0)
-    b.gemm_grouped(0, rows, Ad, 0, Bd, 1, C, 1.25, beta)
+    b.gemm_grouped(0, rows, Ad, 0, Bd, lb, C, 1.25, beta)
     b.tc_sync_status()
     assert np.array_equal(host(C), out["1"])
     for (m, n, k, c0, ldc, A, B) in data:
