@@ -310,7 +310,9 @@ typedef struct tc_grouped_plan tc_grouped_plan;
 
 /* Validate `count` problems (host array) and build a schedule: every problem
  * is cut into output tiles, the tiles are ordered longest-first and stored
- * on the device.  dt: TC_F16 or TC_BF16.  la must be TC_ROW_MAJOR; lb either.
+ * on the device (on the tensor cores a problem with m < n <= 256 is computed
+ * as C^T = B^T A^T and stored to C transposed; n <= 128 takes 256-row
+ * tiles).  dt: TC_F16 or TC_BF16.  la must be TC_ROW_MAJOR; lb either.
  * Constraints: m, n, k >= 1; lda, ldb multiples of 8 and offsets of A and B
  * multiples of 8 (16-byte rows); ldc >= n.  The plan owns its device memory. */
 tc_status gemm_grouped_plan_create(int32_t dt, int32_t count, const tc_problem* problems,

@@ -21,7 +21,13 @@
 //     the two warps of each TMEM lane quarter taking alternate 32-column chunks
 //     (of a tall tile: one warp rows 0-127, the other rows 128-255);
 //     each chunk (32 rows x 32 columns) is transposed through a 4 KB swizzled
-//     shared-memory slot of the warp so that C leaves as whole row segments.
+//     shared-memory slot of the warp so that C leaves as whole row segments;
+//   * a problem with m < n <= 256 runs transposed, C^T = B^T A^T (B's map in
+//     the A operand's place; a row-major B then reads as an MN-major A): a
+//     warp reads only its quarter of the accumulator's lanes, so the n rows of
+//     the transposed tile keep all eight warps busy where m rows would keep a
+//     few.  Its chunks are written into the slots transposed and leave as C
+//     row segments all the same.
 //     (Storing the chunks by TMA instead was measured slower: the stores queue
 //     behind the operand loads in the SM's one TMA unit.)
 #include <cstdlib>
