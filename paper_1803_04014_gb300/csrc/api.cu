@@ -11,6 +11,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -41,18 +42,17 @@ struct Device {
     int sm_count = 0;
     int cc_major = 0, cc_minor = 0;
     int* status = nullptr;  // device status word (first error wins)
-    unsigned* kflags = nullptr;          // kKpartRegions regions of flags for parts of K
-    std::atomic<unsigned> kregion{0};    // next region (launches take them in turn)
+    // flags of the pair kernels' parts of K, one block per stream (per host thread for
+    // cudaStreamPerThread), and the count that gives every launch its token
+    std::mutex kmu;
+    std::map<std::pair<cudaStream_t, std::thread::id>, unsigned long long*> kflags;
+    std::atomic<unsigned long long> ktoken{0};
 };
 
 std::mutex g_mu;
 Device g_dev[64];
 static __device__ __align__(256) int g_status_word[64];  // one copy per device; word 0 is used
-// Flags of the pair kernel's parts of K (static, zero at module load; every launch leaves its region
-// zero).  Launches take the regions in turn, so launches in flight at the same time on different
-// streams use different flags unless kKpartRegions of them are.
-constexpr int kKpartRegions = 64;
-static __device__ __align__(256) unsigned g_kpart_flags[kKpartRegions * tcg::kKpartRegionWords];
+
 
 tc_status get_device(Device** out) {
     int dev = 0;
@@ -71,10 +71,6 @@ tc_status get_device(Device** out) {
         if ((e = cudaGetSymbolAddress(&sw, g_status_word)) != cudaSuccess)
             return cuda_fail(e, "cudaGetSymbolAddress(status)");
         d.status = static_cast<int*>(sw);
-        void* kf = nullptr;
-        if ((e = cudaGetSymbolAddress(&kf, g_kpart_flags)) != cudaSuccess)
-            return cuda_fail(e, "cudaGetSymbolAddress(flags)");
-        d.kflags = static_cast<unsigned*>(kf);
         // keep freed stream-ordered workspace cached in the pool instead of returning it each sync
         cudaMemPool_t pool;
         if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
@@ -87,12 +83,65 @@ tc_status get_device(Device** out) {
     return TC_OK;
 }
 
-// The flags region of one launch of the pair kernel with parts of K.
-unsigned* kpart_region(Device* d) {
-    if (!d->kflags) return nullptr;
-    const unsigned r = d->kregion.fetch_add(1u, std::memory_order_relaxed) % kKpartRegions;
-    return d->kflags + static_cast<size_t>(r) * tcg::kKpartRegionWords;
+// Flags and token of one launch of the pair kernels with parts of K on `st`.  The first part of a
+// cut tile stores the launch's token in its flags and the second waits for that value; tokens count
+// up per device from 1, so flags left by earlier launches never match.
+//  - An eager launch uses its stream's own block (allocated and zeroed on the stream's first such
+//    launch, kept for the process): launches on one stream never run at the same time.
+//  - A launch being captured into a graph uses a block the graph allocates and zeroes at each replay
+//    and frees after the launch (*owned): a replay may run on another stream beside eager launches on
+//    this one, and its token is the same at every replay.
+//  - nullptr when neither can be had; the kernels then cut halves of N instead of parts of K.
+unsigned long long* kpart_flags(Device* d, cudaStream_t st, unsigned long long* token, bool* owned) {
+    *owned = false;
+    *token = d->ktoken.fetch_add(1, std::memory_order_relaxed) + 1;
+    const size_t bytes = sizeof(unsigned long long) * tcg::kKpartFlags;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    void* p = nullptr;
+    if (cs == cudaStreamCaptureStatusActive) {
+        if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        if (cudaMemsetAsync(p, 0, bytes, st) != cudaSuccess) {
+            cudaFreeAsync(p, st);
+            cudaGetLastError();
+            return nullptr;
+        }
+        *owned = true;
+        return static_cast<unsigned long long*>(p);
+    }
+    if (cs != cudaStreamCaptureStatusNone) return nullptr;
+    const auto key = std::make_pair(st, st == cudaStreamPerThread ? std::this_thread::get_id() : std::thread::id());
+    std::lock_guard<std::mutex> lk(d->kmu);
+    auto it = d->kflags.find(key);
+    if (it != d->kflags.end()) return it->second;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaMemsetAsync(p, 0, bytes, st) != cudaSuccess) {
+        cudaFree(p);
+        cudaGetLastError();
+        return nullptr;
+    }
+    d->kflags[key] = static_cast<unsigned long long*>(p);
+    return static_cast<unsigned long long*>(p);
 }
+
+// Frees a graph-owned flags block after the launch that used it was enqueued.
+struct KpartFlagsGuard {
+    unsigned long long* p = nullptr;
+    cudaStream_t st = nullptr;
+    bool owned = false;
+    ~KpartFlagsGuard() {
+        if (owned && p) cudaFreeAsync(p, st);
+    }
+};
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -323,8 +372,6 @@ tc_status tc_sync_status(void* stream) {
         return cuda_fail(e, "read status");
     if (word != 0) {
         cudaMemset(d->status, 0, sizeof(int));
-        // a kernel that gave up may have left flags of parts of K raised
-        cudaMemset(d->kflags, 0, sizeof(unsigned) * kKpartRegions * tcg::kKpartRegionWords);
         return fail(TC_ERR_TIMEOUT, "a kernel gave up on a bounded wait (device status %d)", word);
     }
     return TC_OK;
@@ -451,7 +498,13 @@ tc_status gemm_mixed_impl(int32_t dt, int64_t m, int64_t n, int64_t k, float alp
     p.stall_at = take_stall();
     p.staged_epilogue = gemm_staged_epilogue();
     p.split_tail = cfg.tail;
-    p.kpart_flags = kpart_region(d);
+    KpartFlagsGuard kg;
+    const int64_t kbk = dt == TC_E4M3 ? 128 : 64;
+    if (p.pair && p.split_tail == 2 && (k + kbk - 1) / kbk >= tcg::kKpartMinKb) {
+        p.kpart_flags = kpart_flags(d, st, &p.kpart_token, &kg.owned);
+        kg.p = p.kpart_flags;
+        kg.st = st;
+    }
     p.serpentine = cfg.korder;
     p.quad = (p.pair && !b_mn && cfg.cluster == 4) ? 1 : 0;
     p.m = m; p.n = n; p.k = k;
@@ -575,7 +628,12 @@ tc_status split_gemm(const char* name, int scheme, int32_t piece, int32_t nprod,
         f.stall_at = take_stall();
         f.serpentine = gemm_serpentine();
         f.split_tail = gemm_split_tail();
-        f.kpart_flags = kpart_region(d);
+        KpartFlagsGuard kg;
+        if (f.split_tail == 2 && (k + 63) / 64 >= tcg::kKpartMinKbPromoted) {
+            f.kpart_flags = kpart_flags(d, st, &f.kpart_token, &kg.owned);
+            kg.p = f.kpart_flags;
+            kg.st = st;
+        }
         CUtensorMap ta, tb;
         // K-major: rows of k elements, boxes of 32 k x 128 rows; MN-major: k rows of m (or n)
         // elements, boxes of 32 x 32 k-rows
@@ -638,7 +696,12 @@ tc_status split_gemm(const char* name, int scheme, int32_t piece, int32_t nprod,
         p.group_m = gemm_group_m();
         p.stall_at = take_stall();
         p.split_tail = gemm_split_tail();
-        p.kpart_flags = kpart_region(d);
+        KpartFlagsGuard kg;
+        if (p.pair && p.split_tail == 2 && (k + 63) / 64 >= tcg::kKpartMinKbPromoted) {
+            p.kpart_flags = kpart_flags(d, st, &p.kpart_token, &kg.owned);
+            kg.p = p.kpart_flags;
+            kg.st = st;
+        }
         p.serpentine = gemm_serpentine();
         p.m = m; p.n = n; p.k = k;
         p.alpha = alpha; p.beta = beta;

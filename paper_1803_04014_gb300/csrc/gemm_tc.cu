@@ -41,7 +41,6 @@ constexpr int BM = 128;
 constexpr int kRowBytes = 128;
 constexpr int kATileBytes = BM * kRowBytes;
 constexpr int kThreads = 192;
-constexpr int kKpartMinKb = 48;  // shortest K (in k-blocks) cut into parts
 
 struct Args {
     int m, n, k;
@@ -62,15 +61,17 @@ struct Args {
     // tiles in two lets twice as many CTA pairs share it.
     //   split_tail 1: two 256 x 128 halves (idesc_half is the half-width MMA's descriptor);
     //   split_tail 2: two parts of K, k-blocks [0, kb_split) and [kb_split, num_kb).  The first
-    //     part's epilogue stores alpha * P_1 + beta * C into C and raises one flag per epilogue
-    //     warp in kflags; the second part's warp waits for its flag and stores alpha * P_2 + C.
+    //     part's epilogue stores alpha * P_1 + beta * C into C and sets one flag per epilogue warp
+    //     in kflags to ktoken; the second part's warp waits for that value and stores
+    //     alpha * P_2 + C.
     //     An MMA takes about as long at N = 128 as at N = 256, so halves of N take as long as
     //     whole tiles, and parts of K less.
     int full_units, num_units;
     uint32_t idesc_half;
     int split_tail;  // 0 keeps every unit whole (TCGEMM_PAIR_TAIL=full)
     int kb_split;
-    unsigned* kflags;
+    unsigned long long* kflags;
+    unsigned long long ktoken;  // the value this launch's first parts store in their flags
     // pair kernel with promotion: parts of K only (split_tail 2), cut between chunks: the first part
     // takes chunks [0, chunk_split)
     int chunk_split;
@@ -103,7 +104,7 @@ __device__ __forceinline__ Unit unit_coords(const Args& a, int u) {
 }
 
 // Flag of epilogue warp (rank, quarter) of the unit's tile, for parts of K of the pair kernel.
-__device__ __forceinline__ unsigned* kpart_flag(const Args& a, int u, uint32_t rank, int quarter) {
+__device__ __forceinline__ unsigned long long* kpart_flag(const Args& a, int u, uint32_t rank, int quarter) {
     const int j = (u - a.full_units) >> 1;
     return a.kflags + (j * 2 + static_cast<int>(rank)) * 4 + quarter;
 }
@@ -617,8 +618,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if constexpr (KIND == 1) alpha = alpha * (1.0f / *a.scale_a) * (1.0f / *a.scale_b);
         const float beta_in = a.beta;
         // flag of the first part of K set: a bounded poll with acquire by every lane
-        auto wait_flag = [&](const unsigned* f) {
-            const bool ok = poll_flag_acquire(f, abort_flag, a.status);
+        auto wait_flag = [&](const unsigned long long* f) {
+            const bool ok = poll_flag_acquire(f, a.ktoken, abort_flag, a.status);
             if (!ok) st_shared_cluster_u32(peer_abort, 1u);
             return __all_sync(0xffffffffu, ok);
         };
@@ -626,7 +627,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         auto raise_flag = [&](int u) {
             __threadfence();
             __syncwarp();
-            if (lane == 0) st_release_gpu(kpart_flag(a, u, rank, quarter), 1u);
+            if (lane == 0) st_release_gpu(kpart_flag(a, u, rank, quarter), a.ktoken);
         };
         const bool vec_ok = ((a.ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.C) & 15u) == 0);
         const uint32_t leader_tempty0 = mapa_shared(tempty_bar(0), 0);
@@ -723,7 +724,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 acc ^= 1;
                 if (acc == 0) acc_phase ^= 1u;
                 if (w.kpart == 1) raise_flag(u);
-                if (w.kpart == 2 && lane == 0) *kpart_flag(a, u, rank, quarter) = 0u;  // ready for the next launch
                 continue;
             }
             const bool ok = wait(tfull_bar(acc), acc_phase);
@@ -769,7 +769,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             acc ^= 1;
             if (acc == 0) acc_phase ^= 1u;
             if (w.kpart == 1) raise_flag(u);
-            if (w.kpart == 2 && lane == 0) *kpart_flag(a, u, rank, quarter) = 0u;
         }
     }
 
@@ -816,7 +815,7 @@ cudaError_t run_pair(const CUtensorMap& tmA, const CUtensorMap& tmB, const Args&
     // parts of K need a flag per epilogue warp of each cut tile and a K long enough that the first
     // part's epilogue (about 16 k-blocks' time) ends before the second part's main loop; else halves
     // of N (a short K would chain the two parts' epilogues: 23 us against 11.5 us at m = n = k = 1024)
-    if (a.split_tail == 2 && (a.num_kb < kKpartMinKb || !a.kflags || 8 * rem > kKpartRegionWords)) a.split_tail = 1;
+    if (a.split_tail == 2 && (a.num_kb < kKpartMinKb || !a.kflags || 8 * rem > kKpartFlags)) a.split_tail = 1;
     if (rem > 0 && 2 * rem <= clusters && a.split_tail) a.full_units = a.num_tiles - rem;
     a.num_units = a.full_units + 2 * (a.num_tiles - a.full_units);
     if (clusters > a.num_units) {
@@ -1209,7 +1208,7 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
             }
             if (!ok) break;
             if (pu.kpart == 2) {
-                const bool fl = poll_flag_acquire(part_flag(u), abort_flag, a.status);
+                const bool fl = poll_flag_acquire(part_flag(u), a.ktoken, abort_flag, a.status);
                 if (!fl) st_shared_cluster_u32(peer_abort, 1u);
                 if (!__all_sync(0xffffffffu, fl)) break;
             }
@@ -1244,9 +1243,7 @@ __global__ void __launch_bounds__(kPromoteThreads, 1)
             if (pu.kpart == 1) {   // this warp's stores are visible before its flag is raised
                 __threadfence();
                 __syncwarp();
-                if (lane == 0) st_release_gpu(part_flag(u), 1u);
-            } else if (pu.kpart == 2 && lane == 0) {
-                *part_flag(u) = 0u;   // ready for the next launch
+                if (lane == 0) st_release_gpu(part_flag(u), a.ktoken);
             }
         }
     }
@@ -1287,7 +1284,7 @@ cudaError_t run_pair_promote(const CUtensorMap& tmA, const CUtensorMap& tmB, con
     // cut between chunks as the one-launch kernel cuts them (decided on the nominal grid, so that
     // both paths give the same bits)
     const ChunkPlan cp = plan_chunk_parts(a.num_tiles, clusters, (a.num_kb + CHUNK_KB - 1) / CHUNK_KB,
-                                          a.split_tail == 2 && a.kflags != nullptr, kKpartRegionWords / 16);
+                                          a.split_tail == 2 && a.kflags != nullptr, kKpartFlags / 16);
     a.full_units = cp.full_units;
     a.num_units = cp.num_units;
     a.chunk_split = cp.chunk_split;
@@ -1347,6 +1344,7 @@ cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const
         // the first part of K is 16 k-blocks shorter, so that its epilogue overlaps the second's main loop
         a.kb_split = (a.num_kb - 16) / 2 > 0 ? (a.num_kb - 16) / 2 : 1;
         a.kflags = p.kpart_flags;
+        a.ktoken = p.kpart_token;
         const int max_clusters = p.sm_count / 2;
         const int clusters = a.num_tiles < max_clusters ? a.num_tiles : max_clusters;
         if (clusters <= 0) return cudaSuccess;

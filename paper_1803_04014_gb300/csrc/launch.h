@@ -90,12 +90,18 @@ struct TcGemmLaunch {
     int split_tail;     // pair kernel: a last round of tiles keeping at most half of the pairs busy runs
                         // as two units per tile: 1 = 256 x 128 halves, 2 = two parts of K (which need
                         // kpart_flags; else halves)
-    unsigned* kpart_flags;  // kKpartRegionWords zero words of device memory, zero again when the kernel ends
+    unsigned long long* kpart_flags;  // kKpartFlags 64-bit flags of device memory no other launch uses while
+                                      // this one runs (see kpart_token)
+    unsigned long long kpart_token;   // this launch's flag value: nonzero, never used by another launch
     int quad;           // one product, K-major B: clusters of four CTAs (two pairs) sharing A by TMA
                         // multicast (gemm_quad.cu); tmA then has a 64-row box
 };
-// Flags of one launch of the pair kernel with parts of K: 8 per cut tile (at most 128 tiles).
-constexpr int kKpartRegionWords = 1024;
+// Flags of one launch of the pair kernels with parts of K: 8 (16 with promotion) per cut tile.
+constexpr int kKpartFlags = 1024;
+// Shortest K (in k-blocks) the pair kernel cuts into parts; the promoting kernels cut from 16 chunks
+// (32 k-blocks at the shortest chunk).
+constexpr int kKpartMinKb = 48;
+constexpr int kKpartMinKbPromoted = 32;
 // tmA: 3-D map {k, m, na} with a 128 x (128 bytes) box; tmB: {k, n, nb} with a bn x (128 bytes) box.
 cudaError_t launch_tc_gemm(const CUtensorMap& tmA, const CUtensorMap& tmB, const TcGemmLaunch& p, cudaStream_t st);
 // ---- gemm_quad.cu: the pair GEMM on clusters of four CTAs, A multicast between the two pairs.
@@ -120,7 +126,8 @@ struct SplitFusedLaunch {
     int stall_at;    // test hook: k-block + 1 to withhold, 0 = off
     int serpentine;  // every other round of tiles of a CTA pair walks K downwards
     int split_tail;  // 2: a partial last round of tiles runs as two parts of K (as the two-pass kernel)
-    unsigned* kpart_flags;  // kKpartRegionWords zero words (see TcGemmLaunch)
+    unsigned long long* kpart_flags;  // as in TcGemmLaunch
+    unsigned long long kpart_token;
 };
 // Schemes the one-launch kernel runs (the three-piece BF16 split does not: its pieces and the
 // FP32 staging do not fit in shared memory together).

@@ -76,9 +76,11 @@ struct FusedArgs {
     int stall_kb;  // test hook: >= 0 makes the even CTA of the first pair withhold this k-block
     int serpentine;  // odd rounds of tiles of a CTA pair walk K downwards (as the two-pass kernel)
     // work units (chunk_unit): tiles, then two parts of K of each tile of a cut last round; the
-    // second part's epilogue warp waits for the first part's flag in kflags (8 per CTA and tile)
+    // second part's epilogue warp waits for the first part's flag in kflags (8 per CTA and tile) to
+    // hold ktoken
     int full_units, num_units, chunk_split;
-    unsigned* kflags;
+    unsigned long long* kflags;
+    unsigned long long ktoken;
 };
 
 template <int NA, int NB>
@@ -429,7 +431,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             }
             if (!ok) break;
             if (pu.kpart == 2) {
-                const bool fl = poll_flag_acquire(part_flag(u), abort_flag, a.status);
+                const bool fl = poll_flag_acquire(part_flag(u), a.ktoken, abort_flag, a.status);
                 if (!fl) st_shared_cluster_u32(peer_abort, 1u);
                 if (!__all_sync(0xffffffffu, fl)) break;
             }
@@ -464,9 +466,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             if (pu.kpart == 1) {   // this warp's stores are visible before its flag is raised
                 __threadfence();
                 __syncwarp();
-                if (lane == 0) st_release_gpu(part_flag(u), 1u);
-            } else if (pu.kpart == 2 && lane == 0) {
-                *part_flag(u) = 0u;   // ready for the next launch
+                if (lane == 0) st_release_gpu(part_flag(u), a.ktoken);
             }
         }
     } else if (wg == 0) {
@@ -741,7 +741,7 @@ cudaError_t run_fused(const CUtensorMap& tmA, const CUtensorMap& tmB, const Fuse
     FusedArgs a = args;
     // the same cut as the two-pass kernel's (decided on the nominal grid)
     const ChunkPlan cp = plan_chunk_parts(a.num_tiles, clusters, (a.num_kb + CHUNK_KB - 1) / CHUNK_KB,
-                                          a.kflags != nullptr, kKpartRegionWords / 16);
+                                          a.kflags != nullptr, kKpartFlags / 16);
     a.full_units = cp.full_units;
     a.num_units = cp.num_units;
     a.chunk_split = cp.chunk_split;
@@ -807,6 +807,7 @@ cudaError_t launch_split_fused(const CUtensorMap& tmA, const CUtensorMap& tmB, c
     a.stall_kb = p.stall_at - 1;
     a.serpentine = p.serpentine;
     a.kflags = p.split_tail == 2 ? p.kpart_flags : nullptr;
+    a.ktoken = p.kpart_token;
     a.idesc = make_idesc(256, 256, p.bf16 ? 1u : 0u) | (p.a_mn ? kIdescTransposeA : 0u) |
               (p.b_mn ? kIdescTransposeB : 0u);
     a.corr_scale = 1.0f;

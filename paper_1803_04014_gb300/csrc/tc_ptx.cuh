@@ -92,15 +92,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
-// Bounded poll of a flag in global memory that another CTA of the grid raises with a release
-// store: true once it reads non-zero (with acquire at GPU scope), false on the abort flag or after
-// kWaitLimitNs (then the status word says so).
-__device__ __forceinline__ bool poll_flag_acquire(const unsigned* f, volatile int* abort_flag, int* status) {
+// Bounded poll of a 64-bit flag in global memory that another CTA of the grid sets to `token` with
+// a release store: true once it reads `token` (with acquire at GPU scope), false on the abort flag
+// or after kWaitLimitNs (then the status word says so).  Each launch has its own token, so a flag
+// left by an earlier launch, or set by another launch that shares the memory, never matches.
+__device__ __forceinline__ bool poll_flag_acquire(const unsigned long long* f, unsigned long long token,
+                                                  volatile int* abort_flag, int* status) {
     const uint64_t t0 = global_timer_ns();
     for (uint32_t it = 0;; ++it) {
-        unsigned v;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
-        if (v != 0u) return true;
+        unsigned long long v;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(f) : "memory");
+        if (v == token) return true;
         if (*abort_flag) return false;
         if ((it & 15u) == 15u && global_timer_ns() - t0 > kWaitLimitNs) {
             *abort_flag = 1;
@@ -111,8 +113,8 @@ __device__ __forceinline__ bool poll_flag_acquire(const unsigned* f, volatile in
     }
 }
 
-__device__ __forceinline__ void st_release_gpu(unsigned* f, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
+__device__ __forceinline__ void st_release_gpu(unsigned long long* f, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(f), "l"(v) : "memory");
 }
 
 // try_wait with cluster-scope acquire: for barriers that threads of the peer

@@ -620,6 +620,60 @@ def test_gemm_pair_parts_of_k(b, monkeypatch, epi, beta, case):
     assert np.array_equal(got, again)
 
 
+def test_gemm_pair_parts_of_k_in_graphs_and_on_streams(b, monkeypatch):
+    # parts of K signal through flags: an eager launch uses its stream's own flags and a token of its
+    # own, a captured launch flags that the graph allocates and zeroes at each replay.  Eager launches
+    # on three streams at once (one of them a graph replay) and repeated replays give the bits of one
+    # launch alone.
+    monkeypatch.setenv("TCGEMM_TILE", "pair")
+    m, n, k = 2500, 2520, 3072
+    A = synth.uniform((m, k), seed=181)
+    B = synth.uniform((k, n), seed=182)
+    C0 = dev(synth.uniform((m, n), seed=183))
+    aq, _ = _quant_dev(b, 0, A)
+    bq, _ = _quant_dev(b, 0, B, transpose=True)
+
+    def launch(C, stream):
+        b.gemm_mixed(0, m, n, k, 1.0, aq, k, 0, bq, k, 1, 0.5, C, n, stream=stream)
+
+    main = torch.cuda.current_stream()
+    alone = C0.clone()
+    launch(alone, main)
+    b.tc_sync_status()
+    # a graph of one launch, replayed three times
+    s_cap = torch.cuda.Stream()
+    s_cap.wait_stream(main)
+    Cg = C0.clone()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s_cap):
+        launch(Cg, s_cap)   # one eager launch first: set-up outside the capture
+        torch.cuda.synchronize()
+        Cg.copy_(C0)
+        with torch.cuda.graph(g, stream=s_cap):
+            launch(Cg, s_cap)
+    main.wait_stream(s_cap)
+    for _ in range(3):
+        Cg.copy_(C0)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        b.tc_sync_status()
+        assert torch.equal(Cg, alone)
+    # two eager streams and a replay at once
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    C1, C2 = C0.clone(), C0.clone()
+    Cg.copy_(C0)
+    torch.cuda.synchronize()
+    for s_ in (s1, s2):
+        s_.wait_stream(main)
+    launch(C1, s1)
+    launch(C2, s2)
+    g.replay()
+    torch.cuda.synchronize()
+    b.tc_sync_status()
+    assert torch.equal(C1, alone) and torch.equal(C2, alone) and torch.equal(Cg, alone)
+
+
 @pytest.mark.parametrize("tile", ["single", "pair"])
 @pytest.mark.parametrize("nprod", [2, 3, 4])
 def test_split_tile_kernels(b, monkeypatch, tile, nprod):
