@@ -1436,8 +1436,14 @@ extern "C" size_t gemm_grouped_workspace_bytes(int32_t count, const tc_problem* 
         if (p.m < 1 || p.n < 1) continue;
         mma_tiles += int64_t((p.m + tcg::kGroupedTileM - 1) / tcg::kGroupedTileM) *
                      ((p.n + tcg::kGroupedTileN - 1) / tcg::kGroupedTileN);
-        tc_tiles += int64_t((p.m + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM) *
+        // 128 x 256 tiles of C_g, or of C_g^T for a problem that runs transposed (m < n <= 256:
+        // n rows in one or two tiles); tall tiles only ever take fewer, so the bound holds whether
+        // they are on or not
+        int64_t t = int64_t((p.m + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM) *
                     ((p.n + tcg::kGroupedTcTileN - 1) / tcg::kGroupedTcTileN);
+        if (p.m < p.n && p.n <= tcg::kGroupedTcTileN)
+            t = std::max<int64_t>(t, (p.n + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM);
+        tc_tiles += t;
     }
     // enough for either kernel: the mma.sync schedule or the tensor-core maps and tiles
     const size_t mma = (size_t(count) * sizeof(tcg::GroupedProblemDev) + 255) / 256 * 256 +

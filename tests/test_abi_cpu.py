@@ -126,6 +126,12 @@ def test_grouped_workspace_covers_both_kernels(lib):
     rows = [(16 * (1 + g % 16), 16 * (1 + g % 7), 32, 0, 0, 0, 32, 32, 256) for g in range(1000)]
     sizes = [lib.gemm_grouped_workspace_bytes(c, b.problems_array(rows[:c])) for c in (10, 100, 1000)]
     assert sizes[0] < sizes[1] < sizes[2] and sizes[2] >= 1000 * (2 * 128 + 48)
+    # m < n <= 256 runs transposed: n = 200 rows in two 128-row tiles unless they run as one tall
+    # tile (TCGEMM_GROUPED_TALL=0 turns those off), so the size must cover two
+    wide = b.problems_array([(16, 200, 32, 0, 0, 0, 32, 32, 200)])
+    assert lib.gemm_grouped_workspace_bytes(1, wide) >= 2 * 128 + 2 * 48
+    many = b.problems_array([(16, 200, 32, 0, 0, 0, 32, 32, 200)] * 100)
+    assert lib.gemm_grouped_workspace_bytes(100, many) >= 100 * (2 * 128 + 2 * 48)
     # a workspace that is not a 256-byte aligned device pointer is refused before any device work
     st = lib.gemm_grouped_ws(0, 1, one, ctypes.c_void_p(256), 0, ctypes.c_void_p(256), 0, ctypes.c_void_p(256),
                              1.0, 0.0, None, 1 << 20, None)
