@@ -378,7 +378,10 @@ tc_status gemm_grouped_noalloc(int32_t dt, int32_t count, const tc_problem* prob
  * the mma.sync kernel with TCGEMM_GROUPED=mma); arguments and errors otherwise
  * as gemm_grouped.  Like gemm_grouped_noalloc it uploads the schedule from
  * host memory that it frees on return, so on a stream that is being captured
- * it returns TC_ERR_UNSUPPORTED and enqueues nothing. */
+ * it returns TC_ERR_UNSUPPORTED and enqueues nothing.
+ * gemm_grouped_workspace_bytes: a size that holds either kernel's schedule
+ * under every tile setting (tall tiles on or off, transposed problems);
+ * 0 for count <= 0 or a null array.  Host only. */
 size_t gemm_grouped_workspace_bytes(int32_t count, const tc_problem* problems);
 tc_status gemm_grouped_ws(int32_t dt, int32_t count, const tc_problem* problems,
                           const void* a_base, int32_t la, const void* b_base, int32_t lb,
