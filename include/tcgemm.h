@@ -175,8 +175,18 @@ tc_status tc_split_bf16x3(int64_t rows, int64_t cols, const float* src, int64_t 
  * 48 k-blocks (3072 FP16/BF16, 6144 E4M3 elements) two parts of K, the first
  * storing alpha*P1 + beta*C, the second, once the first has signalled
  * through a device flag, alpha*P2 + C (a fixed order: the same bits every
- * run); with a shorter K two 256 x 128 halves.  TCGEMM_PAIR_TAIL=full keeps
- * whole tiles, =halves always cuts halves.  The kernel is launched with programmatic stream
+ * run); with a shorter K two 256 x 128 halves.  The flags of an eager
+ * launch are 8 KB of device memory per stream handle (per host thread for
+ * cudaStreamPerThread), allocated on the stream's first such launch and kept
+ * for the process; a launch being captured into a graph takes a block the
+ * graph allocates, zeroes and frees at each replay.  No two launches in
+ * flight at once share flags, with one exception: a stream destroyed while
+ * such a launch still runs, whose handle a new stream takes over at once.
+ * The earlier launch's second parts may then wait in vain; they give up
+ * after 2 s with an error status (tc_sync_status) rather than hang.  So
+ * synchronise a stream before destroying it.  TCGEMM_PAIR_TAIL=full keeps
+ * whole tiles, =halves always cuts halves.  The kernel is launched with
+ * programmatic stream
  * serialization: it may run its set-up while the previous kernel of the
  * stream finishes and waits for it before touching A, B, C or the scales
  * (TCGEMM_PDL=0 turns this off). */
