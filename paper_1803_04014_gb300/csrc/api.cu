@@ -860,8 +860,9 @@ namespace {
 // Problems with m < n <= 256 run transposed on the tensor cores: C_g^T = B_g^T A_g^T, so that the n
 // rows of the transposed tile fill the accumulator's lanes (and the epilogue warps that read them)
 // where the m rows would fill a few.  B_g (K-major, or row-major and then read as an MN-major A
-// operand) takes the A operand's place and A_g the K-major B operand's; the tile count does not grow
-// (one tile, or two for m > 128).  Unless TCGEMM_GROUPED_SWAP=0.  (10 000-problem mix with m, n, k
+// operand) takes the A operand's place and A_g the K-major B operand's; with tall tiles the tile count
+// does not grow (one tile, or two for m > 128), without them a problem with m <= 128 < n takes two
+// 128-row tiles instead of one.  Unless TCGEMM_GROUPED_SWAP=0.  (10 000-problem mix with m, n, k
 // uniform over 16..256: 2-3 % faster; problems with m <= 48 and n >= 128 alone: 3.3 -> 3.9 TB/s.)
 bool grouped_swap(const tc_problem& p, int32_t lb) {
     (void)lb;
