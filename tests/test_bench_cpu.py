@@ -48,3 +48,35 @@ def test_traffic_only_for_the_profiled_source_and_configuration(monkeypatch):
 def test_the_profile_was_taken_of_the_untuned_configuration():
     _, _, cfg = _profile_fields()
     assert {k: int(v) for k, v in cfg.items()} == bench.DEFAULT_GEMM_CFG
+
+
+def test_reference_arm_prints_one_contract_line():
+    # the oracle arm runs on the host cores alone: one JSON line with the keys every bench line
+    # carries, its cpu_baseline describing this run, and no host<->device bytes
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=bench.ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1 and d["warmup"] == 3
+    assert d["value"] > 0 and d["higher_is_better"] is True and "workload" in d["config"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_binding_refuses_to_run_without_the_library(monkeypatch, tmp_path):
+    # no CPU fallback: without the built library the binding raises instead of computing anything
+    import pytest
+    from paper_1803_04014_gb300 import binding, builder
+    monkeypatch.setattr(binding, "_LIB", None)
+    monkeypatch.setattr(builder, "LIB", str(tmp_path / "libtcgemm.so"))
+    with pytest.raises(ImportError):
+        binding.load(build_if_needed=False)
