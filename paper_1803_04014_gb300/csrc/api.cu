@@ -15,6 +15,7 @@
 #include <string>
 #include <vector>
 
+#include "grouped_sched.h"
 #include "launch.h"
 #include "tcgemm.h"
 #include "tcgemm_debug.h"
@@ -857,19 +858,10 @@ struct tc_grouped_plan {
 
 namespace {
 
-// Problems with m < n <= 256 run transposed on the tensor cores: C_g^T = B_g^T A_g^T, so that the n
-// rows of the transposed tile fill the accumulator's lanes (and the epilogue warps that read them)
-// where the m rows would fill a few.  B_g (K-major, or row-major and then read as an MN-major A
-// operand) takes the A operand's place and A_g the K-major B operand's; with tall tiles the tile count
-// does not grow (one tile, or two for m > 128), without them a problem with m <= 128 < n takes two
-// 128-row tiles instead of one.  Unless TCGEMM_GROUPED_SWAP=0.  (10 000-problem mix with m, n, k
-// uniform over 16..256: 2-3 % faster; problems with m <= 48 and n >= 128 alone: 3.3 -> 3.9 TB/s.)
-bool grouped_swap(const tc_problem& p, int32_t lb) {
-    (void)lb;
-    if (!(p.m < p.n && p.n <= tcg::kGroupedTcTileN)) return false;
-    const char* env = getenv("TCGEMM_GROUPED_SWAP");
-    return !(env && strcmp(env, "0") == 0);
-}
+using tcg::grouped_swap;
+using tcg::grouped_tall_tiles;
+using tcg::grouped_tc_tile_count;
+using tcg::grouped_tc_tiles;
 
 // Every problem's tensor maps for these bases, two per problem: A_g (dims {k, m}) and B_g
 // (dims {k, n} K-major, or {n, k} row-major); a transposed problem has B_g's map first.
@@ -941,38 +933,6 @@ bool grouped_use_tensor_cores(int32_t lb) {
     return !(env && strcmp(env, "mma") == 0);
 }
 
-// Tensor-core tiles of one problem: 128 x 256, or, for n <= 128, tall 256-row tiles that cover
-// M-blocks tm and tm + 1 with one B tile (an odd last M-block stays 128 rows high).  Tall tiles
-// unless TCGEMM_GROUPED_TALL=0.
-bool grouped_tall_tiles() {
-    const char* env = getenv("TCGEMM_GROUPED_TALL");
-    return !(env && strcmp(env, "0") == 0);
-}
-
-// Rows and columns of the problem's tiled output: m x n, or n x m when it runs transposed.
-int64_t grouped_tc_tile_count(const tc_problem& p, bool tall_on, int32_t lb) {
-    const bool sw = grouped_swap(p, lb);
-    const int64_t rm = sw ? p.n : p.m, rn = sw ? p.m : p.n;
-    const int64_t tm = (rm + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM;
-    const int64_t tn = (rn + tcg::kGroupedTcTileN - 1) / tcg::kGroupedTcTileN;
-    return (tall_on && rn <= tcg::kGroupedTcTileN / 2 ? (tm + 1) / 2 : tm) * tn;
-}
-
-template <class Emit>
-void grouped_tc_tiles(const tc_problem& p, int32_t g, bool tall_on, int32_t lb, Emit&& emit) {
-    const bool sw = grouped_swap(p, lb);
-    const int32_t rm = sw ? p.n : p.m, rn = sw ? p.m : p.n;
-    const bool tall = tall_on && rn <= tcg::kGroupedTcTileN / 2;
-    const int tm = (rm + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM;
-    const int tn = (rn + tcg::kGroupedTcTileN - 1) / tcg::kGroupedTcTileN;
-    for (int i = 0; i < tm;) {
-        const int rows = (tall && i + 1 < tm) ? 2 * tcg::kGroupedTcTileM : tcg::kGroupedTcTileM;
-        for (int j = 0; j < tn; ++j)
-            emit(tcg::GroupedTcTile{g, i, j, rm, rn, p.k, p.ldc, (p.k + 63) / 64, p.off_c, rows,
-                                    sw ? tcg::kGroupedTcSwapped : 0});
-        i += rows / tcg::kGroupedTcTileM;
-    }
-}
 
 }  // namespace
 
@@ -1437,14 +1397,7 @@ extern "C" size_t gemm_grouped_workspace_bytes(int32_t count, const tc_problem* 
         if (p.m < 1 || p.n < 1) continue;
         mma_tiles += int64_t((p.m + tcg::kGroupedTileM - 1) / tcg::kGroupedTileM) *
                      ((p.n + tcg::kGroupedTileN - 1) / tcg::kGroupedTileN);
-        // 128 x 256 tiles of C_g, or of C_g^T for a problem that runs transposed (m < n <= 256:
-        // n rows in one or two tiles); tall tiles only ever take fewer, so the bound holds whether
-        // they are on or not
-        int64_t t = int64_t((p.m + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM) *
-                    ((p.n + tcg::kGroupedTcTileN - 1) / tcg::kGroupedTcTileN);
-        if (p.m < p.n && p.n <= tcg::kGroupedTcTileN)
-            t = std::max<int64_t>(t, (p.n + tcg::kGroupedTcTileM - 1) / tcg::kGroupedTcTileM);
-        tc_tiles += t;
+        tc_tiles += tcg::grouped_tc_tile_bound(p);
     }
     // enough for either kernel: the mma.sync schedule or the tensor-core maps and tiles
     const size_t mma = (size_t(count) * sizeof(tcg::GroupedProblemDev) + 255) / 256 * 256 +
